@@ -1,0 +1,364 @@
+"""Pins of the CPU oracle against facts that do not come from the oracle itself:
+closed forms, exact algebraic identities of Section 4, brute force, textbook
+routines other than the ones the oracle calls, and stated properties of the
+estimator.  A dropped term, a wrong sign, index or transposed operand anywhere
+in ``oracle/mrq.py`` fails at least one of these."""
+import math
+import os
+
+import numpy as np
+import pytest
+from scipy.spatial.distance import cdist
+
+import datagen
+from oracle import mrq, index_file
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _load_golden(name):
+    vals = {}
+    with open(os.path.join(GOLDEN, name)) as f:
+        for line in f:
+            line = line.split("#", 1)[0].strip()
+            if not line:
+                continue
+            key, rest = line.split("=", 1)
+            vals[key.strip()] = np.array([float(t) for t in rest.split()])
+    return vals
+
+
+# ----------------------------------------------------------------- PCA (Alg. 1)
+
+def test_pca_against_svd_and_closed_form():
+    rng = np.random.default_rng(5)
+    X = rng.standard_normal((3000, 12)) * np.linspace(3, 0.2, 12) + 7.0
+    mu, lam, Pp = mrq.pca_train(X)
+    Xc = X - X.mean(axis=0)
+    # independent route: singular values of the centred data
+    sv = np.linalg.svd(Xc, compute_uv=False)
+    np.testing.assert_allclose(lam, sv ** 2 / X.shape[0], rtol=1e-10)
+    np.testing.assert_allclose(Pp @ Pp.T, np.eye(12), atol=1e-12)
+    cov = Xc.T @ Xc / X.shape[0]
+    np.testing.assert_allclose(Pp.T @ np.diag(lam) @ Pp, cov, atol=1e-10 * np.abs(cov).max())
+    # sign convention: largest-magnitude entry of each row is positive
+    for row in Pp:
+        assert row[np.argmax(np.abs(row))] > 0
+
+
+def test_pca_exact_small_case():
+    # four points +-a e1, +-b e2 (plus a mean offset): covariance diag(a^2/2, b^2/2)
+    a, b = 3.0, 1.0
+    X = np.array([[a, 0], [-a, 0], [0, b], [0, -b]]) + np.array([10.0, -4.0])
+    mu, lam, Pp = mrq.pca_train(X)
+    np.testing.assert_allclose(mu, [10.0, -4.0])
+    np.testing.assert_allclose(lam, [a * a / 2, b * b / 2], rtol=1e-14)
+    np.testing.assert_allclose(Pp, np.eye(2), atol=1e-14)
+
+
+def test_orthogonal_from_gaussian():
+    G = datagen.rotation_gaussian(32, 11)
+    P = mrq.orthogonal_from_gaussian(G)
+    np.testing.assert_allclose(P.T @ P, np.eye(32), atol=1e-12)
+    R = P.T @ G                              # G = P R with R upper triangular, diag > 0
+    np.testing.assert_allclose(np.tril(R, -1), 0, atol=1e-10)
+    assert np.all(np.diag(R) > 0)
+
+
+# ---------------------------------------------------------------------- k-means
+
+def test_kmeans_hand_example():
+    X = np.array([[0.0], [1.0], [10.0], [11.0], [12.0]])
+    C, a = mrq.kmeans(X, np.array([[0.0], [5.0]]), iters=1)
+    # assignment to (0, 5): {0, 1} -> 0, {10, 11, 12} -> 1; means 0.5 and 11
+    np.testing.assert_allclose(C[:, 0], [0.5, 11.0])
+    assert a.tolist() == [0, 0, 1, 1, 1]
+    # tie goes to the lower id; an empty list keeps its centroid
+    C2, a2 = mrq.kmeans(np.array([[1.0]]), np.array([[0.0], [2.0], [9.0]]), iters=1)
+    assert a2.tolist() == [0]
+    np.testing.assert_allclose(C2[:, 0], [1.0, 2.0, 9.0])
+
+
+def test_kmeans_final_assignment_is_nearest():
+    rng = np.random.default_rng(3)
+    X = rng.standard_normal((500, 4))
+    C, a = mrq.kmeans(X, X[:7], iters=5)
+    np.testing.assert_array_equal(a, np.argmin(cdist(X, C, "sqeuclidean"), axis=1))
+
+
+# ----------------------------------------------------------------- quantization
+
+def test_encode_golden():
+    g = _load_golden("encode_examples.txt")
+    u1, v1 = mrq.encode(g["o_1bit"][None, :], 1)
+    np.testing.assert_array_equal(u1[0], g["u_1bit"])
+    np.testing.assert_array_equal(v1[0], g["v_1bit"])
+    u2, v2 = mrq.encode(g["o_2bit"][None, :], 2)
+    np.testing.assert_array_equal(u2[0], g["u_2bit"])
+    np.testing.assert_array_equal(v2[0], g["v_2bit"])
+    u3, v3 = mrq.encode(g["o_3bit"][None, :], 3)
+    np.testing.assert_array_equal(u3[0], g["u_3bit"])
+    np.testing.assert_array_equal(v3[0], g["v_3bit"])
+
+
+def test_factor_closed_form_one_hot():
+    # o' = e_1 in d dims: <v, o'> = 1 and <v,o'>/|v| = 1/sqrt(d), so
+    # f_rescale = -2 r and f_err = 2 r sqrt((1 - 1/d) d)/sqrt(d - 1) = 2 r.
+    d, r = 64, 2.5
+    o = np.zeros((1, d)); o[0, 0] = 1.0
+    u, v = mrq.encode(o, 1)
+    f_add, f_res, f_err, ip = mrq.factors(np.array([r]), np.array([0.75]), v, o, d)
+    assert ip[0] == pytest.approx(1.0)
+    assert f_add[0] == pytest.approx(r * r + 0.75)
+    assert f_res[0] == pytest.approx(-2 * r)
+    assert f_err[0] == pytest.approx(2 * r, rel=1e-12)
+
+
+def test_quantize_query_golden_and_grid_identity():
+    g = _load_golden("query_quant_examples.txt")
+    qbar, lo, delta = mrq.quantize_query(g["qprime"], 2)
+    np.testing.assert_array_equal(qbar, g["qbar_2bit"])
+    assert lo == pytest.approx(g["vl"][0]) and delta == pytest.approx(g["delta"][0])
+    # on-grid query: the quantized inner-product identity is exact
+    rng = np.random.default_rng(1)
+    for bits in (1, 2, 4):
+        d = 64
+        top = (1 << bits) - 1
+        u = rng.integers(0, top + 1, size=(50, d))
+        v = 2 * u - top
+        qb = rng.integers(0, 16, size=d); qb[0], qb[1] = 0, 15
+        vl, dl = -0.375, 0.0625                      # exact in binary
+        qp = vl + dl * qb
+        direct = v @ qp
+        formula = dl * (2.0 * (u @ qb) - top * qb.sum()) + vl * (2.0 * u.sum(axis=1) - d * top)
+        np.testing.assert_allclose(formula, direct, rtol=0, atol=1e-12)
+
+
+# --------------------------------------------- decomposition identities (Eq. 1-3)
+
+def test_eq3_decomposition_exact(small_workload, small_oracle_index):
+    w, base, queries = small_workload
+    idx = small_oracle_index
+    qd, qr, qr2, sigma, qp2 = mrq.project_queries(idx, queries[:20])
+    rng = np.random.default_rng(0)
+    pos = rng.integers(0, idx.n, size=300)
+    assign = np.searchsorted(idx.list_offsets, pos, side="right") - 1
+    X = base[idx.ids[pos]].astype(np.float64)
+    for i in range(20):
+        c = idx.centroids[assign]
+        xr = idx.xr[pos]
+        xb = (idx.xd[pos] - c) / idx.resid_norm[pos][:, None]
+        qdc = qd[i][None, :] - c
+        qn = np.linalg.norm(qdc, axis=1)
+        qb = qdc / qn[:, None]
+        C1 = idx.resid_norm[pos] ** 2 + qn ** 2 + np.sum(xr * xr, axis=1) + qr2[i]
+        C2 = -2 * idx.resid_norm[pos] * qn * np.sum(xb * qb, axis=1)
+        C3 = -2 * (xr @ qr[i])
+        true = np.sum((X - queries[i].astype(np.float64)) ** 2, axis=1)
+        np.testing.assert_allclose(C1 + C2 + C3, true, rtol=1e-9)
+        # Eq. 4 with the estimator replaced by the exact <x_b, q_b>, plus C3, is exact
+        op = np.sum(xb * qb, axis=1)
+        est = idx.f_add[pos] + qn ** 2 + qr2[i] + idx.f_rescale[pos] * qn * idx.ip_vo[pos] * op + C3
+        np.testing.assert_allclose(est, true, rtol=1e-9)
+        # Eq. 7 differs from the exact distance by the residual cross term only
+        diso = idx.xnorm2[pos] + qp2[i] - 2 * (idx.xd[pos] @ qd[i])
+        np.testing.assert_allclose(diso + C3, true, rtol=1e-9)
+
+
+def test_residual_variance_identity_and_chebyshev(small_workload, small_oracle_index):
+    # Eq. 6 over the centred base set holds exactly: Var_x <x_r, q_r> = sum q_i^2 lam_i
+    w, base, queries = small_workload
+    idx = small_oracle_index
+    qd, qr, qr2, sigma, qp2 = mrq.project_queries(idx, queries[:10])
+    xr_all = idx.xr
+    for i in range(10):
+        t = xr_all @ qr[i]
+        assert abs(t.mean()) < 1e-9 * (np.abs(t).max() + 1)
+        np.testing.assert_allclose(t.var(), sigma[i] ** 2, rtol=1e-9)
+        for m in (1.5, 2.0, 4.0):                         # Chebyshev
+            assert np.mean(np.abs(t) >= m * sigma[i]) <= 1.0 / m ** 2
+
+
+def test_tail_vanishes_when_d_equals_D():
+    w = datagen.workload("small", n=3000, D=64, n_comp=16)
+    base, queries = datagen.base_and_queries(w, n_query=5)
+    G = datagen.rotation_gaussian(64, 1)
+    idx = mrq.build_index(base, 64, 1, 8, G, init_idx=np.arange(8), kmeans_iters=3)
+    assert idx.xr.shape[1] == 0
+    qd, qr, qr2, sigma, qp2 = mrq.project_queries(idx, queries)
+    assert np.all(sigma == 0) and np.all(qr2 == 0)
+    np.testing.assert_allclose(idx.f_add, idx.resid_norm ** 2)
+    # the estimate is the pure RaBitQ estimate |x-c|^2 + |q-c|^2 - 2|x-c||q-c|<v,q'>/<v,o'>
+    lists, g = mrq.probe(idx, qd[0], 1)
+    j = int(lists[0])
+    e = mrq.estimate_list(idx, j, qd[0], float(g[j]), 0.0, 0.0, 1.9, 4.0)
+    sl = idx.list_slice(j)
+    qprime = (qd[0] - idx.centroids[j]) / math.sqrt(g[j])
+    rabitq = (idx.resid_norm[sl] ** 2 + g[j]
+              - 2 * idx.resid_norm[sl] * math.sqrt(g[j]) * (idx.v[sl] @ qprime) / idx.ip_vo[sl])
+    np.testing.assert_allclose(e["dis"], rabitq, rtol=1e-12)
+    np.testing.assert_allclose(e["ub"] - e["dis"], 1.9 * math.sqrt(g[j]) * idx.f_err[sl], rtol=1e-12)
+
+
+# ----------------------------------------------------- estimator (Section 4.2)
+
+def test_estimator_unbiased_over_rotations():
+    # <x_bar, q>/<x_bar, x> is unbiased for <x, q> over the random rotation
+    rng = np.random.default_rng(7)
+    d = 32
+    x = rng.standard_normal(d); x /= np.linalg.norm(x)
+    q = rng.standard_normal(d); q = 0.6 * x + 0.8 * q / np.linalg.norm(q); q /= np.linalg.norm(q)
+    errs = []
+    for s in range(3000):
+        P = mrq.orthogonal_from_gaussian(datagen.rotation_gaussian(d, 10_000 + s))
+        o = (x @ P)[None, :]                # o' = P^T x
+        qq = q @ P
+        _, v = mrq.encode(o, 1)
+        errs.append((v[0] @ qq) / (v[0] @ o[0]) - x @ q)
+    errs = np.array(errs)
+    assert abs(errs.mean()) < 3 * errs.std() / math.sqrt(errs.size)
+
+
+def test_eq5_interval_holds_for_most_rotations():
+    # |est - <x,q>| <= sqrt((1 - a^2)/a^2) * eps0/sqrt(d - 1), a = <x_bar, x> (Eq. 5)
+    rng = np.random.default_rng(8)
+    d, eps0 = 64, 1.9
+    x = rng.standard_normal(d); x /= np.linalg.norm(x)
+    q = rng.standard_normal(d); q /= np.linalg.norm(q)
+    z = []
+    for s in range(1500):
+        P = mrq.orthogonal_from_gaussian(datagen.rotation_gaussian(d, 20_000 + s))
+        o, qq = x @ P, q @ P
+        _, v = mrq.encode(o[None, :], 1)
+        a = (v[0] @ o) / np.linalg.norm(v[0])
+        err = (v[0] @ qq) / (v[0] @ o) - x @ q
+        z.append(err / (math.sqrt((1 - a * a) / (a * a)) / math.sqrt(d - 1)))
+    z = np.array(z)
+    # RaBitQ's analysis: conditioned on a, the error is a (d-1)-sphere coordinate of
+    # scale sqrt(1 - a^2)/a * sqrt(1 - <x,q>^2), i.e. z ~ N(0, 1 - <x,q>^2) for large d
+    s_theory = math.sqrt(1 - (x @ q) ** 2)
+    assert abs(z.std() - s_theory) < 0.06
+    from scipy.stats import norm
+    p_miss = 2 * norm.sf(eps0 / s_theory)
+    assert abs(np.mean(np.abs(z) > eps0) - p_miss) < 0.025
+
+
+def test_bound_rate_and_multibit_accuracy(small_workload, small_oracle_index):
+    w, base, queries = small_workload
+    idx = small_oracle_index
+    qd, qr, qr2, sigma, qp2 = mrq.project_queries(idx, queries[:30])
+    viol = tot = 0
+    for i in range(30):
+        lists, g = mrq.probe(idx, qd[i], 2)
+        for j in lists:
+            sl = idx.list_slice(int(j))
+            e = mrq.estimate_list(idx, int(j), qd[i], float(g[j]), qr2[i], 0.0, 1.9, 0.0)
+            # exact projected distance |x_d - q_d|^2 + |x_r|^2 + |q_r|^2 (C3 excluded)
+            ref = np.sum((idx.xd[sl] - qd[i]) ** 2, axis=1) + np.sum(idx.xr[sl] ** 2, axis=1) + qr2[i]
+            viol += np.sum((ref < e["lb"]) | (ref > e["ub"]))
+            tot += ref.size
+    assert viol / tot < 0.08          # Eq. 5's interval with eps0 = 1.9 fails for a few %
+    # more bits per dimension -> the estimate approaches the exact inner product
+    rng = np.random.default_rng(2)
+    o = rng.standard_normal((400, 64)); o /= np.linalg.norm(o, axis=1, keepdims=True)
+    q = rng.standard_normal(64); q /= np.linalg.norm(q)
+    errs = []
+    for b in (1, 2, 4, 8):
+        _, v = mrq.encode(o, b)
+        est = (v @ q) / np.sum(v * o, axis=1)
+        errs.append(np.sqrt(np.mean((est - o @ q) ** 2)))
+    assert errs[0] > errs[1] > errs[2] > errs[3]
+    assert errs[3] < 0.02 * errs[0]
+
+
+# -------------------------------------------------------------- search (Alg. 2)
+
+def test_exact_knn_against_cdist():
+    rng = np.random.default_rng(4)
+    S = rng.standard_normal((700, 9)); Q = rng.standard_normal((13, 9))
+    ids, dd = mrq.exact_knn(S, Q, 5)
+    D = cdist(Q, S, "sqeuclidean")
+    for i in range(13):
+        o = np.lexsort((np.arange(700), D[i]))[:5]
+        assert ids[i].tolist() == o.tolist()
+        np.testing.assert_allclose(dd[i], D[i, o], rtol=1e-12)
+
+
+def test_probe_ties_to_lower_id():
+    idx = mrq.OracleIndex(D=2, d=2, bits=1, nlist=4, mu=None, lam=None, Pp=None, Pr=None, W=None,
+                          centroids=np.array([[1.0, 0], [0, 1.0], [-1.0, 0], [5.0, 5.0]]),
+                          list_offsets=np.zeros(5, dtype=np.int64), ids=np.zeros(0, dtype=np.int64),
+                          xd=None, xr=None, xnorm2=None, u=None, v=None, f_add=None, f_rescale=None,
+                          f_err=None, ip_vo=None, resid_norm=None)
+    lists, g = mrq.probe(idx, np.zeros(2), 3)
+    assert lists.tolist() == [0, 1, 2]
+
+
+def test_no_pruning_full_probe_is_brute_force(small_workload, small_oracle_index):
+    w, base, queries = small_workload
+    idx = small_oracle_index
+    Q = queries[:12]
+    ref_ids, ref_d = mrq.exact_knn(base, Q, w.k)
+    for mode in (mrq.MODE_MRQ, mrq.MODE_MRQ_PLUS):
+        for fn in (mrq.search_contract, mrq.search_literal):
+            r = fn(idx, Q, w.k, idx.nlist, eps0=1e9, m=1e9, mode=mode)
+            np.testing.assert_array_equal(r.ids, ref_ids)
+            np.testing.assert_allclose(r.dists, ref_d, rtol=1e-9)
+
+
+def test_contract_equals_literal_when_bounds_hold(small_workload, small_oracle_index):
+    w, base, queries = small_workload
+    idx = small_oracle_index
+    Q = queries[:40]
+    eps0, m = 4.0, 12.0
+    rc = mrq.search_contract(idx, Q, w.k, w.nprobe, eps0=eps0, m=m)
+    rl = mrq.search_literal(idx, Q, w.k, w.nprobe, eps0=eps0, m=m)
+    qd, qr, qr2, sigma, qp2 = mrq.project_queries(idx, Q)
+    checked = 0
+    for i in range(Q.shape[0]):
+        lists, g = mrq.probe(idx, qd[i], w.nprobe)
+        ok = True
+        pos_all = []
+        for j in lists:
+            sl = idx.list_slice(int(j))
+            e = mrq.estimate_list(idx, int(j), qd[i], float(g[j]), qr2[i], sigma[i], eps0, m)
+            ex = np.sum((idx.xd[sl] - qd[i]) ** 2, axis=1) + np.sum((idx.xr[sl] - qr[i]) ** 2, axis=1)
+            diso = idx.xnorm2[sl] + qp2[i] - 2 * idx.xd[sl] @ qd[i]
+            ok &= bool(np.all((e["lb"] <= ex) & (ex <= e["ub"])))
+            ok &= bool(np.all(np.abs(diso - ex) <= m * sigma[i]))
+            pos_all.append(np.arange(sl.start, sl.stop))
+        if not ok:
+            continue
+        checked += 1
+        p = np.concatenate(pos_all)
+        ex = np.sum((idx.xd[p] - qd[i]) ** 2, axis=1) + np.sum((idx.xr[p] - qr[i]) ** 2, axis=1)
+        o = np.lexsort((idx.ids[p], ex))[:w.k]
+        assert rc.ids[i].tolist() == idx.ids[p][o].tolist()
+        assert rl.ids[i].tolist() == idx.ids[p][o].tolist()
+    assert checked >= 20
+    # the contract prunes: far fewer exact computations than candidates
+    assert rc.n_s2.sum() < 0.2 * rc.n_cand.sum()
+
+
+def test_recall_reasonable_and_quantized_query(small_workload, small_oracle_index):
+    w, base, queries = small_workload
+    idx = small_oracle_index
+    truth, _ = mrq.exact_knn(base, queries, w.k)
+    r = mrq.search_contract(idx, queries, w.k, 16)
+    assert mrq.recall_at_k(r.ids, truth) > 0.9
+    rq = mrq.search_contract(idx, queries, w.k, 16, qbits=4)
+    assert mrq.recall_at_k(rq.ids, truth) > 0.85
+    # stage 2 of MRQ+ removes most exact computations that MRQ performs (Exp-3)
+    rm = mrq.search_contract(idx, queries, w.k, 16, mode=mrq.MODE_MRQ)
+    assert r.n_s2.sum() < 0.5 * rm.n_s2.sum()
+
+
+def test_index_file_round_trip(tmp_path, small_oracle_index):
+    idx = small_oracle_index
+    p = str(tmp_path / "i.mrq")
+    index_file.write_index(idx, p)
+    f = index_file.read_index(p)
+    assert f["header"] == dict(n=idx.n, D=idx.D, d=idx.d, bits=idx.bits, nlist=idx.nlist)
+    np.testing.assert_array_equal(f["CODE"].reshape(idx.n, idx.d), idx.u)
+    np.testing.assert_array_equal(f["LOFF"], idx.list_offsets)
+    np.testing.assert_array_equal(f["XD__"].reshape(idx.n, idx.d), idx.xd.astype(np.float32))
