@@ -1,0 +1,416 @@
+#!/usr/bin/env python
+"""Benchmark of the MRQ query path on GB300: QPS at recall@10 >= 0.95.
+
+Workload (default): the GIST-like shape -- N = 1,000,000 base vectors, D = 960,
+power-law spectrum lam_i ~ i^-1.0, 1024 mixture components, 10,000 queries,
+d = 128 leading PCA coordinates at 1 bit, nlist = 4096, k = 10 (synthetic data,
+``datagen``).  One step = one mrq_search of all queries (projection, probe,
+stage-1 scan, stage 2, exact rerank, top-k) at the smallest nprobe of a ladder
+whose recall@10 against exact ground truth reaches 0.95.
+
+Prints one JSON line (rank 0).  ``--impl reference`` times the CPU oracle instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "QPS at recall@10≥0.95 on 1 GB300, plain vs batched/BF16 form; scan HBM GB/s"
+UNIT = "queries/s"
+NPROBE_LADDER = [4, 6, 8, 12, 16, 24, 32, 48, 64, 96, 128, 192, 256, 384, 512]
+
+
+def parse_args(argv=None):
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="mrq", choices=["mrq", "reference"])
+    p.add_argument("--workload", default="gist")
+    p.add_argument("--n", type=int, default=None, help="override base size (quick runs)")
+    p.add_argument("--nq", type=int, default=None, help="override query count")
+    p.add_argument("--d", type=int, default=None)
+    p.add_argument("--bits", type=int, default=None)
+    p.add_argument("--nlist", type=int, default=None)
+    p.add_argument("--recall", type=float, default=0.95)
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--cpu-queries", type=int, default=100)
+    return p.parse_args(argv)
+
+
+def workload_of(args):
+    import datagen
+    over = {}
+    for key, val in (("n", args.n), ("n_query", args.nq), ("d", args.d), ("bits", args.bits),
+                     ("nlist", args.nlist)):
+        if val is not None:
+            over[key] = val
+    return datagen.workload(args.workload, **over)
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            pk = json.load(f)
+        return float(pk["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# ------------------------------------------------------------------ clocks
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling while the timed region runs."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu: int, path: str):
+        self.path, self.proc = path, None
+        try:
+            self.f = open(path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={gpu}", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [t.strip() for t in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = max(mx, float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ----------------------------------------------------------- ground truth
+
+def ground_truth(base_t, q_t, k, chunk=1024):
+    """Exact k-NN (evaluation only): float32 distances pick 32 spare candidates,
+    float64 recomputation orders them."""
+    import torch
+    with torch.no_grad():
+        prev = torch.backends.cuda.matmul.allow_tf32
+        torch.backends.cuda.matmul.allow_tf32 = False
+        bn = (base_t * base_t).sum(1)
+        out = []
+        for s in range(0, q_t.shape[0], chunk):
+            q = q_t[s:s + chunk]
+            dd = bn[None, :] - 2.0 * (q @ base_t.T)
+            cand = torch.topk(dd, k + 32, dim=1, largest=False).indices
+            x = base_t[cand].double()
+            ex = ((x - q.double()[:, None, :]) ** 2).sum(-1)
+            o = torch.argsort(ex, dim=1, stable=True)[:, :k]
+            out.append(torch.gather(cand, 1, o))
+        torch.backends.cuda.matmul.allow_tf32 = prev
+        return torch.cat(out).cpu().numpy()
+
+
+def recall(found, truth):
+    import numpy as np
+    k = truth.shape[1]
+    hit = sum(len(set(f[:k].tolist()) & set(t.tolist())) for f, t in zip(found, truth))
+    return hit / truth.size
+
+
+# ------------------------------------------------------------- CPU oracle
+
+def oracle_sample_setup(w, nprobe, n_queries):
+    """The CPU baseline's bounded sample: the same mixture at 1/16 of the base and
+    1/16 of the lists (so the mean list size and the candidates per query at the
+    same nprobe match the full workload), ``n_queries`` of the workload's queries."""
+    import datagen
+    from oracle import mrq as omrq
+    scale = 16 if w.n >= 16 * 4096 else 1
+    n_s, nlist_s = w.n // scale, max(1, w.nlist // scale)
+    mix = datagen.make_mixture(w)
+    base = datagen.sample(mix, n_s, w.seed("base"))
+    queries = datagen.sample(mix, n_queries, w.seed("queries"))
+    G = datagen.rotation_gaussian(w.d, w.seed("method"))
+    init = datagen.kmeans_init_indices(n_s, nlist_s, w.seed("method") + 1)
+    idx = omrq.build_index(base, w.d, w.bits, nlist_s, G, init_idx=init, kmeans_iters=10)
+    npr = min(nprobe, nlist_s)
+    desc = (f"oracle (numpy float64, 1 thread) on a 1/{scale} sample: N={n_s}, nlist={nlist_s}, "
+            f"nprobe={npr} (same mean list size and candidates per query as the full "
+            f"workload), D={w.D}, d={w.d}, bits={w.bits}, {n_queries} queries")
+    return idx, queries, npr, desc
+
+
+def _oracle_worker(wname, over, nprobe, nq, steps, conn):
+    import datagen
+    from oracle import mrq as omrq
+    w = datagen.workload(wname, **over)
+    idx, queries, npr, desc = oracle_sample_setup(w, nprobe, nq)
+    times = []
+    for _ in range(steps):
+        t0 = time.perf_counter()
+        omrq.search_contract(idx, queries, w.k, npr)
+        times.append(time.perf_counter() - t0)
+    conn.send((times, desc))
+    conn.close()
+
+
+def time_oracle(args, w, nprobe, steps):
+    """Run the oracle in a spawned single-threaded process; returns (qps, desc, times)."""
+    import multiprocessing as mp
+    env_keys = ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS")
+    old = {k: os.environ.get(k) for k in env_keys}
+    for k in env_keys:
+        os.environ[k] = "1"
+    try:
+        ctx = mp.get_context("spawn")
+        a, b = ctx.Pipe(duplex=False)
+        over = {f: getattr(w, f) for f in ("n", "n_query", "d", "bits", "nlist")}
+        p = ctx.Process(target=_oracle_worker,
+                        args=(args.workload, over, nprobe, args.cpu_queries, steps, b))
+        p.start()
+        times, desc = a.recv()
+        p.join()
+    finally:
+        for k, v in old.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+    per = sorted(times)[len(times) // 2]
+    return args.cpu_queries / per, desc, times
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    w = workload_of(args)
+    nprobe = 64
+    steps = max(1, args.steps)
+    qps, desc, times = time_oracle(args, w, nprobe, steps + max(0, args.warmup))
+    times = times[max(0, args.warmup):]
+    ms = 1000.0 * sum(times) / len(times)
+    value = args.cpu_queries * len(times) / sum(times)
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "impl": "reference",
+            "n_gpus": args.gpus, "steps": len(times), "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": w.name, "n": w.n, "D": w.D, "d": w.d,
+                                            "bits": w.bits, "nlist": w.nlist, "nprobe": nprobe,
+                                            "k": w.k},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": desc},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+# --------------------------------------------------------------- GPU arm
+
+def main(argv=None):
+    args = parse_args(argv)
+    if args.impl == "reference":
+        return run_reference(args)
+    import numpy as np
+    import torch
+
+    import paper_2411_06158_gb300 as mrq
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    w = workload_of(args)
+    import datagen
+    t0 = time.time()
+    base, queries = datagen.base_and_queries(w)
+    t_gen = time.time() - t0
+    base_t = torch.from_numpy(base).to(dev)
+    q_t = torch.from_numpy(queries).to(dev)
+    t0 = time.time()
+    idx = mrq.mrq_build(base_t, w.d, w.bits, w.nlist, mrq.mrq_build_opts(seed=w.seed("method")))
+    torch.cuda.synchronize()
+    t_build = time.time() - t0
+    truth = ground_truth(base_t, q_t, w.k)
+    del base_t
+    torch.cuda.empty_cache()
+    stream = torch.cuda.current_stream(dev)
+
+    forms = {
+        "plain_fp32": mrq.mrq_search_opts(query_bits=0, stream=stream),
+        "plain_q4": mrq.mrq_search_opts(query_bits=4, stream=stream),
+    }
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def calibrate(opts):
+        for npb in NPROBE_LADDER:
+            if npb > w.nlist:
+                break
+            ids, _ = mrq.mrq_search(idx, q_t, w.k, npb, opts)
+            torch.cuda.synchronize()
+            r = recall(ids.cpu().numpy(), truth)
+            if r >= args.recall:
+                return npb, r
+        return None, r
+
+    def timed(opts, npb, steps, warmup, profile):
+        o = mrq.mrq_search_opts(eps0=opts.eps0, m=opts.m, mode=opts.mode, precision=opts.precision,
+                                query_bits=opts.query_bits, batched=opts.batched,
+                                profile=1 if profile else 0, stream=stream)
+        ids = torch.empty((w.n_query, w.k), dtype=torch.int64, device=dev)
+        dists = torch.empty((w.n_query, w.k), dtype=torch.float32, device=dev)
+        for _ in range(warmup):
+            mrq.mrq_search(idx, q_t, w.k, npb, o, out=(ids, dists))
+        stage = {s: 0.0 for s in mrq.STAGES}
+        launches = 0
+        per = []
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        for _ in range(steps):
+            flush.zero_()                      # L2 flush between timed steps
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            mrq.mrq_search(idx, q_t, w.k, npb, o, out=(ids, dists))
+            b.record(stream)
+            b.synchronize()
+            per.append(a.elapsed_time(b))
+            if profile:
+                ms, nl = mrq.mrq_last_search_profile(idx)
+                for s in stage:
+                    stage[s] += ms[s]
+                launches += nl
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        return per, stage, launches, ids
+
+    results = {}
+    for name, opts in forms.items():
+        npb, r = calibrate(opts)
+        if npb is None:
+            results[name] = {"nprobe": None, "recall": r}
+            continue
+        per, stage, launches, ids = timed(opts, npb, args.steps, args.warmup, True)
+        st = mrq.mrq_last_search_stats(idx, w.n_query)
+        ms = sum(per) / len(per)
+        results[name] = {"nprobe": npb, "recall": r, "ms_per_step": ms,
+                         "qps": w.n_query / (ms / 1000.0), "stage_ms": {k: v / len(per) for k, v in stage.items()},
+                         "launches_per_step": launches // max(1, len(per)),
+                         "cand_per_query": float(st["n_cand"].mean()),
+                         "s1_per_query": float(st["n_s1"].mean()),
+                         "exact_per_query": float(st["n_exact"].mean()), "per_step_ms": per}
+    ok = {k: v for k, v in results.items() if v.get("qps")}
+    if not ok:
+        print(json.dumps({"metric": METRIC, "error": "no form reached the recall target",
+                          "results": results}))
+        return 1
+    best = max(ok, key=lambda k: ok[k]["qps"])
+    B = ok[best]
+    # max over ranks
+    ms_step = B["ms_per_step"]
+    if world > 1:
+        t = torch.tensor([ms_step], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms_step = float(t.item())
+    value = world * w.n_query / (ms_step / 1000.0)
+
+    # clocks during a second timed pass of the best form
+    clk = ClockSampler(local, os.path.join(ROOT, "gpurun_out", f"clocks_rank{rank}.csv")) \
+        if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else ClockSampler(local, "/tmp/mrq_clocks.csv")
+    timed(forms[best], B["nprobe"], max(args.steps, 20), 1, False)
+    clocks = clk.stop()
+
+    # end to end through the public call with pinned host buffers
+    qh = torch.from_numpy(queries).pin_memory()
+    ih = torch.empty((w.n_query, w.k), dtype=torch.int64).pin_memory()
+    dh = torch.empty((w.n_query, w.k), dtype=torch.float32).pin_memory()
+    o = forms[best]
+    for _ in range(args.warmup):
+        mrq.mrq_search(idx, qh, w.k, B["nprobe"], o, out=(ih, dh))
+    torch.cuda.synchronize()
+    e2e_t = []
+    for _ in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        mrq.mrq_search(idx, qh, w.k, B["nprobe"], o, out=(ih, dh))
+        e2e_t.append(time.perf_counter() - t0)
+    e2e_qps = world * w.n_query / (sum(e2e_t) / len(e2e_t))
+
+    # roofline of the dominant kernel (the stage-1 scan): algorithmic bytes per
+    # candidate = B*d/8 code bytes + 12 bytes of factors (f_add, f_rescale, f_err)
+    peak, peak_kind = load_peaks()
+    bpc = w.bits * w.d / 8 + 12
+    scan_ms = B["stage_ms"]["scan"]
+    n_batches = 1 + (w.n_query - 1) // 16384
+    alg_bytes = B["cand_per_query"] * w.n_query * bpc / n_batches
+    achieved = alg_bytes / (scan_ms / n_batches / 1000.0) / 1e9
+    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak, "traffic": None, "kernel": "k_scan",
+            "peak_kind": peak_kind, "algorithmic_bytes_per_launch": alg_bytes,
+            "launch_ms": scan_ms / n_batches}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        try:
+            cq, desc, _ = time_oracle(args, w, B["nprobe"], 2)
+            cpu = {"value": cq, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc}
+        except Exception as e:  # keep the GPU line even if the CPU leg fails
+            cpu = {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle", "error": str(e)}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": w.name, "n": w.n, "D": w.D, "d": w.d, "bits": w.bits,
+                   "nlist": w.nlist, "k": w.k, "queries_per_step": w.n_query,
+                   "nprobe": B["nprobe"], "recall@10": B["recall"], "form": best,
+                   "l2": "256 MB buffer written between timed steps"},
+        "e2e": {"value": e2e_qps, "unit": UNIT, "h2d_bytes_per_step": w.n_query * w.D * 4,
+                "d2h_bytes_per_step": w.n_query * w.k * 12},
+        "gpu_launches": B["launches_per_step"] * args.steps,
+        "roofline": roof, "cpu_baseline": cpu, "clocks": clocks,
+        "forms": {k: {kk: vv for kk, vv in v.items() if kk != "per_step_ms"} for k, v in results.items()},
+        "build_s": t_build, "datagen_s": t_gen,
+    }
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

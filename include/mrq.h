@@ -1,0 +1,167 @@
+/*
+ * mrq.h — C ABI of the GB300 (sm_103a) implementation of MRQ, the
+ * projection-plus-quantization approximate k-NN method of arXiv 2411.06158
+ * ("Quantization Meets Projection").
+ *
+ * Problem (Section 2.1): given n base vectors in R^D and a query q, return the
+ * k base vectors closest to q under squared Euclidean distance.  MRQ (Sections
+ * 4-5) rotates every vector into its PCA basis, quantizes only the leading d
+ * coordinates (RaBitQ-style codes, B bits per coordinate), summarises the
+ * remaining D-d coordinates by their norm and variance, and searches an IVF
+ * index in three stages: a code-based estimate with error bounds (Eq. 4, Eq. 5,
+ * Eq. 6), a projected-distance check (Eq. 7), and an exact rerank.
+ *
+ * Conventions for every call:
+ *  - Return value: 0 on success, a negative MRQ_E* code on error; then
+ *    mrq_last_error() returns a message for the calling thread.  No call throws.
+ *  - Real arrays are row-major float32; ids are int64.  Distances are squared L2.
+ *  - A pointer argument may be host or device memory (CUDA unified addressing
+ *    tells them apart); the caller owns it and it is only read/written during
+ *    the call (the call synchronises its stream before returning).
+ *  - All device work runs on the current CUDA device, on the stream given in
+ *    the options (NULL = the legacy default stream).
+ *  - An index is not thread-safe: serialise calls that share one index.
+ */
+#ifndef MRQ_H
+#define MRQ_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* error codes */
+#define MRQ_OK 0
+#define MRQ_EINVAL (-1)    /* an argument is out of range (message says which) */
+#define MRQ_ENOMEM (-2)    /* device or host allocation failed */
+#define MRQ_ECUDA (-3)     /* a CUDA runtime/driver call failed */
+#define MRQ_EFORMAT (-4)   /* an index file is malformed or has another version */
+#define MRQ_EIO (-5)       /* a file could not be opened, read or written */
+#define MRQ_ETIMEDOUT (-6) /* a bounded device-side wait gave up */
+
+/* search modes (Section 6.1, algorithm list) */
+#define MRQ_MODE_MRQ 0      /* IVF-MRQ: stage 1 then exact rerank (no stage 2) */
+#define MRQ_MODE_MRQ_PLUS 1 /* IVF-MRQ+: stage 1, stage 2 (Eq. 7), exact rerank */
+
+/* query-projection precision (the first step of Algorithm 2) */
+#define MRQ_PREC_FP32 0   /* float32 CUDA-core GEMM */
+#define MRQ_PREC_BF16 1   /* one bf16 tensor-core product, fp32 accumulate */
+#define MRQ_PREC_BF16X3 2 /* split hi+lo bf16: hi*hi + hi*lo + lo*hi, fp32 accumulate */
+
+typedef struct mrq_index mrq_index; /* opaque; owned by the library */
+
+typedef struct {
+  uint64_t seed;                /* seed of the library's own draws (0 = 1) */
+  int kmeans_iters;             /* Lloyd iterations (Algorithm 1, IVF step); default 20 */
+  const float* init_centroids;  /* nlist x D raw-space initial centroids, or NULL */
+  const int64_t* init_ids;      /* nlist base rows used as initial centroids, or NULL */
+  const double* rotation_gauss; /* d x d Gaussian draw behind P_r (Algorithm 1), or NULL */
+} mrq_build_opts;
+
+typedef struct {
+  float eps0;       /* Eq. 5 confidence parameter; default 1.9 */
+  float m;          /* Chebyshev multiplier of the residual bound (Eq. 6); default 4 */
+  int mode;         /* MRQ_MODE_*; default MRQ_MODE_MRQ_PLUS */
+  int precision;    /* MRQ_PREC_*; default MRQ_PREC_FP32 */
+  int query_bits;   /* 0 = float32 query in the scan; 1..8 = scalar-quantized query */
+  int batched;      /* 0 = one work item per (query, list); 1 = list-major batched scan */
+  int profile;      /* 1 = record CUDA events around each stage (see mrq_last_search_profile) */
+  void* cuda_stream;/* cudaStream_t, or NULL */
+} mrq_search_opts;
+
+/* stages reported by mrq_last_search_profile */
+#define MRQ_STAGE_PROJECT 0  /* query projection GEMM (Algorithm 2, rotate step) */
+#define MRQ_STAGE_QSTATS 1   /* |q_r|^2, sigma (Eq. 6), |q_p|^2 */
+#define MRQ_STAGE_PROBE 2    /* centroid distances */
+#define MRQ_STAGE_SELECT 3   /* top-nprobe selection */
+#define MRQ_STAGE_SCAN 4     /* stage-1 code scan, bounds and survivor compaction */
+#define MRQ_STAGE_FINAL 5    /* thresholds, stage 2 (Eq. 7), exact rerank, top-k */
+#define MRQ_NSTAGES 6
+
+typedef struct {
+  int64_t n;
+  int D, d, bits, nlist;
+  int64_t max_list;     /* largest list size */
+  int64_t device_bytes; /* device memory held by the index */
+} mrq_index_info_t;
+
+/* Fill *opt with the defaults listed above. */
+void mrq_build_opts_default(mrq_build_opts* opt);
+void mrq_search_opts_default(mrq_search_opts* opt);
+
+/*
+ * Build an IVF-MRQ index on the GPU (Algorithm 1).
+ *  base: n x D float32 (host or device).  d: number of leading PCA coordinates
+ *  that are quantized, 0 < d <= D, d % 32 == 0, d >= 32.  bits: code bits per
+ *  quantized coordinate, 1..8 (1 = the paper's sign code).  nlist: IVF lists,
+ *  1 <= nlist <= n.  n must be < 2^31.  opt may be NULL (defaults).
+ * Steps: float64 mean/covariance and float64 Jacobi eigendecomposition (PCA,
+ * residual variances), projection of the base, k-means on the leading d
+ * coordinates, quantization with the random rotation P_r, precomputed factors.
+ * On success *out owns device memory; release it with mrq_free.
+ */
+int mrq_build(const float* base, int64_t n, int D, int d, int bits, int nlist,
+              const mrq_build_opts* opt, mrq_index** out);
+
+/*
+ * Search (Algorithm 2) nq queries for their k nearest neighbours among the
+ * vectors of the nprobe IVF lists nearest to each query.
+ *  queries: nq x D float32 (host or device).  ids: nq x k int64, dists: nq x k
+ *  float32 (host or device, both the same kind).  1 <= k <= 1024,
+ *  1 <= nprobe <= nlist.  Results are sorted by (distance, id); when fewer than
+ *  k vectors reach the exact stage the tail is id -1, distance +inf.
+ * Thresholds follow an order-independent contract (tau_A = k-th smallest stage-1
+ * upper bound, tau_B = min(tau_A, k-th smallest stage-2 upper bound), survivors
+ * are the candidates whose lower bound does not exceed the threshold), so the
+ * answer of a query does not depend on the batch it is searched in.
+ */
+int mrq_search(mrq_index* index, const float* queries, int64_t nq, int k, int nprobe,
+               const mrq_search_opts* opt, int64_t* ids, float* dists);
+
+/*
+ * Per-candidate stage-1 values of one query against one list (diagnostics and
+ * parity tests).  The query is given already projected: qp is the D-vector
+ * [q_d' | q_r] in the index's rotated PCA frame (host or device).  Outputs (host
+ * or device, length = size of list `list`): ip (the inner product <v, q'> the
+ * scan uses), dis (Eq. 4), lb, ub (stage-1 bounds), and, when query_bits > 0,
+ * int_dot (the integer code dot <u, qbar>) else untouched (may be NULL).
+ */
+int mrq_estimate(mrq_index* index, const float* qp, int list, const mrq_search_opts* opt,
+                 float* ip, float* dis, float* lb, float* ub, int32_t* int_dot);
+
+/* Project queries into the index frame: qp = W (q - mu), nq x D (host or device). */
+int mrq_project(mrq_index* index, const float* queries, int64_t nq,
+                const mrq_search_opts* opt, float* qp);
+
+/* Per-query counters of the last mrq_search on this index (host arrays of nq):
+ * candidates scanned, stage-1 survivors, exact distances computed. */
+int mrq_last_search_stats(const mrq_index* index, int64_t nq, int64_t* n_cand,
+                          int64_t* n_s1, int64_t* n_exact);
+
+/* Device time per stage of the last mrq_search run with opts.profile = 1, in
+ * milliseconds summed over its internal batches (CUDA events on the search
+ * stream), and the number of kernels it launched.  stage_ms: MRQ_NSTAGES doubles. */
+int mrq_last_search_profile(const mrq_index* index, double* stage_ms, int64_t* launches);
+
+/* Save / load the index file (format version 1, documented in the design doc). */
+int mrq_save(const mrq_index* index, const char* path);
+int mrq_load(const char* path, mrq_index** out);
+
+int mrq_index_info(const mrq_index* index, mrq_index_info_t* info);
+
+/* Copy one index array to host memory in the file's canonical layout (list-major,
+ * unpadded).  field: 4-character tag of the file format (e.g. "CODE", "XD__"). */
+int mrq_index_export(const mrq_index* index, const char* field, void* host_dst,
+                     size_t bytes);
+
+void mrq_free(mrq_index* index);
+
+/* Message of the last failed call on this thread ("" if none). */
+const char* mrq_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MRQ_H */

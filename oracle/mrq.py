@@ -349,10 +349,13 @@ def search_contract(idx: OracleIndex, Q, k: int, nprobe: int, *, eps0: float = 1
     Whenever every bound holds, the answer equals the exact top-k of the probed
     lists (and so does the paper's sequential loop).
 
-    ``margin`` records, per query, the smallest gap (relative to the distance
-    scale) between a probed/unprobed centroid boundary, a pruning decision and
-    its threshold, or two result distances around rank k; the GPU path (float32)
-    may legitimately decide otherwise only where this gap is tiny.
+    ``margin`` records, per query, the smallest relative gap of any decision
+    that can change the answer: the probed/unprobed centroid boundary, the
+    stage-1 test of a candidate that is in the answer, could enter it (exact
+    distance within the k-th) or could move tau_B (its UB2 among the k smallest),
+    the stage-2 test of an answer-relevant candidate, and consecutive answer
+    distances around rank k.  An implementation computing in float32 may
+    legitimately answer differently only where this gap is at rounding level.
     """
     qd_all, qr_all, qr2_all, sig_all, qp2_all = project_queries(idx, Q)
     nq = qd_all.shape[0]
@@ -381,26 +384,26 @@ def search_contract(idx: OracleIndex, Q, k: int, nprobe: int, *, eps0: float = 1
         sc = np.concatenate(sc) if sc else np.zeros(0)
         n_cand[qi] = pos.size
         tau_a = _kth(ub, k)
-        s1 = lb <= tau_a
-        if pos.size and math.isfinite(tau_a):
-            mg = min(mg, float(np.min(np.abs(lb - tau_a) / sc)))
-        p1 = pos[s1]
-        n_s1[qi] = p1.size
-        if mode == MODE_MRQ_PLUS and p1.size:
-            diso = idx.xnorm2[p1] + qp2_all[qi] - 2.0 * (idx.xd[p1] @ qd)
-            lb2 = diso - m * sig_all[qi]
-            ub2 = diso + m * sig_all[qi]
-            tau_b = min(tau_a, _kth(ub2, k))
-            s2 = lb2 <= tau_b
-            if math.isfinite(tau_b):
-                sc2 = np.maximum(np.abs(diso), idx.xnorm2[p1] + qp2_all[qi])
-                mg = min(mg, float(np.min(np.abs(lb2 - tau_b) / sc2)))
-            p2 = p1[s2]
+        s1 = lb <= tau_a                                    # stage-1 survivors
+        # stage-2 quantities (Eq. 7) of every candidate, used on S1 only
+        diso = idx.xnorm2[pos] + qp2_all[qi] - 2.0 * (idx.xd[pos] @ qd)
+        lb2 = diso - m * sig_all[qi]
+        ub2 = diso + m * sig_all[qi]
+        sc2 = np.maximum(np.abs(diso), idx.xnorm2[pos] + qp2_all[qi])
+        if mode == MODE_MRQ_PLUS and s1.any():
+            kth_ub2 = _kth(ub2[s1], k)
+            tau_b = min(tau_a, kth_ub2)
+            s2 = s1 & (lb2 <= tau_b)
         else:
-            p2 = p1
+            kth_ub2, tau_b = math.inf, math.inf
+            s2 = s1
+        n_s1[qi] = int(s1.sum())
+        p2 = pos[s2]
         n_s2[qi] = p2.size
+        ex_all = (np.sum((idx.xd[pos] - qd) ** 2, axis=1)
+                  + np.sum((idx.xr[pos] - qr) ** 2, axis=1))
         if p2.size:
-            ex = np.sum((idx.xd[p2] - qd) ** 2, axis=1) + np.sum((idx.xr[p2] - qr) ** 2, axis=1)
+            ex = ex_all[s2]
             oid = idx.ids[p2]
             o = np.lexsort((oid, ex))
             kk = min(k, p2.size)
@@ -411,6 +414,17 @@ def search_contract(idx: OracleIndex, Q, k: int, nprobe: int, *, eps0: float = 1
                 lim = min(k + 1, srt.size)
                 gaps = np.diff(srt[:lim]) / np.maximum(srt[1:lim], 1e-30)
                 mg = min(mg, float(np.min(gaps)))
+            dk = srt[kk - 1] if p2.size >= k else math.inf
+        else:
+            dk = math.inf
+        in_ans = np.isin(idx.ids[pos], ids[qi, :min(k, p2.size)])
+        near = in_ans | (ex_all <= dk * (1 + 1e-6))
+        rel1 = near | ((mode == MODE_MRQ_PLUS) & (ub2 <= kth_ub2 * (1 + 1e-6)))
+        if pos.size and math.isfinite(tau_a) and rel1.any():
+            mg = min(mg, float(np.min(np.abs(lb[rel1] - tau_a) / sc[rel1])))
+        rel2 = near & s1
+        if mode == MODE_MRQ_PLUS and math.isfinite(tau_b) and rel2.any():
+            mg = min(mg, float(np.min(np.abs(lb2[rel2] - tau_b) / sc2[rel2])))
         margin[qi] = mg
     return SearchResult(ids, dists, n_cand, n_s1, n_s2, margin)
 

@@ -1,0 +1,498 @@
+// C ABI of libmrq (declared in include/mrq.h): argument checks, host/device
+// staging, batching, index file I/O.  Every entry point catches internal
+// errors and turns them into MRQ_E* codes plus a thread-local message.
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <memory>
+#include <string>
+
+#include "common.cuh"
+
+namespace {
+
+thread_local std::string g_err;
+
+template <class F>
+int guarded(F&& f) {
+  try {
+    f();
+    g_err.clear();
+    return MRQ_OK;
+  } catch (const mrq::Error& e) {
+    g_err = e.msg;
+    return e.code;
+  } catch (const std::bad_alloc&) {
+    g_err = "host allocation failed";
+    return MRQ_ENOMEM;
+  } catch (const std::exception& e) {
+    g_err = e.what();
+    return MRQ_EINVAL;
+  }
+}
+
+bool on_device(const void* p) {
+  if (!p) return false;
+  cudaPointerAttributes a{};
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+cudaStream_t stream_of(const mrq_search_opts& o) { return (cudaStream_t)o.cuda_stream; }
+
+void use_device(const mrq_index* idx) { MRQ_CUDA(cudaSetDevice(idx->device)); }
+
+mrq_search_opts resolve(const mrq_search_opts* opt) {
+  mrq_search_opts o;
+  mrq_search_opts_default(&o);
+  if (opt) o = *opt;
+  MRQ_REQUIRE(o.eps0 >= 0.f && o.m >= 0.f, "eps0 and m must be >= 0");
+  MRQ_REQUIRE(o.mode == MRQ_MODE_MRQ || o.mode == MRQ_MODE_MRQ_PLUS, "mode must be MRQ_MODE_MRQ or MRQ_MODE_MRQ_PLUS");
+  MRQ_REQUIRE(o.precision >= MRQ_PREC_FP32 && o.precision <= MRQ_PREC_BF16X3, "unknown precision");
+  MRQ_REQUIRE(o.query_bits >= 0 && o.query_bits <= 8, "query_bits must be in [0, 8]");
+  return o;
+}
+
+// ---------------------------------------------------------------- file format
+
+constexpr char kMagic[8] = {'M', 'R', 'Q', 'I', 'N', 'D', 'E', 'X'};
+constexpr uint32_t kVersion = 1;
+enum : uint32_t { DT_F32 = 1, DT_F64 = 2, DT_I64 = 3, DT_U8 = 4 };
+
+struct Section {
+  char tag[4];
+  uint32_t dtype;
+  std::vector<uint8_t> data;
+};
+
+size_t dt_size(uint32_t dt) { return dt == DT_F32 ? 4 : dt == DT_F64 ? 8 : dt == DT_I64 ? 8 : 1; }
+
+template <typename T>
+std::vector<uint8_t> d2h_bytes(const T* dev, size_t count, cudaStream_t st) {
+  std::vector<uint8_t> v(count * sizeof(T));
+  if (count) MRQ_CUDA(cudaMemcpyAsync(v.data(), dev, v.size(), cudaMemcpyDeviceToHost, st));
+  return v;
+}
+
+}  // namespace
+
+// ===================================================================== ABI
+
+extern "C" {
+
+const char* mrq_last_error(void) { return g_err.c_str(); }
+
+void mrq_build_opts_default(mrq_build_opts* opt) {
+  if (!opt) return;
+  std::memset(opt, 0, sizeof(*opt));
+  opt->seed = 1;
+  opt->kmeans_iters = 20;
+}
+
+void mrq_search_opts_default(mrq_search_opts* opt) {
+  if (!opt) return;
+  std::memset(opt, 0, sizeof(*opt));
+  opt->eps0 = 1.9f;
+  opt->m = 4.0f;
+  opt->mode = MRQ_MODE_MRQ_PLUS;
+  opt->precision = MRQ_PREC_FP32;
+  opt->query_bits = 0;
+  opt->batched = 0;
+  opt->cuda_stream = nullptr;
+}
+
+int mrq_build(const float* base, int64_t n, int D, int d, int bits, int nlist,
+              const mrq_build_opts* opt, mrq_index** out) {
+  return guarded([&] {
+    MRQ_REQUIRE(out != nullptr, "out is NULL");
+    *out = nullptr;
+    MRQ_REQUIRE(base != nullptr, "base is NULL");
+    MRQ_REQUIRE(n >= 1 && n < (int64_t(1) << 31), "n must be in [1, 2^31)");
+    MRQ_REQUIRE(D >= 32 && D <= 16384, "D must be in [32, 16384]");
+    MRQ_REQUIRE(d >= 32 && d <= D && d % 32 == 0 && d <= 512, "d must be a multiple of 32 in [32, min(D, 512)]");
+    MRQ_REQUIRE(bits >= 1 && bits <= 8, "bits must be in [1, 8]");
+    MRQ_REQUIRE(nlist >= 1 && nlist <= n && nlist <= (1 << 20), "nlist must be in [1, min(n, 2^20)]");
+    mrq_build_opts o;
+    mrq_build_opts_default(&o);
+    if (opt) o = *opt;
+    MRQ_REQUIRE(o.kmeans_iters >= 0 && o.kmeans_iters <= 1000, "kmeans_iters must be in [0, 1000]");
+    std::unique_ptr<mrq_index> idx(new mrq_index());
+    MRQ_CUDA(cudaGetDevice(&idx->device));
+    idx->n = n;
+    idx->D = D;
+    idx->d = d;
+    idx->bits = bits;
+    idx->nlist = nlist;
+    cudaStream_t st = nullptr;
+    mrq::DevBuf<float> staged;
+    const float* X = base;
+    if (!on_device(base)) {
+      staged.alloc((size_t)n * D);
+      MRQ_CUDA(cudaMemcpy(staged.p, base, staged.bytes(), cudaMemcpyHostToDevice));
+      X = staged.p;
+    }
+    mrq::build_index(idx.get(), X, o, st);
+    *out = idx.release();
+  });
+}
+
+int mrq_search(mrq_index* idx, const float* queries, int64_t nq, int k, int nprobe,
+               const mrq_search_opts* opt, int64_t* ids, float* dists) {
+  return guarded([&] {
+    MRQ_REQUIRE(idx != nullptr, "index is NULL");
+    MRQ_REQUIRE(nq >= 0, "nq must be >= 0");
+    MRQ_REQUIRE(k >= 1 && k <= 1024, "k must be in [1, 1024]");
+    MRQ_REQUIRE(nprobe >= 1 && nprobe <= idx->nlist && nprobe <= 16384,
+                "nprobe must be in [1, min(nlist, 16384)]");
+    if (nq == 0) return;
+    MRQ_REQUIRE(queries && ids && dists, "queries, ids and dists must not be NULL");
+    const mrq_search_opts o = resolve(opt);
+    use_device(idx);
+    cudaStream_t st = stream_of(o);
+    const bool qdev = on_device(queries);
+    const bool odev = on_device(ids);
+    MRQ_REQUIRE(odev == on_device(dists), "ids and dists must both be host or both be device memory");
+    const int D = idx->D;
+    const int64_t cap = std::max<int64_t>(idx->cap_by_nprobe[nprobe], 1);
+    // batch size: survivor scratch (6 arrays x 4 B x cap per query) within ~6 GB,
+    // probe matrix within ~1 GB
+    int64_t qb = std::min<int64_t>(nq, 16384);
+    qb = std::min<int64_t>(qb, std::max<int64_t>(1, (int64_t)6e9 / (24 * cap)));
+    qb = std::min<int64_t>(qb, std::max<int64_t>(1, (int64_t)1e9 / (4 * (int64_t)idx->nlist)));
+    auto& ws = idx->ws;
+    ws.stats.reserve((size_t)nq * 3);
+    if (!odev) {
+      ws.oids.reserve((size_t)qb * k);
+      ws.odist.reserve((size_t)qb * k);
+    }
+    if (!qdev) ws.q.reserve((size_t)qb * D);
+    idx->prof_on = o.profile != 0;
+    idx->prof_batches = 0;
+    idx->launches = 0;
+    for (int64_t s = 0; s < nq; s += qb) {
+      const int64_t b = std::min(qb, nq - s);
+      const float* qp = queries + s * D;
+      if (!qdev) {
+        MRQ_CUDA(cudaMemcpyAsync(ws.q.p, qp, 4 * b * D, cudaMemcpyHostToDevice, st));
+        qp = ws.q.p;
+      }
+      int64_t* oi = odev ? ids + s * k : ws.oids.p;
+      float* od = odev ? dists + s * k : ws.odist.p;
+      mrq::search_batch(idx, qp, b, k, nprobe, o, oi, od, ws.stats.p + s * 3, st);
+      if (!odev) {
+        MRQ_CUDA(cudaMemcpyAsync(ids + s * k, oi, 8 * b * k, cudaMemcpyDeviceToHost, st));
+        MRQ_CUDA(cudaMemcpyAsync(dists + s * k, od, 4 * b * k, cudaMemcpyDeviceToHost, st));
+      }
+    }
+    idx->last_stats.resize((size_t)nq * 3);
+    MRQ_CUDA(cudaMemcpyAsync(idx->last_stats.data(), ws.stats.p, 8 * nq * 3, cudaMemcpyDeviceToHost, st));
+    MRQ_CUDA(cudaStreamSynchronize(st));
+    idx->last_nq = nq;
+    for (int s = 0; s < MRQ_NSTAGES; ++s) idx->prof_ms[s] = 0.0;
+    if (idx->prof_on) {
+      for (int b = 0; b < idx->prof_batches; ++b)
+        for (int s = 0; s < MRQ_NSTAGES; ++s) {
+          float ms = 0.f;
+          MRQ_CUDA(cudaEventElapsedTime(&ms, idx->prof_ev[(size_t)b * (MRQ_NSTAGES + 1) + s],
+                                        idx->prof_ev[(size_t)b * (MRQ_NSTAGES + 1) + s + 1]));
+          idx->prof_ms[s] += ms;
+        }
+    }
+  });
+}
+
+int mrq_last_search_profile(const mrq_index* idx, double* stage_ms, int64_t* launches) {
+  return guarded([&] {
+    MRQ_REQUIRE(idx != nullptr, "index is NULL");
+    if (stage_ms)
+      for (int s = 0; s < MRQ_NSTAGES; ++s) stage_ms[s] = idx->prof_ms[s];
+    if (launches) *launches = idx->launches;
+  });
+}
+
+int mrq_project(mrq_index* idx, const float* queries, int64_t nq, const mrq_search_opts* opt,
+                float* qp) {
+  return guarded([&] {
+    MRQ_REQUIRE(idx && queries && qp, "NULL argument");
+    MRQ_REQUIRE(nq >= 1, "nq must be >= 1");
+    const mrq_search_opts o = resolve(opt);
+    use_device(idx);
+    cudaStream_t st = stream_of(o);
+    const int D = idx->D, d = idx->d, r = D - d;
+    auto& ws = idx->ws;
+    mrq::DevBuf<float> qin;
+    const float* q = queries;
+    if (!on_device(queries)) {
+      qin.alloc((size_t)nq * D);
+      MRQ_CUDA(cudaMemcpyAsync(qin.p, queries, 4 * nq * D, cudaMemcpyHostToDevice, st));
+      q = qin.p;
+    }
+    ws.qd.reserve((size_t)nq * d);
+    ws.qr.reserve((size_t)nq * std::max(r, 1));
+    mrq::project_batch(idx, q, nq, o.precision, ws.qd.p, ws.qr.p, st);
+    MRQ_CUDA(cudaMemcpy2DAsync(qp, 4 * D, ws.qd.p, 4 * d, 4 * d, nq, cudaMemcpyDefault, st));
+    if (r > 0)
+      MRQ_CUDA(cudaMemcpy2DAsync(qp + d, 4 * D, ws.qr.p, 4 * r, 4 * r, nq, cudaMemcpyDefault, st));
+    MRQ_CUDA(cudaStreamSynchronize(st));
+  });
+}
+
+int mrq_estimate(mrq_index* idx, const float* qp, int list, const mrq_search_opts* opt, float* ip,
+                 float* dis, float* lb, float* ub, int32_t* int_dot) {
+  return guarded([&] {
+    MRQ_REQUIRE(idx && qp, "NULL argument");
+    MRQ_REQUIRE(list >= 0 && list < idx->nlist, "list out of range");
+    const mrq_search_opts o = resolve(opt);
+    use_device(idx);
+    cudaStream_t st = stream_of(o);
+    const int64_t sz = idx->h_loff[list + 1] - idx->h_loff[list];
+    if (sz == 0) return;
+    MRQ_REQUIRE(ip && dis && lb && ub, "ip, dis, lb and ub must not be NULL");
+    mrq::DevBuf<float> tmp(4 * sz);
+    mrq::DevBuf<int32_t> ti(sz);
+    mrq::DevBuf<float> qdev;
+    const float* q = qp;
+    if (!on_device(qp)) {
+      qdev.alloc(idx->D);
+      MRQ_CUDA(cudaMemcpyAsync(qdev.p, qp, 4 * idx->D, cudaMemcpyHostToDevice, st));
+      q = qdev.p;
+    }
+    mrq::estimate_one(idx, q, list, o, tmp.p, tmp.p + sz, tmp.p + 2 * sz, tmp.p + 3 * sz,
+                      o.query_bits > 0 ? ti.p : nullptr, st);
+    MRQ_CUDA(cudaMemcpyAsync(ip, tmp.p, 4 * sz, cudaMemcpyDefault, st));
+    MRQ_CUDA(cudaMemcpyAsync(dis, tmp.p + sz, 4 * sz, cudaMemcpyDefault, st));
+    MRQ_CUDA(cudaMemcpyAsync(lb, tmp.p + 2 * sz, 4 * sz, cudaMemcpyDefault, st));
+    MRQ_CUDA(cudaMemcpyAsync(ub, tmp.p + 3 * sz, 4 * sz, cudaMemcpyDefault, st));
+    if (o.query_bits > 0 && int_dot)
+      MRQ_CUDA(cudaMemcpyAsync(int_dot, ti.p, 4 * sz, cudaMemcpyDefault, st));
+    MRQ_CUDA(cudaStreamSynchronize(st));
+  });
+}
+
+int mrq_last_search_stats(const mrq_index* idx, int64_t nq, int64_t* n_cand, int64_t* n_s1,
+                          int64_t* n_exact) {
+  return guarded([&] {
+    MRQ_REQUIRE(idx != nullptr, "index is NULL");
+    MRQ_REQUIRE(nq == idx->last_nq, "nq differs from the last search on this index");
+    for (int64_t i = 0; i < nq; ++i) {
+      if (n_cand) n_cand[i] = idx->last_stats[i * 3 + 0];
+      if (n_s1) n_s1[i] = idx->last_stats[i * 3 + 1];
+      if (n_exact) n_exact[i] = idx->last_stats[i * 3 + 2];
+    }
+  });
+}
+
+int mrq_index_info(const mrq_index* idx, mrq_index_info_t* info) {
+  return guarded([&] {
+    MRQ_REQUIRE(idx && info, "NULL argument");
+    info->n = idx->n;
+    info->D = idx->D;
+    info->d = idx->d;
+    info->bits = idx->bits;
+    info->nlist = idx->nlist;
+    info->max_list = idx->max_list;
+    info->device_bytes = (int64_t)(idx->mu.bytes() + idx->lam.bytes() + idx->W.bytes() +
+                                   idx->W_hi.bytes() + idx->W_lo.bytes() + idx->cent.bytes() +
+                                   idx->cent_n2.bytes() + idx->loff.bytes() + idx->ploff.bytes() +
+                                   idx->ids.bytes() + idx->codes.bytes() + idx->fadd.bytes() +
+                                   idx->fres.bytes() + idx->ferr.bytes() + idx->xd.bytes() +
+                                   idx->xr.bytes() + idx->xn2.bytes());
+  });
+}
+
+static void export_field(const mrq_index* idx, const std::string& f, std::vector<uint8_t>& out,
+                         uint32_t& dtype, cudaStream_t st) {
+  const int64_t n = idx->n;
+  const int D = idx->D, d = idx->d, r = D - d;
+  if (f == "MU__") { out = d2h_bytes(idx->mu.p, D, st); dtype = DT_F32; }
+  else if (f == "LAM_") { out = d2h_bytes(idx->lam.p, D, st); dtype = DT_F32; }
+  else if (f == "W___") { out = d2h_bytes(idx->W.p, (size_t)D * D, st); dtype = DT_F32; }
+  else if (f == "CENT") { out = d2h_bytes(idx->cent.p, (size_t)idx->nlist * d, st); dtype = DT_F32; }
+  else if (f == "LOFF") {
+    out.resize(8 * idx->h_loff.size());
+    std::memcpy(out.data(), idx->h_loff.data(), out.size());
+    dtype = DT_I64;
+  } else if (f == "IDS_") { out = d2h_bytes(idx->ids.p, n, st); dtype = DT_I64; }
+  else if (f == "XD__") { out = d2h_bytes(idx->xd.p, (size_t)n * d, st); dtype = DT_F32; }
+  else if (f == "XR__") { out = d2h_bytes(idx->xr.p, (size_t)n * r, st); dtype = DT_F32; }
+  else if (f == "XN2_") { out = d2h_bytes(idx->xn2.p, n, st); dtype = DT_F32; }
+  else if (f == "CODE") {
+    mrq::DevBuf<uint8_t> lv((size_t)std::max<int64_t>(n * d, 1));
+    mrq::export_levels(idx, lv.p, st);
+    out = d2h_bytes(lv.p, (size_t)n * d, st);
+    MRQ_CUDA(cudaStreamSynchronize(st));
+    dtype = DT_U8;
+  } else if (f == "FADD" || f == "FRES" || f == "FERR") {
+    const float* src = f == "FADD" ? idx->fadd.p : f == "FRES" ? idx->fres.p : idx->ferr.p;
+    mrq::DevBuf<float> t((size_t)std::max<int64_t>(n, 1));
+    mrq::export_padded(idx, src, t.p, st);
+    out = d2h_bytes(t.p, n, st);
+    MRQ_CUDA(cudaStreamSynchronize(st));
+    dtype = DT_F32;
+  } else {
+    mrq::fail(MRQ_EINVAL, "unknown field " + f);
+  }
+  MRQ_CUDA(cudaStreamSynchronize(st));
+}
+
+int mrq_index_export(const mrq_index* idx, const char* field, void* host_dst, size_t bytes) {
+  return guarded([&] {
+    MRQ_REQUIRE(idx && field && host_dst, "NULL argument");
+    use_device(idx);
+    std::vector<uint8_t> out;
+    uint32_t dt = 0;
+    export_field(idx, std::string(field, strnlen(field, 4)), out, dt, nullptr);
+    MRQ_REQUIRE(bytes == out.size(), "destination size does not match the field size (" +
+                                         std::to_string(out.size()) + " bytes)");
+    std::memcpy(host_dst, out.data(), out.size());
+  });
+}
+
+static const char* kTags[] = {"MU__", "LAM_", "W___", "CENT", "LOFF", "IDS_", "CODE",
+                              "FADD", "FRES", "FERR", "XD__", "XR__", "XN2_"};
+
+int mrq_save(const mrq_index* idx, const char* path) {
+  return guarded([&] {
+    MRQ_REQUIRE(idx && path, "NULL argument");
+    use_device(idx);
+    FILE* f = std::fopen(path, "wb");
+    if (!f) mrq::fail(MRQ_EIO, std::string("cannot open ") + path + " for writing");
+    std::unique_ptr<FILE, int (*)(FILE*)> guard(f, std::fclose);
+    auto put = [&](const void* p, size_t b) {
+      if (b && std::fwrite(p, 1, b, f) != b) mrq::fail(MRQ_EIO, "write failed");
+    };
+    const uint32_t nsec = sizeof(kTags) / sizeof(kTags[0]);
+    put(kMagic, 8);
+    put(&kVersion, 4);
+    put(&nsec, 4);
+    const int32_t hdr[4] = {idx->D, idx->d, idx->bits, idx->nlist};
+    put(&idx->n, 8);
+    put(hdr, 16);
+    for (const char* tag : kTags) {
+      std::vector<uint8_t> data;
+      uint32_t dt = 0;
+      export_field(idx, tag, data, dt, nullptr);
+      uint64_t count = data.size() / dt_size(dt);
+      put(tag, 4);
+      put(&dt, 4);
+      put(&count, 8);
+      put(data.data(), data.size());
+      static const uint8_t zeros[8] = {0};
+      put(zeros, (8 - data.size() % 8) % 8);
+    }
+  });
+}
+
+int mrq_load(const char* path, mrq_index** out) {
+  return guarded([&] {
+    MRQ_REQUIRE(path && out, "NULL argument");
+    *out = nullptr;
+    FILE* f = std::fopen(path, "rb");
+    if (!f) mrq::fail(MRQ_EIO, std::string("cannot open ") + path);
+    std::unique_ptr<FILE, int (*)(FILE*)> guard(f, std::fclose);
+    auto get = [&](void* p, size_t b) {
+      if (b && std::fread(p, 1, b, f) != b) mrq::fail(MRQ_EFORMAT, "truncated index file");
+    };
+    char magic[8];
+    uint32_t version = 0, nsec = 0;
+    get(magic, 8);
+    if (std::memcmp(magic, kMagic, 8) != 0) mrq::fail(MRQ_EFORMAT, "not an MRQ index file");
+    get(&version, 4);
+    if (version != kVersion) mrq::fail(MRQ_EFORMAT, "unsupported index file version");
+    get(&nsec, 4);
+    int64_t n = 0;
+    int32_t hdr[4];
+    get(&n, 8);
+    get(hdr, 16);
+    const int D = hdr[0], d = hdr[1], bits = hdr[2], nlist = hdr[3];
+    if (!(n >= 1 && n < (int64_t(1) << 31) && D >= 32 && D <= 16384 && d >= 32 && d <= D &&
+          d % 32 == 0 && d <= 512 && bits >= 1 && bits <= 8 && nlist >= 1 && nlist <= n))
+      mrq::fail(MRQ_EFORMAT, "index header out of range");
+    const int r = D - d;
+    std::unique_ptr<mrq_index> idx(new mrq_index());
+    MRQ_CUDA(cudaGetDevice(&idx->device));
+    idx->n = n; idx->D = D; idx->d = d; idx->bits = bits; idx->nlist = nlist;
+    struct Want { const char* tag; uint32_t dt; uint64_t count; };
+    const Want want[] = {
+        {"MU__", DT_F32, (uint64_t)D}, {"LAM_", DT_F32, (uint64_t)D},
+        {"W___", DT_F32, (uint64_t)D * D}, {"CENT", DT_F32, (uint64_t)nlist * d},
+        {"LOFF", DT_I64, (uint64_t)nlist + 1}, {"IDS_", DT_I64, (uint64_t)n},
+        {"CODE", DT_U8, (uint64_t)n * d}, {"FADD", DT_F32, (uint64_t)n},
+        {"FRES", DT_F32, (uint64_t)n}, {"FERR", DT_F32, (uint64_t)n},
+        {"XD__", DT_F32, (uint64_t)n * d}, {"XR__", DT_F32, (uint64_t)n * r},
+        {"XN2_", DT_F32, (uint64_t)n}};
+    std::vector<std::vector<uint8_t>> sec(13);
+    std::vector<bool> seen(13, false);
+    for (uint32_t s = 0; s < nsec; ++s) {
+      char tag[4];
+      uint32_t dt;
+      uint64_t count;
+      get(tag, 4);
+      get(&dt, 4);
+      get(&count, 8);
+      if (dt < DT_F32 || dt > DT_U8) mrq::fail(MRQ_EFORMAT, "bad section dtype");
+      if (count > (uint64_t(1) << 40)) mrq::fail(MRQ_EFORMAT, "section too large");
+      int which = -1;
+      for (int w = 0; w < 13; ++w)
+        if (std::memcmp(tag, want[w].tag, 4) == 0) which = w;
+      size_t bytes = count * dt_size(dt);
+      std::vector<uint8_t> data(bytes);
+      get(data.data(), bytes);
+      uint8_t pad[8];
+      get(pad, (8 - bytes % 8) % 8);
+      if (which < 0) continue;  // unknown sections are skipped
+      if (dt != want[which].dt || count != want[which].count)
+        mrq::fail(MRQ_EFORMAT, std::string("section ") + want[which].tag + " has the wrong type or size");
+      sec[which] = std::move(data);
+      seen[which] = true;
+    }
+    for (int w = 0; w < 13; ++w)
+      if (!seen[w]) mrq::fail(MRQ_EFORMAT, std::string("missing section ") + want[w].tag);
+    idx->h_loff.resize(nlist + 1);
+    std::memcpy(idx->h_loff.data(), sec[4].data(), 8 * (nlist + 1));
+    if (idx->h_loff[0] != 0 || idx->h_loff[nlist] != n) mrq::fail(MRQ_EFORMAT, "bad list offsets");
+    for (int j = 0; j < nlist; ++j)
+      if (idx->h_loff[j + 1] < idx->h_loff[j]) mrq::fail(MRQ_EFORMAT, "bad list offsets");
+    {
+      const int64_t* ids = reinterpret_cast<const int64_t*>(sec[5].data());
+      for (int64_t i = 0; i < n; ++i)
+        if (ids[i] < 0 || ids[i] >= (int64_t(1) << 31)) mrq::fail(MRQ_EFORMAT, "id out of range");
+      const uint8_t* lv = sec[6].data();
+      for (size_t i = 0; i < sec[6].size(); ++i)
+        if (lv[i] >> bits) mrq::fail(MRQ_EFORMAT, "code level exceeds 2^bits - 1");
+    }
+    cudaStream_t st = nullptr;
+    auto up = [&](auto& buf, const std::vector<uint8_t>& data, size_t count) {
+      buf.alloc(std::max<size_t>(count, 1));
+      if (count) MRQ_CUDA(cudaMemcpyAsync(buf.p, data.data(), data.size(), cudaMemcpyHostToDevice, st));
+    };
+    up(idx->mu, sec[0], D);
+    up(idx->lam, sec[1], D);
+    up(idx->W, sec[2], (size_t)D * D);
+    up(idx->cent, sec[3], (size_t)nlist * d);
+    up(idx->ids, sec[5], n);
+    up(idx->xd, sec[10], (size_t)n * d);
+    up(idx->xr, sec[11], (size_t)n * r);
+    up(idx->xn2, sec[12], n);
+    mrq::DevBuf<uint8_t> lv;
+    mrq::DevBuf<float> fa, fr, fe;
+    up(lv, sec[6], (size_t)n * d);
+    up(fa, sec[7], n);
+    up(fr, sec[8], n);
+    up(fe, sec[9], n);
+    mrq::finalize_layout(idx.get(), lv.p, fa.p, fr.p, fe.p, st);
+    MRQ_CUDA(cudaStreamSynchronize(st));
+    *out = idx.release();
+  });
+}
+
+void mrq_free(mrq_index* idx) {
+  if (!idx) return;
+  cudaSetDevice(idx->device);
+  delete idx;
+}
+
+}  // extern "C"

@@ -1,0 +1,194 @@
+// Internal declarations of libmrq (GB300 / sm_103a implementation of MRQ).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <cstdint>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/mrq.h"
+
+namespace mrq {
+
+struct Error {
+  int code;
+  std::string msg;
+};
+
+[[noreturn]] inline void fail(int code, const std::string& msg) { throw Error{code, msg}; }
+
+#define MRQ_CUDA(call)                                                                   \
+  do {                                                                                   \
+    cudaError_t e_ = (call);                                                             \
+    if (e_ != cudaSuccess)                                                               \
+      ::mrq::fail(e_ == cudaErrorMemoryAllocation ? MRQ_ENOMEM : MRQ_ECUDA,              \
+                  std::string(#call) + " -> " + cudaGetErrorString(e_) + " (" __FILE__ ")"); \
+  } while (0)
+
+#define MRQ_CHECK_LAUNCH() MRQ_CUDA(cudaGetLastError())
+
+#define MRQ_REQUIRE(cond, msg)                      \
+  do {                                              \
+    if (!(cond)) ::mrq::fail(MRQ_EINVAL, (msg));    \
+  } while (0)
+
+// Owning device buffer (cudaMalloc / cudaFree).
+template <typename T>
+struct DevBuf {
+  T* p = nullptr;
+  size_t n = 0;
+  DevBuf() = default;
+  explicit DevBuf(size_t count) { alloc(count); }
+  DevBuf(const DevBuf&) = delete;
+  DevBuf& operator=(const DevBuf&) = delete;
+  DevBuf(DevBuf&& o) noexcept : p(o.p), n(o.n) { o.p = nullptr; o.n = 0; }
+  DevBuf& operator=(DevBuf&& o) noexcept {
+    if (this != &o) { release(); p = o.p; n = o.n; o.p = nullptr; o.n = 0; }
+    return *this;
+  }
+  ~DevBuf() { release(); }
+  void alloc(size_t count) {
+    release();
+    if (count == 0) return;
+    MRQ_CUDA(cudaMalloc(&p, count * sizeof(T)));
+    n = count;
+  }
+  // grow-only reallocation (contents are not preserved)
+  void reserve(size_t count) {
+    if (count > n) alloc(count);
+  }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    n = 0;
+  }
+  size_t bytes() const { return n * sizeof(T); }
+  T* get() const { return p; }
+};
+
+// Per-index search scratch, grown on demand and reused across calls.
+struct Workspace {
+  DevBuf<float> q;         // nq x D staged queries (host inputs)
+  DevBuf<float> qd, qr;    // projected queries
+  DevBuf<float> qstat;     // nq x 4: |q_r|^2, sigma, |q_p|^2, unused
+  DevBuf<__nv_bfloat16> qbf;  // nq x D bf16 hi/lo split queries (tensor-core projection)
+  DevBuf<float> gmat;      // nq x nlist probe distances
+  DevBuf<int32_t> plist;   // nq x nprobe probed list ids
+  DevBuf<float> pg;        // nq x nprobe |q_d - c|^2 of the probed lists
+  DevBuf<uint32_t> qcnt;   // nq survivor counters
+  DevBuf<uint32_t> gtau;   // nq running stage-1 thresholds (orderable keys)
+  DevBuf<int32_t> spos;    // nq x cap survivor positions
+  DevBuf<float> slb, sub;  // nq x cap stage-1 bounds of the survivors
+  DevBuf<float> s2a, s2b;  // nq x cap stage-2 scratch
+  DevBuf<int32_t> s2pos;   // nq x cap
+  DevBuf<int64_t> oids;    // nq x k staged results
+  DevBuf<float> odist;
+  DevBuf<int64_t> stats;   // nq x 3
+  DevBuf<uint32_t> work;   // work-queue counters
+  // list-major batched scan
+  DevBuf<int32_t> lcount, loffq, lqueue;  // per-list query buckets
+  DevBuf<int32_t> items;   // work items
+};
+
+}  // namespace mrq
+
+struct mrq_index {
+  int64_t n = 0;
+  int D = 0, d = 0, bits = 1, nlist = 0;
+  int device = 0;
+  int words = 0;   // 32-bit code words per vector = bits * d / 32
+  int vw = 1;      // words per vectorised load (1, 2 or 4)
+  int64_t np = 0;  // padded vector count (every list rounded up to 32)
+  int64_t max_list = 0;
+  std::vector<int64_t> h_loff, h_ploff;
+  std::vector<int64_t> cap_by_nprobe;  // sum of the nprobe largest list sizes
+
+  mrq::DevBuf<float> mu, lam, W;  // D, D, D x D
+  mrq::DevBuf<__nv_bfloat16> W_hi, W_lo;  // bf16 split of W
+  mrq::DevBuf<float> cent, cent_n2;       // nlist x d (rotated frame), nlist
+  mrq::DevBuf<int64_t> loff, ploff;       // nlist + 1
+  mrq::DevBuf<int64_t> ids;               // n, list-major
+  mrq::DevBuf<uint32_t> codes;            // padded bit-plane layout
+  mrq::DevBuf<float> fadd, fres, ferr;    // padded
+  mrq::DevBuf<float> xd, xr, xn2;         // list-major, unpadded
+  mrq::Workspace ws;
+  int64_t last_nq = 0;
+  std::vector<int64_t> last_stats;        // nq x 3 host copy of the last search's counters
+  // profiling of the last search: MRQ_NSTAGES + 1 events per batch
+  std::vector<cudaEvent_t> prof_ev;
+  int prof_batches = 0;
+  bool prof_on = false;
+  double prof_ms[MRQ_NSTAGES] = {0};
+  int64_t launches = 0;
+  ~mrq_index() {
+    for (auto e : prof_ev) cudaEventDestroy(e);
+  }
+};
+
+namespace mrq {
+
+// ---- build-side launchers (build.cu) ----
+void build_index(mrq_index* idx, const float* base_dev, const mrq_build_opts& o, cudaStream_t st);
+// code levels (n x d, u8, list-major) + unpadded factors -> padded device layout
+void finalize_layout(mrq_index* idx, const uint8_t* levels_dev, const float* fadd_dev,
+                     const float* fres_dev, const float* ferr_dev, cudaStream_t st);
+void export_levels(const mrq_index* idx, uint8_t* levels_dev, cudaStream_t st);
+void export_padded(const mrq_index* idx, const float* padded_dev, float* out_dev, cudaStream_t st);
+void make_bf16_split(mrq_index* idx, cudaStream_t st);
+void compute_centroid_norms(mrq_index* idx, cudaStream_t st);
+
+// ---- generic float32 tile kernels (gemm_f32.cu) ----
+// C[M x N] = (A - a_shift) * B^T with A (M x K, lda), B (N x K, ldb).
+// Columns [0, split) go to out0 (ld0), [split, N) to out1 (ld1).
+void gemm_nt_f32(const float* A, int lda, const float* a_shift, const float* B, int ldb,
+                 int M, int N, int K, float* out0, int ld0, float* out1, int ld1, int split,
+                 cudaStream_t st);
+// D[M x N] = sum_k (A[m,k] - B[n,k])^2 stored row-major (ldd).
+void sqdist_f32(const float* A, int lda, const float* B, int ldb, int M, int N, int K,
+                float* Dout, int ldd, cudaStream_t st);
+// argmin_n sum_k (A[m,k]-B[n,k])^2 -> out[m] (ties to the lower n).
+void nearest_f32(const float* A, int lda, const float* B, int ldb, int M, int N, int K,
+                 unsigned long long* scratch, int32_t* out, cudaStream_t st);
+
+// ---- tensor-core projection (gemm_tc.cu) ----
+bool tc_available();
+void project_tc(const float* Q, const float* mu, const __nv_bfloat16* W_hi,
+                const __nv_bfloat16* W_lo, int M, int D, int d, bool split3,
+                __nv_bfloat16* qbf_scratch, float* qd, float* qr, cudaStream_t st);
+
+// ---- search (search.cu) ----
+void search_batch(mrq_index* idx, const float* q_dev, int64_t nq, int k, int nprobe,
+                  const mrq_search_opts& o, int64_t* ids_dev, float* dists_dev,
+                  int64_t* stats_dev, cudaStream_t st);
+void project_batch(mrq_index* idx, const float* q_dev, int64_t nq, int precision, float* qd,
+                   float* qr, cudaStream_t st);
+void estimate_one(mrq_index* idx, const float* qp_dev, int list, const mrq_search_opts& o,
+                  float* ip, float* dis, float* lb, float* ub, int32_t* idot, cudaStream_t st);
+
+// orderable 32-bit key of a float (monotone: a < b  <=>  key(a) < key(b))
+__host__ __device__ inline uint32_t fkey(float f) {
+#ifdef __CUDA_ARCH__
+  uint32_t u = __float_as_uint(f);
+#else
+  uint32_t u;
+  memcpy(&u, &f, 4);
+#endif
+  return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+__host__ __device__ inline float fkey_inv(uint32_t k) {
+  uint32_t u = (k & 0x80000000u) ? (k & 0x7fffffffu) : ~k;
+#ifdef __CUDA_ARCH__
+  return __uint_as_float(u);
+#else
+  float f;
+  memcpy(&f, &u, 4);
+  return f;
+#endif
+}
+
+inline int ceil_div(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
+
+}  // namespace mrq

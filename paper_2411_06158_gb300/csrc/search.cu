@@ -1,0 +1,755 @@
+// Query path of MRQ (Algorithm 2) on the GPU.
+//
+// Per batch of queries:
+//  1. projection  [q_d' | q_r] = W (q - mu)          (gemm_f32.cu / gemm_tc.cu)
+//  2. k_qstats    |q_r|^2, sigma (Eq. 6), |q_p|^2
+//  3. probe       g_j = |q_d' - c_j'|^2 (direct float32 sums), then k_probe_select
+//                 keeps the nprobe smallest, ties to the lower list id
+//  4. k_scan      stage 1 for every (query, probed list) pair, one warp per pair
+//                 from a device work queue: q' = (q_d' - c')/sqrt(g) (Alg. 2 normalise
+//                 and rotate step), the code inner product <v, q'> (float32 nibble
+//                 lookup table, or the quantized query with popcounts), Eq. 4
+//                 estimate, Eq. 5 + Chebyshev bounds, a running upper bound of
+//                 the k-th smallest upper bound, and compaction of the candidates
+//                 whose lower bound does not exceed it
+//  5. k_finalize  one CTA per query: tau_A, stage-1 survivors, stage 2 (Eq. 7),
+//                 tau_B, stage-2 survivors, exact distances, top-k by (dist, id)
+#include <algorithm>
+#include <cfloat>
+
+#include "common.cuh"
+
+namespace mrq {
+namespace {
+
+#define FINF __int_as_float(0x7f800000)
+
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+  for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ float warp_min(float v) {
+#pragma unroll
+  for (int o = 16; o; o >>= 1) v = fminf(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+__device__ __forceinline__ float warp_max(float v) {
+#pragma unroll
+  for (int o = 16; o; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+__device__ __forceinline__ int warp_sum_i(int v) {
+#pragma unroll
+  for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// ------------------------------------------------------------- query stats
+
+__global__ void k_qstats(const float* __restrict__ qd, const float* __restrict__ qr,
+                         const float* __restrict__ lam, int64_t nq, int d, int r,
+                         float* __restrict__ qstat) {
+  int64_t q = (int64_t)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
+  if (q >= nq) return;
+  const int lane = threadIdx.x & 31;
+  float qr2 = 0.f, s2 = 0.f, qd2 = 0.f;
+  for (int i = lane; i < r; i += 32) {
+    float v = qr[q * r + i];
+    qr2 = fmaf(v, v, qr2);
+    s2 = fmaf(v * v, lam[d + i], s2);
+  }
+  for (int i = lane; i < d; i += 32) {
+    float v = qd[q * d + i];
+    qd2 = fmaf(v, v, qd2);
+  }
+  qr2 = warp_sum(qr2);
+  s2 = warp_sum(s2);
+  qd2 = warp_sum(qd2);
+  if (lane == 0) {
+    qstat[q * 4 + 0] = qr2;
+    qstat[q * 4 + 1] = sqrtf(fmaxf(s2, 0.f));
+    qstat[q * 4 + 2] = qd2 + qr2;
+    qstat[q * 4 + 3] = 0.f;
+  }
+}
+
+// ---------------------------------------------------- block-level primitives
+
+template <int NT>
+__device__ __forceinline__ int block_sum_i(int v, int* red) {
+  v = warp_sum_i(v);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) red[wid] = v;
+  __syncthreads();
+  int t = 0;
+#pragma unroll
+  for (int w = 0; w < NT / 32; ++w) t += red[w];
+  return t;
+}
+
+// Smallest orderable key T with #{i : key(vals[i]) <= T} >= k (bisection over the
+// 32-bit key space: exact, 32 rounds).  Requires M >= k.
+template <int NT>
+__device__ uint32_t block_kth_key(const float* vals, int M, int k, int* red) {
+  uint32_t lo = 0u, hi = 0xffffffffu;
+  while (lo < hi) {
+    uint32_t mid = lo + ((hi - lo) >> 1);
+    int c = 0;
+    for (int i = threadIdx.x; i < M; i += NT) c += fkey(vals[i]) <= mid;
+    c = block_sum_i<NT>(c, red);
+    if (c >= k) hi = mid; else lo = mid + 1;
+  }
+  return lo;
+}
+
+// In-shared-memory ascending bitonic sort of n (power of two) 64-bit keys.
+template <int NT>
+__device__ void block_bitonic(unsigned long long* a, int n) {
+  for (int size = 2; size <= n; size <<= 1) {
+    for (int stride = size >> 1; stride > 0; stride >>= 1) {
+      __syncthreads();
+      for (int t = threadIdx.x; t < n / 2; t += NT) {
+        int i = 2 * t - (t & (stride - 1));
+        int j = i + stride;
+        bool up = ((i & size) == 0);
+        unsigned long long x = a[i], y = a[j];
+        if ((x > y) == up) { a[i] = y; a[j] = x; }
+      }
+    }
+  }
+  __syncthreads();
+}
+
+// ------------------------------------------------------------- probe select
+
+constexpr int PS_NT = 256;
+
+// The nprobe smallest (g_j, j) of one query, ascending (Algorithm 2, probing).
+__global__ void __launch_bounds__(PS_NT) k_probe_select(const float* __restrict__ gmat, int nlist,
+                                                        int nprobe, int P2,
+                                                        int32_t* __restrict__ plist,
+                                                        float* __restrict__ pg) {
+  extern __shared__ unsigned long long sel[];  // P2 entries
+  __shared__ int red[PS_NT / 32];
+  __shared__ int s_lt, s_eq;
+  const int64_t q = blockIdx.x;
+  const float* g = gmat + q * nlist;
+  const uint32_t T = block_kth_key<PS_NT>(g, nlist, nprobe, red);
+  // number strictly below T
+  int c = 0;
+  for (int i = threadIdx.x; i < nlist; i += PS_NT) c += fkey(g[i]) < T;
+  const int n_lt = block_sum_i<PS_NT>(c, red);
+  if (threadIdx.x == 0) { s_lt = 0; s_eq = 0; }
+  for (int i = threadIdx.x; i < P2; i += PS_NT) sel[i] = ~0ull;
+  __syncthreads();
+  // keys < T: any slot order; keys == T: the lowest list ids first (ordered pass)
+  for (int i = threadIdx.x; i < nlist; i += PS_NT) {
+    uint32_t kk = fkey(g[i]);
+    if (kk < T) {
+      int at = atomicAdd(&s_lt, 1);
+      sel[at] = ((unsigned long long)kk << 32) | (uint32_t)i;
+    }
+  }
+  __syncthreads();
+  const int need = nprobe - n_lt;
+  for (int base = 0; base < nlist; base += PS_NT) {
+    int i = base + threadIdx.x;
+    bool eq = i < nlist && fkey(g[i]) == T;
+    unsigned m = __ballot_sync(0xffffffffu, eq);
+    int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    __shared__ int wcnt[PS_NT / 32];
+    if (lane == 0) wcnt[wid] = __popc(m);
+    __syncthreads();
+    int before = 0;
+    for (int w = 0; w < wid; ++w) before += wcnt[w];
+    int rank = s_eq + before + __popc(m & ((1u << lane) - 1));
+    if (eq && rank < need) sel[n_lt + rank] = ((unsigned long long)T << 32) | (uint32_t)i;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      int t = 0;
+      for (int w = 0; w < PS_NT / 32; ++w) t += wcnt[w];
+      s_eq += t;
+    }
+    __syncthreads();
+    if (s_eq >= need) break;
+  }
+  block_bitonic<PS_NT>(sel, P2);
+  for (int r = threadIdx.x; r < nprobe; r += PS_NT) {
+    unsigned long long v = sel[r];
+    plist[q * nprobe + r] = (int32_t)(v & 0xffffffffu);
+    pg[q * nprobe + r] = fkey_inv((uint32_t)(v >> 32));
+  }
+}
+
+// ------------------------------------------------------------------ scan
+
+struct ScanParams {
+  const float* qd;      // nq x d
+  const float* qstat;   // nq x 4
+  const int32_t* plist; // nq x nprobe
+  const float* pg;      // nq x nprobe
+  const float* cent;    // nlist x d
+  const int64_t* loff;
+  const int64_t* ploff;
+  const uint32_t* codes;
+  const float* fadd;
+  const float* fres;
+  const float* ferr;
+  int d, bits, words, vw, nprobe, k, qbits;
+  float eps0, m;
+  int64_t npairs;
+  int64_t cap;
+  unsigned int* work;
+  unsigned int* qcnt;
+  unsigned int* gtau;
+  int32_t* spos;
+  float* slb;
+  float* sub;
+  // diagnostics (single pair): per-candidate outputs
+  float* dbg_ip;
+  float* dbg_dis;
+  float* dbg_lb;
+  float* dbg_ub;
+  int32_t* dbg_idot;
+};
+
+__device__ __forceinline__ int64_t code_word(int64_t pp, int w, int words, int vw) {
+  int64_t blk = pp >> 5;
+  int lane = (int)(pp & 31);
+  return ((blk * (words / vw) + w / vw) * 32 + lane) * vw + (w % vw);
+}
+
+constexpr int SCAN_WARPS = 8;
+
+// KM: 0 = warp-sorted top-k list (k <= 32); 1 = per-lane top-m (m = ceil(k/32) <= 4);
+//     2 = no running threshold (k > 128).  QUANT: query quantized to qbits.
+// DBG: diagnostics (one pair, outputs per candidate, no survivors).
+template <int KM, bool QUANT, bool DBG>
+__global__ void __launch_bounds__(SCAN_WARPS * 32) k_scan(ScanParams P) {
+  extern __shared__ float smem[];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int d = P.d;
+  const int nch = d >> 5;  // 32-dim chunks
+  float* qp = smem + wid * (5 * d);  // q' (d)
+  float* lut = qp + d;               // 4d: nibble tables (float32 mode)
+  uint32_t* qw = reinterpret_cast<uint32_t*>(lut);  // qbits x nch words (quantized mode)
+  const int topc = (1 << P.bits) - 1;
+  const int topq = (1 << P.qbits) - 1;
+
+  while (true) {
+    unsigned int w = 0;
+    if (lane == 0) w = DBG ? (unsigned)(blockIdx.x * SCAN_WARPS + wid) : atomicAdd(P.work, 1u);
+    w = __shfl_sync(0xffffffffu, w, 0);
+    if ((int64_t)w >= P.npairs) break;
+    const int64_t q = (int64_t)w / P.nprobe;
+    const int j = P.plist[w];
+    const float g = P.pg[w];
+    const float sg = sqrtf(g);
+    const float qr2 = P.qstat[q * 4 + 0];
+    const float sigma = P.qstat[q * 4 + 1];
+    const float a0 = g + qr2;
+    const float em = P.m * sigma;
+    const float e0 = P.eps0 * sg;
+
+    // q' = (q_d' - c_j')/sqrt(g_j)
+    for (int c = 0; c < nch; ++c) {
+      int i = c * 32 + lane;
+      float v = P.qd[q * d + i] - P.cent[(int64_t)j * d + i];
+      qp[i] = g > 0.f ? v / sg : 0.f;
+    }
+    __syncwarp();
+    float ql = 0.f, qdelta = 0.f;
+    int qsum = 0;
+    if (!QUANT) {
+      // lut[(c*8 + s)*16 + nib] = sum_{e<4} (bit e of nib ? +q'_i : -q'_i), i = c*32 + s*4 + e
+      for (int e = lane; e < 4 * d; e += 32) {
+        int gi = e >> 4, nib = e & 15;
+        const float* qq = qp + gi * 4;
+        float v = ((nib & 1) ? qq[0] : -qq[0]) + ((nib & 2) ? qq[1] : -qq[1]);
+        v += ((nib & 4) ? qq[2] : -qq[2]) + ((nib & 8) ? qq[3] : -qq[3]);
+        lut[e] = v;
+      }
+    } else {
+      float lo = FINF, hi = -FINF;
+      for (int c = 0; c < nch; ++c) {
+        float v = qp[c * 32 + lane];
+        lo = fminf(lo, v);
+        hi = fmaxf(hi, v);
+      }
+      lo = warp_min(lo);
+      hi = warp_max(hi);
+      const float delta = (hi - lo) / (float)topq;
+      int s = 0;
+      for (int c = 0; c < nch; ++c) {
+        int qb = 0;
+        if (delta > 0.f) {
+          float t = (qp[c * 32 + lane] - lo) / delta;
+          qb = min((int)floorf(t + 0.5f), topq);
+          qb = max(qb, 0);
+        }
+        s += qb;
+        for (int b = 0; b < P.qbits; ++b) {
+          unsigned word = __ballot_sync(0xffffffffu, (qb >> b) & 1);
+          if (lane == 0) qw[b * nch + c] = word;
+        }
+      }
+      qsum = warp_sum_i(s);
+      ql = lo;
+      qdelta = delta;
+    }
+    __syncwarp();
+
+    const int64_t lb0 = P.loff[j];
+    const int64_t size = P.loff[j + 1] - lb0;
+    const int64_t pb0 = P.ploff[j];
+    float lst = FINF;         // KM 0: lane i holds the i-th smallest upper bound seen
+    float top4[4] = {FINF, FINF, FINF, FINF};  // KM 1: this lane's smallest upper bounds
+    const int mper = (P.k + 31) >> 5;
+    float tau = FINF;
+    float gt = FINF;
+    if (!DBG && KM != 2) gt = fkey_inv(__ldcg(P.gtau + q));
+
+    for (int64_t b0 = 0; b0 < size; b0 += 32) {
+      const int64_t idx = b0 + lane;
+      const bool valid = idx < size;
+      const int64_t pp = pb0 + idx;  // padded position (always allocated)
+      float ip;
+      int idot = 0;
+      if (!QUANT) {
+        float acc = 0.f;
+        for (int a = 0; a < P.bits; ++a) {
+          float pacc = 0.f;
+          for (int c = 0; c < nch; ++c) {
+            uint32_t word = __ldg(P.codes + code_word(pp, a * nch + c, P.words, P.vw));
+            const float* L = lut + c * 128;
+#pragma unroll
+            for (int s = 0; s < 8; ++s) pacc += L[s * 16 + ((word >> (4 * s)) & 15)];
+          }
+          acc = fmaf((float)(1 << a), pacc, acc);
+        }
+        ip = acc;
+      } else {
+        int dot = 0, su = 0;
+        for (int a = 0; a < P.bits; ++a) {
+          int pd = 0, ps = 0;
+          for (int c = 0; c < nch; ++c) {
+            uint32_t word = __ldg(P.codes + code_word(pp, a * nch + c, P.words, P.vw));
+            ps += __popc(word);
+            for (int bq = 0; bq < P.qbits; ++bq) pd += __popc(word & qw[bq * nch + c]) << bq;
+          }
+          dot += pd << a;
+          su += ps << a;
+        }
+        idot = dot;
+        ip = qdelta * (float)(2 * dot - topc * qsum) + ql * (float)(2 * su - d * topc);
+      }
+      const float fa = __ldg(P.fadd + pp), fr = __ldg(P.fres + pp), fe = __ldg(P.ferr + pp);
+      const float dis = fa + a0 + fr * sg * ip;  // Eq. 4
+      const float eps = e0 * fe + em;             // Eq. 5 + Chebyshev
+      float lb = dis - eps, ub = dis + eps;
+      if (DBG) {
+        if (valid) {
+          P.dbg_ip[idx] = ip;
+          P.dbg_dis[idx] = dis;
+          P.dbg_lb[idx] = lb;
+          P.dbg_ub[idx] = ub;
+          if (QUANT && P.dbg_idot) P.dbg_idot[idx] = idot;
+        }
+        continue;
+      }
+      if (!valid) { lb = FINF; ub = FINF; }
+      // running upper bound of the k-th smallest upper bound
+      if (KM == 0) {
+        float kth = __shfl_sync(0xffffffffu, lst, P.k - 1);
+        unsigned mask = __ballot_sync(0xffffffffu, ub < kth);
+        while (mask) {
+          int src = __ffs(mask) - 1;
+          mask &= mask - 1;
+          float v = __shfl_sync(0xffffffffu, ub, src);
+          float cur = __shfl_sync(0xffffffffu, lst, P.k - 1);
+          if (v < cur) {
+            float prev = __shfl_up_sync(0xffffffffu, lst, 1);
+            float nl = (lst <= v) ? lst : ((lane == 0 || prev <= v) ? v : prev);
+            lst = lane < P.k ? nl : FINF;
+          }
+        }
+        tau = fminf(gt, __shfl_sync(0xffffffffu, lst, P.k - 1));
+      } else if (KM == 1) {
+        // keep this lane's mper smallest upper bounds (sorted, fixed registers)
+        float v = ub;
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+          if (t < mper && v < top4[t]) { float x = top4[t]; top4[t] = v; v = x; }
+        }
+        float mine = mper == 1 ? top4[0] : mper == 2 ? top4[1] : mper == 3 ? top4[2] : top4[3];
+        // every lane holds >= mper values <= mine, 32 * mper >= k of them in all
+        tau = fminf(gt, warp_max(mine));
+      }
+      const bool surv = valid && lb <= tau;
+      const unsigned sm = __ballot_sync(0xffffffffu, surv);
+      if (sm) {
+        unsigned base = 0;
+        if (lane == 0) base = atomicAdd(P.qcnt + q, (unsigned)__popc(sm));
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (surv) {
+          int64_t at = q * P.cap + base + __popc(sm & ((1u << lane) - 1));
+          P.spos[at] = (int32_t)(lb0 + idx);
+          P.slb[at] = lb;
+          P.sub[at] = ub;
+        }
+      }
+    }
+    if (!DBG && KM != 2 && lane == 0 && tau < FINF) atomicMin(P.gtau + q, fkey(tau));
+    __syncwarp();
+    if (DBG) break;
+  }
+}
+
+__global__ void k_scan_init(unsigned int* qcnt, unsigned int* gtau, int64_t nq, unsigned int* work) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < nq) {
+    qcnt[i] = 0u;
+    gtau[i] = fkey(FINF);
+  }
+  if (i == 0) *work = 0u;
+}
+
+// ------------------------------------------------------------------ finalize
+
+constexpr int FN_NT = 256;
+constexpr int FN_SORT = 2048;  // capacity of the final (dist, id) sort
+
+struct FinParams {
+  const float* qd;
+  const float* qr;
+  const float* qstat;
+  const int32_t* plist;
+  const int64_t* loff;
+  const float* xd;
+  const float* xr;
+  const float* xn2;
+  const int64_t* ids;
+  int d, r, nprobe, k, mode;
+  float m;
+  int64_t cap;
+  const unsigned int* qcnt;
+  int32_t* spos;
+  float* slb;
+  float* sub;
+  int32_t* s2pos;
+  float* s2a;
+  float* s2b;
+  int64_t* out_ids;
+  float* out_d;
+  int64_t* stats;
+};
+
+__global__ void __launch_bounds__(FN_NT) k_finalize(FinParams P) {
+  extern __shared__ float fsm[];
+  float* sq = fsm;             // d + r query coordinates
+  unsigned long long* srt = reinterpret_cast<unsigned long long*>(fsm + ((P.d + P.r + 1) & ~1));
+  __shared__ int red[FN_NT / 32];
+  __shared__ unsigned int s_cnt;
+  const int64_t q = blockIdx.x;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int D = P.d + P.r;
+  for (int i = threadIdx.x; i < P.d; i += FN_NT) sq[i] = P.qd[q * P.d + i];
+  for (int i = threadIdx.x; i < P.r; i += FN_NT) sq[P.d + i] = P.qr[q * P.r + i];
+  const float sigma = P.qstat[q * 4 + 1];
+  const float qp2 = P.qstat[q * 4 + 2];
+  const int64_t base = q * P.cap;
+  const int M = (int)min((int64_t)P.qcnt[q], P.cap);
+  int64_t ncand = 0;
+  for (int r = threadIdx.x; r < P.nprobe; r += FN_NT) {
+    int j = P.plist[q * P.nprobe + r];
+    ncand += P.loff[j + 1] - P.loff[j];
+  }
+  // (ncand summed below with a block reduction of two 32-bit halves is unnecessary:
+  //  list sizes are < 2^31 and nprobe <= nlist, so an int64 atomic suffices)
+  __shared__ unsigned long long s_ncand;
+  if (threadIdx.x == 0) s_ncand = 0ull;
+  __syncthreads();
+  if (ncand) atomicAdd(&s_ncand, (unsigned long long)ncand);
+
+  // tau_A: k-th smallest stage-1 upper bound
+  const float tauA = (M >= P.k) ? fkey_inv(block_kth_key<FN_NT>(P.sub + base, M, P.k, red)) : FINF;
+  // S1 = {LB1 <= tau_A}
+  if (threadIdx.x == 0) s_cnt = 0u;
+  __syncthreads();
+  for (int i = threadIdx.x; i < M; i += FN_NT) {
+    if (P.slb[base + i] <= tauA) {
+      unsigned at = atomicAdd(&s_cnt, 1u);
+      P.s2pos[base + at] = P.spos[base + i];
+    }
+  }
+  __syncthreads();
+  const int M1 = (int)s_cnt;
+  int M2;
+  if (P.mode == MRQ_MODE_MRQ_PLUS) {
+    // stage 2 (Eq. 7): dis_o' = |x_p|^2 + |q_p|^2 - 2 <x_d', q_d'>, bounds -+ m sigma
+    const float em = P.m * sigma;
+    for (int i = wid; i < M1; i += FN_NT / 32) {
+      const int64_t pos = P.s2pos[base + i];
+      const float* x = P.xd + pos * P.d;
+      float s = 0.f;
+      for (int c = lane; c < P.d; c += 32) s = fmaf(x[c], sq[c], s);
+      s = warp_sum(s);
+      if (lane == 0) {
+        float diso = P.xn2[pos] + qp2 - 2.f * s;
+        P.s2a[base + i] = diso + em;  // UB2
+        P.s2b[base + i] = diso - em;  // LB2
+      }
+    }
+    __syncthreads();
+    float tauB = tauA;
+    if (M1 >= P.k) tauB = fminf(tauA, fkey_inv(block_kth_key<FN_NT>(P.s2a + base, M1, P.k, red)));
+    if (threadIdx.x == 0) s_cnt = 0u;
+    __syncthreads();
+    for (int i = threadIdx.x; i < M1; i += FN_NT) {
+      if (P.s2b[base + i] <= tauB) {
+        unsigned at = atomicAdd(&s_cnt, 1u);
+        P.spos[base + at] = P.s2pos[base + i];
+      }
+    }
+    __syncthreads();
+    M2 = (int)s_cnt;
+  } else {
+    for (int i = threadIdx.x; i < M1; i += FN_NT) P.spos[base + i] = P.s2pos[base + i];
+    M2 = M1;
+  }
+  __syncthreads();
+  // exact distances |x_d' - q_d'|^2 + |x_r - q_r|^2 (direct sums)
+  for (int i = wid; i < M2; i += FN_NT / 32) {
+    const int64_t pos = P.spos[base + i];
+    const float* x = P.xd + pos * P.d;
+    const float* y = P.xr + pos * P.r;
+    float s = 0.f;
+    for (int c = lane; c < P.d; c += 32) { float t = x[c] - sq[c]; s = fmaf(t, t, s); }
+    for (int c = lane; c < P.r; c += 32) { float t = y[c] - sq[P.d + c]; s = fmaf(t, t, s); }
+    s = warp_sum(s);
+    if (lane == 0) P.slb[base + i] = s;
+  }
+  __syncthreads();
+  // top-k by (distance, id)
+  const int kk = min(P.k, M2);
+  uint32_t T = 0xffffffffu;
+  if (M2 > P.k) T = block_kth_key<FN_NT>(P.slb + base, M2, P.k, red);
+  if (threadIdx.x == 0) s_cnt = 0u;
+  for (int i = threadIdx.x; i < FN_SORT; i += FN_NT) srt[i] = ~0ull;
+  __syncthreads();
+  for (int i = threadIdx.x; i < M2; i += FN_NT) {
+    uint32_t key = fkey(P.slb[base + i]);
+    if (key <= T) {
+      unsigned at = atomicAdd(&s_cnt, 1u);
+      if (at < FN_SORT) srt[at] = ((unsigned long long)key << 32) | (uint32_t)P.ids[P.spos[base + i]];
+    }
+  }
+  __syncthreads();
+  int ns = min((int)s_cnt, FN_SORT);
+  int n2 = 1;
+  while (n2 < ns) n2 <<= 1;
+  block_bitonic<FN_NT>(srt, n2);
+  for (int i = threadIdx.x; i < P.k; i += FN_NT) {
+    if (i < kk && i < ns) {
+      P.out_ids[q * P.k + i] = (int64_t)(uint32_t)(srt[i] & 0xffffffffu);
+      P.out_d[q * P.k + i] = fkey_inv((uint32_t)(srt[i] >> 32));
+    } else {
+      P.out_ids[q * P.k + i] = -1;
+      P.out_d[q * P.k + i] = FINF;
+    }
+  }
+  if (threadIdx.x == 0 && P.stats) {
+    P.stats[q * 3 + 0] = (int64_t)s_ncand;
+    P.stats[q * 3 + 1] = M1;
+    P.stats[q * 3 + 2] = M2;
+  }
+}
+
+int g_num_sms = 0;
+int num_sms() {
+  if (!g_num_sms) {
+    int dev = 0;
+    MRQ_CUDA(cudaGetDevice(&dev));
+    MRQ_CUDA(cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev));
+  }
+  return g_num_sms;
+}
+
+template <int KM, bool QUANT, bool DBG>
+void launch_scan_t(const ScanParams& p, int64_t grid_warps, size_t smem, cudaStream_t st) {
+  auto kern = k_scan<KM, QUANT, DBG>;
+  MRQ_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  int blocks;
+  if (DBG) {
+    blocks = 1;
+  } else {
+    int per_sm = 0;
+    MRQ_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, SCAN_WARPS * 32, smem));
+    per_sm = std::max(per_sm, 1);
+    int64_t want = (grid_warps + SCAN_WARPS - 1) / SCAN_WARPS;
+    blocks = (int)std::min<int64_t>(want, (int64_t)num_sms() * per_sm);
+    blocks = std::max(blocks, 1);
+  }
+  kern<<<blocks, SCAN_WARPS * 32, smem, st>>>(p);
+  MRQ_CHECK_LAUNCH();
+}
+
+void launch_scan(const ScanParams& p, int64_t npairs, cudaStream_t st, bool dbg) {
+  const bool quant = p.qbits > 0;
+  const int km = p.k <= 32 ? 0 : (p.k <= 128 ? 1 : 2);
+  size_t smem = (size_t)SCAN_WARPS * 5 * p.d * sizeof(float);
+  if (dbg) {
+    if (quant) launch_scan_t<2, true, true>(p, 1, smem, st);
+    else launch_scan_t<2, false, true>(p, 1, smem, st);
+    return;
+  }
+#define MRQ_SCAN_CASE(K)                                           \
+  if (km == K) {                                                   \
+    if (quant) launch_scan_t<K, true, false>(p, npairs, smem, st); \
+    else launch_scan_t<K, false, false>(p, npairs, smem, st);      \
+    return;                                                        \
+  }
+  MRQ_SCAN_CASE(0)
+  MRQ_SCAN_CASE(1)
+  MRQ_SCAN_CASE(2)
+#undef MRQ_SCAN_CASE
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------- host side
+
+// CUDA event at a stage boundary of the current batch (profiled searches only)
+static void mark(mrq_index* idx, int s, cudaStream_t st) {
+  if (!idx->prof_on) return;
+  size_t i = (size_t)idx->prof_batches * (MRQ_NSTAGES + 1) + s;
+  while (idx->prof_ev.size() <= i) {
+    cudaEvent_t e;
+    MRQ_CUDA(cudaEventCreate(&e));
+    idx->prof_ev.push_back(e);
+  }
+  MRQ_CUDA(cudaEventRecord(idx->prof_ev[i], st));
+}
+
+void project_batch(mrq_index* idx, const float* q, int64_t nq, int precision, float* qd, float* qr,
+                   cudaStream_t st) {
+  const int D = idx->D, d = idx->d, r = D - d;
+  if (precision == MRQ_PREC_FP32) {
+    gemm_nt_f32(q, D, idx->mu.p, idx->W.p, D, (int)nq, D, D, qd, d, qr, r, d, st);
+  } else {
+    MRQ_REQUIRE(tc_available(), "tensor-core projection is not available on this device");
+    idx->ws.qbf.reserve((size_t)nq * D * 2);
+    project_tc(q, idx->mu.p, idx->W_hi.p, idx->W_lo.p, (int)nq, D, d,
+               precision == MRQ_PREC_BF16X3, idx->ws.qbf.p, qd, qr, st);
+  }
+}
+
+static void qstats(mrq_index* idx, const float* qd, const float* qr, int64_t nq, float* qstat,
+                   cudaStream_t st) {
+  k_qstats<<<ceil_div(nq, 8), 256, 0, st>>>(qd, qr, idx->lam.p, nq, idx->d, idx->D - idx->d, qstat);
+  MRQ_CHECK_LAUNCH();
+}
+
+void search_batch(mrq_index* idx, const float* q, int64_t nq, int k, int nprobe,
+                  const mrq_search_opts& o, int64_t* out_ids, float* out_d, int64_t* stats,
+                  cudaStream_t st) {
+  auto& ws = idx->ws;
+  const int D = idx->D, d = idx->d, r = D - d, nlist = idx->nlist;
+  const int64_t cap = std::max<int64_t>(idx->cap_by_nprobe[nprobe], 1);
+  ws.qd.reserve((size_t)nq * d);
+  ws.qr.reserve((size_t)nq * std::max(r, 1));
+  ws.qstat.reserve((size_t)nq * 4);
+  ws.gmat.reserve((size_t)nq * nlist);
+  ws.plist.reserve((size_t)nq * nprobe);
+  ws.pg.reserve((size_t)nq * nprobe);
+  ws.qcnt.reserve(nq);
+  ws.gtau.reserve(nq);
+  ws.work.reserve(4);
+  const size_t sc = (size_t)nq * cap;
+  ws.spos.reserve(sc);
+  ws.slb.reserve(sc);
+  ws.sub.reserve(sc);
+  ws.s2pos.reserve(sc);
+  ws.s2a.reserve(sc);
+  ws.s2b.reserve(sc);
+
+  // 1-2. projection and query statistics
+  mark(idx, MRQ_STAGE_PROJECT, st);
+  project_batch(idx, q, nq, o.precision, ws.qd.p, ws.qr.p, st);
+  idx->launches += o.precision == MRQ_PREC_FP32 ? 1 : 2;
+  mark(idx, MRQ_STAGE_QSTATS, st);
+  qstats(idx, ws.qd.p, ws.qr.p, nq, ws.qstat.p, st);
+  // 3. probe
+  mark(idx, MRQ_STAGE_PROBE, st);
+  sqdist_f32(ws.qd.p, d, idx->cent.p, d, (int)nq, nlist, d, ws.gmat.p, nlist, st);
+  mark(idx, MRQ_STAGE_SELECT, st);
+  int P2 = 1;
+  while (P2 < nprobe) P2 <<= 1;
+  {
+    size_t sm = (size_t)P2 * 8;
+    MRQ_CUDA(cudaFuncSetAttribute(k_probe_select, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    k_probe_select<<<(unsigned)nq, PS_NT, sm, st>>>(ws.gmat.p, nlist, nprobe, P2, ws.plist.p, ws.pg.p);
+    MRQ_CHECK_LAUNCH();
+  }
+  // 4. scan
+  mark(idx, MRQ_STAGE_SCAN, st);
+  k_scan_init<<<ceil_div(nq, 256), 256, 0, st>>>(ws.qcnt.p, ws.gtau.p, nq, ws.work.p);
+  MRQ_CHECK_LAUNCH();
+  ScanParams sp{};
+  sp.qd = ws.qd.p; sp.qstat = ws.qstat.p; sp.plist = ws.plist.p; sp.pg = ws.pg.p;
+  sp.cent = idx->cent.p; sp.loff = idx->loff.p; sp.ploff = idx->ploff.p; sp.codes = idx->codes.p;
+  sp.fadd = idx->fadd.p; sp.fres = idx->fres.p; sp.ferr = idx->ferr.p;
+  sp.d = d; sp.bits = idx->bits; sp.words = idx->words; sp.vw = idx->vw;
+  sp.nprobe = nprobe; sp.k = k; sp.qbits = o.query_bits;
+  sp.eps0 = o.eps0; sp.m = o.m;
+  sp.npairs = nq * nprobe; sp.cap = cap;
+  sp.work = ws.work.p; sp.qcnt = ws.qcnt.p; sp.gtau = ws.gtau.p;
+  sp.spos = ws.spos.p; sp.slb = ws.slb.p; sp.sub = ws.sub.p;
+  launch_scan(sp, nq * nprobe, st, false);
+  // 5. finalize
+  mark(idx, MRQ_STAGE_FINAL, st);
+  FinParams fp{};
+  fp.qd = ws.qd.p; fp.qr = ws.qr.p; fp.qstat = ws.qstat.p; fp.plist = ws.plist.p;
+  fp.loff = idx->loff.p; fp.xd = idx->xd.p; fp.xr = idx->xr.p; fp.xn2 = idx->xn2.p;
+  fp.ids = idx->ids.p; fp.d = d; fp.r = r; fp.nprobe = nprobe; fp.k = k; fp.mode = o.mode;
+  fp.m = o.m; fp.cap = cap; fp.qcnt = ws.qcnt.p; fp.spos = ws.spos.p; fp.slb = ws.slb.p;
+  fp.sub = ws.sub.p; fp.s2pos = ws.s2pos.p; fp.s2a = ws.s2a.p; fp.s2b = ws.s2b.p;
+  fp.out_ids = out_ids; fp.out_d = out_d; fp.stats = stats;
+  size_t fsm = (size_t)(((D + 1) & ~1) * sizeof(float)) + FN_SORT * 8;
+  MRQ_CUDA(cudaFuncSetAttribute(k_finalize, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsm));
+  k_finalize<<<(unsigned)nq, FN_NT, fsm, st>>>(fp);
+  MRQ_CHECK_LAUNCH();
+  mark(idx, MRQ_NSTAGES, st);
+  if (idx->prof_on) idx->prof_batches++;
+  idx->launches += 6;  // qstats, probe distances, select, scan init, scan, finalize
+}
+
+void estimate_one(mrq_index* idx, const float* qp, int list, const mrq_search_opts& o, float* ip,
+                  float* dis, float* lb, float* ub, int32_t* idot, cudaStream_t st) {
+  auto& ws = idx->ws;
+  const int D = idx->D, d = idx->d, r = D - d;
+  ws.qd.reserve(d);
+  ws.qr.reserve(std::max(r, 1));
+  ws.qstat.reserve(4);
+  ws.plist.reserve(1);
+  ws.pg.reserve(1);
+  MRQ_CUDA(cudaMemcpyAsync(ws.qd.p, qp, 4 * d, cudaMemcpyDefault, st));
+  if (r > 0) MRQ_CUDA(cudaMemcpyAsync(ws.qr.p, qp + d, 4 * r, cudaMemcpyDefault, st));
+  qstats(idx, ws.qd.p, ws.qr.p, 1, ws.qstat.p, st);
+  sqdist_f32(ws.qd.p, d, idx->cent.p + (int64_t)list * d, d, 1, 1, d, ws.pg.p, 1, st);
+  MRQ_CUDA(cudaMemcpyAsync(ws.plist.p, &list, 4, cudaMemcpyHostToDevice, st));
+  ScanParams sp{};
+  sp.qd = ws.qd.p; sp.qstat = ws.qstat.p; sp.plist = ws.plist.p; sp.pg = ws.pg.p;
+  sp.cent = idx->cent.p; sp.loff = idx->loff.p; sp.ploff = idx->ploff.p; sp.codes = idx->codes.p;
+  sp.fadd = idx->fadd.p; sp.fres = idx->fres.p; sp.ferr = idx->ferr.p;
+  sp.d = d; sp.bits = idx->bits; sp.words = idx->words; sp.vw = idx->vw;
+  sp.nprobe = 1; sp.k = 1; sp.qbits = o.query_bits; sp.eps0 = o.eps0; sp.m = o.m;
+  sp.npairs = 1;
+  sp.dbg_ip = ip; sp.dbg_dis = dis; sp.dbg_lb = lb; sp.dbg_ub = ub; sp.dbg_idot = idot;
+  launch_scan(sp, 1, st, true);
+  MRQ_CUDA(cudaStreamSynchronize(st));
+}
+
+}  // namespace mrq

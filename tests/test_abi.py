@@ -1,0 +1,90 @@
+"""The C ABI library loads, exports every entry point that include/mrq.h
+declares, and rejects bad arguments and malformed files before touching a GPU."""
+import ctypes as C
+import os
+import re
+import struct
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "mrq.h")
+
+
+def _declared():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(mrq_[a-z0-9_]+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    import paper_2411_06158_gb300 as m
+    return m
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = _declared()
+    assert "mrq_build" in names and "mrq_search" in names
+    for n in names:
+        assert hasattr(lib._lib, n), f"{n} declared in mrq.h but not exported"
+    assert set(names) == set(lib.EXPORTS)
+
+
+def test_defaults(lib):
+    o = lib.SearchOpts()
+    lib._lib.mrq_search_opts_default(C.byref(o))
+    assert o.eps0 == pytest.approx(1.9) and o.m == pytest.approx(4.0)
+    assert o.mode == lib.MODE_MRQ_PLUS and o.precision == lib.PREC_FP32
+    b = lib.BuildOpts()
+    lib._lib.mrq_build_opts_default(C.byref(b))
+    assert b.kmeans_iters == 20 and b.seed == 1
+
+
+@pytest.mark.parametrize("D,d,bits,nlist,msg", [
+    (128, 48, 1, 8, "d must be"),        # d not a multiple of 32
+    (128, 256, 1, 8, "d must be"),       # d > D
+    (128, 32, 0, 8, "bits"),
+    (128, 32, 9, 8, "bits"),
+    (128, 32, 1, 0, "nlist"),
+    (128, 32, 1, 5000, "nlist"),         # nlist > n
+    (16, 32, 1, 8, "D must be"),
+])
+def test_build_rejects_bad_arguments(lib, D, d, bits, nlist, msg):
+    base = np.zeros((1000, max(D, 1)), dtype=np.float32)
+    h = C.c_void_p()
+    rc = lib._lib.mrq_build(base.ctypes.data, 1000, D, d, bits, nlist, None, C.byref(h))
+    assert rc == lib.MRQ_EINVAL
+    assert msg in lib.mrq_last_error()
+    assert h.value is None
+
+
+def test_null_arguments(lib):
+    h = C.c_void_p()
+    assert lib._lib.mrq_build(None, 10, 64, 32, 1, 2, None, C.byref(h)) == lib.MRQ_EINVAL
+    assert lib._lib.mrq_search(None, None, 1, 1, 1, None, None, None) == lib.MRQ_EINVAL
+    lib._lib.mrq_free(None)  # no-op
+
+
+def test_load_rejects_malformed_files(lib, tmp_path):
+    h = C.c_void_p()
+    assert lib._lib.mrq_load(str(tmp_path / "missing").encode(), C.byref(h)) == lib.MRQ_EIO
+    p = tmp_path / "bad"
+    p.write_bytes(b"NOTANINDEXFILE" + b"\0" * 64)
+    assert lib._lib.mrq_load(str(p).encode(), C.byref(h)) == lib.MRQ_EFORMAT
+    p.write_bytes(b"MRQINDEX" + struct.pack("<II", 2, 0))
+    assert lib._lib.mrq_load(str(p).encode(), C.byref(h)) == lib.MRQ_EFORMAT
+    assert "version" in lib.mrq_last_error()
+    p.write_bytes(b"MRQINDEX" + struct.pack("<II", 1, 0) + struct.pack("<qiiii", 10, 64, 48, 1, 2))
+    assert lib._lib.mrq_load(str(p).encode(), C.byref(h)) == lib.MRQ_EFORMAT
+    p.write_bytes(b"MRQINDEX" + struct.pack("<II", 1, 0))
+    assert lib._lib.mrq_load(str(p).encode(), C.byref(h)) == lib.MRQ_EFORMAT
+    assert "truncated" in lib.mrq_last_error()
+
+
+def test_build_script_targets_sm103a():
+    import sys
+    sys.path.insert(0, os.path.join(ROOT, "paper_2411_06158_gb300"))
+    import build_lib
+    assert build_lib.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]
