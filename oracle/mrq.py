@@ -320,6 +320,20 @@ def estimate_list(idx: OracleIndex, j: int, qd, g_j, qr2, sigma, eps0, m,
     return out
 
 
+def _decision_margin(lb, ub, sc, tau, k, rel) -> float:
+    """Smallest relative distance of a relevant decision lb_i <= tau from flipping.
+    A candidate among the k smallest upper bounds (ub_i <= tau) is kept for sure
+    while it stays among them (lb_i <= ub_i <= tau), so its margin is the larger
+    of |lb_i - tau| and the gap between the k-th and (k+1)-th upper bounds; this
+    covers zero-width bounds (d = D, where lb = ub)."""
+    srt = np.sort(ub)
+    gap_k = (srt[k] - srt[k - 1]) / max(abs(srt[k]), 1e-30) if srt.size > k else math.inf
+    m = np.abs(lb - tau) / sc
+    top = ub <= tau
+    m = np.where(top, np.maximum(m, gap_k), m)
+    return float(np.min(m[rel]))
+
+
 def _kth(values: np.ndarray, k: int) -> float:
     return float(np.partition(values, k - 1)[k - 1]) if values.size >= k else math.inf
 
@@ -421,10 +435,10 @@ def search_contract(idx: OracleIndex, Q, k: int, nprobe: int, *, eps0: float = 1
         near = in_ans | (ex_all <= dk * (1 + 1e-6))
         rel1 = near | ((mode == MODE_MRQ_PLUS) & (ub2 <= kth_ub2 * (1 + 1e-6)))
         if pos.size and math.isfinite(tau_a) and rel1.any():
-            mg = min(mg, float(np.min(np.abs(lb[rel1] - tau_a) / sc[rel1])))
+            mg = min(mg, _decision_margin(lb, ub, sc, tau_a, k, rel1))
         rel2 = near & s1
         if mode == MODE_MRQ_PLUS and math.isfinite(tau_b) and rel2.any():
-            mg = min(mg, float(np.min(np.abs(lb2[rel2] - tau_b) / sc2[rel2])))
+            mg = min(mg, _decision_margin(lb2[s1], ub2[s1], sc2[s1], tau_b, k, rel2[s1]))
         margin[qi] = mg
     return SearchResult(ids, dists, n_cand, n_s1, n_s2, margin)
 
