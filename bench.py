@@ -269,6 +269,8 @@ def main(argv=None):
     forms = {
         "plain_fp32": mrq.mrq_search_opts(query_bits=0, stream=stream),
         "plain_q4": mrq.mrq_search_opts(query_bits=4, stream=stream),
+        "bf16x3_q4": mrq.mrq_search_opts(query_bits=4, precision=mrq.PREC_BF16X3, stream=stream),
+        "bf16_q4": mrq.mrq_search_opts(query_bits=4, precision=mrq.PREC_BF16, stream=stream),
     }
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 

@@ -190,6 +190,8 @@ int mrq_search(mrq_index* idx, const float* queries, int64_t nq, int k, int npro
     idx->last_stats.resize((size_t)nq * 3);
     MRQ_CUDA(cudaMemcpyAsync(idx->last_stats.data(), ws.stats.p, 8 * nq * 3, cudaMemcpyDeviceToHost, st));
     MRQ_CUDA(cudaStreamSynchronize(st));
+    if (o.precision != MRQ_PREC_FP32 && mrq::tc_check_error())
+      mrq::fail(MRQ_ETIMEDOUT, "a tensor-core kernel gave up waiting on its pipeline");
     idx->last_nq = nq;
     for (int s = 0; s < MRQ_NSTAGES; ++s) idx->prof_ms[s] = 0.0;
     if (idx->prof_on) {
@@ -237,6 +239,8 @@ int mrq_project(mrq_index* idx, const float* queries, int64_t nq, const mrq_sear
     if (r > 0)
       MRQ_CUDA(cudaMemcpy2DAsync(qp + d, 4 * D, ws.qr.p, 4 * r, 4 * r, nq, cudaMemcpyDefault, st));
     MRQ_CUDA(cudaStreamSynchronize(st));
+    if (o.precision != MRQ_PREC_FP32 && mrq::tc_check_error())
+      mrq::fail(MRQ_ETIMEDOUT, "a tensor-core kernel gave up waiting on its pipeline");
   });
 }
 
@@ -295,7 +299,7 @@ int mrq_index_info(const mrq_index* idx, mrq_index_info_t* info) {
     info->nlist = idx->nlist;
     info->max_list = idx->max_list;
     info->device_bytes = (int64_t)(idx->mu.bytes() + idx->lam.bytes() + idx->W.bytes() +
-                                   idx->W_hi.bytes() + idx->W_lo.bytes() + idx->cent.bytes() +
+                                   idx->W2.bytes() + idx->cent2.bytes() + idx->cent.bytes() +
                                    idx->cent_n2.bytes() + idx->loff.bytes() + idx->ploff.bytes() +
                                    idx->ids.bytes() + idx->codes.bytes() + idx->fadd.bytes() +
                                    idx->fres.bytes() + idx->ferr.bytes() + idx->xd.bytes() +

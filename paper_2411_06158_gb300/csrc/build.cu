@@ -129,16 +129,13 @@ __global__ void __launch_bounds__(256) k_cov(const float* __restrict__ X, int64_
 }
 
 // Copy cov (D x D, upper tiles filled) into the padded m x m Jacobi matrix,
-// mirroring the strictly-lower tiles from the upper ones and scaling by 1/n.
+// mirroring the upper triangle into the lower one and scaling by 1/n.
 __global__ void k_cov_to_jacobi(const double* __restrict__ C, int D, int m, double inv_n,
                                 double* __restrict__ A, double* __restrict__ V) {
   int j = blockIdx.x * blockDim.x + threadIdx.x, i = blockIdx.y;
   if (j >= m) return;
   double v = 0.0;
-  if (i < D && j < D) {
-    bool upper_tile = (i / CT) <= (j / CT);
-    v = (upper_tile ? C[(int64_t)i * D + j] : C[(int64_t)j * D + i]) * inv_n;
-  }
+  if (i < D && j < D) v = C[(int64_t)min(i, j) * D + max(i, j)] * inv_n;  // exactly symmetric
   A[(int64_t)i * m + j] = v;
   V[(int64_t)i * m + j] = (i == j) ? 1.0 : 0.0;
 }
@@ -496,14 +493,14 @@ __global__ void k_unpad(const float* __restrict__ padded, const int64_t* __restr
   out[p] = padded[ploff[j] + (p - loff[j])];
 }
 
-__global__ void k_bf16_split(const float* __restrict__ W, int64_t n, __nv_bfloat16* __restrict__ hi,
-                             __nv_bfloat16* __restrict__ lo) {
+// hi = bf16(x), lo = bf16(x - hi): rows [0, n) and [n, 2n) of out
+__global__ void k_bf16_split(const float* __restrict__ X, int64_t n, __nv_bfloat16* __restrict__ out) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  float w = W[i];
+  float w = X[i];
   __nv_bfloat16 h = __float2bfloat16_rn(w);
-  hi[i] = h;
-  lo[i] = __float2bfloat16_rn(w - __bfloat162float(h));
+  out[i] = h;
+  out[n + i] = __float2bfloat16_rn(w - __bfloat162float(h));
 }
 
 __global__ void k_cent_norm(const float* __restrict__ C, int nlist, int d, float* __restrict__ out) {
@@ -579,9 +576,12 @@ void export_padded(const mrq_index* idx, const float* padded, float* out, cudaSt
 
 void make_bf16_split(mrq_index* idx, cudaStream_t st) {
   int64_t nn = (int64_t)idx->D * idx->D;
-  idx->W_hi.alloc(nn);
-  idx->W_lo.alloc(nn);
-  k_bf16_split<<<ceil_div(nn, 256), 256, 0, st>>>(idx->W.p, nn, idx->W_hi.p, idx->W_lo.p);
+  idx->W2.alloc(2 * nn);
+  k_bf16_split<<<ceil_div(nn, 256), 256, 0, st>>>(idx->W.p, nn, idx->W2.p);
+  MRQ_CHECK_LAUNCH();
+  int64_t nc = (int64_t)idx->nlist * idx->d;
+  idx->cent2.alloc(2 * nc);
+  k_bf16_split<<<ceil_div(nc, 256), 256, 0, st>>>(idx->cent.p, nc, idx->cent2.p);
   MRQ_CHECK_LAUNCH();
 }
 

@@ -107,7 +107,8 @@ struct mrq_index {
   std::vector<int64_t> cap_by_nprobe;  // sum of the nprobe largest list sizes
 
   mrq::DevBuf<float> mu, lam, W;  // D, D, D x D
-  mrq::DevBuf<__nv_bfloat16> W_hi, W_lo;  // bf16 split of W
+  mrq::DevBuf<__nv_bfloat16> W2;          // bf16 split of W: rows [0,D) hi, [D,2D) lo
+  mrq::DevBuf<__nv_bfloat16> cent2;       // bf16 split of the centroids: [0,nlist) hi, then lo
   mrq::DevBuf<float> cent, cent_n2;       // nlist x d (rotated frame), nlist
   mrq::DevBuf<int64_t> loff, ploff;       // nlist + 1
   mrq::DevBuf<int64_t> ids;               // n, list-major
@@ -153,11 +154,14 @@ void sqdist_f32(const float* A, int lda, const float* B, int ldb, int M, int N, 
 void nearest_f32(const float* A, int lda, const float* B, int ldb, int M, int N, int K,
                  unsigned long long* scratch, int32_t* out, cudaStream_t st);
 
-// ---- tensor-core projection (gemm_tc.cu) ----
+// ---- tensor-core GEMMs (gemm_tc.cu) ----
 bool tc_available();
-void project_tc(const float* Q, const float* mu, const __nv_bfloat16* W_hi,
-                const __nv_bfloat16* W_lo, int M, int D, int d, bool split3,
-                __nv_bfloat16* qbf_scratch, float* qd, float* qr, cudaStream_t st);
+int tc_check_error();  // nonzero if a bounded wait in a tensor-core kernel gave up
+void project_tc(const float* Q, const float* mu, const __nv_bfloat16* W2, int M, int D, int d,
+                bool split3, __nv_bfloat16* qbf, float* qd, float* qr, cudaStream_t st);
+void probe_tc(const float* qd, const float* qstat, const __nv_bfloat16* C2, const float* cn2,
+              int M, int nlist, int d, bool split3, __nv_bfloat16* qbf, float* gmat,
+              cudaStream_t st);
 
 // ---- search (search.cu) ----
 void search_batch(mrq_index* idx, const float* q_dev, int64_t nq, int k, int nprobe,

@@ -70,7 +70,7 @@ __global__ void k_qstats(const float* __restrict__ qd, const float* __restrict__
     qstat[q * 4 + 0] = qr2;
     qstat[q * 4 + 1] = sqrtf(fmaxf(s2, 0.f));
     qstat[q * 4 + 2] = qd2 + qr2;
-    qstat[q * 4 + 3] = 0.f;
+    qstat[q * 4 + 3] = qd2;
   }
 }
 
@@ -181,6 +181,25 @@ __global__ void __launch_bounds__(PS_NT) k_probe_select(const float* __restrict_
     plist[q * nprobe + r] = (int32_t)(v & 0xffffffffu);
     pg[q * nprobe + r] = fkey_inv((uint32_t)(v >> 32));
   }
+}
+
+// g_j = |q_d' - c_j'|^2 of every probed list, as a direct float32 sum (one warp per
+// pair); the scan's estimates use this value whatever precision chose the lists.
+__global__ void k_probe_refine(const float* __restrict__ qd, const float* __restrict__ cent,
+                               const int32_t* __restrict__ plist, int64_t npairs, int nprobe, int d,
+                               float* __restrict__ pg) {
+  int64_t w = (int64_t)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
+  if (w >= npairs) return;
+  const int lane = threadIdx.x & 31;
+  const int64_t q = w / nprobe;
+  const int j = plist[w];
+  float s = 0.f;
+  for (int i = lane; i < d; i += 32) {
+    float t = qd[q * d + i] - cent[(int64_t)j * d + i];
+    s = fmaf(t, t, s);
+  }
+  s = warp_sum(s);
+  if (lane == 0) pg[w] = s;
 }
 
 // ------------------------------------------------------------------ scan
@@ -639,10 +658,10 @@ void project_batch(mrq_index* idx, const float* q, int64_t nq, int precision, fl
   if (precision == MRQ_PREC_FP32) {
     gemm_nt_f32(q, D, idx->mu.p, idx->W.p, D, (int)nq, D, D, qd, d, qr, r, d, st);
   } else {
-    MRQ_REQUIRE(tc_available(), "tensor-core projection is not available on this device");
+    MRQ_REQUIRE(tc_available(), "tensor-core projection needs an sm_103 device");
     idx->ws.qbf.reserve((size_t)nq * D * 2);
-    project_tc(q, idx->mu.p, idx->W_hi.p, idx->W_lo.p, (int)nq, D, d,
-               precision == MRQ_PREC_BF16X3, idx->ws.qbf.p, qd, qr, st);
+    project_tc(q, idx->mu.p, idx->W2.p, (int)nq, D, d, precision == MRQ_PREC_BF16X3,
+               idx->ws.qbf.p, qd, qr, st);
   }
 }
 
@@ -683,7 +702,14 @@ void search_batch(mrq_index* idx, const float* q, int64_t nq, int k, int nprobe,
   qstats(idx, ws.qd.p, ws.qr.p, nq, ws.qstat.p, st);
   // 3. probe
   mark(idx, MRQ_STAGE_PROBE, st);
-  sqdist_f32(ws.qd.p, d, idx->cent.p, d, (int)nq, nlist, d, ws.gmat.p, nlist, st);
+  if (o.precision != MRQ_PREC_FP32 && d >= 64) {
+    ws.qbf.reserve((size_t)nq * D * 2);
+    probe_tc(ws.qd.p, ws.qstat.p, idx->cent2.p, idx->cent_n2.p, (int)nq, nlist, d,
+             o.precision == MRQ_PREC_BF16X3, ws.qbf.p, ws.gmat.p, st);
+    idx->launches += 1;
+  } else {
+    sqdist_f32(ws.qd.p, d, idx->cent.p, d, (int)nq, nlist, d, ws.gmat.p, nlist, st);
+  }
   mark(idx, MRQ_STAGE_SELECT, st);
   int P2 = 1;
   while (P2 < nprobe) P2 <<= 1;
@@ -691,6 +717,9 @@ void search_batch(mrq_index* idx, const float* q, int64_t nq, int k, int nprobe,
     size_t sm = (size_t)P2 * 8;
     MRQ_CUDA(cudaFuncSetAttribute(k_probe_select, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     k_probe_select<<<(unsigned)nq, PS_NT, sm, st>>>(ws.gmat.p, nlist, nprobe, P2, ws.plist.p, ws.pg.p);
+    MRQ_CHECK_LAUNCH();
+    k_probe_refine<<<ceil_div(nq * nprobe, 8), 256, 0, st>>>(ws.qd.p, idx->cent.p, ws.plist.p,
+                                                            nq * nprobe, nprobe, d, ws.pg.p);
     MRQ_CHECK_LAUNCH();
   }
   // 4. scan
@@ -723,7 +752,7 @@ void search_batch(mrq_index* idx, const float* q, int64_t nq, int k, int nprobe,
   MRQ_CHECK_LAUNCH();
   mark(idx, MRQ_NSTAGES, st);
   if (idx->prof_on) idx->prof_batches++;
-  idx->launches += 6;  // qstats, probe distances, select, scan init, scan, finalize
+  idx->launches += 7;  // qstats, probe distances, select, refine, scan init, scan, finalize
 }
 
 void estimate_one(mrq_index* idx, const float* qp, int list, const mrq_search_opts& o, float* ip,
@@ -738,8 +767,9 @@ void estimate_one(mrq_index* idx, const float* qp, int list, const mrq_search_op
   MRQ_CUDA(cudaMemcpyAsync(ws.qd.p, qp, 4 * d, cudaMemcpyDefault, st));
   if (r > 0) MRQ_CUDA(cudaMemcpyAsync(ws.qr.p, qp + d, 4 * r, cudaMemcpyDefault, st));
   qstats(idx, ws.qd.p, ws.qr.p, 1, ws.qstat.p, st);
-  sqdist_f32(ws.qd.p, d, idx->cent.p + (int64_t)list * d, d, 1, 1, d, ws.pg.p, 1, st);
   MRQ_CUDA(cudaMemcpyAsync(ws.plist.p, &list, 4, cudaMemcpyHostToDevice, st));
+  k_probe_refine<<<1, 256, 0, st>>>(ws.qd.p, idx->cent.p, ws.plist.p, 1, 1, d, ws.pg.p);
+  MRQ_CHECK_LAUNCH();
   ScanParams sp{};
   sp.qd = ws.qd.p; sp.qstat = ws.qstat.p; sp.plist = ws.plist.p; sp.pg = ws.pg.p;
   sp.cent = idx->cent.p; sp.loff = idx->loff.p; sp.ploff = idx->ploff.p; sp.codes = idx->codes.p;

@@ -1,0 +1,61 @@
+"""Tensor-core (tcgen05) paths against the CPU oracle: the bf16 and split hi+lo
+bf16 query projection and probe, with ragged query counts and K / N tails.
+Expected error (per output, relative to |q - mu|): bf16 rounds each operand to
+8 significant bits (~2^-9); hi+lo keeps ~16 bits (~2^-17) before float32
+accumulation."""
+import numpy as np
+import pytest
+
+import datagen
+from oracle import mrq as omrq
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+import paper_2411_06158_gb300 as mrq  # noqa: E402
+from oracle import index_file  # noqa: E402
+
+
+def _oracle_index(tmp_path, D, d, n, nlist):
+    w = datagen.workload("small", D=D, d=d, n=n, nlist=nlist, n_comp=32, n_query=333)
+    base, queries = datagen.base_and_queries(w)
+    G = datagen.rotation_gaussian(d, 3)
+    init = datagen.kmeans_init_indices(n, nlist, 4)
+    oi = omrq.build_index(base, d, 1, nlist, G, init_idx=init, kmeans_iters=3)
+    p = str(tmp_path / f"i{D}.mrq")
+    index_file.write_index(oi, p)
+    return w, base, queries, oi.as_stored(), mrq.mrq_load(p)
+
+
+@pytest.mark.parametrize("D,d", [(96, 64), (128, 64), (960, 128)])
+def test_projection_precisions(tmp_path, D, d):
+    w, base, queries, st, gi = _oracle_index(tmp_path, D, d, 4000, 16)
+    qd, qr, *_ = omrq.project_queries(st, queries)
+    ref = np.concatenate([qd, qr], axis=1)
+    scale = np.linalg.norm(queries - st.mu, axis=1)[:, None]
+    errs = {}
+    for prec in (mrq.PREC_FP32, mrq.PREC_BF16X3, mrq.PREC_BF16):
+        got = mrq.mrq_project(gi, queries, mrq.mrq_search_opts(precision=prec))
+        errs[prec] = float(np.max(np.abs(got - ref) / scale))
+    assert errs[mrq.PREC_FP32] < 2e-6
+    assert errs[mrq.PREC_BF16X3] < 5e-5
+    assert errs[mrq.PREC_BF16] < 2e-2
+    assert errs[mrq.PREC_BF16] > 10 * errs[mrq.PREC_BF16X3]   # the lo half is used
+
+
+def test_search_precisions_agree(tmp_path):
+    w, base, queries, st, gi = _oracle_index(tmp_path, 128, 64, 12000, 48)
+    truth, _ = omrq.exact_knn(base, queries, 10)
+    res = {}
+    for prec in (mrq.PREC_FP32, mrq.PREC_BF16X3, mrq.PREC_BF16):
+        ids, dists = mrq.mrq_search(gi, queries, 10, 6, mrq.mrq_search_opts(precision=prec))
+        res[prec] = (ids, dists)
+    i32, d32 = res[mrq.PREC_FP32]
+    i3, d3 = res[mrq.PREC_BF16X3]
+    assert np.mean(i3 == i32) > 0.99
+    np.testing.assert_allclose(d3[i3 == i32], d32[i3 == i32], rtol=1e-4, atol=1e-5)
+    r32 = omrq.recall_at_k(i32, truth)
+    assert omrq.recall_at_k(i3, truth) >= r32 - 0.005
+    assert omrq.recall_at_k(res[mrq.PREC_BF16][0], truth) >= r32 - 0.05
