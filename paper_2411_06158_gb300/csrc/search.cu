@@ -104,6 +104,58 @@ __device__ uint32_t block_kth_key(const float* vals, int M, int k, int* red) {
   return lo;
 }
 
+// Smallest orderable key T with #{i : key_i <= T} >= k, by a 4-pass radix select
+// (8 bits per pass, most significant first).  key_i = fkey(vals[i]) (vals may be
+// in shared or global memory).  Histogram updates are aggregated per warp with
+// __match_any_sync, so equal high bytes do not serialise.  Requires M >= k.
+template <int NT>
+__device__ uint32_t block_radix_kth(const float* vals, int M, int k, int* hist, int* sh) {
+  const int lane = threadIdx.x & 31;
+  uint32_t prefix = 0u, mask = 0u;
+  int kk = k;
+  for (int shift = 24; shift >= 0; shift -= 8) {
+    for (int i = threadIdx.x; i < 256; i += NT) hist[i] = 0;
+    __syncthreads();
+    for (int base = 0; base < M; base += NT) {
+      const int i = base + threadIdx.x;
+      const uint32_t key = i < M ? fkey(vals[i]) : 0u;
+      const bool in = i < M && (key & mask) == prefix;
+      const unsigned act = __ballot_sync(0xffffffffu, in);
+      if (in) {
+        const uint32_t bin = (key >> shift) & 255u;
+        const unsigned peers = __match_any_sync(act, bin);
+        if (lane == __ffs(peers) - 1) atomicAdd(&hist[bin], __popc(peers));
+      }
+    }
+    __syncthreads();
+    if (threadIdx.x < 32) {
+      int c[8], tot = 0;
+#pragma unroll
+      for (int j = 0; j < 8; ++j) { c[j] = hist[lane * 8 + j]; tot += c[j]; }
+      int incl = tot;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        int t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += t;
+      }
+      int acc = incl - tot;
+      if (acc < kk && kk <= incl) {
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          if (acc + c[j] >= kk) { sh[0] = lane * 8 + j; sh[1] = acc; break; }
+          acc += c[j];
+        }
+      }
+    }
+    __syncthreads();
+    prefix |= (uint32_t)sh[0] << shift;
+    mask |= 255u << shift;
+    kk -= sh[1];
+    __syncthreads();
+  }
+  return prefix;
+}
+
 // In-shared-memory ascending bitonic sort of n (power of two) 64-bit keys.
 template <int NT>
 __device__ void block_bitonic(unsigned long long* a, int n) {
@@ -136,7 +188,8 @@ __global__ void __launch_bounds__(PS_NT) k_probe_select(const float* __restrict_
   __shared__ int s_lt, s_eq;
   const int64_t q = blockIdx.x;
   const float* g = gmat + q * nlist;
-  const uint32_t T = block_kth_key<PS_NT>(g, nlist, nprobe, red);
+  __shared__ int hist[256], shv[2];
+  const uint32_t T = block_radix_kth<PS_NT>(g, nlist, nprobe, hist, shv);
   // number strictly below T
   int c = 0;
   for (int i = threadIdx.x; i < nlist; i += PS_NT) c += fkey(g[i]) < T;
@@ -465,36 +518,75 @@ struct FinParams {
   int64_t* stats;
 };
 
+// <row, sq> over n floats with float4 loads (row and sq 16-byte aligned, n % 4 == 0)
+// or scalar loads; per-lane partial sums (the caller reduces across the warp).
+template <bool DOT>
+__device__ __forceinline__ void row_accum2(const float* __restrict__ r0, const float* __restrict__ r1,
+                                           const float* sq, int n, bool vec, int lane, float& s0,
+                                           float& s1) {
+  if (vec) {
+    const float4* a = reinterpret_cast<const float4*>(r0);
+    const float4* b = reinterpret_cast<const float4*>(r1);
+    const float4* qv = reinterpret_cast<const float4*>(sq);
+    const int n4 = n >> 2;
+#pragma unroll 4
+    for (int c = lane; c < n4; c += 32) {
+      const float4 x = __ldg(a + c), y = __ldg(b + c), qq = qv[c];
+      if (DOT) {
+        s0 = fmaf(x.x, qq.x, s0); s0 = fmaf(x.y, qq.y, s0); s0 = fmaf(x.z, qq.z, s0); s0 = fmaf(x.w, qq.w, s0);
+        s1 = fmaf(y.x, qq.x, s1); s1 = fmaf(y.y, qq.y, s1); s1 = fmaf(y.z, qq.z, s1); s1 = fmaf(y.w, qq.w, s1);
+      } else {
+        float t;
+        t = x.x - qq.x; s0 = fmaf(t, t, s0); t = x.y - qq.y; s0 = fmaf(t, t, s0);
+        t = x.z - qq.z; s0 = fmaf(t, t, s0); t = x.w - qq.w; s0 = fmaf(t, t, s0);
+        t = y.x - qq.x; s1 = fmaf(t, t, s1); t = y.y - qq.y; s1 = fmaf(t, t, s1);
+        t = y.z - qq.z; s1 = fmaf(t, t, s1); t = y.w - qq.w; s1 = fmaf(t, t, s1);
+      }
+    }
+  } else {
+#pragma unroll 4
+    for (int c = lane; c < n; c += 32) {
+      const float x = __ldg(r0 + c), y = __ldg(r1 + c), qq = sq[c];
+      if (DOT) { s0 = fmaf(x, qq, s0); s1 = fmaf(y, qq, s1); }
+      else { float t = x - qq; s0 = fmaf(t, t, s0); t = y - qq; s1 = fmaf(t, t, s1); }
+    }
+  }
+}
+
 __global__ void __launch_bounds__(FN_NT) k_finalize(FinParams P) {
-  extern __shared__ float fsm[];
-  float* sq = fsm;             // d + r query coordinates
-  unsigned long long* srt = reinterpret_cast<unsigned long long*>(fsm + ((P.d + P.r + 1) & ~1));
-  __shared__ int red[FN_NT / 32];
+  extern __shared__ __align__(16) float fsm[];
+  float* sq = fsm;  // query coordinates [q_d' | q_r], 16-byte aligned blocks
+  const int dpad = (P.d + 3) & ~3;
+  unsigned long long* srt =
+      reinterpret_cast<unsigned long long*>(fsm + ((dpad + P.r + 3) & ~3));
+  __shared__ int hist[256], shv[2];
   __shared__ unsigned int s_cnt;
+  __shared__ unsigned long long s_ncand;
   const int64_t q = blockIdx.x;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  const int D = P.d + P.r;
+  constexpr int NW = FN_NT / 32;
   for (int i = threadIdx.x; i < P.d; i += FN_NT) sq[i] = P.qd[q * P.d + i];
-  for (int i = threadIdx.x; i < P.r; i += FN_NT) sq[P.d + i] = P.qr[q * P.r + i];
+  for (int i = threadIdx.x; i < P.r; i += FN_NT) sq[dpad + i] = P.qr[q * P.r + i];
+  const bool vd = (P.d & 3) == 0;
+  const bool vr = (P.r & 3) == 0;
   const float sigma = P.qstat[q * 4 + 1];
   const float qp2 = P.qstat[q * 4 + 2];
   const int64_t base = q * P.cap;
   const int M = (int)min((int64_t)P.qcnt[q], P.cap);
-  int64_t ncand = 0;
-  for (int r = threadIdx.x; r < P.nprobe; r += FN_NT) {
-    int j = P.plist[q * P.nprobe + r];
-    ncand += P.loff[j + 1] - P.loff[j];
-  }
-  // (ncand summed below with a block reduction of two 32-bit halves is unnecessary:
-  //  list sizes are < 2^31 and nprobe <= nlist, so an int64 atomic suffices)
-  __shared__ unsigned long long s_ncand;
   if (threadIdx.x == 0) s_ncand = 0ull;
   __syncthreads();
-  if (ncand) atomicAdd(&s_ncand, (unsigned long long)ncand);
+  {
+    int64_t nc = 0;
+    for (int r = threadIdx.x; r < P.nprobe; r += FN_NT) {
+      int j = P.plist[q * P.nprobe + r];
+      nc += P.loff[j + 1] - P.loff[j];
+    }
+    if (nc) atomicAdd(&s_ncand, (unsigned long long)nc);
+  }
 
-  // tau_A: k-th smallest stage-1 upper bound
-  const float tauA = (M >= P.k) ? fkey_inv(block_kth_key<FN_NT>(P.sub + base, M, P.k, red)) : FINF;
-  // S1 = {LB1 <= tau_A}
+  // tau_A: k-th smallest stage-1 upper bound; S1 = {LB1 <= tau_A}
+  const float tauA =
+      (M >= P.k) ? fkey_inv(block_radix_kth<FN_NT>(P.sub + base, M, P.k, hist, shv)) : FINF;
   if (threadIdx.x == 0) s_cnt = 0u;
   __syncthreads();
   for (int i = threadIdx.x; i < M; i += FN_NT) {
@@ -509,21 +601,28 @@ __global__ void __launch_bounds__(FN_NT) k_finalize(FinParams P) {
   if (P.mode == MRQ_MODE_MRQ_PLUS) {
     // stage 2 (Eq. 7): dis_o' = |x_p|^2 + |q_p|^2 - 2 <x_d', q_d'>, bounds -+ m sigma
     const float em = P.m * sigma;
-    for (int i = wid; i < M1; i += FN_NT / 32) {
-      const int64_t pos = P.s2pos[base + i];
-      const float* x = P.xd + pos * P.d;
-      float s = 0.f;
-      for (int c = lane; c < P.d; c += 32) s = fmaf(x[c], sq[c], s);
-      s = warp_sum(s);
+    for (int i = 2 * wid; i < M1; i += 2 * NW) {
+      const bool two = i + 1 < M1;
+      const int64_t p0 = P.s2pos[base + i], p1 = two ? P.s2pos[base + i + 1] : p0;
+      float s0 = 0.f, s1 = 0.f;
+      row_accum2<true>(P.xd + p0 * P.d, P.xd + p1 * P.d, sq, P.d, vd, lane, s0, s1);
+      s0 = warp_sum(s0);
+      s1 = warp_sum(s1);
       if (lane == 0) {
-        float diso = P.xn2[pos] + qp2 - 2.f * s;
-        P.s2a[base + i] = diso + em;  // UB2
-        P.s2b[base + i] = diso - em;  // LB2
+        float diso = P.xn2[p0] + qp2 - 2.f * s0;
+        P.s2a[base + i] = diso + em;
+        P.s2b[base + i] = diso - em;
+        if (two) {
+          diso = P.xn2[p1] + qp2 - 2.f * s1;
+          P.s2a[base + i + 1] = diso + em;
+          P.s2b[base + i + 1] = diso - em;
+        }
       }
     }
     __syncthreads();
     float tauB = tauA;
-    if (M1 >= P.k) tauB = fminf(tauA, fkey_inv(block_kth_key<FN_NT>(P.s2a + base, M1, P.k, red)));
+    if (M1 >= P.k)
+      tauB = fminf(tauA, fkey_inv(block_radix_kth<FN_NT>(P.s2a + base, M1, P.k, hist, shv)));
     if (threadIdx.x == 0) s_cnt = 0u;
     __syncthreads();
     for (int i = threadIdx.x; i < M1; i += FN_NT) {
@@ -539,22 +638,25 @@ __global__ void __launch_bounds__(FN_NT) k_finalize(FinParams P) {
     M2 = M1;
   }
   __syncthreads();
-  // exact distances |x_d' - q_d'|^2 + |x_r - q_r|^2 (direct sums)
-  for (int i = wid; i < M2; i += FN_NT / 32) {
-    const int64_t pos = P.spos[base + i];
-    const float* x = P.xd + pos * P.d;
-    const float* y = P.xr + pos * P.r;
-    float s = 0.f;
-    for (int c = lane; c < P.d; c += 32) { float t = x[c] - sq[c]; s = fmaf(t, t, s); }
-    for (int c = lane; c < P.r; c += 32) { float t = y[c] - sq[P.d + c]; s = fmaf(t, t, s); }
-    s = warp_sum(s);
-    if (lane == 0) P.slb[base + i] = s;
+  // exact distances |x_d' - q_d'|^2 + |x_r - q_r|^2 (direct sums, two candidates per warp)
+  for (int i = 2 * wid; i < M2; i += 2 * NW) {
+    const bool two = i + 1 < M2;
+    const int64_t p0 = P.spos[base + i], p1 = two ? P.spos[base + i + 1] : p0;
+    float s0 = 0.f, s1 = 0.f;
+    row_accum2<false>(P.xd + p0 * P.d, P.xd + p1 * P.d, sq, P.d, vd, lane, s0, s1);
+    row_accum2<false>(P.xr + p0 * P.r, P.xr + p1 * P.r, sq + dpad, P.r, vr, lane, s0, s1);
+    s0 = warp_sum(s0);
+    s1 = warp_sum(s1);
+    if (lane == 0) {
+      P.slb[base + i] = s0;
+      if (two) P.slb[base + i + 1] = s1;
+    }
   }
   __syncthreads();
   // top-k by (distance, id)
   const int kk = min(P.k, M2);
   uint32_t T = 0xffffffffu;
-  if (M2 > P.k) T = block_kth_key<FN_NT>(P.slb + base, M2, P.k, red);
+  if (M2 > P.k) T = block_radix_kth<FN_NT>(P.slb + base, M2, P.k, hist, shv);
   if (threadIdx.x == 0) s_cnt = 0u;
   for (int i = threadIdx.x; i < FN_SORT; i += FN_NT) srt[i] = ~0ull;
   __syncthreads();
@@ -746,7 +848,7 @@ void search_batch(mrq_index* idx, const float* q, int64_t nq, int k, int nprobe,
   fp.m = o.m; fp.cap = cap; fp.qcnt = ws.qcnt.p; fp.spos = ws.spos.p; fp.slb = ws.slb.p;
   fp.sub = ws.sub.p; fp.s2pos = ws.s2pos.p; fp.s2a = ws.s2a.p; fp.s2b = ws.s2b.p;
   fp.out_ids = out_ids; fp.out_d = out_d; fp.stats = stats;
-  size_t fsm = (size_t)(((D + 1) & ~1) * sizeof(float)) + FN_SORT * 8;
+  size_t fsm = (size_t)((((d + 3) & ~3) + r + 3) & ~3) * sizeof(float) + FN_SORT * 8;
   MRQ_CUDA(cudaFuncSetAttribute(k_finalize, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsm));
   k_finalize<<<(unsigned)nq, FN_NT, fsm, st>>>(fp);
   MRQ_CHECK_LAUNCH();
