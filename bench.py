@@ -44,6 +44,9 @@ def parse_args(argv=None):
     p.add_argument("--recall", type=float, default=0.95)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-queries", type=int, default=100)
+    p.add_argument("--form", default=None, help="time only this form (profiling runs)")
+    p.add_argument("--nprobe", type=int, default=None, help="fixed nprobe: skip calibration")
+    p.add_argument("--m", type=float, default=None, help="fixed m with --nprobe")
     return p.parse_args(argv)
 
 
@@ -334,9 +337,17 @@ def main(argv=None):
             torch.distributed.barrier()
         return per, stage, launches, ids
 
+    if args.form:
+        forms = {args.form: forms[args.form]}
     results = {}
     for name, opts in list(forms.items()):
-        m_best, npb, r = calibrate(opts)
+        if args.nprobe:
+            m_best, npb = (args.m if args.m is not None else opts.m), args.nprobe
+            ids, _ = mrq.mrq_search(idx, q_t, w.k, npb, with_m(opts, m_best))
+            torch.cuda.synchronize()
+            r = recall(ids.cpu().numpy(), truth)
+        else:
+            m_best, npb, r = calibrate(opts)
         if npb is None:
             results[name] = {"nprobe": None, "recall": r}
             continue
