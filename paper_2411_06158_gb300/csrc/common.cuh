@@ -88,9 +88,13 @@ struct Workspace {
   DevBuf<float> odist;
   DevBuf<int64_t> stats;   // nq x 3
   DevBuf<uint32_t> work;   // work-queue counters
+  DevBuf<float> qtau;      // nq: tau_A per query (phased finalize)
+  DevBuf<int> qm1, qm2;    // nq: stage-1 / stage-2 survivor counts
+  DevBuf<int> ccnt, coff, nitems;  // long-list chunking: per-pair chunk counts, offsets
+  DevBuf<int64_t> items;   // (pair << 32 | chunk) scan work items
+  DevBuf<uint8_t> cubtmp;  // CUB scan scratch
   // list-major batched scan
   DevBuf<int32_t> lcount, loffq, lqueue;  // per-list query buckets
-  DevBuf<int32_t> items;   // work items
 };
 
 }  // namespace mrq

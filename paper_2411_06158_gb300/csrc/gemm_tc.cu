@@ -235,8 +235,16 @@ __global__ void __launch_bounds__(128, 1)
         if (whole) {
           float* dst = col0 < P.split ? P.out0 + (int64_t)row * P.ld0 + col0
                                       : P.out1 + (int64_t)row * P.ld1 + (col0 - P.split);
+          if ((reinterpret_cast<uintptr_t>(dst) & 15) == 0) {
+            float4* d4 = reinterpret_cast<float4*>(dst);
 #pragma unroll
-          for (int j = 0; j < 32; ++j) dst[j] = __uint_as_float(r[j]);
+            for (int j = 0; j < 8; ++j)
+              d4[j] = make_float4(__uint_as_float(r[4 * j]), __uint_as_float(r[4 * j + 1]),
+                                  __uint_as_float(r[4 * j + 2]), __uint_as_float(r[4 * j + 3]));
+          } else {
+#pragma unroll
+            for (int j = 0; j < 32; ++j) dst[j] = __uint_as_float(r[j]);
+          }
         } else {
 #pragma unroll
           for (int j = 0; j < 32; ++j) {
@@ -249,10 +257,23 @@ __global__ void __launch_bounds__(128, 1)
       } else {
         const float rn = P.rown[(int64_t)row * P.rstride];
         float* dst = P.out0 + (int64_t)row * P.ld0;
+        if (col0 + 32 <= P.N && (reinterpret_cast<uintptr_t>(dst + col0) & 15) == 0) {
+          float4* d4 = reinterpret_cast<float4*>(dst + col0);
+          const float4* c4 = reinterpret_cast<const float4*>(P.coln + col0);
 #pragma unroll
-        for (int j = 0; j < 32; ++j) {
-          int col = col0 + j;
-          if (col < P.N) dst[col] = rn + P.coln[col] - 2.f * __uint_as_float(r[j]);
+          for (int j = 0; j < 8; ++j) {
+            const float4 c = c4[j];
+            d4[j] = make_float4(rn + c.x - 2.f * __uint_as_float(r[4 * j]),
+                                rn + c.y - 2.f * __uint_as_float(r[4 * j + 1]),
+                                rn + c.z - 2.f * __uint_as_float(r[4 * j + 2]),
+                                rn + c.w - 2.f * __uint_as_float(r[4 * j + 3]));
+          }
+        } else {
+#pragma unroll
+          for (int j = 0; j < 32; ++j) {
+            int col = col0 + j;
+            if (col < P.N) dst[col] = rn + P.coln[col] - 2.f * __uint_as_float(r[j]);
+          }
         }
       }
     }

@@ -14,6 +14,8 @@
 //                 whose lower bound does not exceed it
 //  5. k_finalize  one CTA per query: tau_A, stage-1 survivors, stage 2 (Eq. 7),
 //                 tau_B, stage-2 survivors, exact distances, top-k by (dist, id)
+#include <cub/cub.cuh>
+
 #include <algorithm>
 #include <cfloat>
 
@@ -179,58 +181,78 @@ __device__ void block_bitonic(unsigned long long* a, int n) {
 constexpr int PS_NT = 256;
 
 // The nprobe smallest (g_j, j) of one query, ascending (Algorithm 2, probing).
+// Shared memory: sel[cap] (64-bit (key, list) pairs) followed by the staged row
+// when it fits.  Every key <= T (the nprobe-th smallest) is gathered and sorted by
+// (key, list id), so ties go to the lower list id; if ties overflow sel, an
+// ordered pass keeps the lowest ids among the ties instead.
 __global__ void __launch_bounds__(PS_NT) k_probe_select(const float* __restrict__ gmat, int nlist,
-                                                        int nprobe, int P2,
+                                                        int nprobe, int cap, int row_in_smem,
                                                         int32_t* __restrict__ plist,
                                                         float* __restrict__ pg) {
-  extern __shared__ unsigned long long sel[];  // P2 entries
-  __shared__ int red[PS_NT / 32];
-  __shared__ int s_lt, s_eq;
+  extern __shared__ unsigned long long sel[];
+  __shared__ int hist[256], shv[2];
+  __shared__ unsigned int s_cnt;
+  __shared__ int s_eq;
   const int64_t q = blockIdx.x;
   const float* g = gmat + q * nlist;
-  __shared__ int hist[256], shv[2];
+  if (row_in_smem) {
+    float* gs = reinterpret_cast<float*>(sel + cap);
+    for (int i = threadIdx.x; i < nlist; i += PS_NT) gs[i] = g[i];
+    __syncthreads();
+    g = gs;
+  }
   const uint32_t T = block_radix_kth<PS_NT>(g, nlist, nprobe, hist, shv);
-  // number strictly below T
-  int c = 0;
-  for (int i = threadIdx.x; i < nlist; i += PS_NT) c += fkey(g[i]) < T;
-  const int n_lt = block_sum_i<PS_NT>(c, red);
-  if (threadIdx.x == 0) { s_lt = 0; s_eq = 0; }
-  for (int i = threadIdx.x; i < P2; i += PS_NT) sel[i] = ~0ull;
+  if (threadIdx.x == 0) s_cnt = 0u;
   __syncthreads();
-  // keys < T: any slot order; keys == T: the lowest list ids first (ordered pass)
   for (int i = threadIdx.x; i < nlist; i += PS_NT) {
-    uint32_t kk = fkey(g[i]);
-    if (kk < T) {
-      int at = atomicAdd(&s_lt, 1);
-      sel[at] = ((unsigned long long)kk << 32) | (uint32_t)i;
+    const uint32_t kk = fkey(g[i]);
+    if (kk <= T) {
+      const unsigned at = atomicAdd(&s_cnt, 1u);
+      if (at < (unsigned)cap) sel[at] = ((unsigned long long)kk << 32) | (uint32_t)i;
     }
   }
   __syncthreads();
-  const int need = nprobe - n_lt;
-  for (int base = 0; base < nlist; base += PS_NT) {
-    int i = base + threadIdx.x;
-    bool eq = i < nlist && fkey(g[i]) == T;
-    unsigned m = __ballot_sync(0xffffffffu, eq);
-    int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    __shared__ int wcnt[PS_NT / 32];
-    if (lane == 0) wcnt[wid] = __popc(m);
+  int n = (int)s_cnt;
+  if (n > cap) {
+    // overflow by ties: keys < T (fewer than nprobe), then ties in list-id order
+    if (threadIdx.x == 0) { s_cnt = 0u; s_eq = 0; }
     __syncthreads();
-    int before = 0;
-    for (int w = 0; w < wid; ++w) before += wcnt[w];
-    int rank = s_eq + before + __popc(m & ((1u << lane) - 1));
-    if (eq && rank < need) sel[n_lt + rank] = ((unsigned long long)T << 32) | (uint32_t)i;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      int t = 0;
-      for (int w = 0; w < PS_NT / 32; ++w) t += wcnt[w];
-      s_eq += t;
+    for (int i = threadIdx.x; i < nlist; i += PS_NT) {
+      const uint32_t kk = fkey(g[i]);
+      if (kk < T) sel[atomicAdd(&s_cnt, 1u)] = ((unsigned long long)kk << 32) | (uint32_t)i;
     }
     __syncthreads();
-    if (s_eq >= need) break;
+    const int n_lt = (int)s_cnt;
+    const int need = nprobe - n_lt;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    __shared__ int wcnt[PS_NT / 32];
+    for (int b0 = 0; b0 < nlist; b0 += PS_NT) {
+      const int i = b0 + threadIdx.x;
+      const bool eq = i < nlist && fkey(g[i]) == T;
+      const unsigned m = __ballot_sync(0xffffffffu, eq);
+      if (lane == 0) wcnt[wid] = __popc(m);
+      __syncthreads();
+      int before = 0;
+      for (int w = 0; w < wid; ++w) before += wcnt[w];
+      const int rank = s_eq + before + __popc(m & ((1u << lane) - 1));
+      if (eq && rank < need) sel[n_lt + rank] = ((unsigned long long)T << 32) | (uint32_t)i;
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        int t = 0;
+        for (int w = 0; w < PS_NT / 32; ++w) t += wcnt[w];
+        s_eq += t;
+      }
+      __syncthreads();
+      if (s_eq >= need) break;
+    }
+    n = nprobe;
   }
-  block_bitonic<PS_NT>(sel, P2);
+  int n2 = 1;
+  while (n2 < n) n2 <<= 1;
+  for (int i = n + threadIdx.x; i < n2; i += PS_NT) sel[i] = ~0ull;
+  block_bitonic<PS_NT>(sel, n2);
   for (int r = threadIdx.x; r < nprobe; r += PS_NT) {
-    unsigned long long v = sel[r];
+    const unsigned long long v = sel[r];
     plist[q * nprobe + r] = (int32_t)(v & 0xffffffffu);
     pg[q * nprobe + r] = fkey_inv((uint32_t)(v >> 32));
   }
@@ -273,6 +295,9 @@ struct ScanParams {
   float eps0, m;
   int64_t npairs;
   int64_t cap;
+  const int64_t* items;   // (pair << 32 | chunk) work items, or NULL: one item per pair
+  const int* nitems;      // device count of items
+  int chunk;              // candidates per chunk when items != NULL
   unsigned int* work;
   unsigned int* qcnt;
   unsigned int* gtau;
@@ -294,6 +319,7 @@ __device__ __forceinline__ int64_t code_word(int64_t pp, int w, int words, int v
 }
 
 constexpr int SCAN_WARPS = 8;
+constexpr int SCAN_CHUNK = 4096;  // candidates per scan work item for long lists
 
 // KM: 0 = warp-sorted top-k list (k <= 32); 1 = per-lane top-m (m = ceil(k/32) <= 4);
 //     2 = no running threshold (k > 128).  QUANT: query quantized to qbits.
@@ -310,11 +336,19 @@ __global__ void __launch_bounds__(SCAN_WARPS * 32) k_scan(ScanParams P) {
   const int topc = (1 << P.bits) - 1;
   const int topq = (1 << P.qbits) - 1;
 
+  const int64_t n_items = P.items ? (int64_t)*P.nitems : P.npairs;
   while (true) {
-    unsigned int w = 0;
-    if (lane == 0) w = DBG ? (unsigned)(blockIdx.x * SCAN_WARPS + wid) : atomicAdd(P.work, 1u);
-    w = __shfl_sync(0xffffffffu, w, 0);
-    if ((int64_t)w >= P.npairs) break;
+    unsigned int it = 0;
+    if (lane == 0) it = DBG ? (unsigned)(blockIdx.x * SCAN_WARPS + wid) : atomicAdd(P.work, 1u);
+    it = __shfl_sync(0xffffffffu, it, 0);
+    if ((int64_t)it >= n_items) break;
+    int64_t w = it, c_lo = 0, c_hi = -1;  // pair index, candidate range of this item
+    if (P.items) {
+      const int64_t v = P.items[it];
+      w = v >> 32;
+      c_lo = (v & 0xffffffffll) * P.chunk;
+      c_hi = c_lo + P.chunk;
+    }
     const int64_t q = (int64_t)w / P.nprobe;
     const int j = P.plist[w];
     const float g = P.pg[w];
@@ -374,7 +408,8 @@ __global__ void __launch_bounds__(SCAN_WARPS * 32) k_scan(ScanParams P) {
     __syncwarp();
 
     const int64_t lb0 = P.loff[j];
-    const int64_t size = P.loff[j + 1] - lb0;
+    const int64_t lsize = P.loff[j + 1] - lb0;
+    const int64_t size = c_hi < 0 ? lsize : min(lsize, c_hi);
     const int64_t pb0 = P.ploff[j];
     float lst = FINF;         // KM 0: lane i holds the i-th smallest upper bound seen
     float top4[4] = {FINF, FINF, FINF, FINF};  // KM 1: this lane's smallest upper bounds
@@ -383,7 +418,7 @@ __global__ void __launch_bounds__(SCAN_WARPS * 32) k_scan(ScanParams P) {
     float gt = FINF;
     if (!DBG && KM != 2) gt = fkey_inv(__ldcg(P.gtau + q));
 
-    for (int64_t b0 = 0; b0 < size; b0 += 32) {
+    for (int64_t b0 = c_lo; b0 < size; b0 += 32) {
       const int64_t idx = b0 + lane;
       const bool valid = idx < size;
       const int64_t pp = pb0 + idx;  // padded position (always allocated)
@@ -479,6 +514,25 @@ __global__ void __launch_bounds__(SCAN_WARPS * 32) k_scan(ScanParams P) {
   }
 }
 
+// work items for long lists: pair w contributes max(1, ceil(size/chunk)) items
+__global__ void k_chunk_count(const int32_t* __restrict__ plist, const int64_t* __restrict__ loff,
+                              int64_t npairs, int chunk, int* __restrict__ cnt) {
+  int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (w >= npairs) return;
+  const int j = plist[w];
+  const int64_t sz = loff[j + 1] - loff[j];
+  const int64_t c = (sz + chunk - 1) / chunk;
+  cnt[w] = c > 0 ? (int)c : 1;
+}
+__global__ void k_chunk_scatter(const int* __restrict__ cnt, const int* __restrict__ off,
+                                int64_t npairs, int64_t* __restrict__ items, int* __restrict__ nitems) {
+  int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (w >= npairs) return;
+  const int o = off[w], c = cnt[w];
+  for (int i = 0; i < c; ++i) items[o + i] = (w << 32) | (int64_t)i;
+  if (w == npairs - 1) *nitems = o + c;
+}
+
 __global__ void k_scan_init(unsigned int* qcnt, unsigned int* gtau, int64_t nq, unsigned int* work) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < nq) {
@@ -516,6 +570,11 @@ struct FinParams {
   int64_t* out_ids;
   float* out_d;
   int64_t* stats;
+  // phased finalize: per-query threshold and survivor counts
+  float* qtau;
+  int* qm1;
+  int* qm2;
+  int64_t nq;
 };
 
 // <row, sq> over n floats with float4 loads (row and sq 16-byte aligned, n % 4 == 0)
@@ -688,6 +747,274 @@ __global__ void __launch_bounds__(FN_NT) k_finalize(FinParams P) {
   }
 }
 
+// ---------------------------------------------------- warp-per-query finalize
+
+// Warp-local radix select: smallest key T with #{i : fkey(vals[i]) <= T} >= k.
+// hist: 256 ints of this warp's shared memory.  Requires M >= k.
+__device__ uint32_t warp_radix_kth(const float* vals, int M, int k, int* hist) {
+  const int lane = threadIdx.x & 31;
+  uint32_t prefix = 0u, mask = 0u;
+  int kk = k;
+  for (int shift = 24; shift >= 0; shift -= 8) {
+#pragma unroll
+    for (int i = 0; i < 8; ++i) hist[lane * 8 + i] = 0;
+    __syncwarp();
+    for (int b = 0; b < M; b += 32) {
+      const int i = b + lane;
+      const uint32_t key = i < M ? fkey(vals[i]) : 0u;
+      const bool in = i < M && (key & mask) == prefix;
+      const unsigned act = __ballot_sync(0xffffffffu, in);
+      if (in) {
+        const uint32_t bin = (key >> shift) & 255u;
+        const unsigned peers = __match_any_sync(act, bin);
+        if (lane == __ffs(peers) - 1) atomicAdd(&hist[bin], __popc(peers));
+      }
+    }
+    __syncwarp();
+    int c[8], tot = 0;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) { c[j] = hist[lane * 8 + j]; tot += c[j]; }
+    int incl = tot;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      int t = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += t;
+    }
+    int acc = incl - tot;
+    const unsigned who = __ballot_sync(0xffffffffu, acc < kk && kk <= incl);
+    int bin = 0, before = 0;
+    if (lane == __ffs(who) - 1) {
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        if (acc + c[j] >= kk) { bin = lane * 8 + j; before = acc; break; }
+        acc += c[j];
+      }
+    }
+    const int src = __ffs(who) - 1;
+    bin = __shfl_sync(0xffffffffu, bin, src);
+    before = __shfl_sync(0xffffffffu, before, src);
+    prefix |= (uint32_t)bin << shift;
+    mask |= 255u << shift;
+    kk -= before;
+    __syncwarp();
+  }
+  return prefix;
+}
+
+// ordered warp compaction: out[n..] = src[i] for every i < M with keep(i); returns new n
+template <class Keep>
+__device__ __forceinline__ int warp_compact(const int32_t* src, int M, int32_t* out, Keep keep) {
+  const int lane = threadIdx.x & 31;
+  int n = 0;
+  for (int b = 0; b < M; b += 32) {
+    const int i = b + lane;
+    const bool k = i < M && keep(i);
+    const unsigned m = __ballot_sync(0xffffffffu, k);
+    if (k) out[n + __popc(m & ((1u << lane) - 1))] = src[i];
+    n += __popc(m);
+  }
+  __syncwarp();
+  return n;
+}
+
+constexpr int FW_WARPS = 8;   // queries per CTA in the per-query warp phases
+constexpr int FW_BUF = 128;   // per-warp (distance, id) sort buffer: k <= 64 plus ties
+
+// Phased finalize (k <= 64).  Selection/compaction phases run one warp per query
+// and never synchronise a block; gather phases run one CTA (8 independent warps)
+// per query, each lane prefetching one candidate's position per batch of 32.
+
+// phase 1: tau_A = k-th smallest UB1, S1 = {LB1 <= tau_A} (ordered compaction)
+__global__ void __launch_bounds__(FW_WARPS * 32) k_fin_s1(FinParams P) {
+  __shared__ int hist_all[FW_WARPS][256];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int64_t q = (int64_t)blockIdx.x * FW_WARPS + wid;
+  if (q >= P.nq) return;
+  int* hist = hist_all[wid];
+  const int64_t base = q * P.cap;
+  const int M = (int)min((int64_t)P.qcnt[q], P.cap);
+  int64_t nc = 0;
+  for (int r = lane; r < P.nprobe; r += 32) {
+    const int j = P.plist[q * P.nprobe + r];
+    nc += P.loff[j + 1] - P.loff[j];
+  }
+#pragma unroll
+  for (int o = 16; o; o >>= 1) nc += __shfl_xor_sync(0xffffffffu, nc, o);
+  const float tauA = M >= P.k ? fkey_inv(warp_radix_kth(P.sub + base, M, P.k, hist)) : FINF;
+  const float* slb = P.slb + base;
+  const int M1 = warp_compact(P.spos + base, M, P.s2pos + base,
+                              [&](int i) { return slb[i] <= tauA; });
+  if (lane == 0) {
+    P.qtau[q] = tauA;
+    P.qm1[q] = M1;
+    if (P.stats) { P.stats[q * 3 + 0] = nc; P.stats[q * 3 + 1] = M1; }
+  }
+}
+
+// phase 2 (MRQ+): dis_o' = |x_p|^2 + |q_p|^2 - 2 <x_d', q_d'> (Eq. 7), UB2/LB2 = dis_o' -+ m sigma
+__global__ void __launch_bounds__(256) k_fin_stage2(FinParams P) {
+  extern __shared__ __align__(16) float sq[];  // q_d'
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int64_t q = blockIdx.x;
+  for (int i = threadIdx.x; i < P.d; i += 256) sq[i] = P.qd[q * P.d + i];
+  __syncthreads();
+  const int M1 = P.qm1[q];
+  const int64_t base = q * P.cap;
+  const float em = P.m * P.qstat[q * 4 + 1];
+  const float qp2 = P.qstat[q * 4 + 2];
+  const bool vd = (P.d & 3) == 0;
+  for (int b = wid * 32; b < M1; b += 8 * 32) {
+    const int cnt = min(32, M1 - b);
+    const int myp = lane < cnt ? P.s2pos[base + b + lane] : 0;
+    const float myx = lane < cnt ? P.xn2[myp] : 0.f;
+    float mydot = 0.f;
+    for (int t = 0; t < cnt; t += 4) {
+      const int p0 = __shfl_sync(0xffffffffu, myp, t);
+      const int p1 = __shfl_sync(0xffffffffu, myp, min(t + 1, cnt - 1));
+      const int p2 = __shfl_sync(0xffffffffu, myp, min(t + 2, cnt - 1));
+      const int p3 = __shfl_sync(0xffffffffu, myp, min(t + 3, cnt - 1));
+      float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
+      row_accum2<true>(P.xd + (int64_t)p0 * P.d, P.xd + (int64_t)p1 * P.d, sq, P.d, vd, lane, s0, s1);
+      row_accum2<true>(P.xd + (int64_t)p2 * P.d, P.xd + (int64_t)p3 * P.d, sq, P.d, vd, lane, s2, s3);
+      s0 = warp_sum(s0); s1 = warp_sum(s1); s2 = warp_sum(s2); s3 = warp_sum(s3);
+      if (lane == t) mydot = s0;
+      if (lane == t + 1) mydot = s1;
+      if (lane == t + 2) mydot = s2;
+      if (lane == t + 3) mydot = s3;
+    }
+    if (lane < cnt) {
+      const float diso = myx + qp2 - 2.f * mydot;
+      P.s2a[base + b + lane] = diso + em;
+      P.s2b[base + b + lane] = diso - em;
+    }
+  }
+}
+
+// phase 3: tau_B = min(tau_A, k-th smallest UB2 over S1), S2 = {LB2 <= tau_B}
+// (MRQ mode: S2 = S1)
+__global__ void __launch_bounds__(FW_WARPS * 32) k_fin_s2(FinParams P) {
+  __shared__ int hist_all[FW_WARPS][256];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int64_t q = (int64_t)blockIdx.x * FW_WARPS + wid;
+  if (q >= P.nq) return;
+  const int64_t base = q * P.cap;
+  const int M1 = P.qm1[q];
+  int M2;
+  if (P.mode == MRQ_MODE_MRQ_PLUS) {
+    const float tauA = P.qtau[q];
+    const float tauB =
+        M1 >= P.k ? fminf(tauA, fkey_inv(warp_radix_kth(P.s2a + base, M1, P.k, hist_all[wid]))) : tauA;
+    const float* lb2 = P.s2b + base;
+    M2 = warp_compact(P.s2pos + base, M1, P.spos + base, [&](int i) { return lb2[i] <= tauB; });
+  } else {
+    M2 = warp_compact(P.s2pos + base, M1, P.spos + base, [&](int) { return true; });
+  }
+  if (lane == 0) {
+    P.qm2[q] = M2;
+    if (P.stats) P.stats[q * 3 + 2] = M2;
+  }
+}
+
+// phase 4: exact distances |x_d' - q_d'|^2 + |x_r - q_r|^2 (direct sums)
+__global__ void __launch_bounds__(256) k_fin_exact(FinParams P) {
+  extern __shared__ __align__(16) float sq[];  // [q_d' | pad | q_r]
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int64_t q = blockIdx.x;
+  const int dpad = (P.d + 3) & ~3;
+  for (int i = threadIdx.x; i < P.d; i += 256) sq[i] = P.qd[q * P.d + i];
+  for (int i = threadIdx.x; i < P.r; i += 256) sq[dpad + i] = P.qr[q * P.r + i];
+  __syncthreads();
+  const int M2 = P.qm2[q];
+  const int64_t base = q * P.cap;
+  const bool vd = (P.d & 3) == 0, vr = (P.r & 3) == 0;
+  for (int b = wid * 32; b < M2; b += 8 * 32) {
+    const int cnt = min(32, M2 - b);
+    const int myp = lane < cnt ? P.spos[base + b + lane] : 0;
+    float mine = 0.f;
+    for (int t = 0; t < cnt; t += 2) {
+      const int p0 = __shfl_sync(0xffffffffu, myp, t);
+      const int p1 = __shfl_sync(0xffffffffu, myp, min(t + 1, cnt - 1));
+      float s0 = 0.f, s1 = 0.f;
+      row_accum2<false>(P.xd + (int64_t)p0 * P.d, P.xd + (int64_t)p1 * P.d, sq, P.d, vd, lane, s0, s1);
+      row_accum2<false>(P.xr + (int64_t)p0 * P.r, P.xr + (int64_t)p1 * P.r, sq + dpad, P.r, vr, lane, s0, s1);
+      s0 = warp_sum(s0);
+      s1 = warp_sum(s1);
+      if (lane == t) mine = s0;
+      if (lane == t + 1) mine = s1;
+    }
+    if (lane < cnt) P.slb[base + b + lane] = mine;
+  }
+}
+
+// phase 5: the k smallest (distance, id), ties at the k-th distance to the lower ids
+__global__ void __launch_bounds__(FW_WARPS * 32) k_fin_topk(FinParams P) {
+  __shared__ int hist_all[FW_WARPS][256];
+  __shared__ unsigned long long buf_all[FW_WARPS][FW_BUF];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int64_t q = (int64_t)blockIdx.x * FW_WARPS + wid;
+  if (q >= P.nq) return;
+  unsigned long long* buf = buf_all[wid];
+  const int64_t base = q * P.cap;
+  const int M2 = P.qm2[q];
+  const float* dist = P.slb + base;
+  const uint32_t T = M2 > P.k ? warp_radix_kth(dist, M2, P.k, hist_all[wid]) : 0xffffffffu;
+  int n = 0;
+  for (int b = 0; b < M2; b += 32) {  // entries strictly below T (fewer than k)
+    const int i = b + lane;
+    const bool lt = i < M2 && fkey(dist[i]) < T;
+    const unsigned m = __ballot_sync(0xffffffffu, lt);
+    if (lt) buf[n + __popc(m & ((1u << lane) - 1))] =
+        ((unsigned long long)fkey(dist[i]) << 32) | (uint32_t)P.ids[P.spos[base + i]];
+    n += __popc(m);
+  }
+  if (T != 0xffffffffu) {  // ties at T, smallest ids first
+    uint32_t last = 0u;
+    bool first = true;
+    while (n < P.k) {
+      uint32_t best = 0xffffffffu;
+      for (int i = lane; i < M2; i += 32) {
+        if (fkey(dist[i]) == T) {
+          const uint32_t id = (uint32_t)P.ids[P.spos[base + i]];
+          if ((first || id > last) && id < best) best = id;
+        }
+      }
+#pragma unroll
+      for (int o = 16; o; o >>= 1) best = min(best, __shfl_xor_sync(0xffffffffu, best, o));
+      if (best == 0xffffffffu) break;
+      if (lane == 0) buf[n] = ((unsigned long long)T << 32) | best;
+      ++n;
+      last = best;
+      first = false;
+    }
+  }
+  __syncwarp();
+  int n2 = 1;
+  while (n2 < n) n2 <<= 1;
+  for (int i = n + lane; i < n2; i += 32) buf[i] = ~0ull;
+  __syncwarp();
+  for (int size = 2; size <= n2; size <<= 1) {
+    for (int stride = size >> 1; stride > 0; stride >>= 1) {
+      for (int t = lane; t < n2 / 2; t += 32) {
+        const int i = 2 * t - (t & (stride - 1));
+        const int j = i + stride;
+        const bool up = ((i & size) == 0);
+        const unsigned long long x = buf[i], y = buf[j];
+        if ((x > y) == up) { buf[i] = y; buf[j] = x; }
+      }
+      __syncwarp();
+    }
+  }
+  for (int i = lane; i < P.k; i += 32) {
+    if (i < n) {
+      P.out_ids[q * P.k + i] = (int64_t)(uint32_t)(buf[i] & 0xffffffffu);
+      P.out_d[q * P.k + i] = fkey_inv((uint32_t)(buf[i] >> 32));
+    } else {
+      P.out_ids[q * P.k + i] = -1;
+      P.out_d[q * P.k + i] = FINF;
+    }
+  }
+}
+
 int g_num_sms = 0;
 int num_sms() {
   if (!g_num_sms) {
@@ -813,12 +1140,19 @@ void search_batch(mrq_index* idx, const float* q, int64_t nq, int k, int nprobe,
     sqdist_f32(ws.qd.p, d, idx->cent.p, d, (int)nq, nlist, d, ws.gmat.p, nlist, st);
   }
   mark(idx, MRQ_STAGE_SELECT, st);
-  int P2 = 1;
-  while (P2 < nprobe) P2 <<= 1;
   {
-    size_t sm = (size_t)P2 * 8;
+    int P2 = 1;
+    while (P2 < nprobe) P2 <<= 1;
+    // gather capacity: room for the nprobe keys plus ties, a power of two >= nprobe
+    int cap = std::min(nlist, std::max(2 * P2, 256));
+    int c2 = 1;
+    while (c2 < cap) c2 <<= 1;
+    cap = c2;
+    const int in_smem = (size_t)cap * 8 + (size_t)nlist * 4 <= 160 * 1024 ? 1 : 0;
+    size_t sm = (size_t)cap * 8 + (in_smem ? (size_t)nlist * 4 : 0);
     MRQ_CUDA(cudaFuncSetAttribute(k_probe_select, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-    k_probe_select<<<(unsigned)nq, PS_NT, sm, st>>>(ws.gmat.p, nlist, nprobe, P2, ws.plist.p, ws.pg.p);
+    k_probe_select<<<(unsigned)nq, PS_NT, sm, st>>>(ws.gmat.p, nlist, nprobe, cap, in_smem,
+                                                    ws.plist.p, ws.pg.p);
     MRQ_CHECK_LAUNCH();
     k_probe_refine<<<ceil_div(nq * nprobe, 8), 256, 0, st>>>(ws.qd.p, idx->cent.p, ws.plist.p,
                                                             nq * nprobe, nprobe, d, ws.pg.p);
@@ -838,7 +1172,30 @@ void search_batch(mrq_index* idx, const float* q, int64_t nq, int k, int nprobe,
   sp.npairs = nq * nprobe; sp.cap = cap;
   sp.work = ws.work.p; sp.qcnt = ws.qcnt.p; sp.gtau = ws.gtau.p;
   sp.spos = ws.spos.p; sp.slb = ws.slb.p; sp.sub = ws.sub.p;
-  launch_scan(sp, nq * nprobe, st, false);
+  int64_t grid_items = nq * nprobe;
+  if (idx->max_list > SCAN_CHUNK) {
+    // long lists are split into chunks of SCAN_CHUNK candidates (work-item list on device)
+    const int64_t np_ = nq * nprobe;
+    const int64_t max_items = np_ + (nq * idx->cap_by_nprobe[nprobe]) / SCAN_CHUNK + 1;
+    ws.ccnt.reserve(np_);
+    ws.coff.reserve(np_);
+    ws.items.reserve(max_items);
+    ws.nitems.reserve(1);
+    k_chunk_count<<<ceil_div(np_, 256), 256, 0, st>>>(ws.plist.p, idx->loff.p, np_, SCAN_CHUNK, ws.ccnt.p);
+    MRQ_CHECK_LAUNCH();
+    size_t tb = 0;
+    MRQ_CUDA(cub::DeviceScan::ExclusiveSum(nullptr, tb, ws.ccnt.p, ws.coff.p, (int)np_, st));
+    ws.cubtmp.reserve(tb + 16);
+    MRQ_CUDA(cub::DeviceScan::ExclusiveSum(ws.cubtmp.p, tb, ws.ccnt.p, ws.coff.p, (int)np_, st));
+    k_chunk_scatter<<<ceil_div(np_, 256), 256, 0, st>>>(ws.ccnt.p, ws.coff.p, np_, ws.items.p, ws.nitems.p);
+    MRQ_CHECK_LAUNCH();
+    sp.items = ws.items.p;
+    sp.nitems = ws.nitems.p;
+    sp.chunk = SCAN_CHUNK;
+    grid_items = max_items;
+    idx->launches += 3;
+  }
+  launch_scan(sp, grid_items, st, false);
   // 5. finalize
   mark(idx, MRQ_STAGE_FINAL, st);
   FinParams fp{};
@@ -848,9 +1205,31 @@ void search_batch(mrq_index* idx, const float* q, int64_t nq, int k, int nprobe,
   fp.m = o.m; fp.cap = cap; fp.qcnt = ws.qcnt.p; fp.spos = ws.spos.p; fp.slb = ws.slb.p;
   fp.sub = ws.sub.p; fp.s2pos = ws.s2pos.p; fp.s2a = ws.s2a.p; fp.s2b = ws.s2b.p;
   fp.out_ids = out_ids; fp.out_d = out_d; fp.stats = stats;
-  size_t fsm = (size_t)((((d + 3) & ~3) + r + 3) & ~3) * sizeof(float) + FN_SORT * 8;
-  MRQ_CUDA(cudaFuncSetAttribute(k_finalize, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsm));
-  k_finalize<<<(unsigned)nq, FN_NT, fsm, st>>>(fp);
+  if (k <= 64) {
+    ws.qtau.reserve(nq);
+    ws.qm1.reserve(nq);
+    ws.qm2.reserve(nq);
+    fp.qtau = ws.qtau.p; fp.qm1 = ws.qm1.p; fp.qm2 = ws.qm2.p; fp.nq = nq;
+    const unsigned gw = ceil_div(nq, FW_WARPS);
+    k_fin_s1<<<gw, FW_WARPS * 32, 0, st>>>(fp);
+    MRQ_CHECK_LAUNCH();
+    if (o.mode == MRQ_MODE_MRQ_PLUS) {
+      k_fin_stage2<<<(unsigned)nq, 256, (size_t)((d + 3) & ~3) * 4, st>>>(fp);
+      MRQ_CHECK_LAUNCH();
+    }
+    k_fin_s2<<<gw, FW_WARPS * 32, 0, st>>>(fp);
+    MRQ_CHECK_LAUNCH();
+    const size_t esm = (size_t)(((d + 3) & ~3) + r) * 4;
+    MRQ_CUDA(cudaFuncSetAttribute(k_fin_exact, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)esm));
+    k_fin_exact<<<(unsigned)nq, 256, esm, st>>>(fp);
+    MRQ_CHECK_LAUNCH();
+    k_fin_topk<<<gw, FW_WARPS * 32, 0, st>>>(fp);
+    idx->launches += o.mode == MRQ_MODE_MRQ_PLUS ? 4 : 3;
+  } else {
+    size_t fsm = (size_t)((((d + 3) & ~3) + r + 3) & ~3) * sizeof(float) + FN_SORT * 8;
+    MRQ_CUDA(cudaFuncSetAttribute(k_finalize, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsm));
+    k_finalize<<<(unsigned)nq, FN_NT, fsm, st>>>(fp);
+  }
   MRQ_CHECK_LAUNCH();
   mark(idx, MRQ_NSTAGES, st);
   if (idx->prof_on) idx->prof_batches++;

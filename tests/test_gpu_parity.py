@@ -283,3 +283,25 @@ def test_empty_lists(tmp_path):
     ids, dists = mrq.mrq_search(gi, queries, 5, 16, mrq.mrq_search_opts(eps0=1e9, m=1e9))
     truth, _ = omrq.exact_knn(base, queries, 5)
     assert omrq.recall_at_k(ids, truth) > 0.99
+
+
+def test_zipf_lists_chunked_scan(tmp_path):
+    # rank-size Zipf(1.1) list sizes: the largest lists exceed one scan work item
+    # (4096 candidates), so the scan splits them into chunks
+    w = datagen.workload("small", n=40_000, nlist=32, n_query=60)
+    base, centres, sizes = datagen.zipf_clustered(w, w.n, w.nlist, s=1.1)
+    queries = datagen.sample(datagen.make_mixture(w), w.n_query, w.seed("queries"))
+    G = datagen.rotation_gaussian(w.d, 9)
+    oi = omrq.build_index(base, w.d, w.bits, w.nlist, G, init_centroids=centres, kmeans_iters=0)
+    assert np.diff(oi.list_offsets).max() > 2 * 4096
+    p = str(tmp_path / "zipf.mrq")
+    index_file.write_index(oi, p)
+    gi = mrq.mrq_load(p)
+    st = oi.as_stored()
+    for qbits in (0, 4):
+        ids, dists = mrq.mrq_search(gi, queries, w.k, 4, mrq.mrq_search_opts(query_bits=qbits))
+        ref = omrq.search_contract(st, queries, w.k, 4, qbits=qbits)
+        S = dict(base=base, queries=queries)
+        _check_answers(S, ids, dists, ref, w.k)
+        stats = mrq.mrq_last_search_stats(gi, w.n_query)
+        np.testing.assert_array_equal(stats["n_cand"], ref.n_cand)
