@@ -27,6 +27,7 @@ METRIC = "QPS at recall@10≥0.95 on 1 GB300, plain vs batched/BF16 form; scan H
 UNIT = "queries/s"
 NPROBE_LADDER = [2, 3, 4, 6, 8, 12, 16, 24, 32, 48, 64, 96, 128, 192, 256, 384, 512]
 M_LADDER = [4.0, 2.0, 1.0]
+EPS0_LADDER = [1.9, 1.0]
 
 
 def parse_args(argv=None):
@@ -47,6 +48,7 @@ def parse_args(argv=None):
     p.add_argument("--form", default=None, help="time only this form (profiling runs)")
     p.add_argument("--nprobe", type=int, default=None, help="fixed nprobe: skip calibration")
     p.add_argument("--m", type=float, default=None, help="fixed m with --nprobe")
+    p.add_argument("--eps0", type=float, default=None, help="fixed eps0 with --nprobe")
     return p.parse_args(argv)
 
 
@@ -275,38 +277,44 @@ def main(argv=None):
         "plain_q4": mrq.mrq_search_opts(query_bits=4, stream=stream),
         "bf16x3_q4": mrq.mrq_search_opts(query_bits=4, precision=mrq.PREC_BF16X3, stream=stream),
         "bf16_q4": mrq.mrq_search_opts(query_bits=4, precision=mrq.PREC_BF16, stream=stream),
+        "batched_bf16_q4": mrq.mrq_search_opts(query_bits=4, precision=mrq.PREC_BF16, batched=1,
+                                               graph=1, stream=stream),
     }
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
-    def with_m(opts, m):
-        return mrq.mrq_search_opts(eps0=opts.eps0, m=m, mode=opts.mode, precision=opts.precision,
-                                   query_bits=opts.query_bits, batched=opts.batched, stream=stream)
+    def with_m(opts, m, eps0=None):
+        return mrq.mrq_search_opts(eps0=opts.eps0 if eps0 is None else eps0, m=m, mode=opts.mode,
+                                   precision=opts.precision, query_bits=opts.query_bits,
+                                   batched=opts.batched, graph=opts.graph, stream=stream)
 
     def calibrate(opts):
-        """Smallest nprobe reaching the recall target for each Chebyshev multiplier m
-        (Eq. 6 bound; the paper leaves m tunable), then the fastest (m, nprobe)."""
+        """Smallest nprobe reaching the recall target for each bound setting -- the
+        Chebyshev multiplier m (Eq. 6) and the confidence parameter eps0 (Eq. 5),
+        both left tunable by the paper -- then the fastest (eps0, m, nprobe)."""
         best, last_r = None, 0.0
-        for m in M_LADDER:
-            o = with_m(opts, m)
-            for npb in NPROBE_LADDER:
-                if npb > w.nlist:
-                    break
-                ids, _ = mrq.mrq_search(idx, q_t, w.k, npb, o)
-                torch.cuda.synchronize()
-                last_r = recall(ids.cpu().numpy(), truth)
-                if last_r >= args.recall:
-                    per, *_ = timed(o, npb, 3, 1, False)
-                    t = sorted(per)[1]
-                    if best is None or t < best[0]:
-                        best = (t, m, npb, last_r)
-                    break
+        for e0 in EPS0_LADDER:
+            for m in M_LADDER:
+                o = with_m(opts, m, e0)
+                for npb in NPROBE_LADDER:
+                    if npb > w.nlist:
+                        break
+                    ids, _ = mrq.mrq_search(idx, q_t, w.k, npb, o)
+                    torch.cuda.synchronize()
+                    last_r = recall(ids.cpu().numpy(), truth)
+                    if last_r >= args.recall:
+                        per, *_ = timed(o, npb, 3, 1, False)
+                        t = sorted(per)[1]
+                        if best is None or t < best[0]:
+                            best = (t, m, npb, last_r, e0)
+                        break
         if best is None:
-            return None, None, last_r
-        return best[1], best[2], best[3]
+            return None, None, last_r, None
+        return best[1], best[2], best[3], best[4]
 
     def timed(opts, npb, steps, warmup, profile):
         o = mrq.mrq_search_opts(eps0=opts.eps0, m=opts.m, mode=opts.mode, precision=opts.precision,
                                 query_bits=opts.query_bits, batched=opts.batched,
+                                graph=0 if profile else opts.graph,
                                 profile=1 if profile else 0, stream=stream)
         ids = torch.empty((w.n_query, w.k), dtype=torch.int64, device=dev)
         dists = torch.empty((w.n_query, w.k), dtype=torch.float32, device=dev)
@@ -343,24 +351,31 @@ def main(argv=None):
     for name, opts in list(forms.items()):
         if args.nprobe:
             m_best, npb = (args.m if args.m is not None else opts.m), args.nprobe
-            ids, _ = mrq.mrq_search(idx, q_t, w.k, npb, with_m(opts, m_best))
+            e0_best = args.eps0 if args.eps0 is not None else opts.eps0
+            ids, _ = mrq.mrq_search(idx, q_t, w.k, npb, with_m(opts, m_best, e0_best))
             torch.cuda.synchronize()
             r = recall(ids.cpu().numpy(), truth)
         else:
-            m_best, npb, r = calibrate(opts)
+            m_best, npb, r, e0_best = calibrate(opts)
         if npb is None:
             results[name] = {"nprobe": None, "recall": r}
             continue
-        opts = forms[name] = with_m(opts, m_best)
+        opts = forms[name] = with_m(opts, m_best, e0_best)
         per, stage, launches, ids = timed(opts, npb, args.steps, args.warmup, True)
         st = mrq.mrq_last_search_stats(idx, w.n_query)
         ms = sum(per) / len(per)
+        gms = None
+        if opts.graph:  # the same form replayed from a captured CUDA graph (not profiled)
+            gper, *_ = timed(opts, npb, args.steps, args.warmup, False)
+            gms = sum(gper) / len(gper)
         results[name] = {"nprobe": npb, "m": m_best, "eps0": opts.eps0, "recall": r, "ms_per_step": ms,
                          "qps": w.n_query / (ms / 1000.0), "stage_ms": {k: v / len(per) for k, v in stage.items()},
                          "launches_per_step": launches // max(1, len(per)),
                          "cand_per_query": float(st["n_cand"].mean()),
                          "s1_per_query": float(st["n_s1"].mean()),
-                         "exact_per_query": float(st["n_exact"].mean()), "per_step_ms": per}
+                         "exact_per_query": float(st["n_exact"].mean()), "per_step_ms": per,
+                         "graph_ms_per_step": gms,
+                         "graph_qps": None if gms is None else w.n_query / (gms / 1000.0)}
     ok = {k: v for k, v in results.items() if v.get("qps")}
     if not ok:
         print(json.dumps({"metric": METRIC, "error": "no form reached the recall target",
@@ -399,18 +414,30 @@ def main(argv=None):
         e2e_t.append(time.perf_counter() - t0)
     e2e_qps = world * w.n_query / (sum(e2e_t) / len(e2e_t))
 
-    # roofline of the dominant kernel (the stage-1 scan): algorithmic bytes per
-    # candidate = B*d/8 code bytes + 12 bytes of factors (f_add, f_rescale, f_err)
+    # roofline of the dominant kernel.  Algorithmic bytes per query:
+    #   scan   n_c * (B*d/8 code bytes + 12 bytes of f_add, f_rescale, f_err)
+    #   stage2 s1 * (4d row of x_d' + 4 |x_p|^2 + 4 position + 8 bounds written)
+    #   exact  s2 * (4D row of [x_d' | x_r] + 4 position + 4 distance written)
     peak, peak_kind = load_peaks()
-    bpc = w.bits * w.d / 8 + 12
-    scan_ms = B["stage_ms"]["scan"]
     n_batches = 1 + (w.n_query - 1) // 16384
-    alg_bytes = B["cand_per_query"] * w.n_query * bpc / n_batches
-    achieved = alg_bytes / (scan_ms / n_batches / 1000.0) / 1e9
+    per_q = {
+        "scan": ("k_scan", B["cand_per_query"] * (w.bits * w.d / 8 + 12)),
+        "stage2": ("k_fin_stage2", B["s1_per_query"] * (4 * w.d + 16)),
+        "exact": ("k_fin_exact", B["exact_per_query"] * (4 * w.D + 8)),
+    }
+    dom = max(per_q, key=lambda s_: B["stage_ms"][s_])
+    kname, bpq = per_q[dom]
+    launch_ms = B["stage_ms"][dom] / n_batches
+    alg_bytes = bpq * w.n_query / n_batches
+    achieved = alg_bytes / (launch_ms / 1000.0) / 1e9
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-            "frac": achieved / peak, "traffic": None, "kernel": "k_scan",
+            "frac": achieved / peak, "traffic": None, "kernel": kname,
             "peak_kind": peak_kind, "algorithmic_bytes_per_launch": alg_bytes,
-            "launch_ms": scan_ms / n_batches}
+            "launch_ms": launch_ms,
+            "others": {s_: {"kernel": per_q[s_][0],
+                            "GB/s": per_q[s_][1] * w.n_query / n_batches
+                            / (B["stage_ms"][s_] / n_batches / 1000.0) / 1e9}
+                       for s_ in per_q if B["stage_ms"][s_] > 0}}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

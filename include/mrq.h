@@ -68,6 +68,9 @@ typedef struct {
   int query_bits;   /* 0 = float32 query in the scan; 1..8 = scalar-quantized query */
   int batched;      /* 0 = one work item per (query, list); 1 = list-major batched scan */
   int profile;      /* 1 = record CUDA events around each stage (see mrq_last_search_profile) */
+  int graph;        /* 1 = replay a captured CUDA graph when queries, ids and dists are device
+                       memory and every argument equals the previous graph call's (the first
+                       such call runs normally, then captures); ignored with profile = 1 */
   void* cuda_stream;/* cudaStream_t, or NULL */
 } mrq_search_opts;
 
@@ -77,8 +80,12 @@ typedef struct {
 #define MRQ_STAGE_PROBE 2    /* centroid distances */
 #define MRQ_STAGE_SELECT 3   /* top-nprobe selection */
 #define MRQ_STAGE_SCAN 4     /* stage-1 code scan, bounds and survivor compaction */
-#define MRQ_STAGE_FINAL 5    /* thresholds, stage 2 (Eq. 7), exact rerank, top-k */
-#define MRQ_NSTAGES 6
+#define MRQ_STAGE_TAU_A 5    /* tau_A and stage-1 survivors (the whole finalize when k > 64) */
+#define MRQ_STAGE_STAGE2 6   /* stage 2 (Eq. 7) gathers */
+#define MRQ_STAGE_TAU_B 7    /* tau_B and stage-2 survivors */
+#define MRQ_STAGE_EXACT 8    /* exact-distance gathers */
+#define MRQ_STAGE_TOPK 9     /* top-k by (distance, id) */
+#define MRQ_NSTAGES 10
 
 typedef struct {
   int64_t n;

@@ -46,7 +46,7 @@ class BuildOpts(C.Structure):
 class SearchOpts(C.Structure):
     _fields_ = [("eps0", C.c_float), ("m", C.c_float), ("mode", C.c_int),
                 ("precision", C.c_int), ("query_bits", C.c_int), ("batched", C.c_int),
-                ("profile", C.c_int), ("cuda_stream", C.c_void_p)]
+                ("profile", C.c_int), ("graph", C.c_int), ("cuda_stream", C.c_void_p)]
 
 
 class IndexInfo(C.Structure):
@@ -135,11 +135,11 @@ def mrq_build_opts(seed: int = 1, kmeans_iters: int = 20, init_centroids=None, i
 
 def mrq_search_opts(eps0: float = 1.9, m: float = 4.0, mode: int = MODE_MRQ_PLUS,
                     precision: int = PREC_FP32, query_bits: int = 0, batched: int = 0,
-                    profile: int = 0, stream=None) -> SearchOpts:
+                    profile: int = 0, graph: int = 0, stream=None) -> SearchOpts:
     o = SearchOpts()
     _lib.mrq_search_opts_default(C.byref(o))
     o.eps0, o.m, o.mode, o.precision = eps0, m, mode, precision
-    o.query_bits, o.batched, o.profile = query_bits, batched, profile
+    o.query_bits, o.batched, o.profile, o.graph = query_bits, batched, profile, graph
     if stream is not None:
         o.cuda_stream = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
     return o
@@ -230,7 +230,8 @@ def mrq_last_search_stats(index: Index, nq: int):
     return dict(n_cand=a, n_s1=b, n_exact=c)
 
 
-STAGES = ["project", "qstats", "probe", "select", "scan", "final"]
+STAGES = ["project", "qstats", "probe", "select", "scan", "tau_a", "stage2", "tau_b", "exact",
+          "topk"]
 
 
 def mrq_last_search_profile(index: Index):

@@ -172,7 +172,57 @@ int mrq_search(mrq_index* idx, const float* queries, int64_t nq, int k, int npro
     idx->prof_on = o.profile != 0;
     idx->prof_batches = 0;
     idx->launches = 0;
-    for (int64_t s = 0; s < nq; s += qb) {
+    const bool use_graph = o.graph && !o.profile && qdev && odev;
+    mrq_index::GraphKey key{queries, ids, dists, nq, k, nprobe, o.mode, o.precision,
+                            o.query_bits, o.batched, o.eps0, o.m};
+    auto run_batches = [&](cudaStream_t s_) {
+      for (int64_t s = 0; s < nq; s += qb) {
+        const int64_t b = std::min(qb, nq - s);
+        mrq::search_batch(idx, queries + s * D, b, k, nprobe, o, ids + s * k, dists + s * k,
+                          ws.stats.p + s * 3, s_);
+      }
+    };
+    if (use_graph) {
+      if (!idx->graph_stream) {
+        MRQ_CUDA(cudaStreamCreateWithFlags(&idx->graph_stream, cudaStreamNonBlocking));
+        MRQ_CUDA(cudaEventCreateWithFlags(&idx->graph_ev[0], cudaEventDisableTiming));
+        MRQ_CUDA(cudaEventCreateWithFlags(&idx->graph_ev[1], cudaEventDisableTiming));
+      }
+      if (!(idx->graph_valid && idx->graph_key == key)) {
+        // first call with these arguments: run once (sizes scratch), then capture
+        run_batches(st);
+        MRQ_CUDA(cudaStreamSynchronize(st));
+        const int64_t l0 = idx->launches;
+        if (idx->graph_exec) {
+          cudaGraphExecDestroy(idx->graph_exec);
+          idx->graph_exec = nullptr;
+        }
+        idx->graph_valid = false;
+        cudaGraph_t g = nullptr;
+        MRQ_CUDA(cudaStreamBeginCapture(idx->graph_stream, cudaStreamCaptureModeRelaxed));
+        try {
+          run_batches(idx->graph_stream);
+        } catch (...) {
+          cudaStreamEndCapture(idx->graph_stream, &g);
+          if (g) cudaGraphDestroy(g);
+          throw;
+        }
+        MRQ_CUDA(cudaStreamEndCapture(idx->graph_stream, &g));
+        cudaError_t ie = cudaGraphInstantiate(&idx->graph_exec, g, 0);
+        cudaGraphDestroy(g);
+        MRQ_CUDA(ie);
+        idx->graph_key = key;
+        idx->graph_valid = true;
+        idx->graph_launches = idx->launches - l0;
+      }
+      MRQ_CUDA(cudaEventRecord(idx->graph_ev[0], st));
+      MRQ_CUDA(cudaStreamWaitEvent(idx->graph_stream, idx->graph_ev[0], 0));
+      MRQ_CUDA(cudaGraphLaunch(idx->graph_exec, idx->graph_stream));
+      MRQ_CUDA(cudaEventRecord(idx->graph_ev[1], idx->graph_stream));
+      MRQ_CUDA(cudaStreamWaitEvent(st, idx->graph_ev[1], 0));
+      idx->launches = idx->graph_launches;
+    }
+    for (int64_t s = 0; s < nq && !use_graph; s += qb) {
       const int64_t b = std::min(qb, nq - s);
       const float* qp = queries + s * D;
       if (!qdev) {

@@ -76,6 +76,7 @@ struct Workspace {
   DevBuf<float> qstat;     // nq x 4: |q_r|^2, sigma, |q_p|^2, unused
   DevBuf<__nv_bfloat16> qbf;  // nq x D bf16 hi/lo split queries (tensor-core projection)
   DevBuf<float> gmat;      // nq x nlist probe distances
+  DevBuf<unsigned long long> ppart;  // nq x tiles x nprobe fused probe candidates
   DevBuf<int32_t> plist;   // nq x nprobe probed list ids
   DevBuf<float> pg;        // nq x nprobe |q_d - c|^2 of the probed lists
   DevBuf<uint32_t> qcnt;   // nq survivor counters
@@ -94,7 +95,11 @@ struct Workspace {
   DevBuf<int64_t> items;   // (pair << 32 | chunk) scan work items
   DevBuf<uint8_t> cubtmp;  // CUB scan scratch
   // list-major batched scan
-  DevBuf<int32_t> lcount, loffq, lqueue;  // per-list query buckets
+  DevBuf<int32_t> lcount, loffq, lfill, lqueue;  // per-list buckets of (query, list) pairs
+  DevBuf<int32_t> icnt, ioff;              // work items per list and their offsets
+  DevBuf<int64_t> bitems;                  // int4 work items (list, block, group)
+  DevBuf<uint8_t> pq;                      // per-pair query scalars
+  DevBuf<uint32_t> qplanes;                // per-pair quantized query bit planes
 };
 
 }  // namespace mrq
@@ -128,8 +133,32 @@ struct mrq_index {
   bool prof_on = false;
   double prof_ms[MRQ_NSTAGES] = {0};
   int64_t launches = 0;
+  // captured search graph (device-resident calls with identical arguments)
+  struct GraphKey {
+    const void* q;
+    void* ids;
+    void* dists;
+    int64_t nq;
+    int k, nprobe, mode, precision, query_bits, batched;
+    float eps0, m;
+    bool operator==(const GraphKey& o) const {
+      return q == o.q && ids == o.ids && dists == o.dists && nq == o.nq && k == o.k &&
+             nprobe == o.nprobe && mode == o.mode && precision == o.precision &&
+             query_bits == o.query_bits && batched == o.batched && eps0 == o.eps0 && m == o.m;
+    }
+  };
+  bool graph_valid = false;
+  GraphKey graph_key{};
+  cudaGraphExec_t graph_exec = nullptr;
+  cudaStream_t graph_stream = nullptr;
+  cudaEvent_t graph_ev[2] = {nullptr, nullptr};
+  int64_t graph_launches = 0;
   ~mrq_index() {
     for (auto e : prof_ev) cudaEventDestroy(e);
+    if (graph_exec) cudaGraphExecDestroy(graph_exec);
+    if (graph_stream) cudaStreamDestroy(graph_stream);
+    for (auto e : graph_ev)
+      if (e) cudaEventDestroy(e);
   }
 };
 
@@ -166,6 +195,9 @@ void project_tc(const float* Q, const float* mu, const __nv_bfloat16* W2, int M,
 void probe_tc(const float* qd, const float* qstat, const __nv_bfloat16* C2, const float* cn2,
               int M, int nlist, int d, bool split3, __nv_bfloat16* qbf, float* gmat,
               cudaStream_t st);
+int probe_tc_topk(const float* qd, const float* qstat, const __nv_bfloat16* C2, const float* cn2,
+                  int M, int nlist, int d, bool split3, int nsel, __nv_bfloat16* qbf,
+                  unsigned long long* part, cudaStream_t st);
 
 // ---- search (search.cu) ----
 void search_batch(mrq_index* idx, const float* q_dev, int64_t nq, int k, int nprobe,

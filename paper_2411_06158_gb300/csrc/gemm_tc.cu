@@ -139,11 +139,15 @@ struct TcArgs {
   int split;
   const float* rown;  // epi 1: |q_d'|^2 per row (stride rstride)
   int rstride;
-  const float* coln;  // epi 1: |c'|^2 per column
+  const float* coln;  // epi 1/2: |c'|^2 per column
+  unsigned long long* part;  // epi 2: per (row, column tile) the nsel smallest (key << 32 | col)
+  int nsel;
   int* err;
 };
 
-template <int BN>
+constexpr int TC_PSEL = 16;  // largest nprobe selected inside the probe epilogue
+
+template <int BN, int PSEL>
 __global__ void __launch_bounds__(128, 1)
     k_gemm_tc(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtensorMap tb,
               TcArgs P) {
@@ -223,6 +227,9 @@ __global__ void __launch_bounds__(128, 1)
   // epilogue: every warp drains its 32 accumulator lanes (rows)
   const bool have = mbar_wait(&done, 0, &s_abort, P.err, 3);
   tc_fence_after();
+  unsigned long long best[PSEL];
+#pragma unroll
+  for (int t = 0; t < PSEL; ++t) best[t] = ~0ull;
   if (have) {
     const int row = m0 + warp * 32 + lane;
     for (int c = 0; c < BN; c += 32) {
@@ -254,6 +261,25 @@ __global__ void __launch_bounds__(128, 1)
             else P.out1[(int64_t)row * P.ld1 + (col - P.split)] = __uint_as_float(r[j]);
           }
         }
+      } else if (P.epi == 2) {
+        // fused top-nsel: keep this row's smallest (g, list) pairs of the tile
+        const float rn = P.rown[(int64_t)row * P.rstride];
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+          const int col = col0 + j;
+          if (col < P.N) {
+            const float gv = rn + P.coln[col] - 2.f * __uint_as_float(r[j]);
+            unsigned long long v = ((unsigned long long)fkey(gv) << 32) | (uint32_t)col;
+            if (v < best[PSEL - 1]) {
+#pragma unroll
+              for (int t = 0; t < PSEL; ++t) {
+                const unsigned long long lo = v < best[t] ? v : best[t];
+                v = v < best[t] ? best[t] : v;
+                best[t] = lo;
+              }
+            }
+          }
+        }
       } else {
         const float rn = P.rown[(int64_t)row * P.rstride];
         float* dst = P.out0 + (int64_t)row * P.ld0;
@@ -276,6 +302,12 @@ __global__ void __launch_bounds__(128, 1)
           }
         }
       }
+    }
+    if (P.epi == 2 && row < P.M) {
+      unsigned long long* out = P.part + ((int64_t)row * gridDim.y + blockIdx.y) * P.nsel;
+#pragma unroll
+      for (int t = 0; t < PSEL; ++t)
+        if (t < P.nsel) out[t] = best[t];  // constant indices keep best[] in registers
     }
   }
   tc_fence_before();
@@ -327,7 +359,7 @@ CUtensorMap make_map(const void* base, uint64_t rows, uint64_t K, uint32_t box_r
 
 int* g_err = nullptr;
 
-template <int BN>
+template <int BN, int PSEL>
 void launch_tc(const __nv_bfloat16* A2, const __nv_bfloat16* B2, const TcArgs& a, cudaStream_t st) {
   constexpr int STAGE = TC_BM * TC_BK * 2 + BN * TC_BK * 2;
   const size_t smem = (size_t)TC_STAGES * STAGE + 1024;
@@ -335,9 +367,9 @@ void launch_tc(const __nv_bfloat16* A2, const __nv_bfloat16* B2, const TcArgs& a
   const uint64_t brows = (uint64_t)a.N * (a.phases == 3 ? 2 : 1);
   CUtensorMap ta = make_map(A2, arows, a.K, TC_BM);
   CUtensorMap tb = make_map(B2, brows, a.K, BN);
-  MRQ_CUDA(cudaFuncSetAttribute(k_gemm_tc<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  MRQ_CUDA(cudaFuncSetAttribute(k_gemm_tc<BN, PSEL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   dim3 grid(ceil_div(a.M, TC_BM), ceil_div(a.N, BN));
-  k_gemm_tc<BN><<<grid, 128, smem, st>>>(ta, tb, a);
+  k_gemm_tc<BN, PSEL><<<grid, 128, smem, st>>>(ta, tb, a);
   MRQ_CHECK_LAUNCH();
 }
 
@@ -347,9 +379,22 @@ void run_tc(const __nv_bfloat16* A2, const __nv_bfloat16* B2, TcArgs a, cudaStre
     MRQ_CUDA(cudaMemset(g_err, 0, sizeof(int)));
   }
   a.err = g_err;
-  if (a.N <= 64) launch_tc<64>(A2, B2, a, st);
-  else if (a.N <= 128) launch_tc<128>(A2, B2, a, st);
-  else launch_tc<256>(A2, B2, a, st);
+  // the fused top-nsel list is sized to nsel (registers, a divergent insertion per column)
+  if (a.epi == 2 && a.nsel > 4) {
+    if (a.nsel > 8) {
+      if (a.N <= 64) launch_tc<64, 16>(A2, B2, a, st);
+      else if (a.N <= 128) launch_tc<128, 16>(A2, B2, a, st);
+      else launch_tc<256, 16>(A2, B2, a, st);
+    } else {
+      if (a.N <= 64) launch_tc<64, 8>(A2, B2, a, st);
+      else if (a.N <= 128) launch_tc<128, 8>(A2, B2, a, st);
+      else launch_tc<256, 8>(A2, B2, a, st);
+    }
+    return;
+  }
+  if (a.N <= 64) launch_tc<64, 4>(A2, B2, a, st);
+  else if (a.N <= 128) launch_tc<128, 4>(A2, B2, a, st);
+  else launch_tc<256, 4>(A2, B2, a, st);
 }
 
 }  // namespace
@@ -399,6 +444,28 @@ void probe_tc(const float* qd, const float* qstat, const __nv_bfloat16* C2, cons
   a.rown = qstat + 3; a.rstride = 4;
   a.coln = cn2;
   run_tc(qbf, C2, a, st);
+}
+
+// Probe with the top-nsel fused into the epilogue: part[m][tile][nsel] receives, for
+// every query row and 256-column tile, the nsel smallest (fkey(g) << 32 | list).
+int probe_tc_topk(const float* qd, const float* qstat, const __nv_bfloat16* C2, const float* cn2,
+                  int M, int nlist, int d, bool split3, int nsel, __nv_bfloat16* qbf,
+                  unsigned long long* part, cudaStream_t st) {
+  const int64_t tot = (int64_t)M * d;
+  k_split_bf16<<<ceil_div(tot, 256), 256, 0, st>>>(qd, M, d, d, nullptr, split3 ? 1 : 0, qbf);
+  MRQ_CHECK_LAUNCH();
+  TcArgs a{};
+  a.M = M; a.N = nlist; a.K = d;
+  a.phases = split3 ? 3 : 1;
+  a.a_lo = M; a.b_lo = nlist;
+  a.epi = 2;
+  a.rown = qstat + 3; a.rstride = 4;
+  a.coln = cn2;
+  a.part = part;
+  a.nsel = nsel;
+  run_tc(qbf, C2, a, st);
+  const int bn = nlist <= 64 ? 64 : nlist <= 128 ? 128 : 256;
+  return ceil_div(nlist, bn);  // column tiles
 }
 
 }  // namespace mrq

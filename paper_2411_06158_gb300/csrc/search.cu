@@ -258,6 +258,35 @@ __global__ void __launch_bounds__(PS_NT) k_probe_select(const float* __restrict_
   }
 }
 
+// merge of the fused probe candidates: per query (one warp), the nprobe smallest of
+// tiles x nprobe (key, list) pairs, ascending
+__global__ void k_probe_merge(const unsigned long long* __restrict__ part, int64_t nq, int tiles,
+                              int nprobe, int32_t* __restrict__ plist) {
+  __shared__ unsigned long long buf_all[8][256];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int64_t q = (int64_t)blockIdx.x * 8 + wid;
+  if (q >= nq) return;
+  unsigned long long* buf = buf_all[wid];
+  const int n = tiles * nprobe;
+  int n2 = 1;
+  while (n2 < n) n2 <<= 1;
+  for (int i = lane; i < n2; i += 32) buf[i] = i < n ? part[q * n + i] : ~0ull;
+  __syncwarp();
+  for (int size = 2; size <= n2; size <<= 1) {
+    for (int stride = size >> 1; stride > 0; stride >>= 1) {
+      for (int t = lane; t < n2 / 2; t += 32) {
+        const int i = 2 * t - (t & (stride - 1));
+        const int j = i + stride;
+        const bool up = ((i & size) == 0);
+        const unsigned long long x = buf[i], y = buf[j];
+        if ((x > y) == up) { buf[i] = y; buf[j] = x; }
+      }
+      __syncwarp();
+    }
+  }
+  for (int r = lane; r < nprobe; r += 32) plist[q * nprobe + r] = (int32_t)(buf[r] & 0xffffffffu);
+}
+
 // g_j = |q_d' - c_j'|^2 of every probed list, as a direct float32 sum (one warp per
 // pair); the scan's estimates use this value whatever precision chose the lists.
 __global__ void k_probe_refine(const float* __restrict__ qd, const float* __restrict__ cent,
@@ -336,6 +365,7 @@ __global__ void __launch_bounds__(SCAN_WARPS * 32) k_scan(ScanParams P) {
   const int topc = (1 << P.bits) - 1;
   const int topq = (1 << P.qbits) - 1;
 
+  const int lvw = P.vw == 4 ? 2 : P.vw == 2 ? 1 : 0;
   const int64_t n_items = P.items ? (int64_t)*P.nitems : P.npairs;
   while (true) {
     unsigned int it = 0;
@@ -422,6 +452,8 @@ __global__ void __launch_bounds__(SCAN_WARPS * 32) k_scan(ScanParams P) {
       const int64_t idx = b0 + lane;
       const bool valid = idx < size;
       const int64_t pp = pb0 + idx;  // padded position (always allocated)
+      // word w of this candidate: cbase + (w / vw) * 32 * vw + w % vw (vw = 1 << lvw)
+      const uint32_t* cbase = P.codes + (pp >> 5) * (int64_t)P.words * 32 + (pp & 31) * P.vw;
       float ip;
       int idot = 0;
       if (!QUANT) {
@@ -429,7 +461,8 @@ __global__ void __launch_bounds__(SCAN_WARPS * 32) k_scan(ScanParams P) {
         for (int a = 0; a < P.bits; ++a) {
           float pacc = 0.f;
           for (int c = 0; c < nch; ++c) {
-            uint32_t word = __ldg(P.codes + code_word(pp, a * nch + c, P.words, P.vw));
+            const int w = a * nch + c;
+            const uint32_t word = __ldg(cbase + ((w >> lvw) << (5 + lvw)) + (w & (P.vw - 1)));
             const float* L = lut + c * 128;
 #pragma unroll
             for (int s = 0; s < 8; ++s) pacc += L[s * 16 + ((word >> (4 * s)) & 15)];
@@ -442,7 +475,8 @@ __global__ void __launch_bounds__(SCAN_WARPS * 32) k_scan(ScanParams P) {
         for (int a = 0; a < P.bits; ++a) {
           int pd = 0, ps = 0;
           for (int c = 0; c < nch; ++c) {
-            uint32_t word = __ldg(P.codes + code_word(pp, a * nch + c, P.words, P.vw));
+            const int w = a * nch + c;
+            const uint32_t word = __ldg(cbase + ((w >> lvw) << (5 + lvw)) + (w & (P.vw - 1)));
             ps += __popc(word);
             for (int bq = 0; bq < P.qbits; ++bq) pd += __popc(word & qw[bq * nch + c]) << bq;
           }
@@ -540,6 +574,230 @@ __global__ void k_scan_init(unsigned int* qcnt, unsigned int* gtau, int64_t nq, 
     gtau[i] = fkey(FINF);
   }
   if (i == 0) *work = 0u;
+}
+
+// ------------------------------------------------------- batched (list-major) scan
+//
+// The pairs (query, probed list) are bucketed by list; k_pair_prep quantizes each
+// pair's query once (Algorithm 2: normalise, rotate, quantize); a work item is
+// (list j, block of 32 candidates, group of up to BATCH_G pairs probing j).  One
+// warp loads its 32 candidates' code words and factors once (registers) and scores
+// them against every query of the group, so a list's codes are read once per
+// group instead of once per query.
+
+constexpr int BATCH_G = 16;     // queries per work item
+constexpr int BATCH_MAXW = 16;  // code words per vector kept in registers (bits*d/32)
+
+struct PairQ {
+  float sg, a0, e0, em;  // sqrt(g), g + |q_r|^2, eps0*sqrt(g), m*sigma
+  float ql, qdelta;      // q' ~ ql + qdelta * qbar
+  int qsum, pad;
+};
+
+__global__ void k_bucket_count(const int32_t* __restrict__ plist, int64_t npairs,
+                               int* __restrict__ cnt) {
+  int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (w < npairs) atomicAdd(&cnt[plist[w]], 1);
+}
+__global__ void k_bucket_fill(const int32_t* __restrict__ plist, int64_t npairs,
+                              const int* __restrict__ off, int* __restrict__ fill,
+                              int* __restrict__ queue) {
+  int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (w >= npairs) return;
+  const int j = plist[w];
+  queue[off[j] + atomicAdd(&fill[j], 1)] = (int)w;
+}
+// items of list j: (#32-blocks) x (#groups of BATCH_G pairs)
+__global__ void k_batch_count(const int* __restrict__ cnt, const int64_t* __restrict__ loff,
+                              int nlist, int* __restrict__ icnt) {
+  int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= nlist) return;
+  const int64_t sz = loff[j + 1] - loff[j];
+  const int c = cnt[j];
+  icnt[j] = (c > 0 && sz > 0) ? (int)(((sz + 31) / 32) * ((c + BATCH_G - 1) / BATCH_G)) : 0;
+}
+__global__ void k_batch_scatter(const int* __restrict__ cnt, const int* __restrict__ icnt,
+                                const int* __restrict__ ioff, const int64_t* __restrict__ loff,
+                                int nlist, int4* __restrict__ items, int* __restrict__ nitems) {
+  int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= nlist) return;
+  const int n = icnt[j];
+  const int ng = (cnt[j] + BATCH_G - 1) / BATCH_G;
+  for (int i = 0; i < n; ++i) items[ioff[j] + i] = make_int4(j, i / ng, i % ng, 0);
+  if (j == nlist - 1) *nitems = ioff[j] + n;
+}
+
+// per-pair query preparation (one warp per pair): q' and its B_q-bit planes
+__global__ void k_pair_prep(const float* __restrict__ qd, const float* __restrict__ qstat,
+                            const int32_t* __restrict__ plist, const float* __restrict__ pg,
+                            const float* __restrict__ cent, int64_t npairs, int nprobe, int d,
+                            int qbits, float eps0, float m, PairQ* __restrict__ pq,
+                            uint32_t* __restrict__ qplanes) {
+  const int64_t w = (int64_t)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
+  if (w >= npairs) return;
+  const int lane = threadIdx.x & 31;
+  const int64_t q = w / nprobe;
+  const int j = plist[w];
+  const float g = pg[w];
+  const float sg = sqrtf(g);
+  const int nch = d >> 5;
+  const int topq = (1 << qbits) - 1;
+  float v[16];
+  float lo = FINF, hi = -FINF;
+  for (int c = 0; c < nch; ++c) {
+    const int i = c * 32 + lane;
+    const float t = qd[q * d + i] - cent[(int64_t)j * d + i];
+    v[c] = g > 0.f ? t / sg : 0.f;
+    lo = fminf(lo, v[c]);
+    hi = fmaxf(hi, v[c]);
+  }
+  lo = warp_min(lo);
+  hi = warp_max(hi);
+  const float delta = (hi - lo) / (float)topq;
+  int ssum = 0;
+  uint32_t* out = qplanes + w * (int64_t)(qbits * nch);
+  for (int c = 0; c < nch; ++c) {
+    int qb = 0;
+    if (delta > 0.f) {
+      qb = min((int)floorf((v[c] - lo) / delta + 0.5f), topq);
+      qb = max(qb, 0);
+    }
+    ssum += qb;
+    for (int b = 0; b < qbits; ++b) {
+      const unsigned word = __ballot_sync(0xffffffffu, (qb >> b) & 1);
+      if (lane == 0) out[b * nch + c] = word;
+    }
+  }
+  ssum = warp_sum_i(ssum);
+  if (lane == 0) {
+    PairQ r;
+    r.sg = sg;
+    r.a0 = g + qstat[q * 4 + 0];
+    r.e0 = eps0 * sg;
+    r.em = m * qstat[q * 4 + 1];
+    r.ql = lo;
+    r.qdelta = delta;
+    r.qsum = ssum;
+    r.pad = 0;
+    pq[w] = r;
+  }
+}
+
+struct BatchParams {
+  const int4* items;
+  const int* nitems;
+  const int* lqueue;     // pairs bucketed by list
+  const int* loffq;      // bucket offsets
+  const int* lcount;
+  const PairQ* pq;
+  const uint32_t* qplanes;
+  const int64_t* loff;
+  const int64_t* ploff;
+  const uint32_t* codes;
+  const float* fadd;
+  const float* fres;
+  const float* ferr;
+  int d, bits, words, vw, nprobe, k, qbits;
+  int64_t cap;
+  unsigned int* work;
+  unsigned int* qcnt;
+  unsigned int* gtau;
+  int32_t* spos;
+  float* slb;
+  float* sub;
+};
+
+template <int W, int NCH>
+__global__ void __launch_bounds__(256) k_scan_batched(BatchParams P) {
+  constexpr int BITS = W / NCH;
+  const int lane = threadIdx.x & 31;
+  const int topc = (1 << BITS) - 1;
+  const int QW = P.qbits * NCH;
+  const int n_items = *P.nitems;
+  while (true) {
+    unsigned it = 0;
+    if (lane == 0) it = atomicAdd(P.work, 1u);
+    it = __shfl_sync(0xffffffffu, it, 0);
+    if ((int)it >= n_items) break;
+    const int4 item = P.items[it];
+    const int j = item.x, blk = item.y, grp = item.z;
+    const int64_t lb0 = P.loff[j];
+    const int64_t size = P.loff[j + 1] - lb0;
+    const int64_t idx = (int64_t)blk * 32 + lane;
+    const bool valid = idx < size;
+    const int64_t pp = P.ploff[j] + idx;
+    // this lane's candidate: all W code words in registers, plane popcounts, factors
+    const uint32_t* cbase = P.codes + (pp >> 5) * (int64_t)W * 32 + (pp & 31) * P.vw;
+    const int lvw = P.vw == 4 ? 2 : P.vw == 2 ? 1 : 0;
+    uint32_t cw[W];
+#pragma unroll
+    for (int w = 0; w < W; ++w) cw[w] = __ldg(cbase + ((w >> lvw) << (5 + lvw)) + (w & (P.vw - 1)));
+    int su = 0;
+#pragma unroll
+    for (int w = 0; w < W; ++w) su += __popc(cw[w]) << (w / NCH);
+    const float fa = __ldg(P.fadd + pp), fr = __ldg(P.fres + pp), fe = __ldg(P.ferr + pp);
+    const int g0 = P.loffq[j] + grp * BATCH_G;
+    const int g1 = min(P.loffq[j] + P.lcount[j], g0 + BATCH_G);
+    for (int gi = g0; gi < g1; ++gi) {
+      const int w_pair = P.lqueue[gi];
+      const int64_t q = w_pair / P.nprobe;
+      const PairQ pr = P.pq[w_pair];
+      const uint32_t* qp = P.qplanes + (int64_t)w_pair * QW;
+      int dot = 0;
+      for (int b = 0; b < P.qbits; ++b) {
+        int pd = 0;
+#pragma unroll
+        for (int c = 0; c < NCH; ++c) {
+          const uint32_t qwd = __ldg(qp + b * NCH + c);
+#pragma unroll
+          for (int a = 0; a < BITS; ++a) pd += __popc(cw[a * NCH + c] & qwd) << a;
+        }
+        dot += pd << b;
+      }
+      const float ip = pr.qdelta * (float)(2 * dot - topc * pr.qsum) +
+                       pr.ql * (float)(2 * su - P.d * topc);
+      const float dis = fa + pr.a0 + fr * pr.sg * ip;  // Eq. 4
+      const float eps = pr.e0 * fe + pr.em;            // Eq. 5 + Chebyshev
+      const float lb = valid ? dis - eps : FINF;
+      const float ub = valid ? dis + eps : FINF;
+      float tau = fkey_inv(__ldcg(P.gtau + q));
+      if (P.k <= 32) {
+        // this warp's k-th smallest upper bound bounds tau_A from above
+        const unsigned below = __ballot_sync(0xffffffffu, ub < tau);
+        if (__popc(below) >= P.k) {
+          float v = ub < tau ? ub : FINF;
+#pragma unroll
+          for (int size2 = 2; size2 <= 32; size2 <<= 1) {
+#pragma unroll
+            for (int stride = size2 >> 1; stride > 0; stride >>= 1) {
+              const float o = __shfl_xor_sync(0xffffffffu, v, stride);
+              const bool up = ((lane & size2) == 0);
+              const bool lower = (lane & stride) == 0;
+              v = (lower == up) ? fminf(v, o) : fmaxf(v, o);
+            }
+          }
+          const float kth = __shfl_sync(0xffffffffu, v, P.k - 1);
+          if (kth < tau) {
+            tau = kth;
+            if (lane == 0) atomicMin(P.gtau + q, fkey(kth));
+          }
+        }
+      }
+      const bool surv = lb <= tau;
+      const unsigned sm = __ballot_sync(0xffffffffu, surv);
+      if (sm) {
+        unsigned base = 0;
+        if (lane == 0) base = atomicAdd(P.qcnt + q, (unsigned)__popc(sm));
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (surv) {
+          const int64_t at = q * P.cap + base + __popc(sm & ((1u << lane) - 1));
+          P.spos[at] = (int32_t)(lb0 + idx);
+          P.slb[at] = lb;
+          P.sub[at] = ub;
+        }
+      }
+    }
+  }
 }
 
 // ------------------------------------------------------------------ finalize
@@ -863,8 +1121,10 @@ __global__ void __launch_bounds__(256) k_fin_stage2(FinParams P) {
   const float em = P.m * P.qstat[q * 4 + 1];
   const float qp2 = P.qstat[q * 4 + 2];
   const bool vd = (P.d & 3) == 0;
-  for (int b = wid * 32; b < M1; b += 8 * 32) {
-    const int cnt = min(32, M1 - b);
+  // warp wid owns candidates [lo, hi): an even split over the 8 warps
+  const int per = (M1 + 7) / 8, lo = min(M1, wid * per), hi = min(M1, lo + per);
+  for (int b = lo; b < hi; b += 32) {
+    const int cnt = min(32, hi - b);
     const int myp = lane < cnt ? P.s2pos[base + b + lane] : 0;
     const float myx = lane < cnt ? P.xn2[myp] : 0.f;
     float mydot = 0.f;
@@ -927,8 +1187,9 @@ __global__ void __launch_bounds__(256) k_fin_exact(FinParams P) {
   const int M2 = P.qm2[q];
   const int64_t base = q * P.cap;
   const bool vd = (P.d & 3) == 0, vr = (P.r & 3) == 0;
-  for (int b = wid * 32; b < M2; b += 8 * 32) {
-    const int cnt = min(32, M2 - b);
+  const int per = (M2 + 7) / 8, lo = min(M2, wid * per), hi = min(M2, lo + per);
+  for (int b = lo; b < hi; b += 32) {
+    const int cnt = min(32, hi - b);
     const int myp = lane < cnt ? P.spos[base + b + lane] : 0;
     float mine = 0.f;
     for (int t = 0; t < cnt; t += 2) {
@@ -1131,7 +1392,16 @@ void search_batch(mrq_index* idx, const float* q, int64_t nq, int k, int nprobe,
   qstats(idx, ws.qd.p, ws.qr.p, nq, ws.qstat.p, st);
   // 3. probe
   mark(idx, MRQ_STAGE_PROBE, st);
-  if (o.precision != MRQ_PREC_FP32 && d >= 64) {
+  const int tiles_ = nlist <= 64 ? 1 : nlist <= 128 ? 1 : ceil_div(nlist, 256);
+  const bool fused = o.precision != MRQ_PREC_FP32 && d >= 64 && nprobe <= 16 &&
+                     (int64_t)tiles_ * nprobe <= 256;
+  if (fused) {
+    ws.qbf.reserve((size_t)nq * D * 2);
+    ws.ppart.reserve((size_t)nq * tiles_ * nprobe);
+    probe_tc_topk(ws.qd.p, ws.qstat.p, idx->cent2.p, idx->cent_n2.p, (int)nq, nlist, d,
+                  o.precision == MRQ_PREC_BF16X3, nprobe, ws.qbf.p, ws.ppart.p, st);
+    idx->launches += 1;
+  } else if (o.precision != MRQ_PREC_FP32 && d >= 64) {
     ws.qbf.reserve((size_t)nq * D * 2);
     probe_tc(ws.qd.p, ws.qstat.p, idx->cent2.p, idx->cent_n2.p, (int)nq, nlist, d,
              o.precision == MRQ_PREC_BF16X3, ws.qbf.p, ws.gmat.p, st);
@@ -1140,7 +1410,13 @@ void search_batch(mrq_index* idx, const float* q, int64_t nq, int k, int nprobe,
     sqdist_f32(ws.qd.p, d, idx->cent.p, d, (int)nq, nlist, d, ws.gmat.p, nlist, st);
   }
   mark(idx, MRQ_STAGE_SELECT, st);
-  {
+  if (fused) {
+    k_probe_merge<<<ceil_div(nq, 8), 256, 0, st>>>(ws.ppart.p, nq, tiles_, nprobe, ws.plist.p);
+    MRQ_CHECK_LAUNCH();
+    k_probe_refine<<<ceil_div(nq * nprobe, 8), 256, 0, st>>>(ws.qd.p, idx->cent.p, ws.plist.p,
+                                                            nq * nprobe, nprobe, d, ws.pg.p);
+    MRQ_CHECK_LAUNCH();
+  } else {
     int P2 = 1;
     while (P2 < nprobe) P2 <<= 1;
     // gather capacity: room for the nprobe keys plus ties, a power of two >= nprobe
@@ -1172,8 +1448,77 @@ void search_batch(mrq_index* idx, const float* q, int64_t nq, int k, int nprobe,
   sp.npairs = nq * nprobe; sp.cap = cap;
   sp.work = ws.work.p; sp.qcnt = ws.qcnt.p; sp.gtau = ws.gtau.p;
   sp.spos = ws.spos.p; sp.slb = ws.slb.p; sp.sub = ws.sub.p;
+  // batched form: quantized query, code words a power of two (bits in {1,2,4,8}) up to 16
+  const int wds = idx->words;
+  const bool batched = o.batched && o.query_bits > 0 && wds <= BATCH_MAXW &&
+                       (wds & (wds - 1)) == 0 && (idx->bits & (idx->bits - 1)) == 0 &&
+                       ((d / 32) & (d / 32 - 1)) == 0 && !(wds == 16 && d == 32);
+  if (batched) {
+    const int64_t np_ = nq * nprobe;
+    const int nch = d / 32;
+    ws.lcount.reserve(nlist);
+    ws.loffq.reserve(nlist);
+    ws.lfill.reserve(nlist);
+    ws.lqueue.reserve(np_);
+    ws.icnt.reserve(nlist);
+    ws.ioff.reserve(nlist);
+    ws.nitems.reserve(1);
+    const int64_t max_items = np_ + (nq * idx->cap_by_nprobe[nprobe]) / 32 + 1;
+    ws.bitems.reserve(2 * max_items);  // int4 items, two int64 slots each
+    ws.pq.reserve(np_ * sizeof(PairQ));
+    ws.qplanes.reserve(np_ * o.query_bits * nch);
+    MRQ_CUDA(cudaMemsetAsync(ws.lcount.p, 0, 4 * nlist, st));
+    MRQ_CUDA(cudaMemsetAsync(ws.lfill.p, 0, 4 * nlist, st));
+    k_bucket_count<<<ceil_div(np_, 256), 256, 0, st>>>(ws.plist.p, np_, ws.lcount.p);
+    size_t tb = 0;
+    MRQ_CUDA(cub::DeviceScan::ExclusiveSum(nullptr, tb, ws.lcount.p, ws.loffq.p, nlist, st));
+    ws.cubtmp.reserve(tb + 16);
+    MRQ_CUDA(cub::DeviceScan::ExclusiveSum(ws.cubtmp.p, tb, ws.lcount.p, ws.loffq.p, nlist, st));
+    k_bucket_fill<<<ceil_div(np_, 256), 256, 0, st>>>(ws.plist.p, np_, ws.loffq.p, ws.lfill.p,
+                                                      ws.lqueue.p);
+    k_batch_count<<<ceil_div(nlist, 256), 256, 0, st>>>(ws.lcount.p, idx->loff.p, nlist, ws.icnt.p);
+    MRQ_CUDA(cub::DeviceScan::ExclusiveSum(nullptr, tb, ws.icnt.p, ws.ioff.p, nlist, st));
+    ws.cubtmp.reserve(tb + 16);
+    MRQ_CUDA(cub::DeviceScan::ExclusiveSum(ws.cubtmp.p, tb, ws.icnt.p, ws.ioff.p, nlist, st));
+    k_batch_scatter<<<ceil_div(nlist, 256), 256, 0, st>>>(ws.lcount.p, ws.icnt.p, ws.ioff.p,
+                                                          idx->loff.p, nlist,
+                                                          reinterpret_cast<int4*>(ws.bitems.p),
+                                                          ws.nitems.p);
+    k_pair_prep<<<ceil_div(np_, 8), 256, 0, st>>>(ws.qd.p, ws.qstat.p, ws.plist.p, ws.pg.p,
+                                                  idx->cent.p, np_, nprobe, d, o.query_bits,
+                                                  o.eps0, o.m, reinterpret_cast<PairQ*>(ws.pq.p),
+                                                  ws.qplanes.p);
+    MRQ_CHECK_LAUNCH();
+    BatchParams bp{};
+    bp.items = reinterpret_cast<const int4*>(ws.bitems.p); bp.nitems = ws.nitems.p;
+    bp.lqueue = ws.lqueue.p; bp.loffq = ws.loffq.p; bp.lcount = ws.lcount.p;
+    bp.pq = reinterpret_cast<const PairQ*>(ws.pq.p); bp.qplanes = ws.qplanes.p;
+    bp.loff = idx->loff.p; bp.ploff = idx->ploff.p; bp.codes = idx->codes.p;
+    bp.fadd = idx->fadd.p; bp.fres = idx->fres.p; bp.ferr = idx->ferr.p;
+    bp.d = d; bp.bits = idx->bits; bp.words = idx->words; bp.vw = idx->vw;
+    bp.nprobe = nprobe; bp.k = k; bp.qbits = o.query_bits; bp.cap = cap;
+    bp.work = ws.work.p; bp.qcnt = ws.qcnt.p; bp.gtau = ws.gtau.p;
+    bp.spos = ws.spos.p; bp.slb = ws.slb.p; bp.sub = ws.sub.p;
+    auto launch = [&](auto kern) {
+      int per_sm = 0;
+      MRQ_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, 0));
+      kern<<<num_sms() * std::max(per_sm, 1), 256, 0, st>>>(bp);
+    };
+    const int nch_ = d / 32, bits_ = idx->bits;
+#define MRQ_BATCH(Wv, Nv) \
+    else if (idx->words == Wv && nch_ == Nv) launch(k_scan_batched<Wv, Nv>);
+    if (false) {}
+    MRQ_BATCH(1, 1) MRQ_BATCH(2, 1) MRQ_BATCH(2, 2) MRQ_BATCH(4, 1) MRQ_BATCH(4, 2)
+    MRQ_BATCH(4, 4) MRQ_BATCH(8, 1) MRQ_BATCH(8, 2) MRQ_BATCH(8, 4) MRQ_BATCH(8, 8)
+    MRQ_BATCH(16, 2) MRQ_BATCH(16, 4) MRQ_BATCH(16, 8) MRQ_BATCH(16, 16)
+    else fail(MRQ_EINVAL, "batched scan: unsupported code shape");
+#undef MRQ_BATCH
+    (void)bits_;
+    MRQ_CHECK_LAUNCH();
+    idx->launches += 8;
+  }
   int64_t grid_items = nq * nprobe;
-  if (idx->max_list > SCAN_CHUNK) {
+  if (!batched && idx->max_list > SCAN_CHUNK) {
     // long lists are split into chunks of SCAN_CHUNK candidates (work-item list on device)
     const int64_t np_ = nq * nprobe;
     const int64_t max_items = np_ + (nq * idx->cap_by_nprobe[nprobe]) / SCAN_CHUNK + 1;
@@ -1195,9 +1540,9 @@ void search_batch(mrq_index* idx, const float* q, int64_t nq, int k, int nprobe,
     grid_items = max_items;
     idx->launches += 3;
   }
-  launch_scan(sp, grid_items, st, false);
+  if (!batched) launch_scan(sp, grid_items, st, false);
   // 5. finalize
-  mark(idx, MRQ_STAGE_FINAL, st);
+  mark(idx, MRQ_STAGE_TAU_A, st);
   FinParams fp{};
   fp.qd = ws.qd.p; fp.qr = ws.qr.p; fp.qstat = ws.qstat.p; fp.plist = ws.plist.p;
   fp.loff = idx->loff.p; fp.xd = idx->xd.p; fp.xr = idx->xr.p; fp.xn2 = idx->xn2.p;
@@ -1213,22 +1558,27 @@ void search_batch(mrq_index* idx, const float* q, int64_t nq, int k, int nprobe,
     const unsigned gw = ceil_div(nq, FW_WARPS);
     k_fin_s1<<<gw, FW_WARPS * 32, 0, st>>>(fp);
     MRQ_CHECK_LAUNCH();
+    mark(idx, MRQ_STAGE_STAGE2, st);
     if (o.mode == MRQ_MODE_MRQ_PLUS) {
       k_fin_stage2<<<(unsigned)nq, 256, (size_t)((d + 3) & ~3) * 4, st>>>(fp);
       MRQ_CHECK_LAUNCH();
     }
+    mark(idx, MRQ_STAGE_TAU_B, st);
     k_fin_s2<<<gw, FW_WARPS * 32, 0, st>>>(fp);
     MRQ_CHECK_LAUNCH();
+    mark(idx, MRQ_STAGE_EXACT, st);
     const size_t esm = (size_t)(((d + 3) & ~3) + r) * 4;
     MRQ_CUDA(cudaFuncSetAttribute(k_fin_exact, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)esm));
     k_fin_exact<<<(unsigned)nq, 256, esm, st>>>(fp);
     MRQ_CHECK_LAUNCH();
+    mark(idx, MRQ_STAGE_TOPK, st);
     k_fin_topk<<<gw, FW_WARPS * 32, 0, st>>>(fp);
     idx->launches += o.mode == MRQ_MODE_MRQ_PLUS ? 4 : 3;
   } else {
     size_t fsm = (size_t)((((d + 3) & ~3) + r + 3) & ~3) * sizeof(float) + FN_SORT * 8;
     MRQ_CUDA(cudaFuncSetAttribute(k_finalize, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsm));
     k_finalize<<<(unsigned)nq, FN_NT, fsm, st>>>(fp);
+    for (int sidx = MRQ_STAGE_STAGE2; sidx <= MRQ_STAGE_TOPK; ++sidx) mark(idx, sidx, st);
   }
   MRQ_CHECK_LAUNCH();
   mark(idx, MRQ_NSTAGES, st);

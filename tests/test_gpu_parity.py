@@ -305,3 +305,50 @@ def test_zipf_lists_chunked_scan(tmp_path):
         _check_answers(S, ids, dists, ref, w.k)
         stats = mrq.mrq_last_search_stats(gi, w.n_query)
         np.testing.assert_array_equal(stats["n_cand"], ref.n_cand)
+
+
+@pytest.mark.parametrize("fixture", ["small", "multibit"])
+def test_batched_form_equals_per_pair_scan(request, fixture):
+    # the list-major batched scan scores every candidate with the same arithmetic
+    # and the thresholds are order-independent, so answers are bit-identical
+    S = request.getfixturevalue(fixture)
+    w = S["w"]
+    q = torch.from_numpy(S["queries"]).cuda()
+    for npb in (1, 6, w.nlist):
+        a = mrq.mrq_search(S["gidx"], q, w.k, npb, mrq.mrq_search_opts(query_bits=4))
+        sa = mrq.mrq_last_search_stats(S["gidx"], len(S["queries"]))
+        b = mrq.mrq_search(S["gidx"], q, w.k, npb, mrq.mrq_search_opts(query_bits=4, batched=1))
+        sb = mrq.mrq_last_search_stats(S["gidx"], len(S["queries"]))
+        np.testing.assert_array_equal(a[0].cpu().numpy(), b[0].cpu().numpy())
+        np.testing.assert_array_equal(a[1].cpu().numpy(), b[1].cpu().numpy())
+        np.testing.assert_array_equal(sa["n_cand"], sb["n_cand"])
+        np.testing.assert_array_equal(sa["n_s1"], sb["n_s1"])
+    ref = omrq.search_contract(S["stored"], S["queries"], w.k, 6, qbits=4)
+    ids, dists = mrq.mrq_search(S["gidx"], q, w.k, 6, mrq.mrq_search_opts(query_bits=4, batched=1))
+    _check_answers(S, ids.cpu().numpy(), dists.cpu().numpy(), ref, w.k)
+
+
+def test_graph_replay(small):
+    # a captured search graph replays the same pipeline: identical answers, and new
+    # query values written into the same buffer are picked up by the replay
+    S = small
+    w = S["w"]
+    q = torch.from_numpy(S["queries"]).cuda()
+    ids = torch.empty((q.shape[0], w.k), dtype=torch.int64, device="cuda")
+    dists = torch.empty((q.shape[0], w.k), dtype=torch.float32, device="cuda")
+    for form in (dict(query_bits=4, batched=1), dict(query_bits=0)):
+        ref_i, ref_d = mrq.mrq_search(S["gidx"], q, w.k, w.nprobe, mrq.mrq_search_opts(**form))
+        for _ in range(3):
+            mrq.mrq_search(S["gidx"], q, w.k, w.nprobe, mrq.mrq_search_opts(graph=1, **form),
+                           out=(ids, dists))
+            torch.cuda.synchronize()
+            np.testing.assert_array_equal(ids.cpu().numpy(), ref_i.cpu().numpy())
+            np.testing.assert_array_equal(dists.cpu().numpy(), ref_d.cpu().numpy())
+        q2 = q.flip(0).contiguous()
+        ref2 = mrq.mrq_search(S["gidx"], q2, w.k, w.nprobe, mrq.mrq_search_opts(**form))
+        q.copy_(q2)
+        mrq.mrq_search(S["gidx"], q, w.k, w.nprobe, mrq.mrq_search_opts(graph=1, **form),
+                       out=(ids, dists))
+        torch.cuda.synchronize()
+        np.testing.assert_array_equal(ids.cpu().numpy(), ref2[0].cpu().numpy())
+        q.copy_(q2.flip(0))
