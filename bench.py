@@ -120,6 +120,24 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+# ------------------------------------------------------------ multi-rank
+
+def reduce_max(value: float, world: int, device=None) -> float:
+    """Max of a per-rank number over all ranks (the timed region's slowest rank)."""
+    if world <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_qps(queries_per_rank: int, world: int, ms_max: float) -> float:
+    """Whole-job throughput: every rank searches its own batch (replicas, weak scaling)."""
+    return world * queries_per_rank / (ms_max / 1000.0)
+
+
 # ----------------------------------------------------------- ground truth
 
 def ground_truth(base_t, q_t, k, chunk=1024):
@@ -384,12 +402,8 @@ def main(argv=None):
     best = max(ok, key=lambda k: ok[k]["qps"])
     B = ok[best]
     # max over ranks
-    ms_step = B["ms_per_step"]
-    if world > 1:
-        t = torch.tensor([ms_step], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms_step = float(t.item())
-    value = world * w.n_query / (ms_step / 1000.0)
+    ms_step = reduce_max(B["ms_per_step"], world, dev)
+    value = whole_job_qps(w.n_query, world, ms_step)
 
     # clocks during a second timed pass of the best form
     clk = ClockSampler(local, os.path.join(ROOT, "gpurun_out", f"clocks_rank{rank}.csv")) \
@@ -412,7 +426,7 @@ def main(argv=None):
         t0 = time.perf_counter()
         mrq.mrq_search(idx, qh, w.k, B["nprobe"], o, out=(ih, dh))
         e2e_t.append(time.perf_counter() - t0)
-    e2e_qps = world * w.n_query / (sum(e2e_t) / len(e2e_t))
+    e2e_qps = whole_job_qps(w.n_query, world, reduce_max(1000.0 * sum(e2e_t) / len(e2e_t), world, dev))
 
     # roofline of the dominant kernel.  Algorithmic bytes per query:
     #   scan   n_c * (B*d/8 code bytes + 12 bytes of f_add, f_rescale, f_err)

@@ -1,0 +1,125 @@
+"""Planted mistakes in the CPU oracle must be caught by its pins.
+
+Each case swaps one oracle function for a plausibly wrong variant (a dropped
+term, a wrong sign, a wrong index, a missing step), reruns the pin that guards
+it, and expects that pin to fail.  Mistakes are planted in the oracle only, on
+the CPU."""
+import math
+
+import numpy as np
+import pytest
+
+import datagen
+from oracle import mrq
+import test_oracle_pins as pins
+
+
+def _small():
+    w = datagen.workload("small", n=6000, n_comp=24, nlist=24, n_query=60)
+    base, queries = datagen.base_and_queries(w)
+    G = datagen.rotation_gaussian(w.d, 3)
+    init = datagen.kmeans_init_indices(w.n, w.nlist, 4)
+    idx = mrq.build_index(base, w.d, w.bits, w.nlist, G, init_idx=init, kmeans_iters=5)
+    return (w, base, queries), idx
+
+
+def _fails(fn, *args):
+    with pytest.raises(AssertionError):
+        fn(*args)
+
+
+def test_tail_variance_index_off_by_d(monkeypatch):
+    orig = mrq.project_queries
+
+    def wrong(idx, Q):
+        qd, qr, qr2, sigma, qp2 = orig(idx, Q)
+        lam = idx.lam[:idx.D - idx.d]                      # wrong slice of sigma_i^2
+        return qd, qr, qr2, np.sqrt(np.sum(qr * qr * lam[None, :], axis=1)), qp2
+    monkeypatch.setattr(mrq, "project_queries", wrong)
+    wk, idx = _small()
+    _fails(pins.test_residual_variance_identity_and_chebyshev, wk, idx)
+
+
+def test_rescale_sign_flipped(monkeypatch):
+    orig = mrq.factors
+
+    def wrong(*a):
+        f_add, f_res, f_err, ip = orig(*a)
+        return f_add, -f_res, f_err, ip
+    monkeypatch.setattr(mrq, "factors", wrong)
+    wk, idx = _small()
+    _fails(pins.test_eq3_decomposition_exact, wk, idx)
+
+
+def test_error_factor_without_dimension_scaling(monkeypatch):
+    orig = mrq.factors
+
+    def wrong(resid_norm, xr2, v, o, d):
+        f_add, f_res, f_err, ip = orig(resid_norm, xr2, v, o, d)
+        return f_add, f_res, f_err * math.sqrt(d - 1), ip
+    monkeypatch.setattr(mrq, "factors", wrong)
+    _fails(pins.test_factor_closed_form_one_hot)
+
+
+def test_code_sign_inverted(monkeypatch):
+    orig = mrq.encode
+
+    def wrong(o, bits):
+        return orig(-np.asarray(o), bits)
+    monkeypatch.setattr(mrq, "encode", wrong)
+    _fails(pins.test_encode_golden)
+
+
+def test_random_rotation_missing_from_projection(monkeypatch):
+    orig = mrq.build_index
+
+    def wrong(*a, **k):
+        idx = orig(*a, **k)
+        idx.W = idx.Pp.copy()                              # queries no longer rotated by P_r
+        return idx
+    monkeypatch.setattr(mrq, "build_index", wrong)
+    wk, idx = _small()
+    _fails(pins.test_eq3_decomposition_exact, wk, idx)
+
+
+def test_kmeans_update_not_averaged(monkeypatch):
+    def wrong(X, init, iters):
+        C = np.array(init, dtype=np.float64, copy=True)
+        for _ in range(iters):
+            a = mrq._assign(X, C)
+            sums = np.zeros_like(C)
+            np.add.at(sums, a, X)
+            C = sums                                       # forgot to divide by the count
+        return C, mrq._assign(X, C)
+    monkeypatch.setattr(mrq, "kmeans", wrong)
+    _fails(pins.test_kmeans_hand_example)
+
+
+def test_estimate_drops_query_tail_norm(monkeypatch):
+    orig = mrq.estimate_list
+
+    def wrong(idx, j, qd, g_j, qr2, sigma, eps0, m, qbits=0):
+        return orig(idx, j, qd, g_j, 0.0, sigma, eps0, m, qbits)   # |q_r|^2 of Eq. 4 dropped
+    monkeypatch.setattr(mrq, "estimate_list", wrong)
+    wk, idx = _small()
+    _fails(pins.test_bound_rate_and_multibit_accuracy, wk, idx)
+
+
+def test_threshold_from_too_few_upper_bounds(monkeypatch):
+    orig = mrq._kth
+
+    def wrong(values, k):
+        return orig(values, max(1, k // 4))                # tau_A from too few candidates
+    monkeypatch.setattr(mrq, "_kth", wrong)
+    wk, idx = _small()
+    _fails(pins.test_contract_thresholds_by_definition, wk, idx)
+
+
+def test_quantized_inner_product_offset_term_wrong(monkeypatch):
+    orig = mrq.quantize_query
+
+    def wrong(qprime, qbits):
+        qbar, lo, delta = orig(qprime, qbits)
+        return qbar, -lo, delta                             # sign of v_l flipped
+    monkeypatch.setattr(mrq, "quantize_query", wrong)
+    _fails(pins.test_quantize_query_golden_and_grid_identity)
