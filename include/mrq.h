@@ -152,6 +152,51 @@ int mrq_last_search_stats(const mrq_index* index, int64_t nq, int64_t* n_cand,
  * stream), and the number of kernels it launched.  stage_ms: MRQ_NSTAGES doubles. */
 int mrq_last_search_profile(const mrq_index* index, double* stage_ms, int64_t* launches);
 
+/* ---------------------------------------------------------------- serving
+ * Continuous batching: requests (one query each, with its own k and nprobe) are
+ * queued by mrq_submit; a scheduler thread groups pending requests with equal
+ * (k, nprobe), oldest first, and launches a group as one batch when one of
+ * max_inflight stream slots is free and the batch's scratch fits mem_budget
+ * (device bytes; one batch is always admitted); a group smaller than max_batch
+ * waits at most max_wait_us for more requests.  Batches run concurrently on
+ * their own streams.  The answer of every request equals a standalone mrq_search
+ * of that query with the same options.  The index must not be used by other
+ * calls while a server runs on it. */
+typedef struct mrq_server mrq_server;
+typedef struct {
+  size_t mem_budget;       /* device bytes for in-flight batches; default 8 GiB */
+  int max_batch;           /* queries per batch; default 4096 */
+  int max_inflight;        /* concurrently running batches (streams); default 4 */
+  int max_wait_us;         /* longest wait of a partial batch; default 300 */
+  int max_k;               /* largest k accepted; default 128 */
+  mrq_search_opts search;  /* eps0, m, mode, precision, query_bits, batched (stream ignored) */
+} mrq_server_opts;
+typedef struct {
+  int64_t completed, batches, pending;
+  double p50_us, p99_us, max_us;  /* submit-to-completion latency of completed requests */
+  double qps;                     /* completed requests per second since start / reset */
+} mrq_server_stats_t;
+
+void mrq_server_opts_default(mrq_server_opts* opt);
+int mrq_server_start(mrq_index* index, const mrq_server_opts* opt, mrq_server** out);
+/* Queue one query (D floats, host memory, copied); *ticket identifies the request. */
+int mrq_submit(mrq_server* server, const float* query, int k, int nprobe, uint64_t* ticket);
+/* Results of a ticket (k ids and dists, host memory).  Returns 0 and releases the
+ * ticket when done; 1 if still pending after waiting up to wait_ms milliseconds;
+ * a negative MRQ_E* code if its batch failed or the ticket is unknown. */
+int mrq_poll(mrq_server* server, uint64_t ticket, int64_t* ids, float* dists, int wait_ms);
+/* Bulk forms: n queries (n x D, host) with per-request k and nprobe; results of n
+ * tickets into n x kmax arrays (padded with -1 / +inf), status[i] = 0 done (ticket
+ * released), 1 pending, or a negative MRQ_E* code. */
+int mrq_submit_many(mrq_server* server, int64_t n, const float* queries, const int* k,
+                    const int* nprobe, uint64_t* tickets);
+int mrq_poll_many(mrq_server* server, int64_t n, const uint64_t* tickets, int kmax, int64_t* ids,
+                  float* dists, int32_t* status);
+int mrq_server_stats(mrq_server* server, mrq_server_stats_t* stats);
+int mrq_server_reset_stats(mrq_server* server);
+/* Finish queued and running batches, stop the scheduler, free the server. */
+int mrq_server_stop(mrq_server* server);
+
 /* Save / load the index file (format version 1, documented in the design doc). */
 int mrq_save(const mrq_index* index, const char* path);
 int mrq_load(const char* path, mrq_index** out);

@@ -28,6 +28,8 @@ EXPORTS = [
     "mrq_estimate", "mrq_project", "mrq_last_search_stats", "mrq_last_search_profile",
     "mrq_save", "mrq_load",
     "mrq_index_info", "mrq_index_export", "mrq_free", "mrq_last_error",
+    "mrq_server_opts_default", "mrq_server_start", "mrq_submit", "mrq_submit_many", "mrq_poll",
+    "mrq_poll_many", "mrq_server_stats", "mrq_server_reset_stats", "mrq_server_stop",
 ]
 
 
@@ -47,6 +49,17 @@ class SearchOpts(C.Structure):
     _fields_ = [("eps0", C.c_float), ("m", C.c_float), ("mode", C.c_int),
                 ("precision", C.c_int), ("query_bits", C.c_int), ("batched", C.c_int),
                 ("profile", C.c_int), ("graph", C.c_int), ("cuda_stream", C.c_void_p)]
+
+
+class ServerOpts(C.Structure):
+    _fields_ = [("mem_budget", C.c_size_t), ("max_batch", C.c_int), ("max_inflight", C.c_int),
+                ("max_wait_us", C.c_int), ("max_k", C.c_int), ("search", SearchOpts)]
+
+
+class ServerStats(C.Structure):
+    _fields_ = [("completed", C.c_int64), ("batches", C.c_int64), ("pending", C.c_int64),
+                ("p50_us", C.c_double), ("p99_us", C.c_double), ("max_us", C.c_double),
+                ("qps", C.c_double)]
 
 
 class IndexInfo(C.Structure):
@@ -73,10 +86,20 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
     lib.mrq_index_export.argtypes = [vp, C.c_char_p, vp, C.c_size_t]
     lib.mrq_free.argtypes = [vp]
     lib.mrq_free.restype = None
+    lib.mrq_server_opts_default.argtypes = [C.POINTER(ServerOpts)]
+    lib.mrq_server_opts_default.restype = None
+    lib.mrq_server_start.argtypes = [vp, C.POINTER(ServerOpts), C.POINTER(vp)]
+    lib.mrq_submit.argtypes = [vp, vp, i32, i32, vp]
+    lib.mrq_submit_many.argtypes = [vp, i64, vp, vp, vp, vp]
+    lib.mrq_poll.argtypes = [vp, C.c_uint64, vp, vp, i32]
+    lib.mrq_poll_many.argtypes = [vp, i64, vp, i32, vp, vp, vp]
+    lib.mrq_server_stats.argtypes = [vp, C.POINTER(ServerStats)]
+    lib.mrq_server_reset_stats.argtypes = [vp]
+    lib.mrq_server_stop.argtypes = [vp]
     lib.mrq_last_error.restype = C.c_char_p
     for name in EXPORTS:
         if name not in ("mrq_free", "mrq_last_error", "mrq_build_opts_default",
-                        "mrq_search_opts_default"):
+                        "mrq_search_opts_default", "mrq_server_opts_default"):
             getattr(lib, name).restype = C.c_int
     return lib
 
@@ -283,3 +306,80 @@ def mrq_free(index: Index) -> None:
 
 def mrq_last_error() -> str:
     return _lib.mrq_last_error().decode(errors="replace")
+
+
+# ------------------------------------------------------------------ serving
+
+class Server:
+    """Owning handle of an mrq_server (continuous batching over one index)."""
+
+    def __init__(self, index: Index, mem_budget: int | None = None, max_batch: int = 4096,
+                 max_inflight: int = 4, max_wait_us: int = 300, max_k: int = 128,
+                 search: SearchOpts | None = None):
+        o = ServerOpts()
+        _lib.mrq_server_opts_default(C.byref(o))
+        if mem_budget is not None:
+            o.mem_budget = mem_budget
+        o.max_batch, o.max_inflight, o.max_wait_us, o.max_k = max_batch, max_inflight, max_wait_us, max_k
+        if search is not None:
+            o.search = search
+        h = C.c_void_p()
+        _check(_lib.mrq_server_start(index.handle, C.byref(o), C.byref(h)))
+        self.index, self.handle, self.max_k, self.D = index, h, max_k, index.info().D
+
+    def submit(self, query, k: int, nprobe: int) -> int:
+        q = np.ascontiguousarray(query, dtype=np.float32)
+        t = C.c_uint64()
+        _check(_lib.mrq_submit(self.handle, _ptr(q), k, nprobe, C.byref(t)))
+        return t.value
+
+    def submit_many(self, queries, k, nprobe) -> np.ndarray:
+        q = np.ascontiguousarray(queries, dtype=np.float32)
+        n = q.shape[0]
+        ks = np.ascontiguousarray(np.broadcast_to(k, (n,)), dtype=np.int32)
+        ps = np.ascontiguousarray(np.broadcast_to(nprobe, (n,)), dtype=np.int32)
+        t = np.empty(n, dtype=np.uint64)
+        _check(_lib.mrq_submit_many(self.handle, n, _ptr(q), _ptr(ks), _ptr(ps), _ptr(t)))
+        return t
+
+    def poll(self, ticket: int, k: int, wait_ms: int = 0):
+        """(ids, dists) when done, else None."""
+        ids = np.empty(k, dtype=np.int64)
+        d = np.empty(k, dtype=np.float32)
+        rc = _lib.mrq_poll(self.handle, ticket, _ptr(ids), _ptr(d), wait_ms)
+        if rc == 1:
+            return None
+        _check(rc)
+        return ids, d
+
+    def poll_many(self, tickets, kmax: int):
+        t = np.ascontiguousarray(tickets, dtype=np.uint64)
+        n = t.shape[0]
+        ids = np.empty((n, kmax), dtype=np.int64)
+        d = np.empty((n, kmax), dtype=np.float32)
+        st = np.empty(n, dtype=np.int32)
+        _check(_lib.mrq_poll_many(self.handle, n, _ptr(t), kmax, _ptr(ids), _ptr(d), _ptr(st)))
+        return ids, d, st
+
+    def stats(self) -> dict:
+        s = ServerStats()
+        _check(_lib.mrq_server_stats(self.handle, C.byref(s)))
+        return {f: getattr(s, f) for f, _ in ServerStats._fields_}
+
+    def reset_stats(self) -> None:
+        _check(_lib.mrq_server_reset_stats(self.handle))
+
+    def stop(self) -> None:
+        if self.handle is not None and self.handle.value:
+            h, self.handle = self.handle, None
+            _check(_lib.mrq_server_stop(h))
+
+    def __del__(self):
+        try:
+            self.stop()
+        except Exception:
+            pass
+
+
+def mrq_server_start(index: Index, **kw) -> Server:
+    return Server(index, **kw)

@@ -79,6 +79,10 @@ std::vector<uint8_t> d2h_bytes(const T* dev, size_t count, cudaStream_t st) {
 
 }  // namespace
 
+namespace mrq {
+void set_last_error(const std::string& m) { g_err = m; }
+}  // namespace mrq
+
 // ===================================================================== ABI
 
 extern "C" {
@@ -178,7 +182,7 @@ int mrq_search(mrq_index* idx, const float* queries, int64_t nq, int k, int npro
     auto run_batches = [&](cudaStream_t s_) {
       for (int64_t s = 0; s < nq; s += qb) {
         const int64_t b = std::min(qb, nq - s);
-        mrq::search_batch(idx, queries + s * D, b, k, nprobe, o, ids + s * k, dists + s * k,
+        mrq::search_batch(idx, ws, queries + s * D, b, k, nprobe, o, ids + s * k, dists + s * k,
                           ws.stats.p + s * 3, s_);
       }
     };
@@ -231,7 +235,7 @@ int mrq_search(mrq_index* idx, const float* queries, int64_t nq, int k, int npro
       }
       int64_t* oi = odev ? ids + s * k : ws.oids.p;
       float* od = odev ? dists + s * k : ws.odist.p;
-      mrq::search_batch(idx, qp, b, k, nprobe, o, oi, od, ws.stats.p + s * 3, st);
+      mrq::search_batch(idx, ws, qp, b, k, nprobe, o, oi, od, ws.stats.p + s * 3, st);
       if (!odev) {
         MRQ_CUDA(cudaMemcpyAsync(ids + s * k, oi, 8 * b * k, cudaMemcpyDeviceToHost, st));
         MRQ_CUDA(cudaMemcpyAsync(dists + s * k, od, 4 * b * k, cudaMemcpyDeviceToHost, st));
@@ -284,7 +288,7 @@ int mrq_project(mrq_index* idx, const float* queries, int64_t nq, const mrq_sear
     }
     ws.qd.reserve((size_t)nq * d);
     ws.qr.reserve((size_t)nq * std::max(r, 1));
-    mrq::project_batch(idx, q, nq, o.precision, ws.qd.p, ws.qr.p, st);
+    mrq::project_batch(idx, ws, q, nq, o.precision, ws.qd.p, ws.qr.p, st);
     MRQ_CUDA(cudaMemcpy2DAsync(qp, 4 * D, ws.qd.p, 4 * d, 4 * d, nq, cudaMemcpyDefault, st));
     if (r > 0)
       MRQ_CUDA(cudaMemcpy2DAsync(qp + d, 4 * D, ws.qr.p, 4 * r, 4 * r, nq, cudaMemcpyDefault, st));

@@ -19,6 +19,7 @@ struct Error {
 };
 
 [[noreturn]] inline void fail(int code, const std::string& msg) { throw Error{code, msg}; }
+void set_last_error(const std::string& msg);  // message returned by mrq_last_error
 
 #define MRQ_CUDA(call)                                                                   \
   do {                                                                                   \
@@ -200,11 +201,15 @@ int probe_tc_topk(const float* qd, const float* qstat, const __nv_bfloat16* C2, 
                   unsigned long long* part, cudaStream_t st);
 
 // ---- search (search.cu) ----
-void search_batch(mrq_index* idx, const float* q_dev, int64_t nq, int k, int nprobe,
-                  const mrq_search_opts& o, int64_t* ids_dev, float* dists_dev,
+// One batch of the query path on stream st with scratch ws (one Workspace per
+// concurrently running batch); marks/launch counts go to idx.
+void search_batch(mrq_index* idx, Workspace& ws, const float* q_dev, int64_t nq, int k,
+                  int nprobe, const mrq_search_opts& o, int64_t* ids_dev, float* dists_dev,
                   int64_t* stats_dev, cudaStream_t st);
-void project_batch(mrq_index* idx, const float* q_dev, int64_t nq, int precision, float* qd,
-                   float* qr, cudaStream_t st);
+void project_batch(mrq_index* idx, Workspace& ws, const float* q_dev, int64_t nq, int precision,
+                   float* qd, float* qr, cudaStream_t st);
+// device bytes of scratch one batch of nq queries needs (for admission control)
+size_t batch_scratch_bytes(const mrq_index* idx, int64_t nq, int k, int nprobe);
 void estimate_one(mrq_index* idx, const float* qp_dev, int list, const mrq_search_opts& o,
                   float* ip, float* dis, float* lb, float* ub, int32_t* idot, cudaStream_t st);
 

@@ -147,8 +147,8 @@ struct TcArgs {
 
 constexpr int TC_PSEL = 16;  // largest nprobe selected inside the probe epilogue
 
-template <int BN, int PSEL>
-__global__ void __launch_bounds__(128, 1)
+template <int BN, int PSEL, int STAGES>
+__global__ void __launch_bounds__(256, 1)
     k_gemm_tc(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtensorMap tb,
               TcArgs P) {
   constexpr int A_BYTES = TC_BM * TC_BK * 2;
@@ -159,7 +159,7 @@ __global__ void __launch_bounds__(128, 1)
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                              ~static_cast<uintptr_t>(1023));
-  __shared__ __align__(8) uint64_t full[TC_STAGES], empty[TC_STAGES], done;
+  __shared__ __align__(8) uint64_t full[STAGES], empty[STAGES], done;
   __shared__ uint32_t tmem_slot;
   __shared__ volatile int s_abort;
 
@@ -170,7 +170,7 @@ __global__ void __launch_bounds__(128, 1)
 
   if (threadIdx.x == 0) {
     s_abort = 0;
-    for (int s = 0; s < TC_STAGES; ++s) {
+    for (int s = 0; s < STAGES; ++s) {
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 1);
     }
@@ -203,7 +203,7 @@ __global__ void __launch_bounds__(128, 1)
       mbar_expect_tx(&full[stage], STAGE);
       tma_load_2d(sa, &ta, k0, ay, &full[stage]);
       tma_load_2d(sa + A_BYTES, &tb, k0, by, &full[stage]);
-      if (++stage == TC_STAGES) { stage = 0; phase ^= 1u; }
+      if (++stage == STAGES) { stage = 0; phase ^= 1u; }
     }
   } else if (warp == 1 && lane == 0) {
     // MMA issuer
@@ -218,7 +218,7 @@ __global__ void __launch_bounds__(128, 1)
       for (int kk = 0; kk < TC_BK / 16; ++kk)
         tc_mma(tmem, ad + 2ull * kk, bd + 2ull * kk, IDESC, (kb | kk) != 0 ? 1u : 0u);
       tc_commit(&empty[stage]);
-      if (++stage == TC_STAGES) { stage = 0; phase ^= 1u; }
+      if (++stage == STAGES) { stage = 0; phase ^= 1u; }
     }
     if (ok) tc_commit(&done);
   }
@@ -230,11 +230,15 @@ __global__ void __launch_bounds__(128, 1)
   unsigned long long best[PSEL];
 #pragma unroll
   for (int t = 0; t < PSEL; ++t) best[t] = ~0ull;
+  // 8 warps drain the accumulator: warp w reads tensor-memory lanes 32*(w%4) .. +31
+  // (its rows) and the column half w/4 of the tile
+  const int quarter = warp & 3, half = warp >> 2;
+  constexpr int HALF = BN / 2;
   if (have) {
-    const int row = m0 + warp * 32 + lane;
-    for (int c = 0; c < BN; c += 32) {
+    const int row = m0 + quarter * 32 + lane;
+    for (int c = half * HALF; c < half * HALF + HALF; c += 32) {
       uint32_t r[32];
-      tc_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c, r);
+      tc_ld32(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)c, r);
       const int col0 = n0 + c;
       if (row >= P.M || col0 >= P.N) continue;
       if (P.epi == 0) {
@@ -304,7 +308,8 @@ __global__ void __launch_bounds__(128, 1)
       }
     }
     if (P.epi == 2 && row < P.M) {
-      unsigned long long* out = P.part + ((int64_t)row * gridDim.y + blockIdx.y) * P.nsel;
+      unsigned long long* out =
+          P.part + (((int64_t)row * gridDim.y + blockIdx.y) * 2 + half) * P.nsel;
 #pragma unroll
       for (int t = 0; t < PSEL; ++t)
         if (t < P.nsel) out[t] = best[t];  // constant indices keep best[] in registers
@@ -359,17 +364,17 @@ CUtensorMap make_map(const void* base, uint64_t rows, uint64_t K, uint32_t box_r
 
 int* g_err = nullptr;
 
-template <int BN, int PSEL>
+template <int BN, int PSEL, int STAGES>
 void launch_tc(const __nv_bfloat16* A2, const __nv_bfloat16* B2, const TcArgs& a, cudaStream_t st) {
   constexpr int STAGE = TC_BM * TC_BK * 2 + BN * TC_BK * 2;
-  const size_t smem = (size_t)TC_STAGES * STAGE + 1024;
+  const size_t smem = (size_t)STAGES * STAGE + 1024;
   const uint64_t arows = (uint64_t)a.M * (a.phases == 3 ? 2 : 1);
   const uint64_t brows = (uint64_t)a.N * (a.phases == 3 ? 2 : 1);
   CUtensorMap ta = make_map(A2, arows, a.K, TC_BM);
   CUtensorMap tb = make_map(B2, brows, a.K, BN);
-  MRQ_CUDA(cudaFuncSetAttribute(k_gemm_tc<BN, PSEL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  MRQ_CUDA(cudaFuncSetAttribute(k_gemm_tc<BN, PSEL, STAGES>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   dim3 grid(ceil_div(a.M, TC_BM), ceil_div(a.N, BN));
-  k_gemm_tc<BN, PSEL><<<grid, 128, smem, st>>>(ta, tb, a);
+  k_gemm_tc<BN, PSEL, STAGES><<<grid, 256, smem, st>>>(ta, tb, a);
   MRQ_CHECK_LAUNCH();
 }
 
@@ -379,22 +384,24 @@ void run_tc(const __nv_bfloat16* A2, const __nv_bfloat16* B2, TcArgs a, cudaStre
     MRQ_CUDA(cudaMemset(g_err, 0, sizeof(int)));
   }
   a.err = g_err;
-  // the fused top-nsel list is sized to nsel (registers, a divergent insertion per column)
-  if (a.epi == 2 && a.nsel > 4) {
-    if (a.nsel > 8) {
-      if (a.N <= 64) launch_tc<64, 16>(A2, B2, a, st);
-      else if (a.N <= 128) launch_tc<128, 16>(A2, B2, a, st);
-      else launch_tc<256, 16>(A2, B2, a, st);
-    } else {
-      if (a.N <= 64) launch_tc<64, 8>(A2, B2, a, st);
-      else if (a.N <= 128) launch_tc<128, 8>(A2, B2, a, st);
-      else launch_tc<256, 8>(A2, B2, a, st);
-    }
+  // the fused top-nsel list is sized to nsel (registers, a divergent insertion per column);
+  // short contractions (the probe: K = d) use a 2-stage ring so that two CTAs fit per SM
+  const bool short_k = (int64_t)((a.K + TC_BK - 1) / TC_BK) * a.phases <= 2;
+#define MRQ_TC_N(PS, ST)                                  \
+  do {                                                    \
+    if (a.N <= 64) launch_tc<64, PS, ST>(A2, B2, a, st);  \
+    else if (a.N <= 128) launch_tc<128, PS, ST>(A2, B2, a, st); \
+    else launch_tc<256, PS, ST>(A2, B2, a, st);           \
+  } while (0)
+  if (a.epi == 2) {
+    if (a.nsel > 8) { if (short_k) MRQ_TC_N(16, 2); else MRQ_TC_N(16, 4); }
+    else if (a.nsel > 4) { if (short_k) MRQ_TC_N(8, 2); else MRQ_TC_N(8, 4); }
+    else { if (short_k) MRQ_TC_N(4, 2); else MRQ_TC_N(4, 4); }
     return;
   }
-  if (a.N <= 64) launch_tc<64, 4>(A2, B2, a, st);
-  else if (a.N <= 128) launch_tc<128, 4>(A2, B2, a, st);
-  else launch_tc<256, 4>(A2, B2, a, st);
+  if (short_k) MRQ_TC_N(4, 2);
+  else MRQ_TC_N(4, 4);
+#undef MRQ_TC_N
 }
 
 }  // namespace
@@ -465,7 +472,7 @@ int probe_tc_topk(const float* qd, const float* qstat, const __nv_bfloat16* C2, 
   a.nsel = nsel;
   run_tc(qbf, C2, a, st);
   const int bn = nlist <= 64 ? 64 : nlist <= 128 ? 128 : 256;
-  return ceil_div(nlist, bn);  // column tiles
+  return 2 * ceil_div(nlist, bn);  // candidate lists per row: column tiles x 2 halves
 }
 
 }  // namespace mrq

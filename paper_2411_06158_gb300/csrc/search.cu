@@ -262,7 +262,7 @@ __global__ void __launch_bounds__(PS_NT) k_probe_select(const float* __restrict_
 // tiles x nprobe (key, list) pairs, ascending
 __global__ void k_probe_merge(const unsigned long long* __restrict__ part, int64_t nq, int tiles,
                               int nprobe, int32_t* __restrict__ plist) {
-  __shared__ unsigned long long buf_all[8][256];
+  __shared__ unsigned long long buf_all[8][512];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int64_t q = (int64_t)blockIdx.x * 8 + wid;
   if (q >= nq) return;
@@ -1342,16 +1342,16 @@ static void mark(mrq_index* idx, int s, cudaStream_t st) {
   MRQ_CUDA(cudaEventRecord(idx->prof_ev[i], st));
 }
 
-void project_batch(mrq_index* idx, const float* q, int64_t nq, int precision, float* qd, float* qr,
-                   cudaStream_t st) {
+void project_batch(mrq_index* idx, Workspace& ws, const float* q, int64_t nq, int precision,
+                   float* qd, float* qr, cudaStream_t st) {
   const int D = idx->D, d = idx->d, r = D - d;
   if (precision == MRQ_PREC_FP32) {
     gemm_nt_f32(q, D, idx->mu.p, idx->W.p, D, (int)nq, D, D, qd, d, qr, r, d, st);
   } else {
     MRQ_REQUIRE(tc_available(), "tensor-core projection needs an sm_103 device");
-    idx->ws.qbf.reserve((size_t)nq * D * 2);
+    ws.qbf.reserve((size_t)nq * D * 2);
     project_tc(q, idx->mu.p, idx->W2.p, (int)nq, D, d, precision == MRQ_PREC_BF16X3,
-               idx->ws.qbf.p, qd, qr, st);
+               ws.qbf.p, qd, qr, st);
   }
 }
 
@@ -1361,10 +1361,9 @@ static void qstats(mrq_index* idx, const float* qd, const float* qr, int64_t nq,
   MRQ_CHECK_LAUNCH();
 }
 
-void search_batch(mrq_index* idx, const float* q, int64_t nq, int k, int nprobe,
+void search_batch(mrq_index* idx, Workspace& ws, const float* q, int64_t nq, int k, int nprobe,
                   const mrq_search_opts& o, int64_t* out_ids, float* out_d, int64_t* stats,
                   cudaStream_t st) {
-  auto& ws = idx->ws;
   const int D = idx->D, d = idx->d, r = D - d, nlist = idx->nlist;
   const int64_t cap = std::max<int64_t>(idx->cap_by_nprobe[nprobe], 1);
   ws.qd.reserve((size_t)nq * d);
@@ -1386,15 +1385,16 @@ void search_batch(mrq_index* idx, const float* q, int64_t nq, int k, int nprobe,
 
   // 1-2. projection and query statistics
   mark(idx, MRQ_STAGE_PROJECT, st);
-  project_batch(idx, q, nq, o.precision, ws.qd.p, ws.qr.p, st);
+  project_batch(idx, ws, q, nq, o.precision, ws.qd.p, ws.qr.p, st);
   idx->launches += o.precision == MRQ_PREC_FP32 ? 1 : 2;
   mark(idx, MRQ_STAGE_QSTATS, st);
   qstats(idx, ws.qd.p, ws.qr.p, nq, ws.qstat.p, st);
   // 3. probe
   mark(idx, MRQ_STAGE_PROBE, st);
-  const int tiles_ = nlist <= 64 ? 1 : nlist <= 128 ? 1 : ceil_div(nlist, 256);
+  // the fused probe emits nprobe candidates per (column tile, half tile) of each row
+  const int tiles_ = 2 * (nlist <= 64 ? 1 : nlist <= 128 ? 1 : ceil_div(nlist, 256));
   const bool fused = o.precision != MRQ_PREC_FP32 && d >= 64 && nprobe <= 16 &&
-                     (int64_t)tiles_ * nprobe <= 256;
+                     (int64_t)tiles_ * nprobe <= 512;
   if (fused) {
     ws.qbf.reserve((size_t)nq * D * 2);
     ws.ppart.reserve((size_t)nq * tiles_ * nprobe);
@@ -1584,6 +1584,14 @@ void search_batch(mrq_index* idx, const float* q, int64_t nq, int k, int nprobe,
   mark(idx, MRQ_NSTAGES, st);
   if (idx->prof_on) idx->prof_batches++;
   idx->launches += 7;  // qstats, probe distances, select, refine, scan init, scan, finalize
+}
+
+size_t batch_scratch_bytes(const mrq_index* idx, int64_t nq, int k, int nprobe) {
+  const int64_t D = idx->D, d = idx->d;
+  const int64_t cap = std::max<int64_t>(idx->cap_by_nprobe[nprobe], 1);
+  const int64_t per_q = D * 4 * 2 + D * 4 /* bf16 hi+lo */ + 16 + (int64_t)idx->nlist * 4 +
+                        nprobe * (8 + 32 + 8 * (d / 32) * 4 + 16 * 8) + 16 + cap * 24 + k * 12 + 24;
+  return (size_t)(nq * per_q) + (size_t)idx->nlist * 16 + (1 << 20);
 }
 
 void estimate_one(mrq_index* idx, const float* qp, int list, const mrq_search_opts& o, float* ip,

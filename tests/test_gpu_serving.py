@@ -1,0 +1,78 @@
+"""Serving form: continuous batching of requests with mixed k and nprobe.  Every
+answer must equal a standalone mrq_search of the same query (the thresholds do
+not depend on batch composition), whether it ran alone or in the mix."""
+import time
+
+import numpy as np
+import pytest
+
+import datagen
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+import paper_2411_06158_gb300 as mrq  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def index():
+    w = datagen.workload("small", n=30_000, nlist=96, n_query=600)
+    base, queries = datagen.base_and_queries(w)
+    return w, queries, mrq.mrq_build(base, w.d, w.bits, w.nlist, mrq.mrq_build_opts(seed=5))
+
+
+@pytest.mark.parametrize("form", [dict(query_bits=0), dict(query_bits=4, batched=1)])
+def test_mixed_requests_match_standalone_search(index, form):
+    w, queries, idx = index
+    rng = np.random.default_rng(0)
+    ks = rng.choice([1, 10, 50, 100], size=len(queries)).astype(np.int32)
+    nps = rng.choice([2, 8, 32], size=len(queries)).astype(np.int32)
+    opts = mrq.mrq_search_opts(**form)
+    srv = mrq.Server(idx, max_batch=64, max_inflight=3, max_wait_us=200, max_k=100, search=opts)
+    try:
+        tickets = []
+        for a in range(0, len(queries), 50):        # arrivals in waves while batches run
+            tickets.extend(srv.submit_many(queries[a:a + 50], ks[a:a + 50], nps[a:a + 50]).tolist())
+            time.sleep(0.0005)
+        lone = srv.submit(queries[7], int(ks[7]), int(nps[7]))   # the same query again, alone
+        got, deadline = {}, time.time() + 60
+        while len(got) < len(tickets) and time.time() < deadline:
+            open_t = [t for t in tickets if t not in got]
+            ids, dists, st = srv.poll_many(open_t, 100)
+            for i, t in enumerate(open_t):
+                assert st[i] in (0, 1)
+                if st[i] == 0:
+                    got[t] = (ids[i], dists[i])
+            time.sleep(0.001)
+        # a released ticket is no longer known
+        assert srv.poll_many(tickets[:1], 100)[2][0] == mrq.MRQ_EINVAL
+        assert len(got) == len(tickets)
+        alone = srv.poll(lone, int(ks[7]), wait_ms=10_000)
+        assert alone is not None
+        stats = srv.stats()
+        assert stats["completed"] == len(tickets) + 1 and stats["p99_us"] >= stats["p50_us"] > 0
+        assert stats["batches"] >= 9            # nine (k, nprobe) groups at least
+    finally:
+        srv.stop()
+    for i, t in enumerate(tickets):
+        k = int(ks[i])
+        ref_i, ref_d = mrq.mrq_search(idx, queries[i:i + 1], k, int(nps[i]), opts)
+        np.testing.assert_array_equal(got[t][0][:k], ref_i[0])
+        np.testing.assert_array_equal(got[t][1][:k], ref_d[0])
+    np.testing.assert_array_equal(alone[0], got[tickets[7]][0][:int(ks[7])])
+
+
+def test_bad_requests_are_rejected(index):
+    w, queries, idx = index
+    srv = mrq.Server(idx, max_k=16)
+    try:
+        with pytest.raises(mrq.MRQError):
+            srv.submit(queries[0], 17, 4)                       # k above max_k
+        with pytest.raises(mrq.MRQError):
+            srv.submit(queries[0], 5, w.nlist + 1)              # nprobe above nlist
+        with pytest.raises(mrq.MRQError):
+            srv.poll(123456, 5)                                  # unknown ticket
+    finally:
+        srv.stop()
