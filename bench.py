@@ -49,6 +49,11 @@ def parse_args(argv=None):
     p.add_argument("--nprobe", type=int, default=None, help="fixed nprobe: skip calibration")
     p.add_argument("--m", type=float, default=None, help="fixed m with --nprobe")
     p.add_argument("--eps0", type=float, default=None, help="fixed eps0 with --nprobe")
+    p.add_argument("--serve", action="store_true",
+                   help="serving form: Poisson arrivals at swept rates, p50/p99 latency")
+    p.add_argument("--rates", default="20000,100000,500000,2000000",
+                   help="arrival rates (queries/s) for --serve")
+    p.add_argument("--serve-seconds", type=float, default=2.0, help="arrival window per rate")
     return p.parse_args(argv)
 
 
@@ -118,6 +123,17 @@ class ClockSampler:
         sm.sort()
         return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": mx, "reasons": sorted(reasons),
                 "samples": len(sm)}
+
+
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of kernels
+# captured with ncu at the calibrated GIST-like configuration; see
+# profiles/dram_gist-1M-d960_batched-bf16_nprobe3.md.  Used only when the timed
+# run matches that configuration exactly.
+NCU_TRAFFIC = {
+    ("k_fin_exact", "gist-like-1M-d960", "batched_bf16_q4", 3, 1.0, 1.0): 1559690752,
+    ("k_fin_stage2", "gist-like-1M-d960", "batched_bf16_q4", 3, 1.0, 1.0): 523316736,
+    ("k_scan", "gist-like-1M-d960", "batched_bf16_q4", 3, 1.0, 1.0): 41714432,
+}
 
 
 # ------------------------------------------------------------ multi-rank
@@ -255,12 +271,86 @@ def run_reference(args):
     return 0
 
 
+# ----------------------------------------------------------- serving form
+
+def run_serving(args):
+    """Serving form: requests arrive as a Poisson process; each draws k from
+    {10, 50, 100} and nprobe from a ladder; the library's continuous-batching
+    server admits them.  One JSON line per arrival rate: throughput, p50/p99
+    submit-to-completion latency, recall@10 of the k = 10 requests."""
+    import numpy as np
+    import torch
+
+    import datagen
+    import paper_2411_06158_gb300 as mrq
+
+    over = {"n": args.n or 1_000_000, "n_query": args.nq or 20_000}
+    if args.d:
+        over["d"] = args.d
+    if args.bits:
+        over["bits"] = args.bits
+    w = datagen.workload("serve" if args.workload == "gist" else args.workload, **over)
+    dev = torch.device("cuda", 0)
+    base, queries = datagen.base_and_queries(w)
+    base_t = torch.from_numpy(base).to(dev)
+    idx = mrq.mrq_build(base_t, w.d, w.bits, w.nlist, mrq.mrq_build_opts(seed=w.seed("method")))
+    truth = ground_truth(base_t, torch.from_numpy(queries).to(dev), 10)
+    del base_t
+    torch.cuda.empty_cache()
+    rng = np.random.default_rng(7)
+    ks = rng.choice([10, 50, 100], size=w.n_query).astype(np.int32)
+    nprobes = np.array([8, 16, 32], dtype=np.int32)
+    nps = rng.choice(nprobes, size=w.n_query).astype(np.int32)
+    search = mrq.mrq_search_opts(eps0=1.9, m=4.0, query_bits=4, precision=mrq.PREC_BF16, batched=1)
+    for rate in [float(x) for x in args.rates.split(",")]:
+        srv = mrq.Server(idx, max_batch=4096, max_inflight=4, max_wait_us=200, max_k=100,
+                         search=search)
+        n = min(w.n_query, max(1, int(rate * args.serve_seconds)))
+        arrive = np.cumsum(rng.exponential(1.0 / rate, size=n))
+        tickets = np.zeros(n, dtype=np.uint64)
+        t0 = time.perf_counter()
+        sent = 0
+        while sent < n:
+            now = time.perf_counter() - t0
+            upto = int(np.searchsorted(arrive, now, side="right"))
+            if upto > sent:
+                tickets[sent:upto] = srv.submit_many(queries[sent:upto], ks[sent:upto], nps[sent:upto])
+                sent = upto
+            else:
+                time.sleep(min(0.0002, max(0.0, arrive[sent] - now)))
+        got = {}
+        deadline = time.perf_counter() + 120
+        open_idx = np.arange(n)
+        res_ids = np.full((n, 100), -1, dtype=np.int64)
+        while open_idx.size and time.perf_counter() < deadline:
+            ids, _, st = srv.poll_many(tickets[open_idx], 100)
+            done = st == 0
+            res_ids[open_idx[done]] = ids[done]
+            open_idx = open_idx[~done]
+            if open_idx.size:
+                time.sleep(0.001)
+        stats = srv.stats()
+        srv.stop()
+        sel = np.nonzero(ks[:n] == 10)[0]
+        rec = recall(res_ids[sel, :10], truth[sel]) if sel.size else None
+        print(json.dumps({"metric": "serving latency", "rate_qps": rate, "requests": int(n),
+                          "completed": stats["completed"], "throughput_qps": stats["qps"],
+                          "p50_ms": stats["p50_us"] / 1000.0, "p99_ms": stats["p99_us"] / 1000.0,
+                          "max_ms": stats["max_us"] / 1000.0, "batches": stats["batches"],
+                          "recall@10_k10": rec, "workload": w.name, "n": w.n, "D": w.D,
+                          "d": w.d, "bits": w.bits, "nlist": w.nlist,
+                          "k_choices": [10, 50, 100], "nprobe_choices": nprobes.tolist()}))
+    return 0
+
+
 # --------------------------------------------------------------- GPU arm
 
 def main(argv=None):
     args = parse_args(argv)
     if args.impl == "reference":
         return run_reference(args)
+    if args.serve:
+        return run_serving(args)
     import numpy as np
     import torch
 
@@ -444,8 +534,10 @@ def main(argv=None):
     launch_ms = B["stage_ms"][dom] / n_batches
     alg_bytes = bpq * w.n_query / n_batches
     achieved = alg_bytes / (launch_ms / 1000.0) / 1e9
+    tkey = (kname, w.name, best, B["nprobe"], round(B["m"], 3), round(B["eps0"], 3))
+    traffic = NCU_TRAFFIC.get(tkey) if w.n_query == 10_000 else None
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-            "frac": achieved / peak, "traffic": None, "kernel": kname,
+            "frac": achieved / peak, "traffic": traffic, "kernel": kname,
             "peak_kind": peak_kind, "algorithmic_bytes_per_launch": alg_bytes,
             "launch_ms": launch_ms,
             "others": {s_: {"kernel": per_q[s_][0],

@@ -236,4 +236,10 @@ __host__ __device__ inline float fkey_inv(uint32_t k) {
 
 inline int ceil_div(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
 
+// Raise a kernel's dynamic shared-memory limit only when a launch needs more than
+// already granted (host-side cache per kernel; avoids one driver call per launch).
+void ensure_smem(const void* kernel, size_t bytes);
+// Resident CTAs per SM of a kernel at a block size / shared-memory size (cached).
+int occupancy(const void* kernel, int threads, size_t smem);
+
 }  // namespace mrq

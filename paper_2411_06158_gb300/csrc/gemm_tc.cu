@@ -372,7 +372,7 @@ void launch_tc(const __nv_bfloat16* A2, const __nv_bfloat16* B2, const TcArgs& a
   const uint64_t brows = (uint64_t)a.N * (a.phases == 3 ? 2 : 1);
   CUtensorMap ta = make_map(A2, arows, a.K, TC_BM);
   CUtensorMap tb = make_map(B2, brows, a.K, BN);
-  MRQ_CUDA(cudaFuncSetAttribute(k_gemm_tc<BN, PSEL, STAGES>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  ensure_smem((const void*)k_gemm_tc<BN, PSEL, STAGES>, smem);
   dim3 grid(ceil_div(a.M, TC_BM), ceil_div(a.N, BN));
   k_gemm_tc<BN, PSEL, STAGES><<<grid, 256, smem, st>>>(ta, tb, a);
   MRQ_CHECK_LAUNCH();

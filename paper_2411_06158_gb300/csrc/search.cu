@@ -18,6 +18,10 @@
 
 #include <algorithm>
 #include <cfloat>
+#include <map>
+#include <mutex>
+#include <tuple>
+#include <unordered_map>
 
 #include "common.cuh"
 
@@ -1076,9 +1080,9 @@ __device__ __forceinline__ int warp_compact(const int32_t* src, int M, int32_t* 
 }
 
 constexpr int FW_WARPS = 8;   // queries per CTA in the per-query warp phases
-constexpr int FW_BUF = 128;   // per-warp (distance, id) sort buffer: k <= 64 plus ties
+constexpr int FW_BUF = 128;   // per-warp (distance, id) sort buffer: up to k = 128 entries
 
-// Phased finalize (k <= 64).  Selection/compaction phases run one warp per query
+// Phased finalize (k <= 128).  Selection/compaction phases run one warp per query
 // and never synchronise a block; gather phases run one CTA (8 independent warps)
 // per query, each lane prefetching one candidate's position per batch of 32.
 
@@ -1289,14 +1293,12 @@ int num_sms() {
 template <int KM, bool QUANT, bool DBG>
 void launch_scan_t(const ScanParams& p, int64_t grid_warps, size_t smem, cudaStream_t st) {
   auto kern = k_scan<KM, QUANT, DBG>;
-  MRQ_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  ensure_smem((const void*)kern, smem);
   int blocks;
   if (DBG) {
     blocks = 1;
   } else {
-    int per_sm = 0;
-    MRQ_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, SCAN_WARPS * 32, smem));
-    per_sm = std::max(per_sm, 1);
+    const int per_sm = occupancy((const void*)kern, SCAN_WARPS * 32, smem);
     int64_t want = (grid_warps + SCAN_WARPS - 1) / SCAN_WARPS;
     blocks = (int)std::min<int64_t>(want, (int64_t)num_sms() * per_sm);
     blocks = std::max(blocks, 1);
@@ -1329,6 +1331,34 @@ void launch_scan(const ScanParams& p, int64_t npairs, cudaStream_t st, bool dbg)
 }  // namespace
 
 // ---------------------------------------------------------------- host side
+
+void ensure_smem(const void* kernel, size_t bytes) {
+  static std::mutex mu;
+  static std::map<std::pair<int, const void*>, size_t> granted;
+  int dev = 0;
+  MRQ_CUDA(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lk(mu);
+  size_t& g = granted[std::make_pair(dev, kernel)];
+  if (bytes > g) {
+    MRQ_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+    g = bytes;
+  }
+}
+
+int occupancy(const void* kernel, int threads, size_t smem) {
+  static std::mutex mu;
+  static std::map<std::tuple<int, const void*, int, size_t>, int> cache;
+  int dev = 0;
+  MRQ_CUDA(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lk(mu);
+  auto key = std::make_tuple(dev, kernel, threads, smem);
+  auto it = cache.find(key);
+  if (it != cache.end()) return it->second;
+  int per_sm = 0;
+  MRQ_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem));
+  cache[key] = std::max(per_sm, 1);
+  return cache[key];
+}
 
 // CUDA event at a stage boundary of the current batch (profiled searches only)
 static void mark(mrq_index* idx, int s, cudaStream_t st) {
@@ -1426,7 +1456,7 @@ void search_batch(mrq_index* idx, Workspace& ws, const float* q, int64_t nq, int
     cap = c2;
     const int in_smem = (size_t)cap * 8 + (size_t)nlist * 4 <= 160 * 1024 ? 1 : 0;
     size_t sm = (size_t)cap * 8 + (in_smem ? (size_t)nlist * 4 : 0);
-    MRQ_CUDA(cudaFuncSetAttribute(k_probe_select, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    ensure_smem((const void*)k_probe_select, sm);
     k_probe_select<<<(unsigned)nq, PS_NT, sm, st>>>(ws.gmat.p, nlist, nprobe, cap, in_smem,
                                                     ws.plist.p, ws.pg.p);
     MRQ_CHECK_LAUNCH();
@@ -1500,9 +1530,7 @@ void search_batch(mrq_index* idx, Workspace& ws, const float* q, int64_t nq, int
     bp.work = ws.work.p; bp.qcnt = ws.qcnt.p; bp.gtau = ws.gtau.p;
     bp.spos = ws.spos.p; bp.slb = ws.slb.p; bp.sub = ws.sub.p;
     auto launch = [&](auto kern) {
-      int per_sm = 0;
-      MRQ_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, 0));
-      kern<<<num_sms() * std::max(per_sm, 1), 256, 0, st>>>(bp);
+      kern<<<num_sms() * occupancy((const void*)kern, 256, 0), 256, 0, st>>>(bp);
     };
     const int nch_ = d / 32, bits_ = idx->bits;
 #define MRQ_BATCH(Wv, Nv) \
@@ -1550,7 +1578,7 @@ void search_batch(mrq_index* idx, Workspace& ws, const float* q, int64_t nq, int
   fp.m = o.m; fp.cap = cap; fp.qcnt = ws.qcnt.p; fp.spos = ws.spos.p; fp.slb = ws.slb.p;
   fp.sub = ws.sub.p; fp.s2pos = ws.s2pos.p; fp.s2a = ws.s2a.p; fp.s2b = ws.s2b.p;
   fp.out_ids = out_ids; fp.out_d = out_d; fp.stats = stats;
-  if (k <= 64) {
+  if (k <= FW_BUF) {  // phased finalize: the per-warp sort buffer holds next_pow2(k) entries
     ws.qtau.reserve(nq);
     ws.qm1.reserve(nq);
     ws.qm2.reserve(nq);
@@ -1568,7 +1596,7 @@ void search_batch(mrq_index* idx, Workspace& ws, const float* q, int64_t nq, int
     MRQ_CHECK_LAUNCH();
     mark(idx, MRQ_STAGE_EXACT, st);
     const size_t esm = (size_t)(((d + 3) & ~3) + r) * 4;
-    MRQ_CUDA(cudaFuncSetAttribute(k_fin_exact, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)esm));
+    ensure_smem((const void*)k_fin_exact, esm);
     k_fin_exact<<<(unsigned)nq, 256, esm, st>>>(fp);
     MRQ_CHECK_LAUNCH();
     mark(idx, MRQ_STAGE_TOPK, st);
@@ -1576,7 +1604,7 @@ void search_batch(mrq_index* idx, Workspace& ws, const float* q, int64_t nq, int
     idx->launches += o.mode == MRQ_MODE_MRQ_PLUS ? 4 : 3;
   } else {
     size_t fsm = (size_t)((((d + 3) & ~3) + r + 3) & ~3) * sizeof(float) + FN_SORT * 8;
-    MRQ_CUDA(cudaFuncSetAttribute(k_finalize, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsm));
+    ensure_smem((const void*)k_finalize, fsm);
     k_finalize<<<(unsigned)nq, FN_NT, fsm, st>>>(fp);
     for (int sidx = MRQ_STAGE_STAGE2; sidx <= MRQ_STAGE_TOPK; ++sidx) mark(idx, sidx, st);
   }
