@@ -40,6 +40,7 @@ def parse_args(argv=None):
     p.add_argument("--n", type=int, default=None, help="override base size (quick runs)")
     p.add_argument("--nq", type=int, default=None, help="override query count")
     p.add_argument("--d", type=int, default=None)
+    p.add_argument("--D", type=int, default=None, help="override the dimension (scan roofline runs)")
     p.add_argument("--bits", type=int, default=None)
     p.add_argument("--nlist", type=int, default=None)
     p.add_argument("--recall", type=float, default=0.95)
@@ -54,6 +55,8 @@ def parse_args(argv=None):
     p.add_argument("--rates", default="20000,100000,500000,2000000",
                    help="arrival rates (queries/s) for --serve")
     p.add_argument("--serve-seconds", type=float, default=2.0, help="arrival window per rate")
+    p.add_argument("--serve-slots", type=int, default=4, help="concurrent batches (streams)")
+    p.add_argument("--serve-wait-us", type=int, default=200, help="longest wait of a partial batch")
     return p.parse_args(argv)
 
 
@@ -61,7 +64,7 @@ def workload_of(args):
     import datagen
     over = {}
     for key, val in (("n", args.n), ("n_query", args.nq), ("d", args.d), ("bits", args.bits),
-                     ("nlist", args.nlist)):
+                     ("nlist", args.nlist), ("D", args.D)):
         if val is not None:
             over[key] = val
     return datagen.workload(args.workload, **over)
@@ -156,10 +159,12 @@ def whole_job_qps(queries_per_rank: int, world: int, ms_max: float) -> float:
 
 # ----------------------------------------------------------- ground truth
 
-def ground_truth(base_t, q_t, k, chunk=1024):
+def ground_truth(base_t, q_t, k, chunk=None):
     """Exact k-NN (evaluation only): float32 distances pick 32 spare candidates,
     float64 recomputation orders them."""
     import torch
+    if chunk is None:  # keep the chunk's distance matrix near 4 GB
+        chunk = max(16, min(1024, int(1e9 // max(1, base_t.shape[0]))))
     with torch.no_grad():
         prev = torch.backends.cuda.matmul.allow_tf32
         torch.backends.cuda.matmul.allow_tf32 = False
@@ -303,8 +308,8 @@ def run_serving(args):
     nps = rng.choice(nprobes, size=w.n_query).astype(np.int32)
     search = mrq.mrq_search_opts(eps0=1.9, m=4.0, query_bits=4, precision=mrq.PREC_BF16, batched=1)
     for rate in [float(x) for x in args.rates.split(",")]:
-        srv = mrq.Server(idx, max_batch=4096, max_inflight=4, max_wait_us=200, max_k=100,
-                         search=search)
+        srv = mrq.Server(idx, max_batch=4096, max_inflight=args.serve_slots,
+                         max_wait_us=args.serve_wait_us, max_k=100, search=search)
         n = min(w.n_query, max(1, int(rate * args.serve_seconds)))
         arrive = np.cumsum(rng.exponential(1.0 / rate, size=n))
         tickets = np.zeros(n, dtype=np.uint64)
@@ -318,16 +323,16 @@ def run_serving(args):
                 sent = upto
             else:
                 time.sleep(min(0.0002, max(0.0, arrive[sent] - now)))
-        got = {}
         deadline = time.perf_counter() + 120
-        open_idx = np.arange(n)
         res_ids = np.full((n, 100), -1, dtype=np.int64)
-        while open_idx.size and time.perf_counter() < deadline:
-            ids, _, st = srv.poll_many(tickets[open_idx], 100)
-            done = st == 0
-            res_ids[open_idx[done]] = ids[done]
-            open_idx = open_idx[~done]
-            if open_idx.size:
+        pos = {int(t): i for i, t in enumerate(tickets.tolist())}
+        left = n
+        while left and time.perf_counter() < deadline:
+            tk, ids, _, st = srv.poll_completed(65536, 100)
+            for t_, row in zip(tk.tolist(), ids):
+                res_ids[pos[t_]] = row
+            left -= len(tk)
+            if left and not len(tk):
                 time.sleep(0.001)
         stats = srv.stats()
         srv.stop()
@@ -337,6 +342,7 @@ def run_serving(args):
                           "completed": stats["completed"], "throughput_qps": stats["qps"],
                           "p50_ms": stats["p50_us"] / 1000.0, "p99_ms": stats["p99_us"] / 1000.0,
                           "max_ms": stats["max_us"] / 1000.0, "batches": stats["batches"],
+                          "slots": args.serve_slots, "max_wait_us": args.serve_wait_us,
                           "recall@10_k10": rec, "workload": w.name, "n": w.n, "D": w.D,
                           "d": w.d, "bits": w.bits, "nlist": w.nlist,
                           "k_choices": [10, 50, 100], "nprobe_choices": nprobes.tolist()}))

@@ -192,6 +192,11 @@ int mrq_submit_many(mrq_server* server, int64_t n, const float* queries, const i
                     const int* nprobe, uint64_t* tickets);
 int mrq_poll_many(mrq_server* server, int64_t n, const uint64_t* tickets, int kmax, int64_t* ids,
                   float* dists, int32_t* status);
+/* Up to max_n completed requests in completion order (their tickets, results into
+ * max_n x kmax arrays, status 0 or a negative MRQ_E* code), released; returns how
+ * many (>= 0) or a negative MRQ_E* code. */
+int64_t mrq_poll_completed(mrq_server* server, int64_t max_n, int kmax, uint64_t* tickets,
+                           int64_t* ids, float* dists, int32_t* status);
 int mrq_server_stats(mrq_server* server, mrq_server_stats_t* stats);
 int mrq_server_reset_stats(mrq_server* server);
 /* Finish queued and running batches, stop the scheduler, free the server. */

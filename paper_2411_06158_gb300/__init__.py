@@ -29,7 +29,8 @@ EXPORTS = [
     "mrq_save", "mrq_load",
     "mrq_index_info", "mrq_index_export", "mrq_free", "mrq_last_error",
     "mrq_server_opts_default", "mrq_server_start", "mrq_submit", "mrq_submit_many", "mrq_poll",
-    "mrq_poll_many", "mrq_server_stats", "mrq_server_reset_stats", "mrq_server_stop",
+    "mrq_poll_many", "mrq_poll_completed", "mrq_server_stats", "mrq_server_reset_stats",
+    "mrq_server_stop",
 ]
 
 
@@ -93,6 +94,7 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
     lib.mrq_submit_many.argtypes = [vp, i64, vp, vp, vp, vp]
     lib.mrq_poll.argtypes = [vp, C.c_uint64, vp, vp, i32]
     lib.mrq_poll_many.argtypes = [vp, i64, vp, i32, vp, vp, vp]
+    lib.mrq_poll_completed.argtypes = [vp, i64, i32, vp, vp, vp, vp]
     lib.mrq_server_stats.argtypes = [vp, C.POINTER(ServerStats)]
     lib.mrq_server_reset_stats.argtypes = [vp]
     lib.mrq_server_stop.argtypes = [vp]
@@ -101,6 +103,7 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
         if name not in ("mrq_free", "mrq_last_error", "mrq_build_opts_default",
                         "mrq_search_opts_default", "mrq_server_opts_default"):
             getattr(lib, name).restype = C.c_int
+    lib.mrq_poll_completed.restype = C.c_int64
     return lib
 
 
@@ -360,6 +363,17 @@ class Server:
         st = np.empty(n, dtype=np.int32)
         _check(_lib.mrq_poll_many(self.handle, n, _ptr(t), kmax, _ptr(ids), _ptr(d), _ptr(st)))
         return ids, d, st
+
+    def poll_completed(self, max_n: int, kmax: int):
+        """(tickets, ids, dists, status) of up to max_n completed requests, released."""
+        t = np.empty(max_n, dtype=np.uint64)
+        ids = np.empty((max_n, kmax), dtype=np.int64)
+        d = np.empty((max_n, kmax), dtype=np.float32)
+        st = np.empty(max_n, dtype=np.int32)
+        n = _lib.mrq_poll_completed(self.handle, max_n, kmax, _ptr(t), _ptr(ids), _ptr(d), _ptr(st))
+        if n < 0:
+            _check(int(n))
+        return t[:n], ids[:n], d[:n], st[:n]
 
     def stats(self) -> dict:
         s = ServerStats()

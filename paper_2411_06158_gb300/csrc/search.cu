@@ -505,7 +505,13 @@ __global__ void __launch_bounds__(SCAN_WARPS * 32) k_scan(ScanParams P) {
         continue;
       }
       if (!valid) { lb = FINF; ub = FINF; }
-      // running upper bound of the k-th smallest upper bound
+      // running upper bound of the k-th smallest upper bound: this warp's own bound,
+      // tightened by what the query's other work items have published so far
+      if (KM != 2 && b0 > c_lo) {
+        float g2 = 0.f;
+        if (lane == 0) g2 = fkey_inv(__ldcg(P.gtau + q));
+        gt = fminf(gt, __shfl_sync(0xffffffffu, g2, 0));
+      }
       if (KM == 0) {
         float kth = __shfl_sync(0xffffffffu, lst, P.k - 1);
         unsigned mask = __ballot_sync(0xffffffffu, ub < kth);
@@ -532,6 +538,11 @@ __global__ void __launch_bounds__(SCAN_WARPS * 32) k_scan(ScanParams P) {
         // every lane holds >= mper values <= mine, 32 * mper >= k of them in all
         tau = fminf(gt, warp_max(mine));
       }
+      // publish an improved bound (once per 32 candidates at most)
+      if (KM != 2 && lane == 0 && tau < gt) {
+        atomicMin(P.gtau + q, fkey(tau));
+      }
+      if (KM != 2) gt = fminf(gt, tau);
       const bool surv = valid && lb <= tau;
       const unsigned sm = __ballot_sync(0xffffffffu, surv);
       if (sm) {
@@ -546,29 +557,31 @@ __global__ void __launch_bounds__(SCAN_WARPS * 32) k_scan(ScanParams P) {
         }
       }
     }
-    if (!DBG && KM != 2 && lane == 0 && tau < FINF) atomicMin(P.gtau + q, fkey(tau));
     __syncwarp();
     if (DBG) break;
   }
 }
 
-// work items for long lists: pair w contributes max(1, ceil(size/chunk)) items
+// work items: the pairs w = i * stride (i < n) contribute max(1, ceil(size/chunk))
+// items each, (w << 32 | chunk index)
 __global__ void k_chunk_count(const int32_t* __restrict__ plist, const int64_t* __restrict__ loff,
-                              int64_t npairs, int chunk, int* __restrict__ cnt) {
-  int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (w >= npairs) return;
-  const int j = plist[w];
+                              int64_t n, int stride, int chunk, int* __restrict__ cnt) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int j = plist[i * stride];
   const int64_t sz = loff[j + 1] - loff[j];
   const int64_t c = (sz + chunk - 1) / chunk;
-  cnt[w] = c > 0 ? (int)c : 1;
+  cnt[i] = c > 0 ? (int)c : 1;
 }
 __global__ void k_chunk_scatter(const int* __restrict__ cnt, const int* __restrict__ off,
-                                int64_t npairs, int64_t* __restrict__ items, int* __restrict__ nitems) {
-  int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (w >= npairs) return;
-  const int o = off[w], c = cnt[w];
-  for (int i = 0; i < c; ++i) items[o + i] = (w << 32) | (int64_t)i;
-  if (w == npairs - 1) *nitems = o + c;
+                                int64_t n, int stride, int64_t* __restrict__ items,
+                                int* __restrict__ nitems) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int o = off[i], c = cnt[i];
+  const int64_t w = i * stride;
+  for (int t = 0; t < c; ++t) items[o + t] = (w << 32) | (int64_t)t;
+  if (i == n - 1) *nitems = o + c;
 }
 
 __global__ void k_scan_init(unsigned int* qcnt, unsigned int* gtau, int64_t nq, unsigned int* work) {
@@ -577,7 +590,7 @@ __global__ void k_scan_init(unsigned int* qcnt, unsigned int* gtau, int64_t nq, 
     qcnt[i] = 0u;
     gtau[i] = fkey(FINF);
   }
-  if (i == 0) *work = 0u;
+  if (i < 4) work[i] = 0u;  // work-queue counters: [0] per-pair scan, [1] batched scan
 }
 
 // ------------------------------------------------------- batched (list-major) scan
@@ -598,16 +611,17 @@ struct PairQ {
   int qsum, pad;
 };
 
-__global__ void k_bucket_count(const int32_t* __restrict__ plist, int64_t npairs,
-                               int* __restrict__ cnt) {
+// pairs with w % nprobe < first are left out (scanned by the seed pass)
+__global__ void k_bucket_count(const int32_t* __restrict__ plist, int64_t npairs, int nprobe,
+                               int first, int* __restrict__ cnt) {
   int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (w < npairs) atomicAdd(&cnt[plist[w]], 1);
+  if (w < npairs && (int)(w % nprobe) >= first) atomicAdd(&cnt[plist[w]], 1);
 }
-__global__ void k_bucket_fill(const int32_t* __restrict__ plist, int64_t npairs,
-                              const int* __restrict__ off, int* __restrict__ fill,
+__global__ void k_bucket_fill(const int32_t* __restrict__ plist, int64_t npairs, int nprobe,
+                              int first, const int* __restrict__ off, int* __restrict__ fill,
                               int* __restrict__ queue) {
   int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (w >= npairs) return;
+  if (w >= npairs || (int)(w % nprobe) < first) return;
   const int j = plist[w];
   queue[off[j] + atomicAdd(&fill[j], 1)] = (int)w;
 }
@@ -833,6 +847,7 @@ struct FinParams {
   float* out_d;
   int64_t* stats;
   // phased finalize: per-query threshold and survivor counts
+  const unsigned int* gtau;  // the scan's running bound of tau_A per query (orderable key)
   float* qtau;
   int* qm1;
   int* qm2;
@@ -1021,15 +1036,22 @@ __device__ uint32_t warp_radix_kth(const float* vals, int M, int k, int* hist) {
 #pragma unroll
     for (int i = 0; i < 8; ++i) hist[lane * 8 + i] = 0;
     __syncwarp();
-    for (int b = 0; b < M; b += 32) {
-      const int i = b + lane;
-      const uint32_t key = i < M ? fkey(vals[i]) : 0u;
-      const bool in = i < M && (key & mask) == prefix;
-      const unsigned act = __ballot_sync(0xffffffffu, in);
-      if (in) {
-        const uint32_t bin = (key >> shift) & 255u;
-        const unsigned peers = __match_any_sync(act, bin);
-        if (lane == __ffs(peers) - 1) atomicAdd(&hist[bin], __popc(peers));
+    for (int b = 0; b < M; b += 128) {  // four independent loads in flight per lane
+      uint32_t key[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int i = b + 32 * u + lane;
+        key[u] = i < M ? fkey(vals[i]) : 0u;
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const bool in = b + 32 * u + lane < M && (key[u] & mask) == prefix;
+        const unsigned act = __ballot_sync(0xffffffffu, in);
+        if (in) {
+          const uint32_t bin = (key[u] >> shift) & 255u;
+          const unsigned peers = __match_any_sync(act, bin);
+          if (lane == __ffs(peers) - 1) atomicAdd(&hist[bin], __popc(peers));
+        }
       }
     }
     __syncwarp();
@@ -1063,17 +1085,87 @@ __device__ uint32_t warp_radix_kth(const float* vals, int M, int k, int* hist) {
   return prefix;
 }
 
+// count of vals[0..M) that are <= h, gathering up to cap of them into buf
+__device__ __forceinline__ int warp_filter_le(const float* vals, int M, float h, float* buf, int cap) {
+  const int lane = threadIdx.x & 31;
+  const unsigned below = (1u << lane) - 1;
+  int c = 0;
+  for (int b = 0; b < M; b += 128) {  // four independent loads in flight per lane
+    float v[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int i = b + 32 * u + lane;
+      v[u] = i < M ? vals[i] : FINF;
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const bool keep = v[u] <= h && b + 32 * u + lane < M;
+      const unsigned m = __ballot_sync(0xffffffffu, keep);
+      const int at = c + __popc(m & below);
+      if (keep && at < cap) buf[at] = v[u];
+      c += __popc(m);
+    }
+  }
+  __syncwarp();
+  return c;
+}
+
+// Exact k-th smallest key of vals[0..M) (M >= k).  `hint` is an upper bound of it
+// (or +inf).  The values <= a pivot are gathered into the warp's buffer and
+// selected there whenever their count lies in [k, cap]; the pivot is the hint or,
+// failing that, a rank of a strided sample of 256 values chosen so that about
+// cap/2 values are expected below it (rank adjusted and retried); a pivot is used
+// only after counting confirms that at least k values lie below it, so the
+// answer is exact whatever the sample.  Last resort: a radix select over vals.
+__device__ uint32_t warp_kth_filtered(const float* vals, int M, int k, float hint, float* buf,
+                                      int cap, int* hist) {
+  const int lane = threadIdx.x & 31;
+  if (M <= cap) {
+    for (int i = lane; i < M; i += 32) buf[i] = vals[i];
+    __syncwarp();
+    return warp_radix_kth(buf, M, k, hist);
+  }
+  if (hint < FINF) {
+    const int c = warp_filter_le(vals, M, hint, buf, cap);
+    if (c >= k && c <= cap) return warp_radix_kth(buf, c, k, hist);
+  }
+  constexpr int S = 256;
+  const int64_t r0 = ((int64_t)S * (cap / 2)) / M;
+  int r = r0 < 1 ? 1 : (r0 > S ? S : (int)r0);
+  const int64_t rk = ((int64_t)k * S + M - 1) / M;   // at least k values expected below
+  r = max(r, rk > S ? S : (int)rk);
+  for (int attempt = 0; attempt < 4 && cap >= S; ++attempt) {
+    for (int i = lane; i < S; i += 32) buf[i] = vals[(int64_t)i * M / S];
+    __syncwarp();
+    const float h = fkey_inv(warp_radix_kth(buf, S, r, hist));
+    const int c = warp_filter_le(vals, M, h, buf, cap);
+    if (c >= k && c <= cap) return warp_radix_kth(buf, c, k, hist);
+    if (c < k) r = min(S, r * 4);
+    else r = max(1, r / 4);
+    if (c > cap && r == 1) break;
+  }
+  return warp_radix_kth(vals, M, k, hist);
+}
+
 // ordered warp compaction: out[n..] = src[i] for every i < M with keep(i); returns new n
 template <class Keep>
 __device__ __forceinline__ int warp_compact(const int32_t* src, int M, int32_t* out, Keep keep) {
   const int lane = threadIdx.x & 31;
+  const unsigned below = (1u << lane) - 1;
   int n = 0;
-  for (int b = 0; b < M; b += 32) {
-    const int i = b + lane;
-    const bool k = i < M && keep(i);
-    const unsigned m = __ballot_sync(0xffffffffu, k);
-    if (k) out[n + __popc(m & ((1u << lane) - 1))] = src[i];
-    n += __popc(m);
+  for (int b = 0; b < M; b += 128) {  // four independent tests in flight per lane
+    bool k[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int i = b + 32 * u + lane;
+      k[u] = i < M && keep(i);
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const unsigned m = __ballot_sync(0xffffffffu, k[u]);
+      if (k[u]) out[n + __popc(m & below)] = src[b + 32 * u + lane];
+      n += __popc(m);
+    }
   }
   __syncwarp();
   return n;
@@ -1086,9 +1178,13 @@ constexpr int FW_BUF = 128;   // per-warp (distance, id) sort buffer: up to k = 
 // and never synchronise a block; gather phases run one CTA (8 independent warps)
 // per query, each lane prefetching one candidate's position per batch of 32.
 
-// phase 1: tau_A = k-th smallest UB1, S1 = {LB1 <= tau_A} (ordered compaction)
+constexpr int FW_FILT = 768;  // per-warp buffer of a filtered selection
+
+// phase 1: tau_A = k-th smallest UB1, S1 = {LB1 <= tau_A} (ordered compaction).
+// The scan's final per-query bound (>= tau_A) filters the upper bounds first.
 __global__ void __launch_bounds__(FW_WARPS * 32) k_fin_s1(FinParams P) {
   __shared__ int hist_all[FW_WARPS][256];
+  __shared__ float filt_all[FW_WARPS][FW_FILT];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int64_t q = (int64_t)blockIdx.x * FW_WARPS + wid;
   if (q >= P.nq) return;
@@ -1102,7 +1198,11 @@ __global__ void __launch_bounds__(FW_WARPS * 32) k_fin_s1(FinParams P) {
   }
 #pragma unroll
   for (int o = 16; o; o >>= 1) nc += __shfl_xor_sync(0xffffffffu, nc, o);
-  const float tauA = M >= P.k ? fkey_inv(warp_radix_kth(P.sub + base, M, P.k, hist)) : FINF;
+  float tauA = FINF;
+  if (M >= P.k) {
+    const float hint = P.gtau ? fkey_inv(__ldcg(P.gtau + q)) : FINF;
+    tauA = fkey_inv(warp_kth_filtered(P.sub + base, M, P.k, hint, filt_all[wid], FW_FILT, hist));
+  }
   const float* slb = P.slb + base;
   const int M1 = warp_compact(P.spos + base, M, P.s2pos + base,
                               [&](int i) { return slb[i] <= tauA; });
@@ -1158,6 +1258,7 @@ __global__ void __launch_bounds__(256) k_fin_stage2(FinParams P) {
 // (MRQ mode: S2 = S1)
 __global__ void __launch_bounds__(FW_WARPS * 32) k_fin_s2(FinParams P) {
   __shared__ int hist_all[FW_WARPS][256];
+  __shared__ float filt_all[FW_WARPS][FW_FILT];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int64_t q = (int64_t)blockIdx.x * FW_WARPS + wid;
   if (q >= P.nq) return;
@@ -1166,8 +1267,11 @@ __global__ void __launch_bounds__(FW_WARPS * 32) k_fin_s2(FinParams P) {
   int M2;
   if (P.mode == MRQ_MODE_MRQ_PLUS) {
     const float tauA = P.qtau[q];
+    // only upper bounds <= tau_A can lower tau_B = min(tau_A, k-th smallest UB2)
     const float tauB =
-        M1 >= P.k ? fminf(tauA, fkey_inv(warp_radix_kth(P.s2a + base, M1, P.k, hist_all[wid]))) : tauA;
+        M1 >= P.k ? fminf(tauA, fkey_inv(warp_kth_filtered(P.s2a + base, M1, P.k, tauA,
+                                                           filt_all[wid], FW_FILT, hist_all[wid])))
+                  : tauA;
     const float* lb2 = P.s2b + base;
     M2 = warp_compact(P.s2pos + base, M1, P.spos + base, [&](int i) { return lb2[i] <= tauB; });
   } else {
@@ -1478,6 +1582,29 @@ void search_batch(mrq_index* idx, Workspace& ws, const float* q, int64_t nq, int
   sp.npairs = nq * nprobe; sp.cap = cap;
   sp.work = ws.work.p; sp.qcnt = ws.qcnt.p; sp.gtau = ws.gtau.p;
   sp.spos = ws.spos.p; sp.slb = ws.slb.p; sp.sub = ws.sub.p;
+  // per-pair work items (w = i * stride, i < n), long lists split into SCAN_CHUNK chunks
+  auto build_items = [&](int64_t n, int stride) {
+    const int64_t max_items = n + (nq * idx->cap_by_nprobe[nprobe]) / SCAN_CHUNK + 1;
+    ws.ccnt.reserve(n);
+    ws.coff.reserve(n);
+    ws.items.reserve(max_items);
+    ws.nitems.reserve(1);
+    k_chunk_count<<<ceil_div(n, 256), 256, 0, st>>>(ws.plist.p, idx->loff.p, n, stride,
+                                                   SCAN_CHUNK, ws.ccnt.p);
+    MRQ_CHECK_LAUNCH();
+    size_t tb = 0;
+    MRQ_CUDA(cub::DeviceScan::ExclusiveSum(nullptr, tb, ws.ccnt.p, ws.coff.p, (int)n, st));
+    ws.cubtmp.reserve(tb + 16);
+    MRQ_CUDA(cub::DeviceScan::ExclusiveSum(ws.cubtmp.p, tb, ws.ccnt.p, ws.coff.p, (int)n, st));
+    k_chunk_scatter<<<ceil_div(n, 256), 256, 0, st>>>(ws.ccnt.p, ws.coff.p, n, stride, ws.items.p,
+                                                     ws.nitems.p);
+    MRQ_CHECK_LAUNCH();
+    sp.items = ws.items.p;
+    sp.nitems = ws.nitems.p;
+    sp.chunk = SCAN_CHUNK;
+    idx->launches += 3;
+    return max_items;
+  };
   // batched form: quantized query, code words a power of two (bits in {1,2,4,8}) up to 16
   const int wds = idx->words;
   const bool batched = o.batched && o.query_bits > 0 && wds <= BATCH_MAXW &&
@@ -1486,6 +1613,10 @@ void search_batch(mrq_index* idx, Workspace& ws, const float* q, int64_t nq, int
   if (batched) {
     const int64_t np_ = nq * nprobe;
     const int nch = d / 32;
+    // seed pass: each query's nearest list by the per-pair scan, whose warp top-k gives a
+    // tight bound of tau_A early; the batched kernel then scans the remaining pairs
+    const int first = nprobe >= 4 ? 1 : 0;
+    if (first) launch_scan(sp, build_items(nq, nprobe), st, false);
     ws.lcount.reserve(nlist);
     ws.loffq.reserve(nlist);
     ws.lfill.reserve(nlist);
@@ -1499,13 +1630,13 @@ void search_batch(mrq_index* idx, Workspace& ws, const float* q, int64_t nq, int
     ws.qplanes.reserve(np_ * o.query_bits * nch);
     MRQ_CUDA(cudaMemsetAsync(ws.lcount.p, 0, 4 * nlist, st));
     MRQ_CUDA(cudaMemsetAsync(ws.lfill.p, 0, 4 * nlist, st));
-    k_bucket_count<<<ceil_div(np_, 256), 256, 0, st>>>(ws.plist.p, np_, ws.lcount.p);
+    k_bucket_count<<<ceil_div(np_, 256), 256, 0, st>>>(ws.plist.p, np_, nprobe, first, ws.lcount.p);
     size_t tb = 0;
     MRQ_CUDA(cub::DeviceScan::ExclusiveSum(nullptr, tb, ws.lcount.p, ws.loffq.p, nlist, st));
     ws.cubtmp.reserve(tb + 16);
     MRQ_CUDA(cub::DeviceScan::ExclusiveSum(ws.cubtmp.p, tb, ws.lcount.p, ws.loffq.p, nlist, st));
-    k_bucket_fill<<<ceil_div(np_, 256), 256, 0, st>>>(ws.plist.p, np_, ws.loffq.p, ws.lfill.p,
-                                                      ws.lqueue.p);
+    k_bucket_fill<<<ceil_div(np_, 256), 256, 0, st>>>(ws.plist.p, np_, nprobe, first, ws.loffq.p,
+                                                      ws.lfill.p, ws.lqueue.p);
     k_batch_count<<<ceil_div(nlist, 256), 256, 0, st>>>(ws.lcount.p, idx->loff.p, nlist, ws.icnt.p);
     MRQ_CUDA(cub::DeviceScan::ExclusiveSum(nullptr, tb, ws.icnt.p, ws.ioff.p, nlist, st));
     ws.cubtmp.reserve(tb + 16);
@@ -1527,7 +1658,7 @@ void search_batch(mrq_index* idx, Workspace& ws, const float* q, int64_t nq, int
     bp.fadd = idx->fadd.p; bp.fres = idx->fres.p; bp.ferr = idx->ferr.p;
     bp.d = d; bp.bits = idx->bits; bp.words = idx->words; bp.vw = idx->vw;
     bp.nprobe = nprobe; bp.k = k; bp.qbits = o.query_bits; bp.cap = cap;
-    bp.work = ws.work.p; bp.qcnt = ws.qcnt.p; bp.gtau = ws.gtau.p;
+    bp.work = ws.work.p + 1; bp.qcnt = ws.qcnt.p; bp.gtau = ws.gtau.p;
     bp.spos = ws.spos.p; bp.slb = ws.slb.p; bp.sub = ws.sub.p;
     auto launch = [&](auto kern) {
       kern<<<num_sms() * occupancy((const void*)kern, 256, 0), 256, 0, st>>>(bp);
@@ -1546,28 +1677,7 @@ void search_batch(mrq_index* idx, Workspace& ws, const float* q, int64_t nq, int
     idx->launches += 8;
   }
   int64_t grid_items = nq * nprobe;
-  if (!batched && idx->max_list > SCAN_CHUNK) {
-    // long lists are split into chunks of SCAN_CHUNK candidates (work-item list on device)
-    const int64_t np_ = nq * nprobe;
-    const int64_t max_items = np_ + (nq * idx->cap_by_nprobe[nprobe]) / SCAN_CHUNK + 1;
-    ws.ccnt.reserve(np_);
-    ws.coff.reserve(np_);
-    ws.items.reserve(max_items);
-    ws.nitems.reserve(1);
-    k_chunk_count<<<ceil_div(np_, 256), 256, 0, st>>>(ws.plist.p, idx->loff.p, np_, SCAN_CHUNK, ws.ccnt.p);
-    MRQ_CHECK_LAUNCH();
-    size_t tb = 0;
-    MRQ_CUDA(cub::DeviceScan::ExclusiveSum(nullptr, tb, ws.ccnt.p, ws.coff.p, (int)np_, st));
-    ws.cubtmp.reserve(tb + 16);
-    MRQ_CUDA(cub::DeviceScan::ExclusiveSum(ws.cubtmp.p, tb, ws.ccnt.p, ws.coff.p, (int)np_, st));
-    k_chunk_scatter<<<ceil_div(np_, 256), 256, 0, st>>>(ws.ccnt.p, ws.coff.p, np_, ws.items.p, ws.nitems.p);
-    MRQ_CHECK_LAUNCH();
-    sp.items = ws.items.p;
-    sp.nitems = ws.nitems.p;
-    sp.chunk = SCAN_CHUNK;
-    grid_items = max_items;
-    idx->launches += 3;
-  }
+  if (!batched && idx->max_list > SCAN_CHUNK) grid_items = build_items(nq * nprobe, 1);
   if (!batched) launch_scan(sp, grid_items, st, false);
   // 5. finalize
   mark(idx, MRQ_STAGE_TAU_A, st);
@@ -1583,6 +1693,7 @@ void search_batch(mrq_index* idx, Workspace& ws, const float* q, int64_t nq, int
     ws.qm1.reserve(nq);
     ws.qm2.reserve(nq);
     fp.qtau = ws.qtau.p; fp.qm1 = ws.qm1.p; fp.qm2 = ws.qm2.p; fp.nq = nq;
+    fp.gtau = ws.gtau.p;
     const unsigned gw = ceil_div(nq, FW_WARPS);
     k_fin_s1<<<gw, FW_WARPS * 32, 0, st>>>(fp);
     MRQ_CHECK_LAUNCH();

@@ -15,6 +15,7 @@
 #include <condition_variable>
 #include <cstring>
 #include <deque>
+#include <map>
 #include <mutex>
 #include <thread>
 #include <unordered_map>
@@ -65,9 +66,11 @@ struct mrq_server {
   std::thread th;
   std::mutex mu;
   std::condition_variable cv_work, cv_done;
-  std::deque<Req> pending;
+  std::map<std::pair<int, int>, std::deque<Req>> pending;  // FIFO per (k, nprobe) group
+  int64_t n_pending = 0;
   std::unordered_map<uint64_t, Result> done;
   std::unordered_set<uint64_t> live;  // submitted and not yet released by a poll
+  std::deque<uint64_t> completed;     // tickets in completion order (mrq_poll_completed)
   std::vector<Slot> slots;
   uint64_t next_ticket = 1;
   bool stop = false;
@@ -107,6 +110,7 @@ void collect(mrq_server* sv) {
       }
       sv->lat.push_back(t - s.reqs[i].t_submit);
       sv->done.emplace(s.reqs[i].ticket, std::move(r));
+      sv->completed.push_back(s.reqs[i].ticket);
     }
     if (e != cudaSuccess) cudaGetLastError();
     sv->n_done += (int64_t)s.reqs.size();
@@ -118,7 +122,8 @@ void collect(mrq_server* sv) {
   }
 }
 
-// launch one batch on a free slot (lock held; the launch itself is asynchronous)
+// stage and launch one batch on a free slot (called without the lock: only the
+// scheduler thread touches slots)
 void launch(mrq_server* sv, Slot& s, std::vector<Req>&& batch, size_t bytes) {
   mrq_index* idx = sv->idx;
   const int64_t n = (int64_t)batch.size();
@@ -140,9 +145,6 @@ void launch(mrq_server* sv, Slot& s, std::vector<Req>&& batch, size_t bytes) {
   s.k = k;
   s.bytes = bytes;
   s.reqs = std::move(batch);
-  s.busy = true;
-  sv->inflight_bytes += bytes;
-  sv->n_batches++;
 }
 
 void scheduler(mrq_server* sv) {
@@ -152,44 +154,62 @@ void scheduler(mrq_server* sv) {
     collect(sv);
     bool busy_any = false;
     for (auto& s : sv->slots) busy_any |= s.busy;
-    if (sv->stop && sv->pending.empty() && !busy_any) break;
+    if (sv->stop && sv->n_pending == 0 && !busy_any) break;
     bool launched = false;
-    if (!sv->pending.empty() && sv->fatal == MRQ_OK) {
+    if (sv->n_pending > 0 && sv->fatal == MRQ_OK) {
       Slot* free_slot = nullptr;
       for (auto& s : sv->slots)
         if (!s.busy) { free_slot = &s; break; }
       if (free_slot) {
-        // the group of the oldest request: same (k, nprobe), arrival order
-        const Req& first = sv->pending.front();
-        const int k = first.k, np = first.nprobe;
-        int64_t cnt = 0;
-        for (auto& r : sv->pending)
-          if (r.k == k && r.nprobe == np && ++cnt >= sv->opt.max_batch) break;
+        // the group whose oldest request waited longest
+        auto gsel = sv->pending.end();
+        for (auto g = sv->pending.begin(); g != sv->pending.end(); ++g)
+          if (!g->second.empty() &&
+              (gsel == sv->pending.end() || g->second.front().t_submit < gsel->second.front().t_submit))
+            gsel = g;
+        auto& q = gsel->second;
+        const int k = gsel->first.first, np = gsel->first.second;
+        const int64_t cnt = std::min<int64_t>((int64_t)q.size(), sv->opt.max_batch);
         const bool full = cnt >= sv->opt.max_batch;
-        const bool old = now_us() - first.t_submit >= sv->opt.max_wait_us;
+        const bool old = now_us() - q.front().t_submit >= sv->opt.max_wait_us;
         if (full || old || sv->stop) {
           const size_t bytes = mrq::batch_scratch_bytes(sv->idx, cnt, k, np);
           if (sv->inflight_bytes == 0 || sv->inflight_bytes + bytes <= sv->opt.mem_budget) {
             std::vector<Req> batch;
             batch.reserve(cnt);
-            for (auto it = sv->pending.begin(); it != sv->pending.end() && (int64_t)batch.size() < cnt;) {
-              if (it->k == k && it->nprobe == np) {
-                batch.push_back(std::move(*it));
-                it = sv->pending.erase(it);
-              } else {
-                ++it;
-              }
+            for (int64_t i = 0; i < cnt; ++i) {
+              batch.push_back(std::move(q.front()));
+              q.pop_front();
             }
+            sv->n_pending -= cnt;
+            if (q.empty()) sv->pending.erase(gsel);
             std::vector<uint64_t> tks;
             for (auto& r : batch) tks.push_back(r.ticket);
+            free_slot->busy = true;
+            sv->inflight_bytes += bytes;
+            sv->n_batches++;
+            bool ok = true;
+            mrq::Error err{MRQ_OK, ""};
+            lk.unlock();
             try {
               launch(sv, *free_slot, std::move(batch), bytes);
-              launched = true;
             } catch (const mrq::Error& e) {
+              ok = false;
+              err = e;
+            }
+            lk.lock();
+            if (ok) {
+              launched = true;
+            } else {
+              const mrq::Error& e = err;
+              sv->inflight_bytes -= bytes;
               // the batch failed before it ran: its requests complete with the error
               sv->fatal = e.code;
               sv->fatal_msg = e.msg;
-              for (uint64_t t : tks) sv->done[t].rc = e.code;
+              for (uint64_t t : tks) {
+                sv->done[t].rc = e.code;
+                sv->completed.push_back(t);
+              }
               free_slot->reqs.clear();
               free_slot->busy = false;
               sv->cv_done.notify_all();
@@ -284,7 +304,8 @@ int mrq_submit(mrq_server* sv, const float* q, int k, int nprobe, uint64_t* tick
       r.ticket = sv->next_ticket++;
       *ticket = r.ticket;
       sv->live.insert(r.ticket);
-      sv->pending.push_back(std::move(r));
+      sv->pending[std::make_pair(r.k, r.nprobe)].push_back(std::move(r));
+      sv->n_pending++;
     }
     sv->cv_work.notify_one();
   });
@@ -337,7 +358,8 @@ int mrq_submit_many(mrq_server* sv, int64_t n, const float* q, const int* k, con
         rs[i].ticket = sv->next_ticket++;
         tickets[i] = rs[i].ticket;
         sv->live.insert(rs[i].ticket);
-        sv->pending.push_back(std::move(rs[i]));
+        sv->pending[std::make_pair(rs[i].k, rs[i].nprobe)].push_back(std::move(rs[i]));
+        sv->n_pending++;
       }
     }
     sv->cv_work.notify_one();
@@ -367,6 +389,38 @@ int mrq_poll_many(mrq_server* sv, int64_t n, const uint64_t* tickets, int kmax, 
   });
 }
 
+int64_t mrq_poll_completed(mrq_server* sv, int64_t max_n, int kmax, uint64_t* tickets,
+                           int64_t* ids, float* dists, int32_t* status) {
+  int64_t got = 0;
+  int rc = srv_guard([&] {
+    MRQ_REQUIRE(sv && tickets && ids && dists && status && max_n >= 0 && kmax >= 1, "bad argument");
+    std::vector<std::pair<uint64_t, Result>> out;
+    {
+      std::lock_guard<std::mutex> lk(sv->mu);
+      while ((int64_t)out.size() < max_n && !sv->completed.empty()) {
+        const uint64_t t = sv->completed.front();
+        sv->completed.pop_front();
+        auto it = sv->done.find(t);
+        if (it == sv->done.end()) continue;  // already released by mrq_poll
+        out.emplace_back(t, std::move(it->second));
+        sv->done.erase(it);
+        sv->live.erase(t);
+      }
+    }
+    for (size_t i = 0; i < out.size(); ++i) {
+      tickets[i] = out[i].first;
+      status[i] = out[i].second.rc;
+      const auto& r = out[i].second;
+      for (size_t j = 0; j < (size_t)kmax; ++j) {
+        ids[i * kmax + j] = j < r.ids.size() ? r.ids[j] : -1;
+        dists[i * kmax + j] = j < r.dists.size() ? r.dists[j] : __builtin_huge_valf();
+      }
+    }
+    got = (int64_t)out.size();
+  });
+  return rc == MRQ_OK ? got : rc;
+}
+
 int mrq_server_stats(mrq_server* sv, mrq_server_stats_t* st) {
   return srv_guard([&] {
     MRQ_REQUIRE(sv && st, "NULL argument");
@@ -374,7 +428,7 @@ int mrq_server_stats(mrq_server* sv, mrq_server_stats_t* st) {
     std::memset(st, 0, sizeof(*st));
     st->completed = sv->n_done;
     st->batches = sv->n_batches;
-    st->pending = (int64_t)sv->pending.size();
+    st->pending = sv->n_pending;
     std::vector<double> l = sv->lat;
     if (!l.empty()) {
       std::sort(l.begin(), l.end());

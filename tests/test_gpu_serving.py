@@ -76,3 +76,24 @@ def test_bad_requests_are_rejected(index):
             srv.poll(123456, 5)                                  # unknown ticket
     finally:
         srv.stop()
+
+
+def test_poll_completed_returns_each_ticket_once(index):
+    w, queries, idx = index
+    srv = mrq.Server(idx, max_batch=128, max_inflight=2, max_wait_us=100, max_k=10)
+    try:
+        tickets = srv.submit_many(queries[:300], 10, 8)
+        seen = {}
+        deadline = time.time() + 60
+        while len(seen) < 300 and time.time() < deadline:
+            tk, ids, dists, st = srv.poll_completed(64, 10)
+            for t, i in zip(tk.tolist(), ids):
+                assert t not in seen
+                seen[t] = i
+            time.sleep(0.0005)
+        assert sorted(seen) == sorted(tickets.tolist())
+        ref, _ = mrq.mrq_search(idx, queries[:300], 10, 8)
+        for q, t in enumerate(tickets.tolist()):
+            np.testing.assert_array_equal(seen[t], ref[q])
+    finally:
+        srv.stop()
