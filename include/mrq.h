@@ -142,6 +142,44 @@ int mrq_estimate(mrq_index* index, const float* qp, int list, const mrq_search_o
 int mrq_project(mrq_index* index, const float* queries, int64_t nq,
                 const mrq_search_opts* opt, float* qp);
 
+/* Largest scratch, in bytes, that mrq_project_noalloc may use: its bf16 copy
+ * of the centred queries takes 2 * nq * D bytes at MRQ_PREC_BF16 and
+ * 4 * nq * D bytes at MRQ_PREC_BF16X3 (hi and lo halves). */
+#define MRQ_PROJECT_NOALLOC_MAX_BYTES 8388608
+
+/*
+ * mrq_project without any allocation.  The paper has no counterpart: this is
+ * an interface for callers that must not allocate device memory during a
+ * call, such as an application that has given all of the GPU's memory to its
+ * own pool allocator (a new cudaMalloc would fail or fragment that pool), or a
+ * latency-critical serving loop that cannot take the device-wide
+ * synchronisation that cudaMalloc/cudaFree can cause.
+ *
+ * Computes qp = W (q - mu) exactly as mrq_project does with the same opt (same
+ * kernels and tile shapes), but queries (nq x D, row-major float32) and qp
+ * (nq x D) must both be device memory on the index's device, and the work runs
+ * on opt->cuda_stream (NULL opt or stream: the legacy default stream).  The
+ * call returns once qp is written (it synchronises that stream).
+ *
+ * Scratch: MRQ_PREC_FP32 needs none.  The tensor-core precisions stage the
+ * bf16 operand of the query in a fixed static device array of
+ * MRQ_PROJECT_NOALLOC_MAX_BYTES bytes that the library owns; a request that
+ * needs more (nq * D > 4194304 at MRQ_PREC_BF16, > 2097152 at MRQ_PREC_BF16X3)
+ * returns MRQ_EINVAL without launching anything: split the batch.  The
+ * pipeline error word in that array is cleared at the start of every call;
+ * nothing else in it has to start at zero.
+ *
+ * The first call on each device does one-time set-up (it looks up the scratch
+ * array's address and sets kernel attributes), so make that first call before
+ * any stream capture begins.  There is one scratch array per device: calls
+ * that overlap in time on the same device (from two threads, or on two streams)
+ * race on it and may return wrong values.  Errors: MRQ_EINVAL for NULL or host
+ * pointers, nq < 1 or a too-large request; MRQ_ETIMEDOUT if a tensor-core
+ * pipeline wait gave up; MRQ_ECUDA for a CUDA failure.
+ */
+int mrq_project_noalloc(mrq_index* index, const float* queries, int64_t nq,
+                        const mrq_search_opts* opt, float* qp);
+
 /* Per-query counters of the last mrq_search on this index (host arrays of nq):
  * candidates scanned, stage-1 survivors, exact distances computed. */
 int mrq_last_search_stats(const mrq_index* index, int64_t nq, int64_t* n_cand,

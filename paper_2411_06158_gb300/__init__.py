@@ -25,7 +25,7 @@ PREC_FP32, PREC_BF16, PREC_BF16X3 = 0, 1, 2
 
 EXPORTS = [
     "mrq_build_opts_default", "mrq_search_opts_default", "mrq_build", "mrq_search",
-    "mrq_estimate", "mrq_project", "mrq_last_search_stats", "mrq_last_search_profile",
+    "mrq_estimate", "mrq_project", "mrq_project_noalloc", "mrq_last_search_stats", "mrq_last_search_profile",
     "mrq_save", "mrq_load",
     "mrq_index_info", "mrq_index_export", "mrq_free", "mrq_last_error",
     "mrq_server_opts_default", "mrq_server_start", "mrq_submit", "mrq_submit_many", "mrq_poll",
@@ -79,6 +79,7 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
     lib.mrq_search.argtypes = [vp, vp, i64, i32, i32, C.POINTER(SearchOpts), vp, vp]
     lib.mrq_estimate.argtypes = [vp, vp, i32, C.POINTER(SearchOpts), vp, vp, vp, vp, vp]
     lib.mrq_project.argtypes = [vp, vp, i64, C.POINTER(SearchOpts), vp]
+    lib.mrq_project_noalloc.argtypes = [vp, vp, i64, C.POINTER(SearchOpts), vp]
     lib.mrq_last_search_stats.argtypes = [vp, i64, vp, vp, vp]
     lib.mrq_last_search_profile.argtypes = [vp, vp, vp]
     lib.mrq_save.argtypes = [vp, C.c_char_p]
@@ -247,6 +248,15 @@ def mrq_project(index: Index, queries, opts: SearchOpts | None = None):
         if _is_torch(queries) else np.empty((nq, D), dtype=np.float32)
     _check(_lib.mrq_project(index.handle, _ptr(queries), nq,
                             C.byref(opts) if opts is not None else None, _ptr(out)))
+    return out
+
+
+def mrq_project_noalloc(index: Index, queries, out, opts: SearchOpts | None = None):
+    """mrq_project into a caller-owned device tensor `out` (nq x D float32) from
+    device `queries`, through the entry point that allocates no device memory."""
+    nq = queries.shape[0]
+    _check(_lib.mrq_project_noalloc(index.handle, _ptr(queries), nq,
+                                    C.byref(opts) if opts is not None else None, _ptr(out)))
     return out
 
 

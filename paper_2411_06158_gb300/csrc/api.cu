@@ -298,6 +298,19 @@ int mrq_project(mrq_index* idx, const float* queries, int64_t nq, const mrq_sear
   });
 }
 
+int mrq_project_noalloc(mrq_index* idx, const float* queries, int64_t nq,
+                        const mrq_search_opts* opt, float* qp) {
+  return guarded([&] {
+    MRQ_REQUIRE(idx && queries && qp, "NULL argument");
+    MRQ_REQUIRE(nq >= 1, "nq must be >= 1");
+    const mrq_search_opts o = resolve(opt);
+    use_device(idx);
+    MRQ_REQUIRE(on_device(queries) && on_device(qp),
+                "mrq_project_noalloc needs queries and qp in device memory");
+    mrq::project_noalloc(idx, queries, nq, o.precision, qp, stream_of(o));
+  });
+}
+
 int mrq_estimate(mrq_index* idx, const float* qp, int list, const mrq_search_opts* opt, float* ip,
                  float* dis, float* lb, float* ub, int32_t* int_dot) {
   return guarded([&] {

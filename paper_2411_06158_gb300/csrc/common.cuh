@@ -190,6 +190,8 @@ void nearest_f32(const float* A, int lda, const float* B, int ldb, int M, int N,
 
 // ---- tensor-core GEMMs (gemm_tc.cu) ----
 bool tc_available();
+void project_noalloc(mrq_index* idx, const float* q, int64_t nq, int precision, float* qp,
+                     cudaStream_t st);  // static scratch only, no allocation
 int tc_check_error();  // nonzero if a bounded wait in a tensor-core kernel gave up
 void project_tc(const float* Q, const float* mu, const __nv_bfloat16* W2, int M, int D, int d,
                 bool split3, __nv_bfloat16* qbf, float* qd, float* qr, cudaStream_t st);

@@ -18,6 +18,8 @@
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
+#include <mutex>
+
 #include "common.cuh"
 
 namespace mrq {
@@ -473,6 +475,94 @@ int probe_tc_topk(const float* qd, const float* qstat, const __nv_bfloat16* C2, 
   run_tc(qbf, C2, a, st);
   const int bn = nlist <= 64 ? 64 : nlist <= 128 ? 128 : 256;
   return 2 * ceil_div(nlist, bn);  // candidate lists per row: column tiles x 2 halves
+}
+
+}  // namespace mrq
+
+// ---------------------------------------------------------------- projection without allocation
+// Scratch of project_noalloc, one copy per device, created with the module (no
+// allocation call): bytes [0, 256) hold the pipeline error word of the
+// tensor-core GEMM, the rest the bf16 operand of the centred queries.
+static __device__ __align__(256) unsigned char
+    mrq_project_scratch[256 + MRQ_PROJECT_NOALLOC_MAX_BYTES];
+
+namespace mrq {
+namespace {
+
+constexpr int NA_MAX_DEVICES = 64;
+std::mutex g_na_mu;
+unsigned char* g_na_base[NA_MAX_DEVICES] = {};
+
+// Device address of the current device's scratch, looked up on the first call
+// with that device current and kept.
+unsigned char* project_scratch() {
+  int dev = 0;
+  MRQ_CUDA(cudaGetDevice(&dev));
+  MRQ_REQUIRE(dev >= 0 && dev < NA_MAX_DEVICES, "device ordinal too large for the projection scratch table");
+  std::lock_guard<std::mutex> lk(g_na_mu);
+  if (!g_na_base[dev]) {
+    unsigned char* p = nullptr;
+    const cudaError_t rc = cudaGetSymbolAddress((void**)&p, mrq_project_scratch);
+    if (rc != cudaSuccess || !p)
+      fail(MRQ_ECUDA, std::string("cannot get the address of the projection scratch: ") +
+                          cudaGetErrorString(rc));
+    g_na_base[dev] = p;
+  }
+  return g_na_base[dev];
+}
+
+}  // namespace
+
+// qp = W (q - mu) with row stride D for both halves, using only the static
+// scratch above.  The kernels and their tile shapes are the ones project_batch
+// uses for the same precision, so the values match it.
+void project_noalloc(mrq_index* idx, const float* q, int64_t nq, int precision, float* qp,
+                     cudaStream_t st) {
+  const int D = idx->D, d = idx->d;
+  MRQ_REQUIRE(nq >= 1 && nq <= INT32_MAX, "nq must be in [1, 2^31)");
+  if (precision == MRQ_PREC_FP32) {
+    gemm_nt_f32(q, D, idx->mu.p, idx->W.p, D, (int)nq, D, D, qp, D, qp + d, D, d, st);
+    MRQ_CUDA(cudaStreamSynchronize(st));
+    return;
+  }
+  const bool split3 = precision == MRQ_PREC_BF16X3;
+  const int64_t need = nq * D * 2 * (split3 ? 2 : 1);
+  if (need > MRQ_PROJECT_NOALLOC_MAX_BYTES)
+    fail(MRQ_EINVAL, "mrq_project_noalloc: nq * D = " + std::to_string(nq * D) + " needs " +
+                         std::to_string(need) + " bytes of scratch, more than its fixed " +
+                         std::to_string(MRQ_PROJECT_NOALLOC_MAX_BYTES) +
+                         " (nq * D <= " + std::to_string(MRQ_PROJECT_NOALLOC_MAX_BYTES / (split3 ? 4 : 2)) +
+                         " at this precision); split the batch");
+  MRQ_REQUIRE(tc_available(), "tensor-core projection needs an sm_103 device");
+  unsigned char* base = project_scratch();
+  int* err = reinterpret_cast<int*>(base);
+  __nv_bfloat16* qbf = reinterpret_cast<__nv_bfloat16*>(base + 256);
+  MRQ_CUDA(cudaMemsetAsync(err, 0, sizeof(int), st));
+  const int64_t tot = nq * D;
+  k_split_bf16<<<ceil_div(tot, 256), 256, 0, st>>>(q, (int)nq, D, D, idx->mu.p, split3 ? 1 : 0, qbf);
+  MRQ_CHECK_LAUNCH();
+  TcArgs a{};
+  a.M = (int)nq; a.N = D; a.K = D;
+  a.phases = split3 ? 3 : 1;
+  a.a_lo = (int)nq; a.b_lo = D;
+  a.epi = 0;
+  a.out0 = qp; a.ld0 = D; a.out1 = qp + d; a.ld1 = D; a.split = d;
+  a.err = err;
+  const bool short_k = (int64_t)((a.K + TC_BK - 1) / TC_BK) * a.phases <= 2;
+  if (a.N <= 64) {
+    if (short_k) launch_tc<64, 4, 2>(qbf, idx->W2.p, a, st);
+    else launch_tc<64, 4, 4>(qbf, idx->W2.p, a, st);
+  } else if (a.N <= 128) {
+    if (short_k) launch_tc<128, 4, 2>(qbf, idx->W2.p, a, st);
+    else launch_tc<128, 4, 4>(qbf, idx->W2.p, a, st);
+  } else {
+    if (short_k) launch_tc<256, 4, 2>(qbf, idx->W2.p, a, st);
+    else launch_tc<256, 4, 4>(qbf, idx->W2.p, a, st);
+  }
+  int h = 0;
+  MRQ_CUDA(cudaMemcpyAsync(&h, err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  MRQ_CUDA(cudaStreamSynchronize(st));
+  if (h) fail(MRQ_ETIMEDOUT, "a tensor-core kernel gave up waiting on its pipeline");
 }
 
 }  // namespace mrq
