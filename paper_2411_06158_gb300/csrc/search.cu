@@ -889,6 +889,50 @@ __device__ __forceinline__ void row_accum2(const float* __restrict__ r0, const f
   }
 }
 
+// Per-lane partial <x_u, q> and |x_u - q|^2 of up to R rows x_u = X[p[u]] (rows
+// u >= nrow are skipped): all R loads of a column step are issued before any
+// arithmetic, so R loads per lane are in flight.  The caller reduces across the warp.
+template <int R>
+__device__ __forceinline__ void rows_dot_dist2(const float* __restrict__ X, const int (&p)[R],
+                                               int nrow, const float* sq, int n, bool vec, int lane,
+                                               float (&dot)[R], float (&e)[R]) {
+  if (vec) {
+    const float4* qv = reinterpret_cast<const float4*>(sq);
+    const int n4 = n >> 2;
+    for (int c = lane; c < n4; c += 32) {
+      float4 x[R];
+#pragma unroll
+      for (int u = 0; u < R; ++u)
+        x[u] = u < nrow ? __ldg(reinterpret_cast<const float4*>(X + (int64_t)p[u] * n) + c)
+                        : make_float4(0.f, 0.f, 0.f, 0.f);
+      const float4 qq = qv[c];
+#pragma unroll
+      for (int u = 0; u < R; ++u) {
+        float t;
+        dot[u] = fmaf(x[u].x, qq.x, dot[u]); dot[u] = fmaf(x[u].y, qq.y, dot[u]);
+        dot[u] = fmaf(x[u].z, qq.z, dot[u]); dot[u] = fmaf(x[u].w, qq.w, dot[u]);
+        t = x[u].x - qq.x; e[u] = fmaf(t, t, e[u]); t = x[u].y - qq.y; e[u] = fmaf(t, t, e[u]);
+        t = x[u].z - qq.z; e[u] = fmaf(t, t, e[u]); t = x[u].w - qq.w; e[u] = fmaf(t, t, e[u]);
+      }
+    }
+  } else {
+    for (int c = lane; c < n; c += 32) {
+      float x[R];
+#pragma unroll
+      for (int u = 0; u < R; ++u) x[u] = u < nrow ? __ldg(X + (int64_t)p[u] * n + c) : 0.f;
+      const float qq = sq[c];
+#pragma unroll
+      for (int u = 0; u < R; ++u) {
+        dot[u] = fmaf(x[u], qq, dot[u]);
+        const float t = x[u] - qq;
+        e[u] = fmaf(t, t, e[u]);
+      }
+    }
+  }
+}
+
+constexpr int S2_ROWS = 4;  // rows of x_d' in flight per warp in stage 2
+
 __global__ void __launch_bounds__(FN_NT) k_finalize(FinParams P) {
   extern __shared__ __align__(16) float fsm[];
   float* sq = fsm;  // query coordinates [q_d' | q_r], 16-byte aligned blocks
@@ -1171,6 +1215,35 @@ __device__ __forceinline__ int warp_compact(const int32_t* src, int M, int32_t* 
   return n;
 }
 
+// ordered warp compaction that also moves one float per kept entry (val -> vout)
+template <class Keep>
+__device__ __forceinline__ int warp_compact_val(const int32_t* src, const float* val, int M,
+                                                int32_t* out, float* vout, Keep keep) {
+  const int lane = threadIdx.x & 31;
+  const unsigned below = (1u << lane) - 1;
+  int n = 0;
+  for (int b = 0; b < M; b += 128) {
+    bool k[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int i = b + 32 * u + lane;
+      k[u] = i < M && keep(i);
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const unsigned m = __ballot_sync(0xffffffffu, k[u]);
+      if (k[u]) {
+        const int at = n + __popc(m & below);
+        out[at] = src[b + 32 * u + lane];
+        vout[at] = val[b + 32 * u + lane];
+      }
+      n += __popc(m);
+    }
+  }
+  __syncwarp();
+  return n;
+}
+
 constexpr int FW_WARPS = 8;   // queries per CTA in the per-query warp phases
 constexpr int FW_BUF = 128;   // per-warp (distance, id) sort buffer: up to k = 128 entries
 
@@ -1213,7 +1286,10 @@ __global__ void __launch_bounds__(FW_WARPS * 32) k_fin_s1(FinParams P) {
   }
 }
 
-// phase 2 (MRQ+): dis_o' = |x_p|^2 + |q_p|^2 - 2 <x_d', q_d'> (Eq. 7), UB2/LB2 = dis_o' -+ m sigma
+// phase 2 (MRQ+): dis_o' = |x_p|^2 + |q_p|^2 - 2 <x_d', q_d'> (Eq. 7), UB2/LB2 = dis_o' -+ m sigma.
+// The same pass over x_d' also sums |x_d' - q_d'|^2 directly, the leading part of the
+// exact distance, into sub (free once tau_A is known), so that the exact rerank
+// reads only x_r.
 __global__ void __launch_bounds__(256) k_fin_stage2(FinParams P) {
   extern __shared__ __align__(16) float sq[];  // q_d'
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -1231,25 +1307,28 @@ __global__ void __launch_bounds__(256) k_fin_stage2(FinParams P) {
     const int cnt = min(32, hi - b);
     const int myp = lane < cnt ? P.s2pos[base + b + lane] : 0;
     const float myx = lane < cnt ? P.xn2[myp] : 0.f;
-    float mydot = 0.f;
-    for (int t = 0; t < cnt; t += 4) {
-      const int p0 = __shfl_sync(0xffffffffu, myp, t);
-      const int p1 = __shfl_sync(0xffffffffu, myp, min(t + 1, cnt - 1));
-      const int p2 = __shfl_sync(0xffffffffu, myp, min(t + 2, cnt - 1));
-      const int p3 = __shfl_sync(0xffffffffu, myp, min(t + 3, cnt - 1));
-      float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
-      row_accum2<true>(P.xd + (int64_t)p0 * P.d, P.xd + (int64_t)p1 * P.d, sq, P.d, vd, lane, s0, s1);
-      row_accum2<true>(P.xd + (int64_t)p2 * P.d, P.xd + (int64_t)p3 * P.d, sq, P.d, vd, lane, s2, s3);
-      s0 = warp_sum(s0); s1 = warp_sum(s1); s2 = warp_sum(s2); s3 = warp_sum(s3);
-      if (lane == t) mydot = s0;
-      if (lane == t + 1) mydot = s1;
-      if (lane == t + 2) mydot = s2;
-      if (lane == t + 3) mydot = s3;
+    float mydot = 0.f, myd2 = 0.f;
+    for (int t = 0; t < cnt; t += S2_ROWS) {
+      int pr[S2_ROWS];
+      float sd[S2_ROWS], se[S2_ROWS];
+#pragma unroll
+      for (int u = 0; u < S2_ROWS; ++u) {
+        pr[u] = __shfl_sync(0xffffffffu, myp, min(t + u, cnt - 1));
+        sd[u] = 0.f;
+        se[u] = 0.f;
+      }
+      rows_dot_dist2<S2_ROWS>(P.xd, pr, cnt - t, sq, P.d, vd, lane, sd, se);
+#pragma unroll
+      for (int u = 0; u < S2_ROWS; ++u) {
+        const float a = warp_sum(sd[u]), e = warp_sum(se[u]);
+        if (lane == t + u) { mydot = a; myd2 = e; }
+      }
     }
     if (lane < cnt) {
       const float diso = myx + qp2 - 2.f * mydot;
       P.s2a[base + b + lane] = diso + em;
       P.s2b[base + b + lane] = diso - em;
+      P.sub[base + b + lane] = myd2;
     }
   }
 }
@@ -1273,7 +1352,9 @@ __global__ void __launch_bounds__(FW_WARPS * 32) k_fin_s2(FinParams P) {
                                                            filt_all[wid], FW_FILT, hist_all[wid])))
                   : tauA;
     const float* lb2 = P.s2b + base;
-    M2 = warp_compact(P.s2pos + base, M1, P.spos + base, [&](int i) { return lb2[i] <= tauB; });
+    // positions to spos, their |x_d' - q_d'|^2 (stage 2, in sub) to slb
+    M2 = warp_compact_val(P.s2pos + base, P.sub + base, M1, P.spos + base, P.slb + base,
+                          [&](int i) { return lb2[i] <= tauB; });
   } else {
     M2 = warp_compact(P.s2pos + base, M1, P.spos + base, [&](int) { return true; });
   }
@@ -1310,6 +1391,61 @@ __global__ void __launch_bounds__(256) k_fin_exact(FinParams P) {
       s1 = warp_sum(s1);
       if (lane == t) mine = s0;
       if (lane == t + 1) mine = s1;
+    }
+    if (lane < cnt) P.slb[base + b + lane] = mine;
+  }
+}
+
+// phase 4, MRQ+ with r % 4 == 0: |x_d' - q_d'|^2 is already in slb (stage 2), so only
+// the x_r rows are read.  A warp takes two rows at a time and keeps EX_U float4 of
+// each in flight per lane.
+constexpr int EX_U = 4;
+__global__ void __launch_bounds__(256) k_fin_exact_r(FinParams P) {
+  extern __shared__ __align__(16) float sq[];  // q_r
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int64_t q = blockIdx.x;
+  const int r4 = P.r >> 2;
+  for (int i = threadIdx.x; i < P.r; i += 256) sq[i] = P.qr[q * P.r + i];
+  __syncthreads();
+  const float4* qv = reinterpret_cast<const float4*>(sq);
+  const int M2 = P.qm2[q];
+  const int64_t base = q * P.cap;
+  const int per = (M2 + 7) / 8, lo = min(M2, wid * per), hi = min(M2, lo + per);
+  for (int b = lo; b < hi; b += 32) {
+    const int cnt = min(32, hi - b);
+    const int myp = lane < cnt ? P.spos[base + b + lane] : 0;
+    float mine = lane < cnt ? P.slb[base + b + lane] : 0.f;
+    for (int t = 0; t < cnt; t += 2) {
+      const int p0 = __shfl_sync(0xffffffffu, myp, t);
+      const int p1 = __shfl_sync(0xffffffffu, myp, min(t + 1, cnt - 1));
+      const float4* x0 = reinterpret_cast<const float4*>(P.xr + (int64_t)p0 * P.r);
+      const float4* x1 = reinterpret_cast<const float4*>(P.xr + (int64_t)p1 * P.r);
+      float s0 = 0.f, s1 = 0.f;
+      for (int c0 = lane; c0 < r4; c0 += 32 * EX_U) {
+        float4 a[EX_U], bb[EX_U];
+#pragma unroll
+        for (int u = 0; u < EX_U; ++u) {
+          const int c = c0 + 32 * u;
+          a[u] = c < r4 ? __ldg(x0 + c) : make_float4(0.f, 0.f, 0.f, 0.f);
+          bb[u] = c < r4 ? __ldg(x1 + c) : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+#pragma unroll
+        for (int u = 0; u < EX_U; ++u) {
+          const int c = c0 + 32 * u;
+          if (c < r4) {
+            const float4 qq = qv[c];
+            float e;
+            e = a[u].x - qq.x; s0 = fmaf(e, e, s0); e = a[u].y - qq.y; s0 = fmaf(e, e, s0);
+            e = a[u].z - qq.z; s0 = fmaf(e, e, s0); e = a[u].w - qq.w; s0 = fmaf(e, e, s0);
+            e = bb[u].x - qq.x; s1 = fmaf(e, e, s1); e = bb[u].y - qq.y; s1 = fmaf(e, e, s1);
+            e = bb[u].z - qq.z; s1 = fmaf(e, e, s1); e = bb[u].w - qq.w; s1 = fmaf(e, e, s1);
+          }
+        }
+      }
+      s0 = warp_sum(s0);
+      s1 = warp_sum(s1);
+      if (lane == t) mine += s0;
+      if (lane == t + 1) mine += s1;
     }
     if (lane < cnt) P.slb[base + b + lane] = mine;
   }
@@ -1706,9 +1842,16 @@ void search_batch(mrq_index* idx, Workspace& ws, const float* q, int64_t nq, int
     k_fin_s2<<<gw, FW_WARPS * 32, 0, st>>>(fp);
     MRQ_CHECK_LAUNCH();
     mark(idx, MRQ_STAGE_EXACT, st);
-    const size_t esm = (size_t)(((d + 3) & ~3) + r) * 4;
-    ensure_smem((const void*)k_fin_exact, esm);
-    k_fin_exact<<<(unsigned)nq, 256, esm, st>>>(fp);
+    if (o.mode == MRQ_MODE_MRQ_PLUS && (r & 3) == 0) {
+      // the d-part of every exact distance came out of stage 2
+      const size_t esm = (size_t)std::max(r, 4) * 4;
+      ensure_smem((const void*)k_fin_exact_r, esm);
+      k_fin_exact_r<<<(unsigned)nq, 256, esm, st>>>(fp);
+    } else {
+      const size_t esm = (size_t)(((d + 3) & ~3) + r) * 4;
+      ensure_smem((const void*)k_fin_exact, esm);
+      k_fin_exact<<<(unsigned)nq, 256, esm, st>>>(fp);
+    }
     MRQ_CHECK_LAUNCH();
     mark(idx, MRQ_STAGE_TOPK, st);
     k_fin_topk<<<gw, FW_WARPS * 32, 0, st>>>(fp);
