@@ -29,6 +29,8 @@ constexpr int TC_BM = 128;
 constexpr int TC_BK = 64;      // 64 bf16 = one 128-byte swizzle row
 constexpr int TC_STAGES = 4;
 constexpr uint64_t WAIT_NS = 2000000000ull;
+#define FLT_MAX_F __int_as_float(0x7f7fffff)
+#define FLT_INF_F __int_as_float(0x7f800000)
 
 __device__ __forceinline__ uint32_t su32(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -55,13 +57,26 @@ __device__ __forceinline__ bool mbar_try(uint64_t* b, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
-// bounded wait; false (and *abort set) when it gives up or another thread gave up
+// try_wait that may suspend the thread for up to ns nanoseconds until the phase completes
+__device__ __forceinline__ bool mbar_try_sleep(uint64_t* b, uint32_t parity, uint32_t ns) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n"
+      " selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(su32(b)), "r"(parity), "r"(ns)
+      : "memory");
+  return ok != 0;
+}
+// bounded wait; false (and *abort set) when it gives up or another thread gave up.
+// sleep_ns > 0 lets the waiting threads sleep between tries (warps that only wait
+// for the accumulator then leave the issue slots to the co-resident CTA).
 __device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity, volatile int* abort,
-                                          int* err, int code) {
+                                          int* err, int code, uint32_t sleep_ns = 0) {
   if (mbar_try(b, parity)) return true;
   const uint64_t t0 = gtimer();
   while (true) {
-    if (mbar_try(b, parity)) return true;
+    if (sleep_ns ? mbar_try_sleep(b, parity, sleep_ns) : mbar_try(b, parity)) return true;
     if (*abort) return false;
     if (gtimer() - t0 > WAIT_NS) {
       *abort = 1;
@@ -164,6 +179,7 @@ __global__ void __launch_bounds__(256, 1)
   __shared__ __align__(8) uint64_t full[STAGES], empty[STAGES], done;
   __shared__ uint32_t tmem_slot;
   __shared__ volatile int s_abort;
+  __shared__ __align__(16) float s_coln[BN];  // epi 2: |c'|^2 of this tile's columns
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int m0 = blockIdx.x * TC_BM, n0 = blockIdx.y * BN;
@@ -227,20 +243,23 @@ __global__ void __launch_bounds__(256, 1)
   __syncwarp();
 
   // epilogue: every warp drains its 32 accumulator lanes (rows)
-  const bool have = mbar_wait(&done, 0, &s_abort, P.err, 3);
+  if (P.epi == 2) {
+    for (int t = threadIdx.x; t < BN; t += blockDim.x)
+      s_coln[t] = n0 + t < P.N ? P.coln[n0 + t] : 0.f;
+    __syncthreads();
+  }
+  const bool have = mbar_wait(&done, 0, &s_abort, P.err, 3, 20000);
   tc_fence_after();
-  unsigned long long best[PSEL];
-#pragma unroll
-  for (int t = 0; t < PSEL; ++t) best[t] = ~0ull;
   // 8 warps drain the accumulator: warp w reads tensor-memory lanes 32*(w%4) .. +31
   // (its rows) and the column half w/4 of the tile
   const int quarter = warp & 3, half = warp >> 2;
   constexpr int HALF = BN / 2;
-  if (have) {
+  const uint32_t trow = tmem + ((uint32_t)(quarter * 32) << 16);
+  if (have && P.epi != 2) {
     const int row = m0 + quarter * 32 + lane;
     for (int c = half * HALF; c < half * HALF + HALF; c += 32) {
       uint32_t r[32];
-      tc_ld32(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)c, r);
+      tc_ld32(trow + (uint32_t)c, r);
       const int col0 = n0 + c;
       if (row >= P.M || col0 >= P.N) continue;
       if (P.epi == 0) {
@@ -267,25 +286,6 @@ __global__ void __launch_bounds__(256, 1)
             else P.out1[(int64_t)row * P.ld1 + (col - P.split)] = __uint_as_float(r[j]);
           }
         }
-      } else if (P.epi == 2) {
-        // fused top-nsel: keep this row's smallest (g, list) pairs of the tile
-        const float rn = P.rown[(int64_t)row * P.rstride];
-#pragma unroll
-        for (int j = 0; j < 32; ++j) {
-          const int col = col0 + j;
-          if (col < P.N) {
-            const float gv = rn + P.coln[col] - 2.f * __uint_as_float(r[j]);
-            unsigned long long v = ((unsigned long long)fkey(gv) << 32) | (uint32_t)col;
-            if (v < best[PSEL - 1]) {
-#pragma unroll
-              for (int t = 0; t < PSEL; ++t) {
-                const unsigned long long lo = v < best[t] ? v : best[t];
-                v = v < best[t] ? best[t] : v;
-                best[t] = lo;
-              }
-            }
-          }
-        }
       } else {
         const float rn = P.rown[(int64_t)row * P.rstride];
         float* dst = P.out0 + (int64_t)row * P.ld0;
@@ -309,13 +309,94 @@ __global__ void __launch_bounds__(256, 1)
         }
       }
     }
-    if (P.epi == 2 && row < P.M) {
-      unsigned long long* out =
-          P.part + (((int64_t)row * gridDim.y + blockIdx.y) * 2 + half) * P.nsel;
+  } else if (have) {
+    // fused top-nsel of g = |q_d'|^2 + |c'|^2 - 2 <q_d', c'> over this row's half
+    // tile.  Pass 1 keeps the PSEL smallest g in a branch-free min/max insertion
+    // network; pass 2 recomputes g, marks the columns at or below the nsel-th
+    // smallest in a bit mask, and emits those below it plus ties at it in column
+    // order (lower list ids first).  g is never -0 (its terms are sums of squares
+    // and an exact cancellation rounds to +0), so float and key order agree.
+    const int row = m0 + quarter * 32 + lane;
+    const bool rv = row < P.M;
+    const float rn = rv ? P.rown[(int64_t)row * P.rstride] : 0.f;
+    float b[PSEL];
 #pragma unroll
-      for (int t = 0; t < PSEL; ++t)
-        if (t < P.nsel) out[t] = best[t];  // constant indices keep best[] in registers
+    for (int t = 0; t < PSEL; ++t) b[t] = FLT_MAX_F;
+    for (int c = half * HALF; c < half * HALF + HALF; c += 32) {
+      uint32_t r[32];
+      tc_ld32(trow + (uint32_t)c, r);
+      const int col0 = n0 + c;
+      if (col0 + 32 <= P.N) {
+#pragma unroll
+        for (int j = 0; j < 32; j += 4) {
+          const float4 cn = *reinterpret_cast<const float4*>(s_coln + c + j);
+          const float g4[4] = {fmaf(-2.f, __uint_as_float(r[j]), rn + cn.x),
+                               fmaf(-2.f, __uint_as_float(r[j + 1]), rn + cn.y),
+                               fmaf(-2.f, __uint_as_float(r[j + 2]), rn + cn.z),
+                               fmaf(-2.f, __uint_as_float(r[j + 3]), rn + cn.w)};
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+#pragma unroll
+            for (int t = PSEL - 1; t >= 1; --t) b[t] = fminf(b[t], fmaxf(b[t - 1], g4[u]));
+            b[0] = fminf(b[0], g4[u]);
+          }
+        }
+      } else {
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+          if (col0 + j < P.N) {
+            const float g = fmaf(-2.f, __uint_as_float(r[j]), rn + s_coln[c + j]);
+#pragma unroll
+            for (int t = PSEL - 1; t >= 1; --t) b[t] = fminf(b[t], fmaxf(b[t - 1], g));
+            b[0] = fminf(b[0], g);
+          }
+        }
+      }
     }
+    float thr = b[0];  // b[] is ascending: b[nsel - 1] is the largest of the first nsel
+#pragma unroll
+    for (int t = 1; t < PSEL; ++t) thr = t < P.nsel ? fmaxf(thr, b[t]) : thr;
+    int ns = 0;  // values strictly below the threshold (all of them are among b[])
+#pragma unroll
+    for (int t = 0; t < PSEL; ++t) ns += (t < P.nsel && b[t] < thr) ? 1 : 0;
+    unsigned long long* out =
+        P.part + (((int64_t)row * gridDim.y + blockIdx.y) * 2 + half) * P.nsel;
+    int si = 0, ti = 0;
+    const int tcap = P.nsel - ns;
+    // this lane's g values of one chunk, in the operand ring (idle once the MMAs are done)
+    float* gs = reinterpret_cast<float*>(smem) + (warp * 32 + lane) * 36;
+    for (int c = half * HALF; c < half * HALF + HALF; c += 32) {
+      uint32_t r[32];
+      tc_ld32(trow + (uint32_t)c, r);
+      const int col0 = n0 + c;
+      uint32_t mask = 0;
+#pragma unroll
+      for (int j = 0; j < 32; j += 4) {
+        const float4 cn = *reinterpret_cast<const float4*>(s_coln + c + j);
+        const float4 g4 = make_float4(fmaf(-2.f, __uint_as_float(r[j]), rn + cn.x),
+                                      fmaf(-2.f, __uint_as_float(r[j + 1]), rn + cn.y),
+                                      fmaf(-2.f, __uint_as_float(r[j + 2]), rn + cn.z),
+                                      fmaf(-2.f, __uint_as_float(r[j + 3]), rn + cn.w));
+        mask |= (g4.x <= thr ? 1u : 0u) << j;
+        mask |= (g4.y <= thr ? 1u : 0u) << (j + 1);
+        mask |= (g4.z <= thr ? 1u : 0u) << (j + 2);
+        mask |= (g4.w <= thr ? 1u : 0u) << (j + 3);
+        *reinterpret_cast<float4*>(gs + j) = g4;
+      }
+      if (!rv) mask = 0;
+      if (col0 + 32 > P.N) mask &= P.N > col0 ? (0xffffffffu >> (32 - (P.N - col0))) : 0u;
+      while (mask) {
+        const int jj = __ffs(mask) - 1;
+        mask &= mask - 1;
+        const float g = gs[jj];
+        const unsigned long long key =
+            ((unsigned long long)fkey(g) << 32) | (uint32_t)(col0 + jj);
+        if (g < thr) out[si++] = key;
+        else if (ti < tcap) out[ns + ti++] = key;
+      }
+    }
+    if (rv)
+      for (int t = ns + ti; t < P.nsel; ++t) out[t] = ~0ull;  // fewer than nsel columns
   }
   tc_fence_before();
   __syncthreads();
@@ -324,18 +405,63 @@ __global__ void __launch_bounds__(256, 1)
                  : "memory");
 }
 
-// x = X[m, k] - shift[k] -> hi = bf16(x) (row m), lo = bf16(x - hi) (row M + m)
+// x = X[m, k] - shift[k] -> hi = bf16(x) (row m), lo = bf16(x - hi) (row M + m).
+// One warp per row (8 rows per block); with vec (K, ld multiples of 4 and X, shift,
+// out 16-byte aligned) each lane converts 4 consecutive k per step.
 __global__ void k_split_bf16(const float* __restrict__ X, int M, int K, int ld,
-                             const float* __restrict__ shift, int two,
+                             const float* __restrict__ shift, int two, int vec,
                              __nv_bfloat16* __restrict__ out) {
-  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= (int64_t)M * K) return;
-  int64_t m = i / K;
-  int k = (int)(i % K);
-  float x = X[m * ld + k] - (shift ? shift[k] : 0.f);
-  __nv_bfloat16 h = __float2bfloat16_rn(x);
-  out[i] = h;
-  if (two) out[(int64_t)M * K + i] = __float2bfloat16_rn(x - __bfloat162float(h));
+  const int lane = threadIdx.x & 31;
+  const int64_t m = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
+  if (m >= M) return;
+  const float* x = X + m * ld;
+  __nv_bfloat16* hi = out + m * K;
+  __nv_bfloat16* lo = out + ((int64_t)M + m) * K;
+  if (vec) {
+    const int k4 = K >> 2;
+#pragma unroll 2
+    for (int c = lane; c < k4; c += 32) {
+      float4 v = __ldg(reinterpret_cast<const float4*>(x) + c);
+      if (shift) {
+        const float4 sh = __ldg(reinterpret_cast<const float4*>(shift) + c);
+        v.x -= sh.x; v.y -= sh.y; v.z -= sh.z; v.w -= sh.w;
+      }
+      const __nv_bfloat162 h0 = __floats2bfloat162_rn(v.x, v.y);
+      const __nv_bfloat162 h1 = __floats2bfloat162_rn(v.z, v.w);
+      uint2 hv;
+      hv.x = *reinterpret_cast<const uint32_t*>(&h0);
+      hv.y = *reinterpret_cast<const uint32_t*>(&h1);
+      reinterpret_cast<uint2*>(hi)[c] = hv;
+      if (two) {
+        const float2 f0 = __bfloat1622float2(h0), f1 = __bfloat1622float2(h1);
+        const __nv_bfloat162 l0 = __floats2bfloat162_rn(v.x - f0.x, v.y - f0.y);
+        const __nv_bfloat162 l1 = __floats2bfloat162_rn(v.z - f1.x, v.w - f1.y);
+        uint2 lv;
+        lv.x = *reinterpret_cast<const uint32_t*>(&l0);
+        lv.y = *reinterpret_cast<const uint32_t*>(&l1);
+        reinterpret_cast<uint2*>(lo)[c] = lv;
+      }
+    }
+  } else {
+    for (int k = lane; k < K; k += 32) {
+      const float v = x[k] - (shift ? shift[k] : 0.f);
+      const __nv_bfloat16 h = __float2bfloat16_rn(v);
+      hi[k] = h;
+      if (two) lo[k] = __float2bfloat16_rn(v - __bfloat162float(h));
+    }
+  }
+}
+
+// launch of k_split_bf16 for an M x K block of X (row stride ld)
+void split_bf16(const float* X, int M, int K, int ld, const float* shift, bool two,
+                __nv_bfloat16* out, cudaStream_t st) {
+  auto al16 = [](const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; };
+  const int vec = (K % 4 == 0 && ld % 4 == 0 && al16(X) && (!shift || al16(shift)) &&
+                   (reinterpret_cast<uintptr_t>(out) & 7) == 0)
+                      ? 1
+                      : 0;
+  k_split_bf16<<<ceil_div(M, 8), 256, 0, st>>>(X, M, K, ld, shift, two ? 1 : 0, vec, out);
+  MRQ_CHECK_LAUNCH();
 }
 
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
@@ -426,9 +552,7 @@ int tc_check_error() {
 
 void project_tc(const float* Q, const float* mu, const __nv_bfloat16* W2, int M, int D, int d,
                 bool split3, __nv_bfloat16* qbf, float* qd, float* qr, cudaStream_t st) {
-  const int64_t tot = (int64_t)M * D;
-  k_split_bf16<<<ceil_div(tot, 256), 256, 0, st>>>(Q, M, D, D, mu, split3 ? 1 : 0, qbf);
-  MRQ_CHECK_LAUNCH();
+  split_bf16(Q, M, D, D, mu, split3, qbf, st);
   TcArgs a{};
   a.M = M; a.N = D; a.K = D;
   a.phases = split3 ? 3 : 1;
@@ -441,9 +565,7 @@ void project_tc(const float* Q, const float* mu, const __nv_bfloat16* W2, int M,
 void probe_tc(const float* qd, const float* qstat, const __nv_bfloat16* C2, const float* cn2,
               int M, int nlist, int d, bool split3, __nv_bfloat16* qbf, float* gmat,
               cudaStream_t st) {
-  const int64_t tot = (int64_t)M * d;
-  k_split_bf16<<<ceil_div(tot, 256), 256, 0, st>>>(qd, M, d, d, nullptr, split3 ? 1 : 0, qbf);
-  MRQ_CHECK_LAUNCH();
+  split_bf16(qd, M, d, d, nullptr, split3, qbf, st);
   TcArgs a{};
   a.M = M; a.N = nlist; a.K = d;
   a.phases = split3 ? 3 : 1;
@@ -460,9 +582,7 @@ void probe_tc(const float* qd, const float* qstat, const __nv_bfloat16* C2, cons
 int probe_tc_topk(const float* qd, const float* qstat, const __nv_bfloat16* C2, const float* cn2,
                   int M, int nlist, int d, bool split3, int nsel, __nv_bfloat16* qbf,
                   unsigned long long* part, cudaStream_t st) {
-  const int64_t tot = (int64_t)M * d;
-  k_split_bf16<<<ceil_div(tot, 256), 256, 0, st>>>(qd, M, d, d, nullptr, split3 ? 1 : 0, qbf);
-  MRQ_CHECK_LAUNCH();
+  split_bf16(qd, M, d, d, nullptr, split3, qbf, st);
   TcArgs a{};
   a.M = M; a.N = nlist; a.K = d;
   a.phases = split3 ? 3 : 1;
@@ -538,9 +658,7 @@ void project_noalloc(mrq_index* idx, const float* q, int64_t nq, int precision, 
   int* err = reinterpret_cast<int*>(base);
   __nv_bfloat16* qbf = reinterpret_cast<__nv_bfloat16*>(base + 256);
   MRQ_CUDA(cudaMemsetAsync(err, 0, sizeof(int), st));
-  const int64_t tot = nq * D;
-  k_split_bf16<<<ceil_div(tot, 256), 256, 0, st>>>(q, (int)nq, D, D, idx->mu.p, split3 ? 1 : 0, qbf);
-  MRQ_CHECK_LAUNCH();
+  split_bf16(q, (int)nq, D, D, idx->mu.p, split3, qbf, st);
   TcArgs a{};
   a.M = (int)nq; a.N = D; a.K = D;
   a.phases = split3 ? 3 : 1;

@@ -60,14 +60,32 @@ __global__ void k_qstats(const float* __restrict__ qd, const float* __restrict__
   if (q >= nq) return;
   const int lane = threadIdx.x & 31;
   float qr2 = 0.f, s2 = 0.f, qd2 = 0.f;
-  for (int i = lane; i < r; i += 32) {
-    float v = qr[q * r + i];
-    qr2 = fmaf(v, v, qr2);
-    s2 = fmaf(v * v, lam[d + i], s2);
+  if ((r & 3) == 0) {  // rows and lam + d are 16-byte aligned (d is a multiple of 32)
+    const float4* x = reinterpret_cast<const float4*>(qr + q * r);
+    const float4* l = reinterpret_cast<const float4*>(lam + d);
+#pragma unroll 4
+    for (int i = lane; i < (r >> 2); i += 32) {
+      const float4 v = __ldg(x + i), w = __ldg(l + i);
+      qr2 = fmaf(v.x, v.x, qr2); qr2 = fmaf(v.y, v.y, qr2);
+      qr2 = fmaf(v.z, v.z, qr2); qr2 = fmaf(v.w, v.w, qr2);
+      s2 = fmaf(v.x * v.x, w.x, s2); s2 = fmaf(v.y * v.y, w.y, s2);
+      s2 = fmaf(v.z * v.z, w.z, s2); s2 = fmaf(v.w * v.w, w.w, s2);
+    }
+  } else {
+    for (int i = lane; i < r; i += 32) {
+      float v = qr[q * r + i];
+      qr2 = fmaf(v, v, qr2);
+      s2 = fmaf(v * v, lam[d + i], s2);
+    }
   }
-  for (int i = lane; i < d; i += 32) {
-    float v = qd[q * d + i];
-    qd2 = fmaf(v, v, qd2);
+  {
+    const float4* x = reinterpret_cast<const float4*>(qd + q * d);
+#pragma unroll 4
+    for (int i = lane; i < (d >> 2); i += 32) {
+      const float4 v = __ldg(x + i);
+      qd2 = fmaf(v.x, v.x, qd2); qd2 = fmaf(v.y, v.y, qd2);
+      qd2 = fmaf(v.z, v.z, qd2); qd2 = fmaf(v.w, v.w, qd2);
+    }
   }
   qr2 = warp_sum(qr2);
   s2 = warp_sum(s2);
@@ -263,32 +281,36 @@ __global__ void __launch_bounds__(PS_NT) k_probe_select(const float* __restrict_
 }
 
 // merge of the fused probe candidates: per query (one warp), the nprobe smallest of
-// tiles x nprobe (key, list) pairs, ascending
+// the n = tiles x nprobe (key, list) pairs, ascending.  The n <= 32 * SL keys sit in
+// registers (SL per lane); each of nprobe rounds takes a warp-wide minimum and
+// retires it (the keys are distinct: every list appears in one tile).
+template <int SL>
 __global__ void k_probe_merge(const unsigned long long* __restrict__ part, int64_t nq, int tiles,
                               int nprobe, int32_t* __restrict__ plist) {
-  __shared__ unsigned long long buf_all[8][512];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int64_t q = (int64_t)blockIdx.x * 8 + wid;
   if (q >= nq) return;
-  unsigned long long* buf = buf_all[wid];
   const int n = tiles * nprobe;
-  int n2 = 1;
-  while (n2 < n) n2 <<= 1;
-  for (int i = lane; i < n2; i += 32) buf[i] = i < n ? part[q * n + i] : ~0ull;
-  __syncwarp();
-  for (int size = 2; size <= n2; size <<= 1) {
-    for (int stride = size >> 1; stride > 0; stride >>= 1) {
-      for (int t = lane; t < n2 / 2; t += 32) {
-        const int i = 2 * t - (t & (stride - 1));
-        const int j = i + stride;
-        const bool up = ((i & size) == 0);
-        const unsigned long long x = buf[i], y = buf[j];
-        if ((x > y) == up) { buf[i] = y; buf[j] = x; }
-      }
-      __syncwarp();
-    }
+  unsigned long long v[SL];
+#pragma unroll
+  for (int s = 0; s < SL; ++s) {
+    const int i = s * 32 + lane;
+    v[s] = i < n ? part[q * n + i] : ~0ull;
   }
-  for (int r = lane; r < nprobe; r += 32) plist[q * nprobe + r] = (int32_t)(buf[r] & 0xffffffffu);
+  for (int r = 0; r < nprobe; ++r) {
+    unsigned long long m = v[0];
+#pragma unroll
+    for (int s = 1; s < SL; ++s) m = v[s] < m ? v[s] : m;
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+      const unsigned long long y = __shfl_xor_sync(0xffffffffu, m, o);
+      m = y < m ? y : m;
+    }
+    if (lane == 0) plist[q * nprobe + r] = (int32_t)(m & 0xffffffffu);
+#pragma unroll
+    for (int s = 0; s < SL; ++s)
+      if (v[s] == m) v[s] = ~0ull;
+  }
 }
 
 // g_j = |q_d' - c_j'|^2 of every probed list, as a direct float32 sum (one warp per
@@ -660,14 +682,17 @@ __global__ void k_pair_prep(const float* __restrict__ qd, const float* __restric
   const float sg = sqrtf(g);
   const int nch = d >> 5;
   const int topq = (1 << qbits) - 1;
-  float v[16];
+  // q'_i = (q_d'_i - c'_i) / sqrt(g); computed twice (range, then codes) so that no
+  // per-lane array is indexed at run time
+  const float* qrow = qd + q * d;
+  const float* crow = cent + (int64_t)j * d;
   float lo = FINF, hi = -FINF;
+#pragma unroll 4
   for (int c = 0; c < nch; ++c) {
     const int i = c * 32 + lane;
-    const float t = qd[q * d + i] - cent[(int64_t)j * d + i];
-    v[c] = g > 0.f ? t / sg : 0.f;
-    lo = fminf(lo, v[c]);
-    hi = fmaxf(hi, v[c]);
+    const float v = g > 0.f ? (qrow[i] - crow[i]) / sg : 0.f;
+    lo = fminf(lo, v);
+    hi = fmaxf(hi, v);
   }
   lo = warp_min(lo);
   hi = warp_max(hi);
@@ -675,9 +700,11 @@ __global__ void k_pair_prep(const float* __restrict__ qd, const float* __restric
   int ssum = 0;
   uint32_t* out = qplanes + w * (int64_t)(qbits * nch);
   for (int c = 0; c < nch; ++c) {
+    const int i = c * 32 + lane;
+    const float v = g > 0.f ? (qrow[i] - crow[i]) / sg : 0.f;
     int qb = 0;
     if (delta > 0.f) {
-      qb = min((int)floorf((v[c] - lo) / delta + 0.5f), topq);
+      qb = min((int)floorf((v - lo) / delta + 0.5f), topq);
       qb = max(qb, 0);
     }
     ssum += qb;
@@ -1681,7 +1708,13 @@ void search_batch(mrq_index* idx, Workspace& ws, const float* q, int64_t nq, int
   }
   mark(idx, MRQ_STAGE_SELECT, st);
   if (fused) {
-    k_probe_merge<<<ceil_div(nq, 8), 256, 0, st>>>(ws.ppart.p, nq, tiles_, nprobe, ws.plist.p);
+    const int nsl = ceil_div(tiles_ * nprobe, 32);
+    const unsigned mg = ceil_div(nq, 8);
+    if (nsl <= 1) k_probe_merge<1><<<mg, 256, 0, st>>>(ws.ppart.p, nq, tiles_, nprobe, ws.plist.p);
+    else if (nsl <= 2) k_probe_merge<2><<<mg, 256, 0, st>>>(ws.ppart.p, nq, tiles_, nprobe, ws.plist.p);
+    else if (nsl <= 4) k_probe_merge<4><<<mg, 256, 0, st>>>(ws.ppart.p, nq, tiles_, nprobe, ws.plist.p);
+    else if (nsl <= 8) k_probe_merge<8><<<mg, 256, 0, st>>>(ws.ppart.p, nq, tiles_, nprobe, ws.plist.p);
+    else k_probe_merge<16><<<mg, 256, 0, st>>>(ws.ppart.p, nq, tiles_, nprobe, ws.plist.p);
     MRQ_CHECK_LAUNCH();
     k_probe_refine<<<ceil_div(nq * nprobe, 8), 256, 0, st>>>(ws.qd.p, idx->cent.p, ws.plist.p,
                                                             nq * nprobe, nprobe, d, ws.pg.p);
