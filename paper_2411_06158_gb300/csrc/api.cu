@@ -41,6 +41,18 @@ bool on_device(const void* p) {
   return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
+// page-locked host memory (cudaHostAlloc / cudaHostRegister): copies from it can be
+// asynchronous and captured in a CUDA graph
+bool pinned_host(const void* p) {
+  if (!p) return false;
+  cudaPointerAttributes a{};
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeHost;
+}
+
 cudaStream_t stream_of(const mrq_search_opts& o) { return (cudaStream_t)o.cuda_stream; }
 
 void use_device(const mrq_index* idx) { MRQ_CUDA(cudaSetDevice(idx->device)); }
@@ -176,14 +188,27 @@ int mrq_search(mrq_index* idx, const float* queries, int64_t nq, int k, int npro
     idx->prof_on = o.profile != 0;
     idx->prof_batches = 0;
     idx->launches = 0;
-    const bool use_graph = o.graph && !o.profile && qdev && odev;
+    // a captured graph also covers host buffers when they are page-locked (its copy
+    // nodes then read and write those buffers on every replay)
+    const bool use_graph = o.graph && !o.profile && (qdev || pinned_host(queries)) &&
+                           (odev || (pinned_host(ids) && pinned_host(dists)));
     mrq_index::GraphKey key{queries, ids, dists, nq, k, nprobe, o.mode, o.precision,
                             o.query_bits, o.batched, o.eps0, o.m};
     auto run_batches = [&](cudaStream_t s_) {
       for (int64_t s = 0; s < nq; s += qb) {
         const int64_t b = std::min(qb, nq - s);
-        mrq::search_batch(idx, ws, queries + s * D, b, k, nprobe, o, ids + s * k, dists + s * k,
-                          ws.stats.p + s * 3, s_);
+        const float* qp = queries + s * D;
+        if (!qdev) {
+          MRQ_CUDA(cudaMemcpyAsync(ws.q.p, qp, 4 * b * D, cudaMemcpyHostToDevice, s_));
+          qp = ws.q.p;
+        }
+        int64_t* oi = odev ? ids + s * k : ws.oids.p;
+        float* od = odev ? dists + s * k : ws.odist.p;
+        mrq::search_batch(idx, ws, qp, b, k, nprobe, o, oi, od, ws.stats.p + s * 3, s_);
+        if (!odev) {
+          MRQ_CUDA(cudaMemcpyAsync(ids + s * k, oi, 8 * b * k, cudaMemcpyDeviceToHost, s_));
+          MRQ_CUDA(cudaMemcpyAsync(dists + s * k, od, 4 * b * k, cudaMemcpyDeviceToHost, s_));
+        }
       }
     };
     if (use_graph) {
@@ -226,27 +251,19 @@ int mrq_search(mrq_index* idx, const float* queries, int64_t nq, int k, int npro
       MRQ_CUDA(cudaStreamWaitEvent(st, idx->graph_ev[1], 0));
       idx->launches = idx->graph_launches;
     }
-    for (int64_t s = 0; s < nq && !use_graph; s += qb) {
-      const int64_t b = std::min(qb, nq - s);
-      const float* qp = queries + s * D;
-      if (!qdev) {
-        MRQ_CUDA(cudaMemcpyAsync(ws.q.p, qp, 4 * b * D, cudaMemcpyHostToDevice, st));
-        qp = ws.q.p;
-      }
-      int64_t* oi = odev ? ids + s * k : ws.oids.p;
-      float* od = odev ? dists + s * k : ws.odist.p;
-      mrq::search_batch(idx, ws, qp, b, k, nprobe, o, oi, od, ws.stats.p + s * 3, st);
-      if (!odev) {
-        MRQ_CUDA(cudaMemcpyAsync(ids + s * k, oi, 8 * b * k, cudaMemcpyDeviceToHost, st));
-        MRQ_CUDA(cudaMemcpyAsync(dists + s * k, od, 4 * b * k, cudaMemcpyDeviceToHost, st));
-      }
+    if (!use_graph) run_batches(st);
+    // the tensor-core kernels' error word comes back with the results (one small
+    // asynchronous copy); the per-query counters stay on the device until asked for
+    int* herr = o.precision != MRQ_PREC_FP32 ? mrq::tc_error_mirror() : nullptr;
+    if (herr) {
+      *herr = 0;
+      MRQ_CUDA(cudaMemcpyAsync(herr, mrq::tc_error_word(), sizeof(int), cudaMemcpyDeviceToHost, st));
     }
-    idx->last_stats.resize((size_t)nq * 3);
-    MRQ_CUDA(cudaMemcpyAsync(idx->last_stats.data(), ws.stats.p, 8 * nq * 3, cudaMemcpyDeviceToHost, st));
     MRQ_CUDA(cudaStreamSynchronize(st));
-    if (o.precision != MRQ_PREC_FP32 && mrq::tc_check_error())
+    if (herr && *herr && mrq::tc_check_error())
       mrq::fail(MRQ_ETIMEDOUT, "a tensor-core kernel gave up waiting on its pipeline");
     idx->last_nq = nq;
+    idx->last_stats_dev = true;
     for (int s = 0; s < MRQ_NSTAGES; ++s) idx->prof_ms[s] = 0.0;
     if (idx->prof_on) {
       for (int b = 0; b < idx->prof_batches; ++b)
@@ -348,6 +365,13 @@ int mrq_last_search_stats(const mrq_index* idx, int64_t nq, int64_t* n_cand, int
   return guarded([&] {
     MRQ_REQUIRE(idx != nullptr, "index is NULL");
     MRQ_REQUIRE(nq == idx->last_nq, "nq differs from the last search on this index");
+    if (idx->last_stats_dev) {
+      use_device(idx);
+      idx->last_stats.resize((size_t)nq * 3);
+      MRQ_CUDA(cudaMemcpy(idx->last_stats.data(), idx->ws.stats.p, 8 * nq * 3,
+                          cudaMemcpyDeviceToHost));
+      idx->last_stats_dev = false;
+    }
     for (int64_t i = 0; i < nq; ++i) {
       if (n_cand) n_cand[i] = idx->last_stats[i * 3 + 0];
       if (n_s1) n_s1[i] = idx->last_stats[i * 3 + 1];

@@ -127,7 +127,8 @@ struct mrq_index {
   mrq::DevBuf<float> xd, xr, xn2;         // list-major, unpadded
   mrq::Workspace ws;
   int64_t last_nq = 0;
-  std::vector<int64_t> last_stats;        // nq x 3 host copy of the last search's counters
+  mutable bool last_stats_dev = false;  // last search's counters still in ws.stats (device)
+  mutable std::vector<int64_t> last_stats;        // nq x 3 host copy of the last search's counters
   // profiling of the last search: MRQ_NSTAGES + 1 events per batch
   std::vector<cudaEvent_t> prof_ev;
   int prof_batches = 0;
@@ -192,6 +193,8 @@ void nearest_f32(const float* A, int lda, const float* B, int ldb, int M, int N,
 bool tc_available();
 void project_noalloc(mrq_index* idx, const float* q, int64_t nq, int precision, float* qp,
                      cudaStream_t st);  // static scratch only, no allocation
+int* tc_error_word();    // device word the tensor-core kernels set when a wait gives up
+int* tc_error_mirror();  // page-locked host int for reading it back asynchronously
 int tc_check_error();  // nonzero if a bounded wait in a tensor-core kernel gave up
 void project_tc(const float* Q, const float* mu, const __nv_bfloat16* W2, int M, int D, int d,
                 bool split3, __nv_bfloat16* qbf, float* qd, float* qr, cudaStream_t st);

@@ -507,11 +507,7 @@ void launch_tc(const __nv_bfloat16* A2, const __nv_bfloat16* B2, const TcArgs& a
 }
 
 void run_tc(const __nv_bfloat16* A2, const __nv_bfloat16* B2, TcArgs a, cudaStream_t st) {
-  if (!g_err) {
-    MRQ_CUDA(cudaMalloc(&g_err, sizeof(int)));
-    MRQ_CUDA(cudaMemset(g_err, 0, sizeof(int)));
-  }
-  a.err = g_err;
+  a.err = tc_error_word();
   // the fused top-nsel list is sized to nsel (registers, a divergent insertion per column);
   // short contractions (the probe: K = d) use a 2-stage ring so that two CTAs fit per SM
   const bool short_k = (int64_t)((a.K + TC_BK - 1) / TC_BK) * a.phases <= 2;
@@ -540,6 +536,20 @@ bool tc_available() {
   cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev);
   cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev);
   return major == 10 && minor == 3;
+}
+
+int* tc_error_word() {
+  if (!g_err) {
+    MRQ_CUDA(cudaMalloc(&g_err, sizeof(int)));
+    MRQ_CUDA(cudaMemset(g_err, 0, sizeof(int)));
+  }
+  return g_err;
+}
+
+int* tc_error_mirror() {
+  static int* h = nullptr;
+  if (!h) MRQ_CUDA(cudaHostAlloc(reinterpret_cast<void**>(&h), sizeof(int), cudaHostAllocDefault));
+  return h;
 }
 
 int tc_check_error() {

@@ -630,7 +630,7 @@ constexpr int BATCH_MAXW = 16;  // code words per vector kept in registers (bits
 struct PairQ {
   float sg, a0, e0, em;  // sqrt(g), g + |q_r|^2, eps0*sqrt(g), m*sigma
   float ql, qdelta;      // q' ~ ql + qdelta * qbar
-  int qsum, pad;
+  int qsum, q;           // q: the pair's query
 };
 
 // pairs with w % nprobe < first are left out (scanned by the seed pass)
@@ -723,7 +723,7 @@ __global__ void k_pair_prep(const float* __restrict__ qd, const float* __restric
     r.ql = lo;
     r.qdelta = delta;
     r.qsum = ssum;
-    r.pad = 0;
+    r.q = (int)q;
     pq[w] = r;
   }
 }
@@ -782,11 +782,12 @@ __global__ void __launch_bounds__(256) k_scan_batched(BatchParams P) {
     for (int w = 0; w < W; ++w) su += __popc(cw[w]) << (w / NCH);
     const float fa = __ldg(P.fadd + pp), fr = __ldg(P.fres + pp), fe = __ldg(P.ferr + pp);
     const int g0 = P.loffq[j] + grp * BATCH_G;
-    const int g1 = min(P.loffq[j] + P.lcount[j], g0 + BATCH_G);
-    for (int gi = g0; gi < g1; ++gi) {
-      const int w_pair = P.lqueue[gi];
-      const int64_t q = w_pair / P.nprobe;
+    const int ng = min(P.loffq[j] + P.lcount[j], g0 + BATCH_G) - g0;
+    const int my_pair = lane < ng ? P.lqueue[g0 + lane] : 0;  // the group's pairs, one per lane
+    for (int t = 0; t < ng; ++t) {
+      const int w_pair = __shfl_sync(0xffffffffu, my_pair, t);
       const PairQ pr = P.pq[w_pair];
+      const int64_t q = pr.q;
       const uint32_t* qp = P.qplanes + (int64_t)w_pair * QW;
       int dot = 0;
       for (int b = 0; b < P.qbits; ++b) {
@@ -1156,6 +1157,41 @@ __device__ uint32_t warp_radix_kth(const float* vals, int M, int k, int* hist) {
   return prefix;
 }
 
+// k-th smallest key (k <= 32) of vals[0..M), M >= k.  The k smallest seen so far are
+// kept sorted across the lanes (lane i holds the i-th smallest); values arrive 32 at
+// a time and only those below the current k-th (and not above `hint`, an upper bound
+// of the answer, or +inf) are inserted, one at a time.
+__device__ uint32_t warp_kth_small(const float* vals, int M, int k, float hint) {
+  const int lane = threadIdx.x & 31;
+  const uint32_t hk = fkey(hint);
+  uint32_t lst = 0xffffffffu;
+  uint32_t kth = 0xffffffffu;
+  for (int b = 0; b < M; b += 128) {  // four chunks of loads in flight
+    uint32_t x[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int i = b + 32 * u + lane;
+      x[u] = i < M ? fkey(vals[i]) : 0xffffffffu;
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      unsigned cand = __ballot_sync(0xffffffffu, x[u] < kth && x[u] <= hk);
+      while (cand) {
+        const int src = __ffs(cand) - 1;
+        cand &= cand - 1;
+        const uint32_t y = __shfl_sync(0xffffffffu, x[u], src);
+        if (y < kth) {
+          const int pos = __popc(__ballot_sync(0xffffffffu, lst < y));
+          const uint32_t up = __shfl_up_sync(0xffffffffu, lst, 1);
+          lst = lane > pos ? up : (lane == pos ? y : lst);
+          kth = __shfl_sync(0xffffffffu, lst, k - 1);
+        }
+      }
+    }
+  }
+  return kth;
+}
+
 // count of vals[0..M) that are <= h, gathering up to cap of them into buf
 __device__ __forceinline__ int warp_filter_le(const float* vals, int M, float h, float* buf, int cap) {
   const int lane = threadIdx.x & 31;
@@ -1301,7 +1337,13 @@ __global__ void __launch_bounds__(FW_WARPS * 32) k_fin_s1(FinParams P) {
   float tauA = FINF;
   if (M >= P.k) {
     const float hint = P.gtau ? fkey_inv(__ldcg(P.gtau + q)) : FINF;
-    tauA = fkey_inv(warp_kth_filtered(P.sub + base, M, P.k, hint, filt_all[wid], FW_FILT, hist));
+    if (P.k <= 32) {
+      uint32_t kt = warp_kth_small(P.sub + base, M, P.k, hint);
+      if (kt == 0xffffffffu) kt = warp_kth_small(P.sub + base, M, P.k, FINF);  // hint too low
+      tauA = fkey_inv(kt);
+    } else {
+      tauA = fkey_inv(warp_kth_filtered(P.sub + base, M, P.k, hint, filt_all[wid], FW_FILT, hist));
+    }
   }
   const float* slb = P.slb + base;
   const int M1 = warp_compact(P.spos + base, M, P.s2pos + base,
@@ -1374,10 +1416,17 @@ __global__ void __launch_bounds__(FW_WARPS * 32) k_fin_s2(FinParams P) {
   if (P.mode == MRQ_MODE_MRQ_PLUS) {
     const float tauA = P.qtau[q];
     // only upper bounds <= tau_A can lower tau_B = min(tau_A, k-th smallest UB2)
-    const float tauB =
-        M1 >= P.k ? fminf(tauA, fkey_inv(warp_kth_filtered(P.s2a + base, M1, P.k, tauA,
-                                                           filt_all[wid], FW_FILT, hist_all[wid])))
-                  : tauA;
+    float tauB = tauA;
+    if (M1 >= P.k) {
+      if (P.k <= 32) {
+        // fewer than k upper bounds <= tau_A: the k-th exceeds tau_A, tau_B = tau_A
+        const uint32_t kt = warp_kth_small(P.s2a + base, M1, P.k, tauA);
+        if (kt != 0xffffffffu) tauB = fminf(tauA, fkey_inv(kt));
+      } else {
+        tauB = fminf(tauA, fkey_inv(warp_kth_filtered(P.s2a + base, M1, P.k, tauA, filt_all[wid],
+                                                      FW_FILT, hist_all[wid])));
+      }
+    }
     const float* lb2 = P.s2b + base;
     // positions to spos, their |x_d' - q_d'|^2 (stage 2, in sub) to slb
     M2 = warp_compact_val(P.s2pos + base, P.sub + base, M1, P.spos + base, P.slb + base,
@@ -1489,7 +1538,9 @@ __global__ void __launch_bounds__(FW_WARPS * 32) k_fin_topk(FinParams P) {
   const int64_t base = q * P.cap;
   const int M2 = P.qm2[q];
   const float* dist = P.slb + base;
-  const uint32_t T = M2 > P.k ? warp_radix_kth(dist, M2, P.k, hist_all[wid]) : 0xffffffffu;
+  const uint32_t T = M2 > P.k ? (P.k <= 32 ? warp_kth_small(dist, M2, P.k, FINF)
+                                           : warp_radix_kth(dist, M2, P.k, hist_all[wid]))
+                              : 0xffffffffu;
   int n = 0;
   for (int b = 0; b < M2; b += 32) {  // entries strictly below T (fewer than k)
     const int i = b + lane;
