@@ -194,11 +194,23 @@ int mrq_search(mrq_index* idx, const float* queries, int64_t nq, int k, int npro
                            (odev || (pinned_host(ids) && pinned_host(dists)));
     mrq_index::GraphKey key{queries, ids, dists, nq, k, nprobe, o.mode, o.precision,
                             o.query_bits, o.batched, o.eps0, o.m};
+    // tensor-core forms read each query once (the bf16 split), so page-locked host
+    // queries are read in place through their device mapping instead of copied first
+    const float* qmap = nullptr;
+    if (!qdev && o.precision != MRQ_PREC_FP32 && pinned_host(queries)) {
+      void* dp = nullptr;
+      if (cudaHostGetDevicePointer(&dp, const_cast<float*>(queries), 0) == cudaSuccess)
+        qmap = static_cast<const float*>(dp);
+      else
+        cudaGetLastError();
+    }
     auto run_batches = [&](cudaStream_t s_) {
       for (int64_t s = 0; s < nq; s += qb) {
         const int64_t b = std::min(qb, nq - s);
         const float* qp = queries + s * D;
-        if (!qdev) {
+        if (qmap) {
+          qp = qmap + s * D;
+        } else if (!qdev) {
           MRQ_CUDA(cudaMemcpyAsync(ws.q.p, qp, 4 * b * D, cudaMemcpyHostToDevice, s_));
           qp = ws.q.p;
         }
