@@ -584,6 +584,172 @@ __global__ void __launch_bounds__(SCAN_WARPS * 32) k_scan(ScanParams P) {
   }
 }
 
+// Quantized-query scan with the code shape fixed at compile time: NCH 32-dim chunks,
+// BITS code planes, QB query planes.  The same arithmetic, in the same order, as
+// k_scan<KM, true, false>, with the query planes in registers (warp-uniform ballot
+// words), the candidate's code words fetched with VW-wide loads and every loop
+// unrolled; no shared memory.  The insertion into the warp's top-k list (KM 0) skips
+// upper bounds not below the query's published bound, which cannot lower tau.
+template <int KM, int NCH, int BITS, int QB>
+__global__ void __launch_bounds__(SCAN_WARPS * 32) k_scan_q(ScanParams P) {
+  constexpr int W = BITS * NCH;
+  constexpr int VW = (W % 4 == 0) ? 4 : (W % 2 == 0) ? 2 : 1;
+  constexpr int topc = (1 << BITS) - 1;
+  constexpr int topq = (1 << QB) - 1;
+  constexpr int d = NCH * 32;
+  const int lane = threadIdx.x & 31;
+  const int64_t n_items = P.items ? (int64_t)*P.nitems : P.npairs;
+  while (true) {
+    unsigned int it = 0;
+    if (lane == 0) it = atomicAdd(P.work, 1u);
+    it = __shfl_sync(0xffffffffu, it, 0);
+    if ((int64_t)it >= n_items) break;
+    int64_t w = it, c_lo = 0, c_hi = -1;
+    if (P.items) {
+      const int64_t v = P.items[it];
+      w = v >> 32;
+      c_lo = (v & 0xffffffffll) * P.chunk;
+      c_hi = c_lo + P.chunk;
+    }
+    const int64_t q = (int64_t)w / P.nprobe;
+    const int j = P.plist[w];
+    const float g = P.pg[w];
+    const float sg = sqrtf(g);
+    const float qr2 = P.qstat[q * 4 + 0];
+    const float sigma = P.qstat[q * 4 + 1];
+    const float a0 = g + qr2;
+    const float em = P.m * sigma;
+    const float e0 = P.eps0 * sg;
+
+    // q' = (q_d' - c_j')/sqrt(g_j), quantized to QB bits on the [min, max] grid
+    float qv[NCH];
+    float lo = FINF, hi = -FINF;
+#pragma unroll
+    for (int c = 0; c < NCH; ++c) {
+      const int i = c * 32 + lane;
+      const float v = P.qd[q * d + i] - P.cent[(int64_t)j * d + i];
+      qv[c] = g > 0.f ? v / sg : 0.f;
+      lo = fminf(lo, qv[c]);
+      hi = fmaxf(hi, qv[c]);
+    }
+    lo = warp_min(lo);
+    hi = warp_max(hi);
+    const float delta = (hi - lo) / (float)topq;
+    uint32_t qw[QB][NCH];
+    int s = 0;
+#pragma unroll
+    for (int c = 0; c < NCH; ++c) {
+      int qb = 0;
+      if (delta > 0.f) {
+        const float t = (qv[c] - lo) / delta;
+        qb = min((int)floorf(t + 0.5f), topq);
+        qb = max(qb, 0);
+      }
+      s += qb;
+#pragma unroll
+      for (int b = 0; b < QB; ++b) qw[b][c] = __ballot_sync(0xffffffffu, (qb >> b) & 1);
+    }
+    const int qsum = warp_sum_i(s);
+    const float ql = lo, qdelta = delta;
+
+    const int64_t lb0 = P.loff[j];
+    const int64_t lsize = P.loff[j + 1] - lb0;
+    const int64_t size = c_hi < 0 ? lsize : min(lsize, c_hi);
+    const int64_t pb0 = P.ploff[j];
+    float lst = FINF;
+    float top4[4] = {FINF, FINF, FINF, FINF};
+    const int mper = (P.k + 31) >> 5;
+    float tau = FINF;
+    float gt = KM != 2 ? fkey_inv(__ldcg(P.gtau + q)) : FINF;
+
+    for (int64_t b0 = c_lo; b0 < size; b0 += 32) {
+      const int64_t idx = b0 + lane;
+      const bool valid = idx < size;
+      const int64_t pp = pb0 + idx;
+      const uint32_t* cbase = P.codes + (pp >> 5) * (int64_t)(W * 32) + (pp & 31) * VW;
+      uint32_t cw[W];
+#pragma unroll
+      for (int gq = 0; gq < W / VW; ++gq) {
+        const uint32_t* src = cbase + gq * 32 * VW;
+        if (VW == 4) {
+          const uint4 v = __ldg(reinterpret_cast<const uint4*>(src));
+          cw[gq * 4] = v.x; cw[gq * 4 + 1] = v.y; cw[gq * 4 + 2] = v.z; cw[gq * 4 + 3] = v.w;
+        } else if (VW == 2) {
+          const uint2 v = __ldg(reinterpret_cast<const uint2*>(src));
+          cw[gq * 2] = v.x; cw[gq * 2 + 1] = v.y;
+        } else {
+          cw[gq] = __ldg(src);
+        }
+      }
+      const float fa = __ldg(P.fadd + pp), fr = __ldg(P.fres + pp), fe = __ldg(P.ferr + pp);
+      int dot = 0, su = 0;
+#pragma unroll
+      for (int a = 0; a < BITS; ++a) {
+        int pd = 0, ps = 0;
+#pragma unroll
+        for (int c = 0; c < NCH; ++c) {
+          const uint32_t word = cw[a * NCH + c];
+          ps += __popc(word);
+#pragma unroll
+          for (int bq = 0; bq < QB; ++bq) pd += __popc(word & qw[bq][c]) << bq;
+        }
+        dot += pd << a;
+        su += ps << a;
+      }
+      const float ip = qdelta * (float)(2 * dot - topc * qsum) + ql * (float)(2 * su - d * topc);
+      const float dis = fa + a0 + fr * sg * ip;  // Eq. 4
+      const float eps = e0 * fe + em;             // Eq. 5 + Chebyshev
+      float lb = dis - eps, ub = dis + eps;
+      if (!valid) { lb = FINF; ub = FINF; }
+      if (KM != 2 && b0 > c_lo) {
+        float g2 = 0.f;
+        if (lane == 0) g2 = fkey_inv(__ldcg(P.gtau + q));
+        gt = fminf(gt, __shfl_sync(0xffffffffu, g2, 0));
+      }
+      if (KM == 0) {
+        float kth = __shfl_sync(0xffffffffu, lst, P.k - 1);
+        unsigned mask = __ballot_sync(0xffffffffu, ub < kth && ub < gt);
+        while (mask) {
+          int src = __ffs(mask) - 1;
+          mask &= mask - 1;
+          float v = __shfl_sync(0xffffffffu, ub, src);
+          float cur = __shfl_sync(0xffffffffu, lst, P.k - 1);
+          if (v < cur) {
+            float prev = __shfl_up_sync(0xffffffffu, lst, 1);
+            float nl = (lst <= v) ? lst : ((lane == 0 || prev <= v) ? v : prev);
+            lst = lane < P.k ? nl : FINF;
+          }
+        }
+        tau = fminf(gt, __shfl_sync(0xffffffffu, lst, P.k - 1));
+      } else if (KM == 1) {
+        float v = ub;
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+          if (t < mper && v < top4[t]) { float x = top4[t]; top4[t] = v; v = x; }
+        }
+        float mine = mper == 1 ? top4[0] : mper == 2 ? top4[1] : mper == 3 ? top4[2] : top4[3];
+        tau = fminf(gt, warp_max(mine));
+      }
+      if (KM != 2 && lane == 0 && tau < gt) atomicMin(P.gtau + q, fkey(tau));
+      if (KM != 2) gt = fminf(gt, tau);
+      const bool surv = valid && lb <= tau;
+      const unsigned sm = __ballot_sync(0xffffffffu, surv);
+      if (sm) {
+        unsigned base = 0;
+        if (lane == 0) base = atomicAdd(P.qcnt + q, (unsigned)__popc(sm));
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (surv) {
+          const int64_t at = q * P.cap + base + __popc(sm & ((1u << lane) - 1));
+          P.spos[at] = (int32_t)(lb0 + idx);
+          P.slb[at] = lb;
+          P.sub[at] = ub;
+        }
+      }
+    }
+    __syncwarp();
+  }
+}
+
 // work items: the pairs w = i * stride (i < n) contribute max(1, ceil(size/chunk))
 // items each, (w << 32 | chunk index)
 __global__ void k_chunk_count(const int32_t* __restrict__ plist, const int64_t* __restrict__ loff,
@@ -1625,9 +1791,36 @@ void launch_scan_t(const ScanParams& p, int64_t grid_warps, size_t smem, cudaStr
   MRQ_CHECK_LAUNCH();
 }
 
+template <int KM, int NCH, int BITS, int QB>
+void launch_scan_q(const ScanParams& p, int64_t grid_warps, cudaStream_t st) {
+  auto kern = k_scan_q<KM, NCH, BITS, QB>;
+  const int per_sm = occupancy((const void*)kern, SCAN_WARPS * 32, 0);
+  int64_t want = (grid_warps + SCAN_WARPS - 1) / SCAN_WARPS;
+  int blocks = (int)std::min<int64_t>(want, (int64_t)num_sms() * per_sm);
+  kern<<<std::max(blocks, 1), SCAN_WARPS * 32, 0, st>>>(p);
+  MRQ_CHECK_LAUNCH();
+}
+
+// the specialised quantized scan for the common code shapes (k <= 128, 4-bit queries)
+bool launch_scan_fixed(const ScanParams& p, int64_t npairs, cudaStream_t st) {
+  if (p.qbits != 4 || p.k > 128) return false;
+  const int nch = p.d >> 5;
+#define MRQ_SQ(B, N)                                                        \
+  if (p.bits == B && nch == N) {                                             \
+    if (p.k <= 32) launch_scan_q<0, N, B, 4>(p, npairs, st);                 \
+    else launch_scan_q<1, N, B, 4>(p, npairs, st);                           \
+    return true;                                                             \
+  }
+  MRQ_SQ(1, 1) MRQ_SQ(1, 2) MRQ_SQ(1, 4) MRQ_SQ(1, 8)
+  MRQ_SQ(2, 2) MRQ_SQ(2, 4) MRQ_SQ(2, 8) MRQ_SQ(4, 1) MRQ_SQ(4, 4) MRQ_SQ(4, 8)
+#undef MRQ_SQ
+  return false;
+}
+
 void launch_scan(const ScanParams& p, int64_t npairs, cudaStream_t st, bool dbg) {
   const bool quant = p.qbits > 0;
   const int km = p.k <= 32 ? 0 : (p.k <= 128 ? 1 : 2);
+  if (!dbg && quant && launch_scan_fixed(p, npairs, st)) return;
   size_t smem = (size_t)SCAN_WARPS * 5 * p.d * sizeof(float);
   if (dbg) {
     if (quant) launch_scan_t<2, true, true>(p, 1, smem, st);
