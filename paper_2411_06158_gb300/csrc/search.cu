@@ -662,12 +662,10 @@ __global__ void __launch_bounds__(SCAN_WARPS * 32) k_scan_q(ScanParams P) {
     float tau = FINF;
     float gt = KM != 2 ? fkey_inv(__ldcg(P.gtau + q)) : FINF;
 
-    for (int64_t b0 = c_lo; b0 < size; b0 += 32) {
-      const int64_t idx = b0 + lane;
-      const bool valid = idx < size;
-      const int64_t pp = pb0 + idx;
+    // a block's code words and factors (its 32 candidates' padded positions)
+    auto fetch = [&](int64_t b0, uint32_t (&cw)[W], float& fa, float& fr, float& fe) {
+      const int64_t pp = pb0 + b0 + lane;
       const uint32_t* cbase = P.codes + (pp >> 5) * (int64_t)(W * 32) + (pp & 31) * VW;
-      uint32_t cw[W];
 #pragma unroll
       for (int gq = 0; gq < W / VW; ++gq) {
         const uint32_t* src = cbase + gq * 32 * VW;
@@ -681,7 +679,31 @@ __global__ void __launch_bounds__(SCAN_WARPS * 32) k_scan_q(ScanParams P) {
           cw[gq] = __ldg(src);
         }
       }
-      const float fa = __ldg(P.fadd + pp), fr = __ldg(P.fres + pp), fe = __ldg(P.ferr + pp);
+      fa = __ldg(P.fadd + pp);
+      fr = __ldg(P.fres + pp);
+      fe = __ldg(P.ferr + pp);
+    };
+    // software pipeline (short codes): the next block's loads are in flight while this
+    // one is scored; long codes (W > 16) are popcount-bound and keep the registers
+    constexpr bool PF = W <= 16;
+    uint32_t nw[W];
+    float nfa = 0.f, nfr = 0.f, nfe = 0.f;
+    if constexpr (PF) {
+      if (c_lo < size) fetch(c_lo, nw, nfa, nfr, nfe);
+    }
+    for (int64_t b0 = c_lo; b0 < size; b0 += 32) {
+      const int64_t idx = b0 + lane;
+      const bool valid = idx < size;
+      uint32_t cw[W];
+      float fa, fr, fe;
+      if constexpr (PF) {
+#pragma unroll
+        for (int t = 0; t < W; ++t) cw[t] = nw[t];
+        fa = nfa; fr = nfr; fe = nfe;
+        if (b0 + 32 < size) fetch(b0 + 32, nw, nfa, nfr, nfe);
+      } else {
+        fetch(b0, cw, fa, fr, fe);
+      }
       int dot = 0, su = 0;
 #pragma unroll
       for (int a = 0; a < BITS; ++a) {
