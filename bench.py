@@ -407,6 +407,9 @@ def main(argv=None):
         "bf16_q4": mrq.mrq_search_opts(query_bits=4, precision=mrq.PREC_BF16, stream=stream),
         "batched_bf16_q4": mrq.mrq_search_opts(query_bits=4, precision=mrq.PREC_BF16, batched=1,
                                                graph=1, stream=stream),
+        # the scan decomposition picked by the library's autotuner at the timed nprobe
+        "tuned_bf16_q4": mrq.mrq_search_opts(query_bits=4, precision=mrq.PREC_BF16,
+                                             batched=mrq.SCAN_AUTO, graph=1, stream=stream),
     }
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
@@ -489,6 +492,9 @@ def main(argv=None):
             results[name] = {"nprobe": None, "recall": r}
             continue
         opts = forms[name] = with_m(opts, m_best, e0_best)
+        tune = None
+        if opts.batched == mrq.SCAN_AUTO:
+            tune = mrq.mrq_autotune(idx, q_t, w.k, npb, opts)
         # stage times from a profiled pass (CUDA events between the stages, no graph);
         # the step time from an unprofiled pass of the form as a user runs it (replayed
         # from a captured CUDA graph when the form asks for one)
@@ -505,7 +511,8 @@ def main(argv=None):
                          "launches_per_step": launches // max(1, len(pper)),
                          "cand_per_query": float(st["n_cand"].mean()),
                          "s1_per_query": float(st["n_s1"].mean()),
-                         "exact_per_query": float(st["n_exact"].mean()), "per_step_ms": per}
+                         "exact_per_query": float(st["n_exact"].mean()), "per_step_ms": per,
+                         "autotune": tune}
     ok = {k: v for k, v in results.items() if v.get("qps")}
     if not ok:
         print(json.dumps({"metric": METRIC, "error": "no form reached the recall target",

@@ -66,13 +66,20 @@ typedef struct {
   int mode;         /* MRQ_MODE_*; default MRQ_MODE_MRQ_PLUS */
   int precision;    /* MRQ_PREC_*; default MRQ_PREC_FP32 */
   int query_bits;   /* 0 = float32 query in the scan; 1..8 = scalar-quantized query */
-  int batched;      /* 0 = one work item per (query, list); 1 = list-major batched scan */
+  int batched;      /* MRQ_SCAN_PAIRS (0): one work item per (query, list);
+                       MRQ_SCAN_BATCHED (1): list-major batched scan;
+                       MRQ_SCAN_AUTO (2): the configuration mrq_autotune chose for this
+                       (k, nprobe, query_bits), else batched when nq * nprobe / nlist >= 16 */
   int profile;      /* 1 = record CUDA events around each stage (see mrq_last_search_profile) */
   int graph;        /* 1 = replay a captured CUDA graph when queries, ids and dists are device
                        memory and every argument equals the previous graph call's (the first
                        such call runs normally, then captures); ignored with profile = 1 */
   void* cuda_stream;/* cudaStream_t, or NULL */
 } mrq_search_opts;
+
+#define MRQ_SCAN_PAIRS 0
+#define MRQ_SCAN_BATCHED 1
+#define MRQ_SCAN_AUTO 2
 
 /* stages reported by mrq_last_search_profile */
 #define MRQ_STAGE_PROJECT 0  /* query projection GEMM (Algorithm 2, rotate step) */
@@ -179,6 +186,32 @@ int mrq_project(mrq_index* index, const float* queries, int64_t nq,
  */
 int mrq_project_noalloc(mrq_index* index, const float* queries, int64_t nq,
                         const mrq_search_opts* opt, float* qp);
+
+/* Result of mrq_autotune: the chosen scan configuration and what it cost. */
+typedef struct {
+  int scan;        /* MRQ_SCAN_PAIRS or MRQ_SCAN_BATCHED */
+  int chunk;       /* candidates per work item of a long list (per-pair scan) */
+  int group;       /* queries per work item of the batched scan (1..16) */
+  double ms;       /* median device time of one search of the tuning batch with it */
+  double ms_default; /* the same for the untuned configuration of opt->batched */
+  int n_tried;     /* configurations timed */
+  int consistent;  /* 1 when every configuration returned identical ids and distances */
+} mrq_tune_result_t;
+
+/*
+ * Autotuner of the scan's work decomposition (not a step of the paper, which scans
+ * one list per query on a CPU): times, on the given queries, the per-pair scan with
+ * long lists cut into work items of 1024, 4096 or 16384 candidates and the batched
+ * scan with 4, 8 or 16 queries per work item (where the code shape allows it), each
+ * as a median of 3 CUDA-event timed searches after one warm-up, and records the
+ * fastest for (k, nprobe, opt->query_bits) in the index; searches with
+ * opt->batched = MRQ_SCAN_AUTO then use it.  All configurations compute the same
+ * answer (the threshold contract does not depend on the decomposition), which the
+ * call checks.  queries: nq x D row-major float32, host or device.  Not to be called
+ * while other searches on the index are running.  Errors as mrq_search.
+ */
+int mrq_autotune(mrq_index* index, const float* queries, int64_t nq, int k, int nprobe,
+                 const mrq_search_opts* opt, mrq_tune_result_t* result);
 
 /* Per-query counters of the last mrq_search on this index (host arrays of nq):
  * candidates scanned, stage-1 survivors, exact distances computed. */

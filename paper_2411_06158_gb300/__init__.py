@@ -22,10 +22,11 @@ MRQ_OK = 0
 MRQ_EINVAL, MRQ_ENOMEM, MRQ_ECUDA, MRQ_EFORMAT, MRQ_EIO, MRQ_ETIMEDOUT = -1, -2, -3, -4, -5, -6
 MODE_MRQ, MODE_MRQ_PLUS = 0, 1
 PREC_FP32, PREC_BF16, PREC_BF16X3 = 0, 1, 2
+SCAN_PAIRS, SCAN_BATCHED, SCAN_AUTO = 0, 1, 2
 
 EXPORTS = [
     "mrq_build_opts_default", "mrq_search_opts_default", "mrq_build", "mrq_search",
-    "mrq_estimate", "mrq_project", "mrq_project_noalloc", "mrq_last_search_stats", "mrq_last_search_profile",
+    "mrq_estimate", "mrq_project", "mrq_project_noalloc", "mrq_autotune", "mrq_last_search_stats", "mrq_last_search_profile",
     "mrq_save", "mrq_load",
     "mrq_index_info", "mrq_index_export", "mrq_free", "mrq_last_error",
     "mrq_server_opts_default", "mrq_server_start", "mrq_submit", "mrq_submit_many", "mrq_poll",
@@ -63,6 +64,11 @@ class ServerStats(C.Structure):
                 ("qps", C.c_double)]
 
 
+class TuneResult(C.Structure):
+    _fields_ = [("scan", C.c_int), ("chunk", C.c_int), ("group", C.c_int), ("ms", C.c_double),
+                ("ms_default", C.c_double), ("n_tried", C.c_int), ("consistent", C.c_int)]
+
+
 class IndexInfo(C.Structure):
     _fields_ = [("n", C.c_int64), ("D", C.c_int), ("d", C.c_int), ("bits", C.c_int),
                 ("nlist", C.c_int), ("max_list", C.c_int64), ("device_bytes", C.c_int64)]
@@ -80,6 +86,7 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
     lib.mrq_estimate.argtypes = [vp, vp, i32, C.POINTER(SearchOpts), vp, vp, vp, vp, vp]
     lib.mrq_project.argtypes = [vp, vp, i64, C.POINTER(SearchOpts), vp]
     lib.mrq_project_noalloc.argtypes = [vp, vp, i64, C.POINTER(SearchOpts), vp]
+    lib.mrq_autotune.argtypes = [vp, vp, i64, i32, i32, C.POINTER(SearchOpts), C.POINTER(TuneResult)]
     lib.mrq_last_search_stats.argtypes = [vp, i64, vp, vp, vp]
     lib.mrq_last_search_profile.argtypes = [vp, vp, vp]
     lib.mrq_save.argtypes = [vp, C.c_char_p]
@@ -258,6 +265,16 @@ def mrq_project_noalloc(index: Index, queries, out, opts: SearchOpts | None = No
     _check(_lib.mrq_project_noalloc(index.handle, _ptr(queries), nq,
                                     C.byref(opts) if opts is not None else None, _ptr(out)))
     return out
+
+
+def mrq_autotune(index: Index, queries, k: int, nprobe: int, opts: SearchOpts | None = None):
+    """Time the scan decompositions on `queries` and record the fastest for
+    (k, nprobe, opts.query_bits); searches with batched=SCAN_AUTO use it."""
+    queries = _f32(queries)
+    r = TuneResult()
+    _check(_lib.mrq_autotune(index.handle, _ptr(queries), queries.shape[0], k, nprobe,
+                             C.byref(opts) if opts is not None else None, C.byref(r)))
+    return {f: getattr(r, f) for f, _ in TuneResult._fields_}
 
 
 def mrq_last_search_stats(index: Index, nq: int):

@@ -13,6 +13,13 @@ namespace {
 
 thread_local std::string g_err;
 
+// a nested public call inside a guarded body: rethrow its error
+#define MRQ_CHECK_RC(call)                                \
+  do {                                                    \
+    const int rc_ = (call);                               \
+    if (rc_ != MRQ_OK) ::mrq::fail(rc_, std::string(g_err)); \
+  } while (0)
+
 template <class F>
 int guarded(F&& f) {
   try {
@@ -65,6 +72,8 @@ mrq_search_opts resolve(const mrq_search_opts* opt) {
   MRQ_REQUIRE(o.mode == MRQ_MODE_MRQ || o.mode == MRQ_MODE_MRQ_PLUS, "mode must be MRQ_MODE_MRQ or MRQ_MODE_MRQ_PLUS");
   MRQ_REQUIRE(o.precision >= MRQ_PREC_FP32 && o.precision <= MRQ_PREC_BF16X3, "unknown precision");
   MRQ_REQUIRE(o.query_bits >= 0 && o.query_bits <= 8, "query_bits must be in [0, 8]");
+  MRQ_REQUIRE(o.batched >= MRQ_SCAN_PAIRS && o.batched <= MRQ_SCAN_AUTO,
+              "batched must be MRQ_SCAN_PAIRS, MRQ_SCAN_BATCHED or MRQ_SCAN_AUTO");
   return o;
 }
 
@@ -286,6 +295,98 @@ int mrq_search(mrq_index* idx, const float* queries, int64_t nq, int k, int npro
           idx->prof_ms[s] += ms;
         }
     }
+  });
+}
+
+int mrq_autotune(mrq_index* idx, const float* queries, int64_t nq, int k, int nprobe,
+                 const mrq_search_opts* opt, mrq_tune_result_t* result) {
+  return guarded([&] {
+    MRQ_REQUIRE(idx && queries && result, "NULL argument");
+    MRQ_REQUIRE(nq >= 1, "nq must be >= 1");
+    mrq_search_opts o = resolve(opt);
+    o.graph = 0;
+    o.profile = 0;
+    use_device(idx);
+    cudaStream_t st = stream_of(o);
+    const int D = idx->D;
+    // device copies of the queries and two output sets (this config's, the first one's)
+    mrq::DevBuf<float> qd_;
+    const float* q = queries;
+    if (!on_device(queries)) {
+      qd_.alloc((size_t)nq * D);
+      MRQ_CUDA(cudaMemcpyAsync(qd_.p, queries, 4 * nq * D, cudaMemcpyHostToDevice, st));
+      q = qd_.p;
+    }
+    mrq::DevBuf<int64_t> ids(nq * k);
+    mrq::DevBuf<float> dists(nq * k);
+    std::vector<int64_t> ref_i((size_t)nq * k), got_i((size_t)nq * k);
+    std::vector<float> ref_d((size_t)nq * k), got_d((size_t)nq * k);
+    cudaEvent_t e0, e1;
+    MRQ_CUDA(cudaEventCreate(&e0));
+    MRQ_CUDA(cudaEventCreate(&e1));
+    struct EvGuard {
+      cudaEvent_t a, b;
+      ~EvGuard() { cudaEventDestroy(a); cudaEventDestroy(b); }
+    } evg{e0, e1};
+    auto time_cfg = [&](const mrq::ScanConfig* c) {
+      mrq::ScopedScanConfig force(c);
+      MRQ_CHECK_RC(mrq_search(idx, q, nq, k, nprobe, &o, ids.p, dists.p));  // warm-up
+      std::vector<float> t;
+      for (int r = 0; r < 3; ++r) {
+        MRQ_CUDA(cudaEventRecord(e0, st));
+        MRQ_CHECK_RC(mrq_search(idx, q, nq, k, nprobe, &o, ids.p, dists.p));
+        MRQ_CUDA(cudaEventRecord(e1, st));
+        MRQ_CUDA(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        MRQ_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+        t.push_back(ms);
+      }
+      std::sort(t.begin(), t.end());
+      return (double)t[1];
+    };
+    // candidates
+    std::vector<mrq::ScanConfig> cands;
+    for (int chunk : {1024, 4096, 16384}) {
+      if (chunk != 4096 && idx->max_list <= 1024) continue;  // no list is long enough to cut
+      cands.push_back({MRQ_SCAN_PAIRS, chunk, 16});
+    }
+    const int wds = idx->words, nch = idx->d / 32;
+    const bool can_batch = o.query_bits > 0 && wds <= 16 && (wds & (wds - 1)) == 0 &&
+                           (idx->bits & (idx->bits - 1)) == 0 && (nch & (nch - 1)) == 0 &&
+                           !(wds == 16 && idx->d == 32);
+    if (can_batch)
+      for (int g : {4, 8, 16}) cands.push_back({MRQ_SCAN_BATCHED, 4096, g});
+    const mrq::ScanConfig dflt = mrq::scan_config(idx, o, nq, k, nprobe);
+    result->consistent = 1;
+    double best = 1e300;
+    mrq::ScanConfig pick = cands[0];
+    for (size_t c = 0; c < cands.size(); ++c) {
+      const double ms = time_cfg(&cands[c]);
+      MRQ_CUDA(cudaMemcpy(got_i.data(), ids.p, 8 * nq * k, cudaMemcpyDeviceToHost));
+      MRQ_CUDA(cudaMemcpy(got_d.data(), dists.p, 4 * nq * k, cudaMemcpyDeviceToHost));
+      if (c == 0) {
+        ref_i = got_i;
+        ref_d = got_d;
+      } else if (got_i != ref_i ||
+                 std::memcmp(got_d.data(), ref_d.data(), 4 * (size_t)nq * k) != 0) {
+        result->consistent = 0;
+      }
+      if (ms < best) {
+        best = ms;
+        pick = cands[c];
+      }
+    }
+    result->ms_default = time_cfg(&dflt);
+    result->scan = pick.scan;
+    result->chunk = pick.chunk;
+    result->group = pick.group;
+    result->ms = best;
+    result->n_tried = (int)cands.size();
+    {
+      std::lock_guard<std::mutex> lk(idx->tune_mu);
+      idx->tuned[std::make_tuple(mrq::scan_kclass(k), nprobe, o.query_bits)] = pick;
+    }
+    idx->graph_valid = false;  // a captured graph may hold the old configuration
   });
 }
 

@@ -7,6 +7,9 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <map>
+#include <mutex>
+#include <tuple>
 #include <vector>
 
 #include "../../include/mrq.h"
@@ -105,6 +108,15 @@ struct Workspace {
 
 }  // namespace mrq
 
+namespace mrq {
+// scan configuration the autotuner chooses between
+struct ScanConfig {
+  int scan;   // MRQ_SCAN_PAIRS or MRQ_SCAN_BATCHED
+  int chunk;  // candidates per work item of a long list (per-pair scan)
+  int group;  // queries per work item (batched scan), <= 16
+};
+}  // namespace mrq
+
 struct mrq_index {
   int64_t n = 0;
   int D = 0, d = 0, bits = 1, nlist = 0;
@@ -127,7 +139,10 @@ struct mrq_index {
   mrq::DevBuf<float> xd, xr, xn2;         // list-major, unpadded
   mrq::Workspace ws;
   int64_t last_nq = 0;
-  mutable bool last_stats_dev = false;  // last search's counters still in ws.stats (device)
+  mutable bool last_stats_dev = false;
+  // autotuned scan configurations, keyed by (k class, nprobe, query bits)
+  std::mutex tune_mu;
+  std::map<std::tuple<int, int, int>, mrq::ScanConfig> tuned;  // last search's counters still in ws.stats (device)
   mutable std::vector<int64_t> last_stats;        // nq x 3 host copy of the last search's counters
   // profiling of the last search: MRQ_NSTAGES + 1 events per batch
   std::vector<cudaEvent_t> prof_ev;
@@ -213,6 +228,14 @@ void search_batch(mrq_index* idx, Workspace& ws, const float* q_dev, int64_t nq,
                   int64_t* stats_dev, cudaStream_t st);
 void project_batch(mrq_index* idx, Workspace& ws, const float* q_dev, int64_t nq, int precision,
                    float* qd, float* qr, cudaStream_t st);
+// the scan configuration a search uses; a ScopedScanConfig forces one on this thread
+ScanConfig scan_config(mrq_index* idx, const mrq_search_opts& o, int64_t nq, int k, int nprobe);
+int scan_kclass(int k);
+struct ScopedScanConfig {
+  explicit ScopedScanConfig(const ScanConfig* c);
+  ~ScopedScanConfig();
+  const ScanConfig* prev;
+};
 // device bytes of scratch one batch of nq queries needs (for admission control)
 size_t batch_scratch_bytes(const mrq_index* idx, int64_t nq, int k, int nprobe);
 void estimate_one(mrq_index* idx, const float* qp_dev, int list, const mrq_search_opts& o,

@@ -807,12 +807,12 @@ __global__ void k_scan_init(unsigned int* qcnt, unsigned int* gtau, int64_t nq, 
 //
 // The pairs (query, probed list) are bucketed by list; k_pair_prep quantizes each
 // pair's query once (Algorithm 2: normalise, rotate, quantize); a work item is
-// (list j, block of 32 candidates, group of up to BATCH_G pairs probing j).  One
+// (list j, block of 32 candidates, group of up to `group` pairs probing j).  One
 // warp loads its 32 candidates' code words and factors once (registers) and scores
 // them against every query of the group, so a list's codes are read once per
 // group instead of once per query.
 
-constexpr int BATCH_G = 16;     // queries per work item
+constexpr int BATCH_G = 16;     // largest number of queries per work item
 constexpr int BATCH_MAXW = 16;  // code words per vector kept in registers (bits*d/32)
 
 struct PairQ {
@@ -837,20 +837,20 @@ __global__ void k_bucket_fill(const int32_t* __restrict__ plist, int64_t npairs,
 }
 // items of list j: (#32-blocks) x (#groups of BATCH_G pairs)
 __global__ void k_batch_count(const int* __restrict__ cnt, const int64_t* __restrict__ loff,
-                              int nlist, int* __restrict__ icnt) {
+                              int nlist, int group, int* __restrict__ icnt) {
   int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= nlist) return;
   const int64_t sz = loff[j + 1] - loff[j];
   const int c = cnt[j];
-  icnt[j] = (c > 0 && sz > 0) ? (int)(((sz + 31) / 32) * ((c + BATCH_G - 1) / BATCH_G)) : 0;
+  icnt[j] = (c > 0 && sz > 0) ? (int)(((sz + 31) / 32) * ((c + group - 1) / group)) : 0;
 }
 __global__ void k_batch_scatter(const int* __restrict__ cnt, const int* __restrict__ icnt,
                                 const int* __restrict__ ioff, const int64_t* __restrict__ loff,
-                                int nlist, int4* __restrict__ items, int* __restrict__ nitems) {
+                                int nlist, int group, int4* __restrict__ items, int* __restrict__ nitems) {
   int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= nlist) return;
   const int n = icnt[j];
-  const int ng = (cnt[j] + BATCH_G - 1) / BATCH_G;
+  const int ng = (cnt[j] + group - 1) / group;
   for (int i = 0; i < n; ++i) items[ioff[j] + i] = make_int4(j, i / ng, i % ng, 0);
   if (j == nlist - 1) *nitems = ioff[j] + n;
 }
@@ -931,6 +931,7 @@ struct BatchParams {
   const float* fres;
   const float* ferr;
   int d, bits, words, vw, nprobe, k, qbits;
+  int group;             // queries per work item (<= BATCH_G)
   int64_t cap;
   unsigned int* work;
   unsigned int* qcnt;
@@ -969,8 +970,8 @@ __global__ void __launch_bounds__(256) k_scan_batched(BatchParams P) {
 #pragma unroll
     for (int w = 0; w < W; ++w) su += __popc(cw[w]) << (w / NCH);
     const float fa = __ldg(P.fadd + pp), fr = __ldg(P.fres + pp), fe = __ldg(P.ferr + pp);
-    const int g0 = P.loffq[j] + grp * BATCH_G;
-    const int ng = min(P.loffq[j] + P.lcount[j], g0 + BATCH_G) - g0;
+    const int g0 = P.loffq[j] + grp * P.group;
+    const int ng = min(P.loffq[j] + P.lcount[j], g0 + P.group) - g0;
     const int my_pair = lane < ng ? P.lqueue[g0 + lane] : 0;  // the group's pairs, one per lane
     for (int t = 0; t < ng; ++t) {
       const int w_pair = __shfl_sync(0xffffffffu, my_pair, t);
@@ -1924,6 +1925,30 @@ static void qstats(mrq_index* idx, const float* qd, const float* qr, int64_t nq,
   MRQ_CHECK_LAUNCH();
 }
 
+// ---------------------------------------------------------------- scan configuration
+
+thread_local const ScanConfig* g_force_cfg = nullptr;
+
+ScopedScanConfig::ScopedScanConfig(const ScanConfig* c) : prev(g_force_cfg) { g_force_cfg = c; }
+ScopedScanConfig::~ScopedScanConfig() { g_force_cfg = prev; }
+
+int scan_kclass(int k) { return k <= 32 ? 0 : k <= 128 ? 1 : 2; }
+
+ScanConfig scan_config(mrq_index* idx, const mrq_search_opts& o, int64_t nq, int k, int nprobe) {
+  if (g_force_cfg) return *g_force_cfg;
+  ScanConfig c{o.batched == MRQ_SCAN_BATCHED ? MRQ_SCAN_BATCHED : MRQ_SCAN_PAIRS, SCAN_CHUNK, BATCH_G};
+  if (o.batched != MRQ_SCAN_AUTO) return c;
+  {
+    std::lock_guard<std::mutex> lk(idx->tune_mu);
+    auto it = idx->tuned.find(std::make_tuple(scan_kclass(k), nprobe, o.query_bits));
+    if (it != idx->tuned.end()) return it->second;
+  }
+  // untuned rule: batch when each probed list is shared by many queries of the batch
+  const double share = (double)nq * nprobe / std::max(1, idx->nlist);
+  c.scan = share >= 16.0 ? MRQ_SCAN_BATCHED : MRQ_SCAN_PAIRS;
+  return c;
+}
+
 void search_batch(mrq_index* idx, Workspace& ws, const float* q, int64_t nq, int k, int nprobe,
                   const mrq_search_opts& o, int64_t* out_ids, float* out_d, int64_t* stats,
                   cudaStream_t st) {
@@ -2017,15 +2042,17 @@ void search_batch(mrq_index* idx, Workspace& ws, const float* q, int64_t nq, int
   sp.npairs = nq * nprobe; sp.cap = cap;
   sp.work = ws.work.p; sp.qcnt = ws.qcnt.p; sp.gtau = ws.gtau.p;
   sp.spos = ws.spos.p; sp.slb = ws.slb.p; sp.sub = ws.sub.p;
-  // per-pair work items (w = i * stride, i < n), long lists split into SCAN_CHUNK chunks
+  // scan configuration: forced (autotuner), tuned for this (k, nprobe), or the rule
+  const ScanConfig cfg = scan_config(idx, o, nq, k, nprobe);
+  // per-pair work items (w = i * stride, i < n), long lists split into cfg.chunk chunks
   auto build_items = [&](int64_t n, int stride) {
-    const int64_t max_items = n + (nq * idx->cap_by_nprobe[nprobe]) / SCAN_CHUNK + 1;
+    const int64_t max_items = n + (nq * idx->cap_by_nprobe[nprobe]) / cfg.chunk + 1;
     ws.ccnt.reserve(n);
     ws.coff.reserve(n);
     ws.items.reserve(max_items);
     ws.nitems.reserve(1);
     k_chunk_count<<<ceil_div(n, 256), 256, 0, st>>>(ws.plist.p, idx->loff.p, n, stride,
-                                                   SCAN_CHUNK, ws.ccnt.p);
+                                                   cfg.chunk, ws.ccnt.p);
     MRQ_CHECK_LAUNCH();
     size_t tb = 0;
     MRQ_CUDA(cub::DeviceScan::ExclusiveSum(nullptr, tb, ws.ccnt.p, ws.coff.p, (int)n, st));
@@ -2036,13 +2063,13 @@ void search_batch(mrq_index* idx, Workspace& ws, const float* q, int64_t nq, int
     MRQ_CHECK_LAUNCH();
     sp.items = ws.items.p;
     sp.nitems = ws.nitems.p;
-    sp.chunk = SCAN_CHUNK;
+    sp.chunk = cfg.chunk;
     idx->launches += 3;
     return max_items;
   };
   // batched form: quantized query, code words a power of two (bits in {1,2,4,8}) up to 16
   const int wds = idx->words;
-  const bool batched = o.batched && o.query_bits > 0 && wds <= BATCH_MAXW &&
+  const bool batched = cfg.scan == MRQ_SCAN_BATCHED && o.query_bits > 0 && wds <= BATCH_MAXW &&
                        (wds & (wds - 1)) == 0 && (idx->bits & (idx->bits - 1)) == 0 &&
                        ((d / 32) & (d / 32 - 1)) == 0 && !(wds == 16 && d == 32);
   if (batched) {
@@ -2072,12 +2099,13 @@ void search_batch(mrq_index* idx, Workspace& ws, const float* q, int64_t nq, int
     MRQ_CUDA(cub::DeviceScan::ExclusiveSum(ws.cubtmp.p, tb, ws.lcount.p, ws.loffq.p, nlist, st));
     k_bucket_fill<<<ceil_div(np_, 256), 256, 0, st>>>(ws.plist.p, np_, nprobe, first, ws.loffq.p,
                                                       ws.lfill.p, ws.lqueue.p);
-    k_batch_count<<<ceil_div(nlist, 256), 256, 0, st>>>(ws.lcount.p, idx->loff.p, nlist, ws.icnt.p);
+    k_batch_count<<<ceil_div(nlist, 256), 256, 0, st>>>(ws.lcount.p, idx->loff.p, nlist, cfg.group,
+                                                        ws.icnt.p);
     MRQ_CUDA(cub::DeviceScan::ExclusiveSum(nullptr, tb, ws.icnt.p, ws.ioff.p, nlist, st));
     ws.cubtmp.reserve(tb + 16);
     MRQ_CUDA(cub::DeviceScan::ExclusiveSum(ws.cubtmp.p, tb, ws.icnt.p, ws.ioff.p, nlist, st));
     k_batch_scatter<<<ceil_div(nlist, 256), 256, 0, st>>>(ws.lcount.p, ws.icnt.p, ws.ioff.p,
-                                                          idx->loff.p, nlist,
+                                                          idx->loff.p, nlist, cfg.group,
                                                           reinterpret_cast<int4*>(ws.bitems.p),
                                                           ws.nitems.p);
     k_pair_prep<<<ceil_div(np_, 8), 256, 0, st>>>(ws.qd.p, ws.qstat.p, ws.plist.p, ws.pg.p,
@@ -2092,7 +2120,7 @@ void search_batch(mrq_index* idx, Workspace& ws, const float* q, int64_t nq, int
     bp.loff = idx->loff.p; bp.ploff = idx->ploff.p; bp.codes = idx->codes.p;
     bp.fadd = idx->fadd.p; bp.fres = idx->fres.p; bp.ferr = idx->ferr.p;
     bp.d = d; bp.bits = idx->bits; bp.words = idx->words; bp.vw = idx->vw;
-    bp.nprobe = nprobe; bp.k = k; bp.qbits = o.query_bits; bp.cap = cap;
+    bp.nprobe = nprobe; bp.k = k; bp.qbits = o.query_bits; bp.cap = cap; bp.group = cfg.group;
     bp.work = ws.work.p + 1; bp.qcnt = ws.qcnt.p; bp.gtau = ws.gtau.p;
     bp.spos = ws.spos.p; bp.slb = ws.slb.p; bp.sub = ws.sub.p;
     auto launch = [&](auto kern) {
@@ -2112,7 +2140,7 @@ void search_batch(mrq_index* idx, Workspace& ws, const float* q, int64_t nq, int
     idx->launches += 8;
   }
   int64_t grid_items = nq * nprobe;
-  if (!batched && idx->max_list > SCAN_CHUNK) grid_items = build_items(nq * nprobe, 1);
+  if (!batched && idx->max_list > cfg.chunk) grid_items = build_items(nq * nprobe, 1);
   if (!batched) launch_scan(sp, grid_items, st, false);
   // 5. finalize
   mark(idx, MRQ_STAGE_TAU_A, st);
