@@ -138,6 +138,9 @@ class ClockSampler:
 # profiles/dram_gist-1M-d960_batched-bf16_nprobe3.md.  Used only when the timed
 # run matches that configuration exactly.
 NCU_TRAFFIC = {
+    ("k_fin_exact_r", "gist-like-1M-d960", "tuned_bf16_q4", 3, 1.0, 1.0): 1346369280,
+    ("k_fin_stage2", "gist-like-1M-d960", "tuned_bf16_q4", 3, 1.0, 1.0): 529527040,
+    ("k_scan_q", "gist-like-1M-d960", "tuned_bf16_q4", 3, 1.0, 1.0): 41773824,
 }
 
 
@@ -556,11 +559,21 @@ def main(argv=None):
     #   exact  s2 * (4(D - d) row of x_r + 4 position + 4 |x_d' - q_d'|^2 + 4 distance written)
     peak, peak_kind = load_peaks()
     n_batches = 1 + (w.n_query - 1) // 16384
+    # the scan kernel the timed form ran: batched, or the per-pair scan (specialised
+    # k_scan_q for 4-bit queries and the common code shapes, else the generic k_scan)
+    o_best = forms[best]
+    scan_mode = o_best.batched
+    if scan_mode == mrq.SCAN_AUTO:
+        scan_mode = (B.get("autotune") or {}).get("scan", mrq.SCAN_PAIRS)
+    fixed = (o_best.query_bits == 4 and w.k <= 128 and
+             (w.bits, w.d // 32) in {(1, 1), (1, 2), (1, 4), (1, 8), (2, 2), (2, 4), (2, 8),
+                                     (4, 1), (4, 4), (4, 8)})
+    scan_kernel = ("k_scan_batched" if scan_mode == mrq.SCAN_BATCHED
+                   else "k_scan_q" if fixed else "k_scan")
     per_q = {
-        "scan": ("k_scan_batched" if forms[best].batched else "k_scan",
-                 B["cand_per_query"] * (w.bits * w.d / 8 + 12)),
+        "scan": (scan_kernel, B["cand_per_query"] * (w.bits * w.d / 8 + 12)),
         "stage2": ("k_fin_stage2", B["s1_per_query"] * (4 * w.d + 20)),
-        "exact": ("k_fin_exact", B["exact_per_query"] * (4 * (w.D - w.d) + 12)),
+        "exact": ("k_fin_exact_r", B["exact_per_query"] * (4 * (w.D - w.d) + 12)),
     }
     dom = max(per_q, key=lambda s_: B["stage_ms"][s_])
     kname, bpq = per_q[dom]

@@ -611,7 +611,7 @@ __global__ void __launch_bounds__(SCAN_WARPS * 32) k_scan_q(ScanParams P) {
       c_lo = (v & 0xffffffffll) * P.chunk;
       c_hi = c_lo + P.chunk;
     }
-    const int64_t q = (int64_t)w / P.nprobe;
+    const int64_t q = (int64_t)((uint32_t)w / (uint32_t)P.nprobe);  // pairs < 2^31
     const int j = P.plist[w];
     const float g = P.pg[w];
     const float sg = sqrtf(g);
@@ -730,7 +730,31 @@ __global__ void __launch_bounds__(SCAN_WARPS * 32) k_scan_q(ScanParams P) {
       }
       if (KM == 0) {
         float kth = __shfl_sync(0xffffffffu, lst, P.k - 1);
-        unsigned mask = __ballot_sync(0xffffffffu, ub < kth && ub < gt);
+        const bool in = ub < kth && ub < gt;
+        unsigned mask = __ballot_sync(0xffffffffu, in);
+        if (__popc(mask) > 6) {
+          // many: sort this block's bounds across the lanes and merge the two ascending
+          // lists (the k smallest of the union are the same values in any order)
+          float v = in ? ub : FINF;
+#pragma unroll
+          for (int size2 = 2; size2 <= 32; size2 <<= 1) {
+#pragma unroll
+            for (int stride = size2 >> 1; stride > 0; stride >>= 1) {
+              const float o = __shfl_xor_sync(0xffffffffu, v, stride);
+              const bool up = (lane & size2) == 0, lower = (lane & stride) == 0;
+              v = (lower == up) ? fminf(v, o) : fmaxf(v, o);
+            }
+          }
+          // min(lst[i], v[31 - i]) are the 32 smallest of both, a bitonic sequence
+          float mg = fminf(lst, __shfl_sync(0xffffffffu, v, 31 - lane));
+#pragma unroll
+          for (int stride = 16; stride > 0; stride >>= 1) {
+            const float o = __shfl_xor_sync(0xffffffffu, mg, stride);
+            mg = (lane & stride) == 0 ? fminf(mg, o) : fmaxf(mg, o);
+          }
+          lst = lane < P.k ? mg : FINF;
+          mask = 0;
+        }
         while (mask) {
           int src = __ffs(mask) - 1;
           mask &= mask - 1;
