@@ -410,6 +410,9 @@ def main(argv=None):
         "bf16_q4": mrq.mrq_search_opts(query_bits=4, precision=mrq.PREC_BF16, stream=stream),
         "batched_bf16_q4": mrq.mrq_search_opts(query_bits=4, precision=mrq.PREC_BF16, batched=1,
                                                graph=1, stream=stream),
+        "batched_tc_bf16_q4": mrq.mrq_search_opts(query_bits=4, precision=mrq.PREC_BF16,
+                                                  batched=mrq.SCAN_BATCHED_TC, graph=1,
+                                                  stream=stream),
         # the scan decomposition picked by the library's autotuner at the timed nprobe
         "tuned_bf16_q4": mrq.mrq_search_opts(query_bits=4, precision=mrq.PREC_BF16,
                                              batched=mrq.SCAN_AUTO, graph=1, stream=stream),
@@ -568,7 +571,8 @@ def main(argv=None):
     fixed = (o_best.query_bits == 4 and w.k <= 128 and
              (w.bits, w.d // 32) in {(1, 1), (1, 2), (1, 4), (1, 8), (2, 2), (2, 4), (2, 8),
                                      (4, 1), (4, 4), (4, 8)})
-    scan_kernel = ("k_scan_batched" if scan_mode == mrq.SCAN_BATCHED
+    scan_kernel = ("k_scan_tc" if scan_mode == mrq.SCAN_BATCHED_TC
+                   else "k_scan_batched" if scan_mode == mrq.SCAN_BATCHED
                    else "k_scan_q" if fixed else "k_scan")
     per_q = {
         "scan": (scan_kernel, B["cand_per_query"] * (w.bits * w.d / 8 + 12)),

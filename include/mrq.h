@@ -68,6 +68,9 @@ typedef struct {
   int query_bits;   /* 0 = float32 query in the scan; 1..8 = scalar-quantized query */
   int batched;      /* MRQ_SCAN_PAIRS (0): one work item per (query, list);
                        MRQ_SCAN_BATCHED (1): list-major batched scan;
+                       MRQ_SCAN_BATCHED_TC (3): list-major batched scan whose code dots
+                       are tensor-core MMAs (bits <= 4, query_bits 1..4; others fall
+                       back to MRQ_SCAN_BATCHED);
                        MRQ_SCAN_AUTO (2): the configuration mrq_autotune chose for this
                        (k, nprobe, query_bits), else batched when nq * nprobe / nlist >= 16 */
   int profile;      /* 1 = record CUDA events around each stage (see mrq_last_search_profile) */
@@ -80,6 +83,7 @@ typedef struct {
 #define MRQ_SCAN_PAIRS 0
 #define MRQ_SCAN_BATCHED 1
 #define MRQ_SCAN_AUTO 2
+#define MRQ_SCAN_BATCHED_TC 3
 
 /* stages reported by mrq_last_search_profile */
 #define MRQ_STAGE_PROJECT 0  /* query projection GEMM (Algorithm 2, rotate step) */
@@ -189,7 +193,7 @@ int mrq_project_noalloc(mrq_index* index, const float* queries, int64_t nq,
 
 /* Result of mrq_autotune: the chosen scan configuration and what it cost. */
 typedef struct {
-  int scan;        /* MRQ_SCAN_PAIRS or MRQ_SCAN_BATCHED */
+  int scan;        /* MRQ_SCAN_PAIRS, MRQ_SCAN_BATCHED or MRQ_SCAN_BATCHED_TC */
   int chunk;       /* candidates per work item of a long list (per-pair scan) */
   int group;       /* queries per work item of the batched scan (1..16) */
   double ms;       /* median device time of one search of the tuning batch with it */
@@ -202,7 +206,8 @@ typedef struct {
  * Autotuner of the scan's work decomposition (not a step of the paper, which scans
  * one list per query on a CPU): times, on the given queries, the per-pair scan with
  * long lists cut into work items of 1024, 4096 or 16384 candidates and the batched
- * scan with 4, 8 or 16 queries per work item (where the code shape allows it), each
+ * scan with 4, 8 or 16 queries per work item and the tensor-core batched scan (where
+ * the code shape allows them), each
  * as a median of 3 CUDA-event timed searches after one warm-up, and records the
  * fastest for (k, nprobe, opt->query_bits) in the index; searches with
  * opt->batched = MRQ_SCAN_AUTO then use it.  All configurations compute the same

@@ -22,7 +22,7 @@ MRQ_OK = 0
 MRQ_EINVAL, MRQ_ENOMEM, MRQ_ECUDA, MRQ_EFORMAT, MRQ_EIO, MRQ_ETIMEDOUT = -1, -2, -3, -4, -5, -6
 MODE_MRQ, MODE_MRQ_PLUS = 0, 1
 PREC_FP32, PREC_BF16, PREC_BF16X3 = 0, 1, 2
-SCAN_PAIRS, SCAN_BATCHED, SCAN_AUTO = 0, 1, 2
+SCAN_PAIRS, SCAN_BATCHED, SCAN_AUTO, SCAN_BATCHED_TC = 0, 1, 2, 3
 
 EXPORTS = [
     "mrq_build_opts_default", "mrq_search_opts_default", "mrq_build", "mrq_search",

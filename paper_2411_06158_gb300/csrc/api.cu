@@ -72,8 +72,8 @@ mrq_search_opts resolve(const mrq_search_opts* opt) {
   MRQ_REQUIRE(o.mode == MRQ_MODE_MRQ || o.mode == MRQ_MODE_MRQ_PLUS, "mode must be MRQ_MODE_MRQ or MRQ_MODE_MRQ_PLUS");
   MRQ_REQUIRE(o.precision >= MRQ_PREC_FP32 && o.precision <= MRQ_PREC_BF16X3, "unknown precision");
   MRQ_REQUIRE(o.query_bits >= 0 && o.query_bits <= 8, "query_bits must be in [0, 8]");
-  MRQ_REQUIRE(o.batched >= MRQ_SCAN_PAIRS && o.batched <= MRQ_SCAN_AUTO,
-              "batched must be MRQ_SCAN_PAIRS, MRQ_SCAN_BATCHED or MRQ_SCAN_AUTO");
+  MRQ_REQUIRE(o.batched >= MRQ_SCAN_PAIRS && o.batched <= MRQ_SCAN_BATCHED_TC,
+              "batched must be MRQ_SCAN_PAIRS, MRQ_SCAN_BATCHED, MRQ_SCAN_AUTO or MRQ_SCAN_BATCHED_TC");
   return o;
 }
 
@@ -356,6 +356,8 @@ int mrq_autotune(mrq_index* idx, const float* queries, int64_t nq, int k, int np
                            !(wds == 16 && idx->d == 32);
     if (can_batch)
       for (int g : {4, 8, 16}) cands.push_back({MRQ_SCAN_BATCHED, 4096, g});
+    if (mrq::tc_available() && mrq::scan_tc_supported(idx->d, idx->bits, o.query_bits))
+      cands.push_back({MRQ_SCAN_BATCHED_TC, 4096, mrq::TC_SCAN_GROUP});
     const mrq::ScanConfig dflt = mrq::scan_config(idx, o, nq, k, nprobe);
     result->consistent = 1;
     double best = 1e300;

@@ -103,6 +103,7 @@ struct Workspace {
   DevBuf<int32_t> icnt, ioff;              // work items per list and their offsets
   DevBuf<int64_t> bitems;                  // int4 work items (list, block, group)
   DevBuf<uint8_t> pq;                      // per-pair query scalars
+  DevBuf<__nv_bfloat16> qrow;              // per-pair query codes as bf16 (tensor-core scan)
   DevBuf<uint32_t> qplanes;                // per-pair quantized query bit planes
 };
 
@@ -111,10 +112,51 @@ struct Workspace {
 namespace mrq {
 // scan configuration the autotuner chooses between
 struct ScanConfig {
-  int scan;   // MRQ_SCAN_PAIRS or MRQ_SCAN_BATCHED
+  int scan;   // MRQ_SCAN_PAIRS, MRQ_SCAN_BATCHED or MRQ_SCAN_BATCHED_TC
   int chunk;  // candidates per work item of a long list (per-pair scan)
   int group;  // queries per work item (batched scan), <= 16
 };
+
+// per-(query, list) scalars of the batched scans (Algorithm 2: normalise, quantize)
+struct __align__(16) PairQ {
+  float sg, a0, e0, em;  // sqrt(g), g + |q_r|^2, eps0*sqrt(g), m*sigma
+  float ql, qdelta;      // q' ~ ql + qdelta * qbar
+  int qsum, q;           // q: the pair's query
+};
+
+// the tensor-core batched scan: a work item is (list j, tile of 128 candidates, group
+// of up to 64 pairs probing j); the integer code dots of the tile against the group's
+// quantized queries are one bf16 MMA (levels and query codes are small integers)
+struct TcScanParams {
+  const int4* items;     // (j, tile, group)
+  const int* nitems;
+  const int* lqueue;     // pairs bucketed by list
+  const int* loffq;      // bucket offsets
+  const int* lcount;
+  const PairQ* pq;
+  const __nv_bfloat16* qrow;  // per pair: d query codes as bf16
+  const int64_t* loff;
+  const int64_t* ploff;
+  const uint32_t* codes;
+  const float* fadd;
+  const float* fres;
+  const float* ferr;
+  int nprobe, k;
+  int64_t cap;
+  unsigned int* work;    // item counter (zero before the launch)
+  unsigned int* qcnt;
+  unsigned int* gtau;
+  int32_t* spos;
+  float* slb;
+  float* sub;
+  int* err;
+};
+constexpr int TC_SCAN_TILE = 128;  // candidates per item
+constexpr int TC_SCAN_GROUP = 64;  // queries per item (MMA N)
+// whether the tensor-core scan has a kernel for this code shape (exact fp32 sums too)
+bool scan_tc_supported(int d, int bits, int qbits);
+// persistent launch; the kernel pulls items from p.work until *p.nitems
+void scan_tc(const TcScanParams& p, int d, int bits, cudaStream_t st);
 }  // namespace mrq
 
 struct mrq_index {

@@ -824,7 +824,7 @@ __global__ void k_scan_init(unsigned int* qcnt, unsigned int* gtau, int64_t nq, 
     qcnt[i] = 0u;
     gtau[i] = fkey(FINF);
   }
-  if (i < 4) work[i] = 0u;  // work-queue counters: [0] per-pair scan, [1] batched scan
+  if (i < 4) work[i] = 0u;  // work-queue counters: [0] per-pair, [1] batched, [2] tensor-core scan
 }
 
 // ------------------------------------------------------- batched (list-major) scan
@@ -839,11 +839,6 @@ __global__ void k_scan_init(unsigned int* qcnt, unsigned int* gtau, int64_t nq, 
 constexpr int BATCH_G = 16;     // largest number of queries per work item
 constexpr int BATCH_MAXW = 16;  // code words per vector kept in registers (bits*d/32)
 
-struct PairQ {
-  float sg, a0, e0, em;  // sqrt(g), g + |q_r|^2, eps0*sqrt(g), m*sigma
-  float ql, qdelta;      // q' ~ ql + qdelta * qbar
-  int qsum, q;           // q: the pair's query
-};
 
 // pairs with w % nprobe < first are left out (scanned by the seed pass)
 __global__ void k_bucket_count(const int32_t* __restrict__ plist, int64_t npairs, int nprobe,
@@ -861,12 +856,12 @@ __global__ void k_bucket_fill(const int32_t* __restrict__ plist, int64_t npairs,
 }
 // items of list j: (#32-blocks) x (#groups of BATCH_G pairs)
 __global__ void k_batch_count(const int* __restrict__ cnt, const int64_t* __restrict__ loff,
-                              int nlist, int group, int* __restrict__ icnt) {
+                              int nlist, int blk, int group, int* __restrict__ icnt) {
   int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= nlist) return;
   const int64_t sz = loff[j + 1] - loff[j];
   const int c = cnt[j];
-  icnt[j] = (c > 0 && sz > 0) ? (int)(((sz + 31) / 32) * ((c + group - 1) / group)) : 0;
+  icnt[j] = (c > 0 && sz > 0) ? (int)(((sz + blk - 1) / blk) * ((c + group - 1) / group)) : 0;
 }
 __global__ void k_batch_scatter(const int* __restrict__ cnt, const int* __restrict__ icnt,
                                 const int* __restrict__ ioff, const int64_t* __restrict__ loff,
@@ -884,7 +879,7 @@ __global__ void k_pair_prep(const float* __restrict__ qd, const float* __restric
                             const int32_t* __restrict__ plist, const float* __restrict__ pg,
                             const float* __restrict__ cent, int64_t npairs, int nprobe, int d,
                             int qbits, float eps0, float m, PairQ* __restrict__ pq,
-                            uint32_t* __restrict__ qplanes) {
+                            uint32_t* __restrict__ qplanes, __nv_bfloat16* __restrict__ qcode) {
   const int64_t w = (int64_t)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
   if (w >= npairs) return;
   const int lane = threadIdx.x & 31;
@@ -920,6 +915,7 @@ __global__ void k_pair_prep(const float* __restrict__ qd, const float* __restric
       qb = max(qb, 0);
     }
     ssum += qb;
+    if (qcode) qcode[w * d + i] = __float2bfloat16_rn((float)qb);  // exact: qb <= 255
     for (int b = 0; b < qbits; ++b) {
       const unsigned word = __ballot_sync(0xffffffffu, (qb >> b) & 1);
       if (lane == 0) out[b * nch + c] = word;
@@ -1960,7 +1956,7 @@ int scan_kclass(int k) { return k <= 32 ? 0 : k <= 128 ? 1 : 2; }
 
 ScanConfig scan_config(mrq_index* idx, const mrq_search_opts& o, int64_t nq, int k, int nprobe) {
   if (g_force_cfg) return *g_force_cfg;
-  ScanConfig c{o.batched == MRQ_SCAN_BATCHED ? MRQ_SCAN_BATCHED : MRQ_SCAN_PAIRS, SCAN_CHUNK, BATCH_G};
+  ScanConfig c{o.batched == MRQ_SCAN_AUTO ? MRQ_SCAN_PAIRS : o.batched, SCAN_CHUNK, BATCH_G};
   if (o.batched != MRQ_SCAN_AUTO) return c;
   {
     std::lock_guard<std::mutex> lk(idx->tune_mu);
@@ -2091,11 +2087,15 @@ void search_batch(mrq_index* idx, Workspace& ws, const float* q, int64_t nq, int
     idx->launches += 3;
     return max_items;
   };
-  // batched form: quantized query, code words a power of two (bits in {1,2,4,8}) up to 16
+  // batched forms: quantized query; the popcount kernel needs code words a power of two
+  // (bits in {1,2,4,8}) up to 16, the tensor-core kernel bits <= 4 and query_bits <= 4
   const int wds = idx->words;
-  const bool batched = cfg.scan == MRQ_SCAN_BATCHED && o.query_bits > 0 && wds <= BATCH_MAXW &&
-                       (wds & (wds - 1)) == 0 && (idx->bits & (idx->bits - 1)) == 0 &&
-                       ((d / 32) & (d / 32 - 1)) == 0 && !(wds == 16 && d == 32);
+  const bool pop_ok = o.query_bits > 0 && wds <= BATCH_MAXW && (wds & (wds - 1)) == 0 &&
+                      (idx->bits & (idx->bits - 1)) == 0 && ((d / 32) & (d / 32 - 1)) == 0 &&
+                      !(wds == 16 && d == 32);
+  const bool use_tc = cfg.scan == MRQ_SCAN_BATCHED_TC && tc_available() &&
+                      scan_tc_supported(d, idx->bits, o.query_bits);
+  const bool batched = use_tc || ((cfg.scan == MRQ_SCAN_BATCHED || cfg.scan == MRQ_SCAN_BATCHED_TC) && pop_ok);
   if (batched) {
     const int64_t np_ = nq * nprobe;
     const int nch = d / 32;
@@ -2114,6 +2114,9 @@ void search_batch(mrq_index* idx, Workspace& ws, const float* q, int64_t nq, int
     ws.bitems.reserve(2 * max_items);  // int4 items, two int64 slots each
     ws.pq.reserve(np_ * sizeof(PairQ));
     ws.qplanes.reserve(np_ * o.query_bits * nch);
+    if (use_tc) ws.qrow.reserve(np_ * d);
+    const int blk = use_tc ? TC_SCAN_TILE : 32;
+    const int group = use_tc ? TC_SCAN_GROUP : cfg.group;
     MRQ_CUDA(cudaMemsetAsync(ws.lcount.p, 0, 4 * nlist, st));
     MRQ_CUDA(cudaMemsetAsync(ws.lfill.p, 0, 4 * nlist, st));
     k_bucket_count<<<ceil_div(np_, 256), 256, 0, st>>>(ws.plist.p, np_, nprobe, first, ws.lcount.p);
@@ -2123,20 +2126,36 @@ void search_batch(mrq_index* idx, Workspace& ws, const float* q, int64_t nq, int
     MRQ_CUDA(cub::DeviceScan::ExclusiveSum(ws.cubtmp.p, tb, ws.lcount.p, ws.loffq.p, nlist, st));
     k_bucket_fill<<<ceil_div(np_, 256), 256, 0, st>>>(ws.plist.p, np_, nprobe, first, ws.loffq.p,
                                                       ws.lfill.p, ws.lqueue.p);
-    k_batch_count<<<ceil_div(nlist, 256), 256, 0, st>>>(ws.lcount.p, idx->loff.p, nlist, cfg.group,
+    k_batch_count<<<ceil_div(nlist, 256), 256, 0, st>>>(ws.lcount.p, idx->loff.p, nlist, blk, group,
                                                         ws.icnt.p);
     MRQ_CUDA(cub::DeviceScan::ExclusiveSum(nullptr, tb, ws.icnt.p, ws.ioff.p, nlist, st));
     ws.cubtmp.reserve(tb + 16);
     MRQ_CUDA(cub::DeviceScan::ExclusiveSum(ws.cubtmp.p, tb, ws.icnt.p, ws.ioff.p, nlist, st));
     k_batch_scatter<<<ceil_div(nlist, 256), 256, 0, st>>>(ws.lcount.p, ws.icnt.p, ws.ioff.p,
-                                                          idx->loff.p, nlist, cfg.group,
+                                                          idx->loff.p, nlist, group,
                                                           reinterpret_cast<int4*>(ws.bitems.p),
                                                           ws.nitems.p);
     k_pair_prep<<<ceil_div(np_, 8), 256, 0, st>>>(ws.qd.p, ws.qstat.p, ws.plist.p, ws.pg.p,
                                                   idx->cent.p, np_, nprobe, d, o.query_bits,
                                                   o.eps0, o.m, reinterpret_cast<PairQ*>(ws.pq.p),
-                                                  ws.qplanes.p);
+                                                  ws.qplanes.p, use_tc ? ws.qrow.p : nullptr);
     MRQ_CHECK_LAUNCH();
+    if (use_tc) {
+      TcScanParams tp{};
+      tp.items = reinterpret_cast<const int4*>(ws.bitems.p); tp.nitems = ws.nitems.p;
+      tp.lqueue = ws.lqueue.p; tp.loffq = ws.loffq.p; tp.lcount = ws.lcount.p;
+      tp.pq = reinterpret_cast<const PairQ*>(ws.pq.p); tp.qrow = ws.qrow.p;
+      tp.loff = idx->loff.p; tp.ploff = idx->ploff.p; tp.codes = idx->codes.p;
+      tp.fadd = idx->fadd.p; tp.fres = idx->fres.p; tp.ferr = idx->ferr.p;
+      tp.nprobe = nprobe; tp.k = k; tp.cap = cap;
+      tp.work = ws.work.p + 2; tp.qcnt = ws.qcnt.p; tp.gtau = ws.gtau.p;
+      tp.spos = ws.spos.p; tp.slb = ws.slb.p; tp.sub = ws.sub.p;
+      tp.err = tc_error_word();
+      // items, per list: ceil(size / 128) tiles x ceil(pairs / 64) groups, fewer than the
+      // popcount form's items that bitems is sized for
+      scan_tc(tp, d, idx->bits, st);
+      idx->launches += 8;
+    } else {
     BatchParams bp{};
     bp.items = reinterpret_cast<const int4*>(ws.bitems.p); bp.nitems = ws.nitems.p;
     bp.lqueue = ws.lqueue.p; bp.loffq = ws.loffq.p; bp.lcount = ws.lcount.p;
@@ -2162,6 +2181,7 @@ void search_batch(mrq_index* idx, Workspace& ws, const float* q, int64_t nq, int
     (void)bits_;
     MRQ_CHECK_LAUNCH();
     idx->launches += 8;
+    }
   }
   int64_t grid_items = nq * nprobe;
   if (!batched && idx->max_list > cfg.chunk) grid_items = build_items(nq * nprobe, 1);
