@@ -103,7 +103,7 @@ struct Workspace {
   DevBuf<int32_t> icnt, ioff;              // work items per list and their offsets
   DevBuf<int64_t> bitems;                  // int4 work items (list, block, group)
   DevBuf<uint8_t> pq;                      // per-pair query scalars
-  DevBuf<__nv_bfloat16> qrow;              // per-pair query codes as bf16 (tensor-core scan)
+  DevBuf<uint8_t> qrow;                    // per-pair query codes as e4m3 bytes (tensor-core scan)
   DevBuf<uint32_t> qplanes;                // per-pair quantized query bit planes
 };
 
@@ -125,8 +125,8 @@ struct __align__(16) PairQ {
 };
 
 // the tensor-core batched scan: a work item is (list j, tile of 128 candidates, group
-// of up to 64 pairs probing j); the integer code dots of the tile against the group's
-// quantized queries are one bf16 MMA (levels and query codes are small integers)
+// of up to 128 pairs probing j); the integer code dots of the tile against the group's
+// quantized queries are one e4m3 MMA chain (levels and query codes 0..15 are exact)
 struct TcScanParams {
   const int4* items;     // (j, tile, group)
   const int* nitems;
@@ -134,7 +134,7 @@ struct TcScanParams {
   const int* loffq;      // bucket offsets
   const int* lcount;
   const PairQ* pq;
-  const __nv_bfloat16* qrow;  // per pair: d query codes as bf16
+  const uint8_t* qrow;   // per pair: d query codes as e4m3 bytes
   const int64_t* loff;
   const int64_t* ploff;
   const uint32_t* codes;
@@ -152,7 +152,7 @@ struct TcScanParams {
   int* err;
 };
 constexpr int TC_SCAN_TILE = 128;  // candidates per item
-constexpr int TC_SCAN_GROUP = 64;  // queries per item (MMA N)
+constexpr int TC_SCAN_GROUP = 128;  // queries per item (MMA N)
 // whether the tensor-core scan has a kernel for this code shape (exact fp32 sums too)
 bool scan_tc_supported(int d, int bits, int qbits);
 // persistent launch; the kernel pulls items from p.work until *p.nitems

@@ -20,6 +20,8 @@
 
 #include <mutex>
 
+#include <cuda_fp8.h>
+
 #include "common.cuh"
 
 namespace mrq {
@@ -699,23 +701,46 @@ void project_noalloc(mrq_index* idx, const float* q, int64_t nq, int precision, 
 namespace mrq {
 namespace {
 
-// byte offset of element (row, k) of a K-major bf16 tile of `rows` rows stored as 128-byte
-// swizzled K slices (64 elements per row per slice; chunk c of row r at c ^ (r % 8)),
-// the layout TMA writes with CU_TENSOR_MAP_SWIZZLE_128B and the MMA descriptor reads
-__device__ __forceinline__ uint32_t sw128_off(int rows, int row, int k) {
-  const int slice = k >> 6, kin = k & 63;
+// byte offset of element (row, k) of a K-major one-byte (e4m3) tile of `rows` rows stored
+// as 128-byte swizzled K slices (128 elements per row per slice; 16-byte chunk c of row r
+// at c ^ (r % 8)), the layout TMA writes with CU_TENSOR_MAP_SWIZZLE_128B and the MMA
+// descriptor reads
+__device__ __forceinline__ uint32_t sw128_off8(int rows, int row, int k) {
+  const int slice = k >> 7, kin = k & 127;
   return (uint32_t)(slice * rows * 128 + (row >> 3) * 1024 + (row & 7) * 128 +
-                    ((((kin >> 3) ^ (row & 7)) << 4) | ((kin & 7) << 1)));
+                    ((((kin >> 4) ^ (row & 7)) << 4) | (kin & 15)));
+}
+
+// Instruction descriptor, kind::f8f6f4: D f32 (bits 4-5 = 1), A and B e4m3 (format 0 in
+// bits 7-9 and 10-12), both K-major, N >> 3 at bit 17, M >> 4 at bit 24.
+template <int N>
+__host__ __device__ constexpr uint32_t idesc_e4m3() {
+  return (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(TC_BM >> 4) << 24);
+}
+__device__ __forceinline__ void tc_mma_f8(uint32_t dtmem, uint64_t a, uint64_t b, uint32_t idesc,
+                                          uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n}" ::"r"(dtmem),
+      "l"(a), "l"(b), "r"(idesc), "r"(acc)
+      : "memory");
+}
+
+// e4m3 bytes of two small non-negative integers (exact up to 16)
+__device__ __forceinline__ uint32_t e4m3x2(int v0, int v1) {
+  return (uint32_t)__nv_cvt_float2_to_fp8x2(make_float2((float)v0, (float)v1), __NV_SATFINITE,
+                                            __NV_E4M3);
 }
 
 // Stage 1 (Eq. 4, Eq. 5, the bound test of Algorithm 2) for a work item (list j, tile
-// of 128 candidates, group of up to 64 pairs probing j).  The candidates' B-bit levels
-// u and the pairs' quantized query codes qbar are written to shared memory as bf16
-// (small integers, exact) and one tcgen05 MMA chain gives every integer dot <u, qbar>
-// in fp32 (exact below 2^24).  The epilogue applies the same arithmetic, bound updates
-// and survivor compaction as the popcount batched scan, per (pair, 32 candidates).
-// 256 threads: two per candidate row for the expansion; the eight warps drain the
-// accumulator (warp w: rows 32*(w%4).., columns 32*(w/4)..).  Persistent over items.
+// of 128 candidates, group of up to 128 pairs probing j).  The candidates' B-bit levels
+// u and the pairs' quantized query codes qbar (integers 0..15, exact in e4m3) are written
+// to shared memory as e4m3 bytes and one tcgen05 MMA chain (kind::f8f6f4) gives every
+// integer dot <u, qbar> in fp32 (exact below 2^24).  The epilogue applies the same
+// arithmetic, bound updates and survivor compaction as the popcount batched scan, per
+// (pair, 32 candidates).  256 threads: two per candidate row for the expansion; the
+// eight warps drain the accumulator (warp w: rows 32*(w%4).., columns 64*(w/4)..).
+// Persistent over items.
 template <int NCH, int BITS>
 __global__ void __launch_bounds__(256) k_scan_tc(TcScanParams P) {
   constexpr int DQ = NCH * 32;
@@ -723,11 +748,11 @@ __global__ void __launch_bounds__(256) k_scan_tc(TcScanParams P) {
   constexpr int VW = (W % 4 == 0) ? 4 : (W % 2 == 0) ? 2 : 1;
   constexpr int NQ = TC_SCAN_GROUP;
   constexpr int TR = TC_SCAN_TILE;
-  constexpr int KS = DQ / 64;
-  constexpr int HC = NCH / 2;  // chunks expanded by each of a row's two threads
+  constexpr int KS = DQ / 128;  // 128-byte K slices
+  constexpr int HC = NCH / 2;   // 32-dim chunks expanded by each of a row's two threads
   constexpr int topc = (1 << BITS) - 1;
-  constexpr uint32_t IDESC = idesc_bf16<NQ>();
-  constexpr int A_BYTES = TR * DQ * 2;
+  constexpr uint32_t IDESC = idesc_e4m3<NQ>();
+  constexpr int A_BYTES = TR * DQ;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* sA = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                            ~static_cast<uintptr_t>(1023));
@@ -777,7 +802,7 @@ __global__ void __launch_bounds__(256) k_scan_tc(TcScanParams P) {
       s_pair[tid] = w;
       if (w >= 0) s_pq[tid] = P.pq[w];
     }
-    // A: levels of this row's candidate (two threads per row, HC chunks each)
+    // A: levels of this row's candidate (two threads per row, HC chunks each), e4m3
     {
       const int64_t idx = (int64_t)item.y * TR + row;
       const bool valid = idx < size;
@@ -793,33 +818,34 @@ __global__ void __launch_bounds__(256) k_scan_tc(TcScanParams P) {
           pw[a] = valid ? __ldg(cbase + (wi / VW) * 32 * VW + (wi % VW)) : 0u;
         }
 #pragma unroll
-        for (int by = 0; by < 4; ++by) {
+        for (int hx = 0; hx < 2; ++hx) {  // 16 dims (one 16-byte chunk) at a time
           uint32_t packed[4];
 #pragma unroll
-          for (int t = 0; t < 8; t += 2) {
-            int v0 = 0, v1 = 0;
+          for (int t4 = 0; t4 < 4; ++t4) {
+            int v[4];
 #pragma unroll
-            for (int a = 0; a < BITS; ++a) {
-              const uint32_t wd = pw[a] >> (by * 8 + t);
-              v0 |= (int)(wd & 1u) << a;
-              v1 |= (int)((wd >> 1) & 1u) << a;
+            for (int u = 0; u < 4; ++u) {
+              const int bit = hx * 16 + t4 * 4 + u;
+              int val = 0;
+#pragma unroll
+              for (int a = 0; a < BITS; ++a) val |= (int)((pw[a] >> bit) & 1u) << a;
+              v[u] = val;
             }
-            const __nv_bfloat162 h2 = __floats2bfloat162_rn((float)v0, (float)v1);
-            packed[t >> 1] = *reinterpret_cast<const uint32_t*>(&h2);
+            packed[t4] = e4m3x2(v[0], v[1]) | (e4m3x2(v[2], v[3]) << 16);
           }
-          *reinterpret_cast<uint4*>(sA + sw128_off(TR, row, c * 32 + by * 8)) =
+          *reinterpret_cast<uint4*>(sA + sw128_off8(TR, row, c * 32 + hx * 16)) =
               make_uint4(packed[0], packed[1], packed[2], packed[3]);
         }
       }
     }
     __syncthreads();  // s_pair / s_pq visible
     // B: the group's query codes, zero rows past the group
-    for (int e = tid; e < NQ * (DQ / 8); e += 256) {
-      const int n = e / (DQ / 8), kc = e % (DQ / 8);
+    for (int e = tid; e < NQ * (DQ / 16); e += 256) {
+      const int n = e / (DQ / 16), kc = e % (DQ / 16);
       uint4 v = make_uint4(0u, 0u, 0u, 0u);
       const int w = s_pair[n];
       if (w >= 0) v = __ldg(reinterpret_cast<const uint4*>(P.qrow + (int64_t)w * DQ) + kc);
-      *reinterpret_cast<uint4*>(sB + sw128_off(NQ, n, kc * 8)) = v;
+      *reinterpret_cast<uint4*>(sB + sw128_off8(NQ, n, kc * 16)) = v;
     }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // visible to the MMA
     tc_fence_before();
@@ -831,7 +857,7 @@ __global__ void __launch_bounds__(256) k_scan_tc(TcScanParams P) {
         const uint64_t ad = sdesc(su32(sA + s * TR * 128)), bd = sdesc(su32(sB + s * NQ * 128));
 #pragma unroll
         for (int kk = 0; kk < 4; ++kk)
-          tc_mma(tmem, ad + 2ull * kk, bd + 2ull * kk, IDESC, (s | kk) != 0 ? 1u : 0u);
+          tc_mma_f8(tmem, ad + 2ull * kk, bd + 2ull * kk, IDESC, (s | kk) != 0 ? 1u : 0u);
       }
       tc_commit(&mbar);
     }
@@ -840,19 +866,14 @@ __global__ void __launch_bounds__(256) k_scan_tc(TcScanParams P) {
     tc_fence_after();
     __syncthreads();  // every thread past the wait (or all of them told to stop)
     if (s_abort) break;
-    // epilogue: warp (quarter, half) scores rows 32*quarter.. against columns 32*half..,
-    // staging its 32 x 32 block of dots in the (now idle) operand area
+    // epilogue: warp (quarter, half) scores rows 32*quarter.. against columns 64*half..,
+    // 32 columns at a time, staging each 32 x 32 block of dots in the idle operand area
     {
       const int r = quarter * 32 + lane;
       const int64_t idx = (int64_t)item.y * TR + r;
       const bool valid = idx < size;
       const int64_t pp = P.ploff[j] + idx;
       float* stg = reinterpret_cast<float*>(sA) + warp * (32 * 33);
-      uint32_t acc[32];
-      tc_ld32(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(half * 32), acc);
-#pragma unroll
-      for (int t = 0; t < 32; ++t) stg[lane * 33 + t] = __uint_as_float(acc[t]);
-      __syncwarp();
       float fa = 0.f, fr = 0.f, fe = 0.f;
       int su = 0;
       if (valid) {
@@ -864,57 +885,67 @@ __global__ void __launch_bounds__(256) k_scan_tc(TcScanParams P) {
         for (int wi = 0; wi < W; ++wi)
           su += __popc(__ldg(cbase + (wi / VW) * 32 * VW + (wi % VW))) << (wi / NCH);
       }
-      const int c0 = half * 32;
-      const int ncol = min(32, ng - c0);
-      // the running bounds of the columns' queries, one lane each
-      const float my_tau = lane < ncol ? fkey_inv(__ldcg(P.gtau + s_pq[c0 + lane].q)) : FLT_INF_F;
-      for (int t = 0; t < ncol; ++t) {
-        const PairQ pr = s_pq[c0 + t];
-        const int64_t q = pr.q;
-        const int dot = (int)stg[lane * 33 + t];
-        const float ip = pr.qdelta * (float)(2 * dot - topc * pr.qsum) +
-                         pr.ql * (float)(2 * su - DQ * topc);
-        const float dis = fa + pr.a0 + fr * pr.sg * ip;  // Eq. 4
-        const float eps = pr.e0 * fe + pr.em;            // Eq. 5 + Chebyshev
-        const float lb = valid ? dis - eps : FLT_INF_F;
-        const float ub = valid ? dis + eps : FLT_INF_F;
-        // the bound as read at the start of this block of columns (a valid upper bound of
-        // tau_A; later tightening by other warps only means more survivors, filtered later)
-        float tau = __shfl_sync(0xffffffffu, my_tau, t);
-        if (P.k <= 32) {
-          const unsigned below = __ballot_sync(0xffffffffu, ub < tau);
-          if (__popc(below) >= P.k) {
-            float v = ub < tau ? ub : FLT_INF_F;
+      for (int cb = 0; cb < 2; ++cb) {
+        const int c0 = half * 64 + cb * 32;
+        if (c0 >= ng) break;  // warp-uniform
+        uint32_t acc[32];
+        tc_ld32(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)c0, acc);
+        __syncwarp();
 #pragma unroll
-            for (int size2 = 2; size2 <= 32; size2 <<= 1) {
+        for (int t = 0; t < 32; ++t) stg[lane * 33 + t] = __uint_as_float(acc[t]);
+        __syncwarp();
+        const int ncol = min(32, ng - c0);
+        // the running bounds of the columns' queries, one lane each
+        const float my_tau = lane < ncol ? fkey_inv(__ldcg(P.gtau + s_pq[c0 + lane].q)) : FLT_INF_F;
+        for (int t = 0; t < ncol; ++t) {
+          const PairQ pr = s_pq[c0 + t];
+          const int64_t q = pr.q;
+          const int dot = (int)stg[lane * 33 + t];
+          const float ip = pr.qdelta * (float)(2 * dot - topc * pr.qsum) +
+                           pr.ql * (float)(2 * su - DQ * topc);
+          const float dis = fa + pr.a0 + fr * pr.sg * ip;  // Eq. 4
+          const float eps = pr.e0 * fe + pr.em;            // Eq. 5 + Chebyshev
+          const float lb = valid ? dis - eps : FLT_INF_F;
+          const float ub = valid ? dis + eps : FLT_INF_F;
+          // the bound as read at the start of these columns (a valid upper bound of tau_A;
+          // tightening by other warps since only means more survivors, filtered later)
+          float tau = __shfl_sync(0xffffffffu, my_tau, t);
+          if (P.k <= 32) {
+            const unsigned below = __ballot_sync(0xffffffffu, ub < tau);
+            if (__popc(below) >= P.k) {
+              float v = ub < tau ? ub : FLT_INF_F;
 #pragma unroll
-              for (int stride = size2 >> 1; stride > 0; stride >>= 1) {
-                const float o = __shfl_xor_sync(0xffffffffu, v, stride);
-                const bool up = ((lane & size2) == 0);
-                const bool lower = (lane & stride) == 0;
-                v = (lower == up) ? fminf(v, o) : fmaxf(v, o);
+              for (int size2 = 2; size2 <= 32; size2 <<= 1) {
+#pragma unroll
+                for (int stride = size2 >> 1; stride > 0; stride >>= 1) {
+                  const float o = __shfl_xor_sync(0xffffffffu, v, stride);
+                  const bool up = ((lane & size2) == 0);
+                  const bool lower = (lane & stride) == 0;
+                  v = (lower == up) ? fminf(v, o) : fmaxf(v, o);
+                }
+              }
+              const float kth = __shfl_sync(0xffffffffu, v, P.k - 1);
+              if (kth < tau) {
+                tau = kth;
+                if (lane == 0) atomicMin(P.gtau + q, fkey(kth));
               }
             }
-            const float kth = __shfl_sync(0xffffffffu, v, P.k - 1);
-            if (kth < tau) {
-              tau = kth;
-              if (lane == 0) atomicMin(P.gtau + q, fkey(kth));
+          }
+          const bool surv = lb <= tau;
+          const unsigned sm = __ballot_sync(0xffffffffu, surv);
+          if (sm) {
+            unsigned base = 0;
+            if (lane == 0) base = atomicAdd(P.qcnt + q, (unsigned)__popc(sm));
+            base = __shfl_sync(0xffffffffu, base, 0);
+            if (surv) {
+              const int64_t at = q * P.cap + base + __popc(sm & ((1u << lane) - 1));
+              P.spos[at] = (int32_t)(lb0 + idx);
+              P.slb[at] = lb;
+              P.sub[at] = ub;
             }
           }
         }
-        const bool surv = lb <= tau;
-        const unsigned sm = __ballot_sync(0xffffffffu, surv);
-        if (sm) {
-          unsigned base = 0;
-          if (lane == 0) base = atomicAdd(P.qcnt + q, (unsigned)__popc(sm));
-          base = __shfl_sync(0xffffffffu, base, 0);
-          if (surv) {
-            const int64_t at = q * P.cap + base + __popc(sm & ((1u << lane) - 1));
-            P.spos[at] = (int32_t)(lb0 + idx);
-            P.slb[at] = lb;
-            P.sub[at] = ub;
-          }
-        }
+        __syncwarp();
       }
     }
     tc_fence_before();
@@ -930,19 +961,20 @@ __global__ void __launch_bounds__(256) k_scan_tc(TcScanParams P) {
 template <int NCH, int BITS>
 void launch_scan_tc(const TcScanParams& p, cudaStream_t st) {
   constexpr int DQ = NCH * 32;
-  const size_t ab = (size_t)TC_SCAN_TILE * DQ * 2 + (size_t)TC_SCAN_GROUP * DQ * 2;
+  const size_t ab = (size_t)TC_SCAN_TILE * DQ + (size_t)TC_SCAN_GROUP * DQ;
   const size_t smem = std::max(ab, (size_t)8 * 32 * 33 * 4) + 1024;
   auto kern = k_scan_tc<NCH, BITS>;
   ensure_smem((const void*)kern, smem);
-  // prefer the largest shared-memory carveout, so that two CTAs fit per SM
+  // prefer the largest shared-memory carveout
   MRQ_CUDA(cudaFuncSetAttribute((const void*)kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
   // The occupancy calculator reports one CTA per SM for kernels that allocate tensor
-  // memory; two of these (2 x 64 columns, 2 x ~100 KB shared) fit, so launch two per SM.
-  // CTAs that cannot be resident simply start later and find the item queue drained.
+  // memory; with 128 columns and ~65 KB of shared memory each, three fit per SM (the
+  // register file allows three at 80 registers), so launch three per SM.  CTAs that are
+  // not resident start later and find the item queue drained.
   int dev = 0, nsm = 0;
   MRQ_CUDA(cudaGetDevice(&dev));
   MRQ_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-  const int per_sm = smem <= 110 * 1024 ? 2 : 1;
+  const int per_sm = smem <= 70 * 1024 ? 3 : smem <= 110 * 1024 ? 2 : 1;
   kern<<<nsm * per_sm, 256, smem, st>>>(p);
   MRQ_CHECK_LAUNCH();
 }
@@ -950,7 +982,7 @@ void launch_scan_tc(const TcScanParams& p, cudaStream_t st) {
 }  // namespace
 
 bool scan_tc_supported(int d, int bits, int qbits) {
-  if (d % 64 != 0 || d < 64 || d > 512) return false;
+  if (d % 128 != 0 || d < 128 || d > 512) return false;  // whole 128-byte e4m3 slices
   if (!(bits == 1 || bits == 2 || bits == 4) || qbits < 1 || qbits > 4) return false;
   const int64_t top = (int64_t)d * ((1 << bits) - 1) * ((1 << qbits) - 1);
   return top < (1 << 24);
@@ -963,8 +995,8 @@ void scan_tc(const TcScanParams& p, int d, int bits, cudaStream_t st) {
     launch_scan_tc<N, B>(p, st);           \
     return;                                \
   }
-  MRQ_STC(2, 1) MRQ_STC(2, 2) MRQ_STC(2, 4) MRQ_STC(4, 1) MRQ_STC(4, 2) MRQ_STC(4, 4)
-  MRQ_STC(8, 1) MRQ_STC(8, 2) MRQ_STC(8, 4) MRQ_STC(16, 1) MRQ_STC(16, 2) MRQ_STC(16, 4)
+  MRQ_STC(4, 1) MRQ_STC(4, 2) MRQ_STC(4, 4) MRQ_STC(8, 1) MRQ_STC(8, 2) MRQ_STC(8, 4)
+  MRQ_STC(12, 1) MRQ_STC(12, 2) MRQ_STC(12, 4) MRQ_STC(16, 1) MRQ_STC(16, 2) MRQ_STC(16, 4)
 #undef MRQ_STC
   fail(MRQ_EINVAL, "tensor-core scan: unsupported code shape");
 }

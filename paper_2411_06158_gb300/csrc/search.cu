@@ -23,6 +23,8 @@
 #include <tuple>
 #include <unordered_map>
 
+#include <cuda_fp8.h>
+
 #include "common.cuh"
 
 namespace mrq {
@@ -879,7 +881,7 @@ __global__ void k_pair_prep(const float* __restrict__ qd, const float* __restric
                             const int32_t* __restrict__ plist, const float* __restrict__ pg,
                             const float* __restrict__ cent, int64_t npairs, int nprobe, int d,
                             int qbits, float eps0, float m, PairQ* __restrict__ pq,
-                            uint32_t* __restrict__ qplanes, __nv_bfloat16* __restrict__ qcode) {
+                            uint32_t* __restrict__ qplanes, uint8_t* __restrict__ qcode) {
   const int64_t w = (int64_t)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
   if (w >= npairs) return;
   const int lane = threadIdx.x & 31;
@@ -915,7 +917,7 @@ __global__ void k_pair_prep(const float* __restrict__ qd, const float* __restric
       qb = max(qb, 0);
     }
     ssum += qb;
-    if (qcode) qcode[w * d + i] = __float2bfloat16_rn((float)qb);  // exact: qb <= 255
+    if (qcode) qcode[w * d + i] = (uint8_t)__nv_cvt_float_to_fp8((float)qb, __NV_SATFINITE, __NV_E4M3);  // exact: qb <= 15
     for (int b = 0; b < qbits; ++b) {
       const unsigned word = __ballot_sync(0xffffffffu, (qb >> b) & 1);
       if (lane == 0) out[b * nch + c] = word;
