@@ -204,6 +204,49 @@ __device__ void block_bitonic(unsigned long long* a, int n) {
 
 constexpr int PS_NT = 256;
 
+// Top-nprobe (nprobe <= 32) of one row of the probe-distance matrix, one warp per
+// query: the nprobe smallest keys (fkey(g) << 32 | list), which orders ties by the lower
+// list id, are kept sorted across the lanes; the row streams through 32 values at a time
+// and only keys below the current nprobe-th are inserted.  Writes plist and pg (the
+// matrix value; the refine step recomputes g exactly afterwards).
+__global__ void __launch_bounds__(256) k_probe_select_warp(const float* __restrict__ gmat,
+                                                           int64_t nq, int nlist, int nprobe,
+                                                           int32_t* __restrict__ plist,
+                                                           float* __restrict__ pg) {
+  const int lane = threadIdx.x & 31;
+  const int64_t q = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
+  if (q >= nq) return;
+  const float* row = gmat + q * nlist;
+  unsigned long long lst = ~0ull, kth = ~0ull;
+  for (int b = 0; b < nlist; b += 128) {  // four chunks of loads in flight
+    unsigned long long x[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int c = b + 32 * u + lane;
+      x[u] = c < nlist ? (((unsigned long long)fkey(row[c]) << 32) | (uint32_t)c) : ~0ull;
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      unsigned cand = __ballot_sync(0xffffffffu, x[u] < kth);
+      while (cand) {
+        const int src = __ffs(cand) - 1;
+        cand &= cand - 1;
+        const unsigned long long y = __shfl_sync(0xffffffffu, x[u], src);
+        if (y < kth) {
+          const int pos = __popc(__ballot_sync(0xffffffffu, lst < y));
+          const unsigned long long up = __shfl_up_sync(0xffffffffu, lst, 1);
+          lst = lane > pos ? up : (lane == pos ? y : lst);
+          kth = __shfl_sync(0xffffffffu, lst, nprobe - 1);
+        }
+      }
+    }
+  }
+  if (lane < nprobe) {
+    plist[q * nprobe + lane] = (int32_t)(lst & 0xffffffffu);
+    pg[q * nprobe + lane] = fkey_inv((uint32_t)(lst >> 32));
+  }
+}
+
 // The nprobe smallest (g_j, j) of one query, ascending (Algorithm 2, probing).
 // Shared memory: sel[cap] (64-bit (key, list) pairs) followed by the staged row
 // when it fits.  Every key <= T (the nprobe-th smallest) is gathered and sorted by
@@ -2042,9 +2085,14 @@ void search_batch(mrq_index* idx, Workspace& ws, const float* q, int64_t nq, int
     cap = c2;
     const int in_smem = (size_t)cap * 8 + (size_t)nlist * 4 <= 160 * 1024 ? 1 : 0;
     size_t sm = (size_t)cap * 8 + (in_smem ? (size_t)nlist * 4 : 0);
-    ensure_smem((const void*)k_probe_select, sm);
-    k_probe_select<<<(unsigned)nq, PS_NT, sm, st>>>(ws.gmat.p, nlist, nprobe, cap, in_smem,
-                                                    ws.plist.p, ws.pg.p);
+    if (nprobe <= 32) {
+      k_probe_select_warp<<<ceil_div(nq, 8), 256, 0, st>>>(ws.gmat.p, nq, nlist, nprobe,
+                                                          ws.plist.p, ws.pg.p);
+    } else {
+      ensure_smem((const void*)k_probe_select, sm);
+      k_probe_select<<<(unsigned)nq, PS_NT, sm, st>>>(ws.gmat.p, nlist, nprobe, cap, in_smem,
+                                                      ws.plist.p, ws.pg.p);
+    }
     MRQ_CHECK_LAUNCH();
     k_probe_refine<<<ceil_div(nq * nprobe, 8), 256, 0, st>>>(ws.qd.p, idx->cent.p, ws.plist.p,
                                                             nq * nprobe, nprobe, d, ws.pg.p);
