@@ -55,6 +55,10 @@ def parse_args(argv=None):
     p.add_argument("--eps0", type=float, default=None, help="fixed eps0 with --nprobe")
     p.add_argument("--clock-seconds", type=float, default=2.5,
                    help="length of the clock-sampling pass (0: one short pass)")
+    p.add_argument("--precision-report", action="store_true",
+                   help="precision form: projection error of each precision against a float64 "
+                        "projection with the index's own W and mu, and recall@10 (one JSON line "
+                        "per (d, precision); embedding-like workload unless --workload is given)")
     p.add_argument("--serve", action="store_true",
                    help="serving form: Poisson arrivals at swept rates, p50/p99 latency")
     p.add_argument("--rates", default="20000,100000,500000,2000000",
@@ -368,12 +372,70 @@ def run_serving(args):
 
 # --------------------------------------------------------------- GPU arm
 
+def run_precision_report(args):
+    """Precision form: for d in {64, 128, 256} and each projection precision (float32
+    CUDA cores, bf16 and split hi+lo bf16 tensor cores), the max and mean relative error
+    of the projected query coordinates [q_d' | q_r] against a float64 projection with
+    the index's exported W and mu (relative to |q - mu|), the error of the stage-1
+    estimate dis' it implies, and recall@10 at a fixed nprobe."""
+    import numpy as np
+    import torch
+
+    import datagen
+    import paper_2411_06158_gb300 as mrq
+
+    dev = torch.device("cuda", 0)
+    wname = args.workload if args.workload != "gist" else "embed"
+    nprobe = args.nprobe or 32
+    for d in ([args.d] if args.d else [64, 128, 256]):
+        over = {"d": d}
+        if args.n:
+            over["n"] = args.n
+        if args.nq:
+            over["n_query"] = args.nq
+        w = datagen.workload(wname, **over)
+        base, queries = datagen.base_and_queries(w)
+        base_t = torch.from_numpy(base).to(dev)
+        q_t = torch.from_numpy(queries).to(dev)
+        idx = mrq.mrq_build(base_t, w.d, w.bits, w.nlist, mrq.mrq_build_opts(seed=w.seed("method")))
+        truth = ground_truth(base_t, q_t, w.k)
+        del base_t
+        torch.cuda.empty_cache()
+        W = mrq.mrq_index_export(idx, "W___").astype(np.float64).reshape(w.D, w.D)
+        mu = mrq.mrq_index_export(idx, "MU__").astype(np.float64)
+        qc = queries.astype(np.float64) - mu
+        ref = qc @ W.T                                    # [q_d' | q_r] in float64
+        scale = np.linalg.norm(qc, axis=1, keepdims=True)
+        ids_fp32 = None
+        for name, prec in (("fp32", mrq.PREC_FP32), ("bf16", mrq.PREC_BF16),
+                           ("bf16x3", mrq.PREC_BF16X3)):
+            o = mrq.mrq_search_opts(precision=prec, query_bits=4, batched=mrq.SCAN_AUTO)
+            got = mrq.mrq_project(idx, q_t, o).cpu().numpy().astype(np.float64)
+            rel = np.abs(got - ref) / scale
+            ids, _ = mrq.mrq_search(idx, q_t, w.k, nprobe, o)
+            ids = ids.cpu().numpy()
+            if ids_fp32 is None:
+                ids_fp32 = ids
+            print(json.dumps({
+                "metric": "precision form", "workload": w.name, "n": w.n, "D": w.D, "d": d,
+                "bits": w.bits, "nlist": w.nlist, "nprobe": nprobe, "k": w.k,
+                "queries": int(q_t.shape[0]), "precision": name,
+                "projection_rel_err_max": float(rel.max()),
+                "projection_rel_err_mean": float(rel.mean()),
+                "recall@10": recall(ids, truth),
+                "same_ids_as_fp32": float(np.mean(ids == ids_fp32))}))
+        del idx
+    return 0
+
+
 def main(argv=None):
     args = parse_args(argv)
     if args.impl == "reference":
         return run_reference(args)
     if args.serve:
         return run_serving(args)
+    if args.precision_report:
+        return run_precision_report(args)
     import numpy as np
     import torch
 
