@@ -327,7 +327,10 @@ def run_serving(args):
     ks = rng.choice([10, 50, 100], size=w.n_query).astype(np.int32)
     nprobes = np.array([8, 16, 32], dtype=np.int32)
     nps = rng.choice(nprobes, size=w.n_query).astype(np.int32)
-    search = mrq.mrq_search_opts(eps0=1.9, m=4.0, query_bits=4, precision=mrq.PREC_BF16, batched=1)
+    # the scan decomposition per batch by the library's rule (per-pair for small batches,
+    # batched once each probed list is shared by many of the batch's queries)
+    search = mrq.mrq_search_opts(eps0=1.9, m=4.0, query_bits=4, precision=mrq.PREC_BF16,
+                                 batched=mrq.SCAN_AUTO)
     for rate in [float(x) for x in args.rates.split(",")]:
         srv = mrq.Server(idx, max_batch=4096, max_inflight=args.serve_slots,
                          max_wait_us=args.serve_wait_us, max_k=100, search=search)
