@@ -57,10 +57,18 @@ __device__ __forceinline__ int warp_sum_i(int v) {
 
 __global__ void k_qstats(const float* __restrict__ qd, const float* __restrict__ qr,
                          const float* __restrict__ lam, int64_t nq, int d, int r,
-                         float* __restrict__ qstat) {
+                         float* __restrict__ qstat, unsigned int* __restrict__ qcnt,
+                         unsigned int* __restrict__ gtau, unsigned int* __restrict__ work) {
   int64_t q = (int64_t)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
+  // the scan's per-query survivor count and running bound, and its work counters,
+  // start from zero / +inf (when given)
+  if (work && blockIdx.x == 0 && threadIdx.x < 4) work[threadIdx.x] = 0u;
   if (q >= nq) return;
   const int lane = threadIdx.x & 31;
+  if (qcnt && lane == 0) {
+    qcnt[q] = 0u;
+    gtau[q] = fkey(__int_as_float(0x7f800000));
+  }
   float qr2 = 0.f, s2 = 0.f, qd2 = 0.f;
   if ((r & 3) == 0) {  // rows and lam + d are 16-byte aligned (d is a multiple of 32)
     const float4* x = reinterpret_cast<const float4*>(qr + q * r);
@@ -325,13 +333,17 @@ __global__ void __launch_bounds__(PS_NT) k_probe_select(const float* __restrict_
   }
 }
 
-// merge of the fused probe candidates: per query (one warp), the nprobe smallest of
-// the n = tiles x nprobe (key, list) pairs, ascending.  The n <= 32 * SL keys sit in
-// registers (SL per lane); each of nprobe rounds takes a warp-wide minimum and
-// retires it (the keys are distinct: every list appears in one tile).
+// Merge of the fused probe candidates, then the refine step of the selected lists in the
+// same warp.  Per query (one warp): the nprobe smallest of the n = tiles x nprobe
+// (key, list) pairs, ascending; the n <= 32 * SL keys sit in registers (SL per lane) and
+// each of nprobe rounds takes a warp-wide minimum and retires it (the keys are distinct:
+// every list appears in one tile).  Then g_j = |q_d' - c_j'|^2 as a direct float32 sum
+// (lane-strided, then the warp tree, as k_probe_refine computes it).
 template <int SL>
-__global__ void k_probe_merge(const unsigned long long* __restrict__ part, int64_t nq, int tiles,
-                              int nprobe, int32_t* __restrict__ plist) {
+__global__ void k_probe_merge_refine(const unsigned long long* __restrict__ part, int64_t nq,
+                                     int tiles, int nprobe, const float* __restrict__ qd,
+                                     const float* __restrict__ cent, int d,
+                                     int32_t* __restrict__ plist, float* __restrict__ pg) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int64_t q = (int64_t)blockIdx.x * 8 + wid;
   if (q >= nq) return;
@@ -351,10 +363,20 @@ __global__ void k_probe_merge(const unsigned long long* __restrict__ part, int64
       const unsigned long long y = __shfl_xor_sync(0xffffffffu, m, o);
       m = y < m ? y : m;
     }
-    if (lane == 0) plist[q * nprobe + r] = (int32_t)(m & 0xffffffffu);
 #pragma unroll
     for (int s = 0; s < SL; ++s)
       if (v[s] == m) v[s] = ~0ull;
+    const int j = (int)(m & 0xffffffffu);
+    float g = 0.f;
+    for (int i = lane; i < d; i += 32) {
+      const float t = qd[q * d + i] - cent[(int64_t)j * d + i];
+      g = fmaf(t, t, g);
+    }
+    g = warp_sum(g);
+    if (lane == 0) {
+      plist[q * nprobe + r] = j;
+      pg[q * nprobe + r] = g;
+    }
   }
 }
 
@@ -863,14 +885,6 @@ __global__ void k_chunk_scatter(const int* __restrict__ cnt, const int* __restri
   if (i == n - 1) *nitems = o + c;
 }
 
-__global__ void k_scan_init(unsigned int* qcnt, unsigned int* gtau, int64_t nq, unsigned int* work) {
-  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < nq) {
-    qcnt[i] = 0u;
-    gtau[i] = fkey(FINF);
-  }
-  if (i < 4) work[i] = 0u;  // work-queue counters: [0] per-pair, [1] batched, [2] tensor-core scan
-}
 
 // ------------------------------------------------------- batched (list-major) scan
 //
@@ -1985,8 +1999,10 @@ void project_batch(mrq_index* idx, Workspace& ws, const float* q, int64_t nq, in
 }
 
 static void qstats(mrq_index* idx, const float* qd, const float* qr, int64_t nq, float* qstat,
-                   cudaStream_t st) {
-  k_qstats<<<ceil_div(nq, 8), 256, 0, st>>>(qd, qr, idx->lam.p, nq, idx->d, idx->D - idx->d, qstat);
+                   cudaStream_t st, unsigned int* qcnt = nullptr, unsigned int* gtau = nullptr,
+                   unsigned int* work = nullptr) {
+  k_qstats<<<ceil_div(nq, 8), 256, 0, st>>>(qd, qr, idx->lam.p, nq, idx->d, idx->D - idx->d, qstat,
+                                            qcnt, gtau, work);
   MRQ_CHECK_LAUNCH();
 }
 
@@ -2041,7 +2057,7 @@ void search_batch(mrq_index* idx, Workspace& ws, const float* q, int64_t nq, int
   project_batch(idx, ws, q, nq, o.precision, ws.qd.p, ws.qr.p, st);
   idx->launches += o.precision == MRQ_PREC_FP32 ? 1 : 2;
   mark(idx, MRQ_STAGE_QSTATS, st);
-  qstats(idx, ws.qd.p, ws.qr.p, nq, ws.qstat.p, st);
+  qstats(idx, ws.qd.p, ws.qr.p, nq, ws.qstat.p, st, ws.qcnt.p, ws.gtau.p, ws.work.p);
   // 3. probe
   mark(idx, MRQ_STAGE_PROBE, st);
   // the fused probe emits nprobe candidates per (column tile, half tile) of each row
@@ -2066,14 +2082,15 @@ void search_batch(mrq_index* idx, Workspace& ws, const float* q, int64_t nq, int
   if (fused) {
     const int nsl = ceil_div(tiles_ * nprobe, 32);
     const unsigned mg = ceil_div(nq, 8);
-    if (nsl <= 1) k_probe_merge<1><<<mg, 256, 0, st>>>(ws.ppart.p, nq, tiles_, nprobe, ws.plist.p);
-    else if (nsl <= 2) k_probe_merge<2><<<mg, 256, 0, st>>>(ws.ppart.p, nq, tiles_, nprobe, ws.plist.p);
-    else if (nsl <= 4) k_probe_merge<4><<<mg, 256, 0, st>>>(ws.ppart.p, nq, tiles_, nprobe, ws.plist.p);
-    else if (nsl <= 8) k_probe_merge<8><<<mg, 256, 0, st>>>(ws.ppart.p, nq, tiles_, nprobe, ws.plist.p);
-    else k_probe_merge<16><<<mg, 256, 0, st>>>(ws.ppart.p, nq, tiles_, nprobe, ws.plist.p);
-    MRQ_CHECK_LAUNCH();
-    k_probe_refine<<<ceil_div(nq * nprobe, 8), 256, 0, st>>>(ws.qd.p, idx->cent.p, ws.plist.p,
-                                                            nq * nprobe, nprobe, d, ws.pg.p);
+#define MRQ_MR(SLv)                                                                          \
+    k_probe_merge_refine<SLv><<<mg, 256, 0, st>>>(ws.ppart.p, nq, tiles_, nprobe, ws.qd.p, \
+                                                  idx->cent.p, d, ws.plist.p, ws.pg.p)
+    if (nsl <= 1) MRQ_MR(1);
+    else if (nsl <= 2) MRQ_MR(2);
+    else if (nsl <= 4) MRQ_MR(4);
+    else if (nsl <= 8) MRQ_MR(8);
+    else MRQ_MR(16);
+#undef MRQ_MR
     MRQ_CHECK_LAUNCH();
   } else {
     int P2 = 1;
@@ -2100,8 +2117,7 @@ void search_batch(mrq_index* idx, Workspace& ws, const float* q, int64_t nq, int
   }
   // 4. scan
   mark(idx, MRQ_STAGE_SCAN, st);
-  k_scan_init<<<ceil_div(nq, 256), 256, 0, st>>>(ws.qcnt.p, ws.gtau.p, nq, ws.work.p);
-  MRQ_CHECK_LAUNCH();
+  // (the survivor counts, running bounds and work counters were reset by k_qstats)
   ScanParams sp{};
   sp.qd = ws.qd.p; sp.qstat = ws.qstat.p; sp.plist = ws.plist.p; sp.pg = ws.pg.p;
   sp.cent = idx->cent.p; sp.loff = idx->loff.p; sp.ploff = idx->ploff.p; sp.codes = idx->codes.p;
@@ -2286,7 +2302,9 @@ void search_batch(mrq_index* idx, Workspace& ws, const float* q, int64_t nq, int
   MRQ_CHECK_LAUNCH();
   mark(idx, MRQ_NSTAGES, st);
   if (idx->prof_on) idx->prof_batches++;
-  idx->launches += 7;  // qstats, probe distances, select, refine, scan init, scan, finalize
+  // qstats, the probe's bf16 split (or fp32 distances), select + refine (one kernel in
+  // the fused probe), scan, the first finalize phase
+  idx->launches += fused ? 5 : 6;
 }
 
 size_t batch_scratch_bytes(const mrq_index* idx, int64_t nq, int k, int nprobe) {
