@@ -79,6 +79,7 @@ struct Workspace {
   DevBuf<float> qd, qr;    // projected queries
   DevBuf<float> qstat;     // nq x 4: |q_r|^2, sigma, |q_p|^2, unused
   DevBuf<__nv_bfloat16> qbf;  // nq x D bf16 hi/lo split queries (tensor-core projection)
+  DevBuf<__nv_bfloat16> qbf2;  // nq x d bf16 hi/lo split q_d' (tensor-core probe operand)
   DevBuf<float> gmat;      // nq x nlist probe distances
   DevBuf<unsigned long long> ppart;  // nq x tiles x nprobe fused probe candidates
   DevBuf<int32_t> plist;   // nq x nprobe probed list ids
@@ -253,14 +254,17 @@ void project_noalloc(mrq_index* idx, const float* q, int64_t nq, int precision, 
 int* tc_error_word();    // device word the tensor-core kernels set when a wait gives up
 int* tc_error_mirror();  // page-locked host int for reading it back asynchronously
 int tc_check_error();  // nonzero if a bounded wait in a tensor-core kernel gave up
+// probe_bf (optional, M x d bf16, twice with split3): the projection's epilogue also
+// writes the probe's split operand of q_d', so the probe can skip its split (presplit)
 void project_tc(const float* Q, const float* mu, const __nv_bfloat16* W2, int M, int D, int d,
-                bool split3, __nv_bfloat16* qbf, float* qd, float* qr, cudaStream_t st);
+                bool split3, __nv_bfloat16* qbf, float* qd, float* qr, cudaStream_t st,
+                __nv_bfloat16* probe_bf = nullptr);
 void probe_tc(const float* qd, const float* qstat, const __nv_bfloat16* C2, const float* cn2,
               int M, int nlist, int d, bool split3, __nv_bfloat16* qbf, float* gmat,
-              cudaStream_t st);
+              cudaStream_t st, bool presplit = false);
 int probe_tc_topk(const float* qd, const float* qstat, const __nv_bfloat16* C2, const float* cn2,
                   int M, int nlist, int d, bool split3, int nsel, __nv_bfloat16* qbf,
-                  unsigned long long* part, cudaStream_t st);
+                  unsigned long long* part, cudaStream_t st, bool presplit = false);
 
 // ---- search (search.cu) ----
 // One batch of the query path on stream st with scratch ws (one Workspace per
@@ -269,7 +273,7 @@ void search_batch(mrq_index* idx, Workspace& ws, const float* q_dev, int64_t nq,
                   int nprobe, const mrq_search_opts& o, int64_t* ids_dev, float* dists_dev,
                   int64_t* stats_dev, cudaStream_t st);
 void project_batch(mrq_index* idx, Workspace& ws, const float* q_dev, int64_t nq, int precision,
-                   float* qd, float* qr, cudaStream_t st);
+                   float* qd, float* qr, cudaStream_t st, __nv_bfloat16* probe_bf = nullptr);
 // the scan configuration a search uses; a ScopedScanConfig forces one on this thread
 ScanConfig scan_config(mrq_index* idx, const mrq_search_opts& o, int64_t nq, int k, int nprobe);
 int scan_kclass(int k);

@@ -162,6 +162,8 @@ struct TcArgs {
   unsigned long long* part;  // epi 2: per (row, column tile) the nsel smallest (key << 32 | col)
   int nsel;
   int* err;
+  __nv_bfloat16* pbf;  // epi 0, optional: the first `split` columns again, split into bf16
+  int pbf_two;         // hi (rows 0..M-1) and, when set, lo (rows M..2M-1) for the probe
 };
 
 constexpr int TC_PSEL = 16;  // largest nprobe selected inside the probe epilogue
@@ -265,6 +267,29 @@ __global__ void __launch_bounds__(256, 1)
       const int col0 = n0 + c;
       if (row >= P.M || col0 >= P.N) continue;
       if (P.epi == 0) {
+        if (P.pbf && col0 + 32 <= P.split) {
+          // the probe's bf16 operand (hi, and lo = x - hi) of these 32 q_d' coordinates,
+          // as the bf16 split kernel would compute it from the stored values
+          uint32_t hw[16], lw[16];
+#pragma unroll
+          for (int t = 0; t < 16; ++t) {
+            const float x0 = __uint_as_float(r[2 * t]), x1 = __uint_as_float(r[2 * t + 1]);
+            const __nv_bfloat162 h = __floats2bfloat162_rn(x0, x1);
+            const float2 hf = __bfloat1622float2(h);
+            const __nv_bfloat162 l = __floats2bfloat162_rn(x0 - hf.x, x1 - hf.y);
+            hw[t] = *reinterpret_cast<const uint32_t*>(&h);
+            lw[t] = *reinterpret_cast<const uint32_t*>(&l);
+          }
+          uint4* dh = reinterpret_cast<uint4*>(P.pbf + (int64_t)row * P.split + col0);
+#pragma unroll
+          for (int t = 0; t < 4; ++t) dh[t] = make_uint4(hw[4 * t], hw[4 * t + 1], hw[4 * t + 2], hw[4 * t + 3]);
+          if (P.pbf_two) {
+            uint4* dl = reinterpret_cast<uint4*>(P.pbf + ((int64_t)P.M + row) * P.split + col0);
+#pragma unroll
+            for (int t = 0; t < 4; ++t)
+              dl[t] = make_uint4(lw[4 * t], lw[4 * t + 1], lw[4 * t + 2], lw[4 * t + 3]);
+          }
+        }
         const bool whole = col0 + 32 <= P.N && (col0 + 32 <= P.split || col0 >= P.split);
         if (whole) {
           float* dst = col0 < P.split ? P.out0 + (int64_t)row * P.ld0 + col0
@@ -563,7 +588,8 @@ int tc_check_error() {
 }
 
 void project_tc(const float* Q, const float* mu, const __nv_bfloat16* W2, int M, int D, int d,
-                bool split3, __nv_bfloat16* qbf, float* qd, float* qr, cudaStream_t st) {
+                bool split3, __nv_bfloat16* qbf, float* qd, float* qr, cudaStream_t st,
+                __nv_bfloat16* probe_bf) {
   split_bf16(Q, M, D, D, mu, split3, qbf, st);
   TcArgs a{};
   a.M = M; a.N = D; a.K = D;
@@ -571,13 +597,15 @@ void project_tc(const float* Q, const float* mu, const __nv_bfloat16* W2, int M,
   a.a_lo = M; a.b_lo = D;
   a.epi = 0;
   a.out0 = qd; a.ld0 = d; a.out1 = qr; a.ld1 = D - d; a.split = d;
+  a.pbf = (d % 32 == 0) ? probe_bf : nullptr;
+  a.pbf_two = split3 ? 1 : 0;
   run_tc(qbf, W2, a, st);
 }
 
 void probe_tc(const float* qd, const float* qstat, const __nv_bfloat16* C2, const float* cn2,
               int M, int nlist, int d, bool split3, __nv_bfloat16* qbf, float* gmat,
-              cudaStream_t st) {
-  split_bf16(qd, M, d, d, nullptr, split3, qbf, st);
+              cudaStream_t st, bool presplit) {
+  if (!presplit) split_bf16(qd, M, d, d, nullptr, split3, qbf, st);
   TcArgs a{};
   a.M = M; a.N = nlist; a.K = d;
   a.phases = split3 ? 3 : 1;
@@ -593,8 +621,8 @@ void probe_tc(const float* qd, const float* qstat, const __nv_bfloat16* C2, cons
 // every query row and 256-column tile, the nsel smallest (fkey(g) << 32 | list).
 int probe_tc_topk(const float* qd, const float* qstat, const __nv_bfloat16* C2, const float* cn2,
                   int M, int nlist, int d, bool split3, int nsel, __nv_bfloat16* qbf,
-                  unsigned long long* part, cudaStream_t st) {
-  split_bf16(qd, M, d, d, nullptr, split3, qbf, st);
+                  unsigned long long* part, cudaStream_t st, bool presplit) {
+  if (!presplit) split_bf16(qd, M, d, d, nullptr, split3, qbf, st);
   TcArgs a{};
   a.M = M; a.N = nlist; a.K = d;
   a.phases = split3 ? 3 : 1;

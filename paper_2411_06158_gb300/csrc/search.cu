@@ -1986,7 +1986,7 @@ static void mark(mrq_index* idx, int s, cudaStream_t st) {
 }
 
 void project_batch(mrq_index* idx, Workspace& ws, const float* q, int64_t nq, int precision,
-                   float* qd, float* qr, cudaStream_t st) {
+                   float* qd, float* qr, cudaStream_t st, __nv_bfloat16* probe_bf) {
   const int D = idx->D, d = idx->d, r = D - d;
   if (precision == MRQ_PREC_FP32) {
     gemm_nt_f32(q, D, idx->mu.p, idx->W.p, D, (int)nq, D, D, qd, d, qr, r, d, st);
@@ -1994,7 +1994,7 @@ void project_batch(mrq_index* idx, Workspace& ws, const float* q, int64_t nq, in
     MRQ_REQUIRE(tc_available(), "tensor-core projection needs an sm_103 device");
     ws.qbf.reserve((size_t)nq * D * 2);
     project_tc(q, idx->mu.p, idx->W2.p, (int)nq, D, d, precision == MRQ_PREC_BF16X3,
-               ws.qbf.p, qd, qr, st);
+               ws.qbf.p, qd, qr, st, probe_bf);
   }
 }
 
@@ -2052,9 +2052,12 @@ void search_batch(mrq_index* idx, Workspace& ws, const float* q, int64_t nq, int
   ws.s2a.reserve(sc);
   ws.s2b.reserve(sc);
 
-  // 1-2. projection and query statistics
+  // 1-2. projection and query statistics; a tensor-core probe takes its bf16 operand
+  // of q_d' straight from the projection's epilogue
+  const bool tc_probe = o.precision != MRQ_PREC_FP32 && d >= 64;
+  if (tc_probe) ws.qbf2.reserve((size_t)nq * d * 2);
   mark(idx, MRQ_STAGE_PROJECT, st);
-  project_batch(idx, ws, q, nq, o.precision, ws.qd.p, ws.qr.p, st);
+  project_batch(idx, ws, q, nq, o.precision, ws.qd.p, ws.qr.p, st, tc_probe ? ws.qbf2.p : nullptr);
   idx->launches += o.precision == MRQ_PREC_FP32 ? 1 : 2;
   mark(idx, MRQ_STAGE_QSTATS, st);
   qstats(idx, ws.qd.p, ws.qr.p, nq, ws.qstat.p, st, ws.qcnt.p, ws.gtau.p, ws.work.p);
@@ -2068,12 +2071,12 @@ void search_batch(mrq_index* idx, Workspace& ws, const float* q, int64_t nq, int
     ws.qbf.reserve((size_t)nq * D * 2);
     ws.ppart.reserve((size_t)nq * tiles_ * nprobe);
     probe_tc_topk(ws.qd.p, ws.qstat.p, idx->cent2.p, idx->cent_n2.p, (int)nq, nlist, d,
-                  o.precision == MRQ_PREC_BF16X3, nprobe, ws.qbf.p, ws.ppart.p, st);
+                  o.precision == MRQ_PREC_BF16X3, nprobe, ws.qbf2.p, ws.ppart.p, st, true);
     idx->launches += 1;
   } else if (o.precision != MRQ_PREC_FP32 && d >= 64) {
     ws.qbf.reserve((size_t)nq * D * 2);
     probe_tc(ws.qd.p, ws.qstat.p, idx->cent2.p, idx->cent_n2.p, (int)nq, nlist, d,
-             o.precision == MRQ_PREC_BF16X3, ws.qbf.p, ws.gmat.p, st);
+             o.precision == MRQ_PREC_BF16X3, ws.qbf2.p, ws.gmat.p, st, true);
     idx->launches += 1;
   } else {
     sqdist_f32(ws.qd.p, d, idx->cent.p, d, (int)nq, nlist, d, ws.gmat.p, nlist, st);
@@ -2302,9 +2305,10 @@ void search_batch(mrq_index* idx, Workspace& ws, const float* q, int64_t nq, int
   MRQ_CHECK_LAUNCH();
   mark(idx, MRQ_NSTAGES, st);
   if (idx->prof_on) idx->prof_batches++;
-  // qstats, the probe's bf16 split (or fp32 distances), select + refine (one kernel in
-  // the fused probe), scan, the first finalize phase
-  idx->launches += fused ? 5 : 6;
+  // qstats, fp32 probe distances (the tensor-core probe's operand comes from the
+  // projection), select + refine (one kernel in the fused probe), scan, the first
+  // finalize phase
+  idx->launches += fused ? 4 : tc_probe ? 5 : 6;
 }
 
 size_t batch_scratch_bytes(const mrq_index* idx, int64_t nq, int k, int nprobe) {
