@@ -694,6 +694,7 @@ void project_noalloc(mrq_index* idx, const float* q, int64_t nq, int precision, 
                          " (nq * D <= " + std::to_string(MRQ_PROJECT_NOALLOC_MAX_BYTES / (split3 ? 4 : 2)) +
                          " at this precision); split the batch");
   MRQ_REQUIRE(tc_available(), "tensor-core projection needs an sm_103 device");
+  MRQ_REQUIRE(D % 8 == 0, "tensor-core precisions need D to be a multiple of 8 (16-byte bf16 rows)");
   unsigned char* base = project_scratch();
   int* err = reinterpret_cast<int*>(base);
   __nv_bfloat16* qbf = reinterpret_cast<__nv_bfloat16*>(base + 256);

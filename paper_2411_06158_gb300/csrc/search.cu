@@ -1992,6 +1992,7 @@ void project_batch(mrq_index* idx, Workspace& ws, const float* q, int64_t nq, in
     gemm_nt_f32(q, D, idx->mu.p, idx->W.p, D, (int)nq, D, D, qd, d, qr, r, d, st);
   } else {
     MRQ_REQUIRE(tc_available(), "tensor-core projection needs an sm_103 device");
+    MRQ_REQUIRE(D % 8 == 0, "tensor-core precisions need D to be a multiple of 8 (16-byte bf16 rows)");
     ws.qbf.reserve((size_t)nq * D * 2);
     project_tc(q, idx->mu.p, idx->W2.p, (int)nq, D, d, precision == MRQ_PREC_BF16X3,
                ws.qbf.p, qd, qr, st, probe_bf);

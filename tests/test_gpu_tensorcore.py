@@ -78,3 +78,16 @@ def test_pinned_host_queries_match_device_queries(tmp_path, graph):
             mrq.mrq_search(gi, qh, 10, 6, o, out=(ih, dh))
             assert torch.equal(ih, ref_i.cpu())
             assert torch.equal(dh, ref_d.cpu())
+
+
+def test_tensor_core_precision_needs_whole_bf16_rows():
+    # bf16 rows of D elements must be 16-byte multiples for the TMA loads: D = 100 is
+    # rejected with a clear error before any tensor-core launch; fp32 still works
+    w = datagen.workload("small", D=100, d=32, n=3000, nlist=8, n_comp=16, n_query=20)
+    base, queries = datagen.base_and_queries(w)
+    gi = mrq.mrq_build(base, 32, 1, 8, mrq.mrq_build_opts(seed=2, kmeans_iters=2))
+    ids, _ = mrq.mrq_search(gi, queries, 5, 2, mrq.mrq_search_opts())
+    assert ids.shape == (20, 5)
+    with pytest.raises(mrq.MRQError) as e:
+        mrq.mrq_search(gi, queries, 5, 2, mrq.mrq_search_opts(precision=mrq.PREC_BF16))
+    assert e.value.code == mrq.MRQ_EINVAL and "multiple of 8" in str(e.value)
