@@ -46,6 +46,7 @@ def parse_args(argv=None):
     p.add_argument("--D", type=int, default=None, help="override the dimension (scan roofline runs)")
     p.add_argument("--bits", type=int, default=None)
     p.add_argument("--nlist", type=int, default=None)
+    p.add_argument("--k", type=int, default=None, help="override k")
     p.add_argument("--recall", type=float, default=0.95)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-queries", type=int, default=100)
@@ -73,7 +74,7 @@ def workload_of(args):
     import datagen
     over = {}
     for key, val in (("n", args.n), ("n_query", args.nq), ("d", args.d), ("bits", args.bits),
-                     ("nlist", args.nlist), ("D", args.D)):
+                     ("nlist", args.nlist), ("D", args.D), ("k", args.k)):
         if val is not None:
             over[key] = val
     return datagen.workload(args.workload, **over)
@@ -455,12 +456,21 @@ def main(argv=None):
     w = workload_of(args)
     import datagen
     t0 = time.time()
-    base, queries = datagen.base_and_queries(w)
+    zipf = "zipf" in w.name
+    if zipf:
+        # Deep-like batching form: every list generated around its own centre with Zipf(1.1)
+        # sizes; the centres are passed as the IVF centroids and k-means is skipped
+        base, centres, _ = datagen.zipf_clustered(w, w.n, w.nlist, s=1.1)
+        queries = datagen.sample(datagen.make_mixture(w), w.n_query, w.seed("queries"))
+        bopts = mrq.mrq_build_opts(seed=w.seed("method"), kmeans_iters=0, init_centroids=centres)
+    else:
+        base, queries = datagen.base_and_queries(w)
+        bopts = mrq.mrq_build_opts(seed=w.seed("method"))
     t_gen = time.time() - t0
     base_t = torch.from_numpy(base).to(dev)
     q_t = torch.from_numpy(queries).to(dev)
     t0 = time.time()
-    idx = mrq.mrq_build(base_t, w.d, w.bits, w.nlist, mrq.mrq_build_opts(seed=w.seed("method")))
+    idx = mrq.mrq_build(base_t, w.d, w.bits, w.nlist, bopts)
     torch.cuda.synchronize()
     t_build = time.time() - t0
     truth = ground_truth(base_t, q_t, w.k)

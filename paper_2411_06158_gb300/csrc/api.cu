@@ -182,10 +182,22 @@ int mrq_search(mrq_index* idx, const float* queries, int64_t nq, int k, int npro
     MRQ_REQUIRE(odev == on_device(dists), "ids and dists must both be host or both be device memory");
     const int D = idx->D;
     const int64_t cap = std::max<int64_t>(idx->cap_by_nprobe[nprobe], 1);
-    // batch size: survivor scratch (6 arrays x 4 B x cap per query) within ~6 GB,
-    // probe matrix within ~1 GB
+    // batch size: survivor scratch (6 arrays x 4 B x cap per query) within the budget
+    // below, probe matrix within ~1 GB
     int64_t qb = std::min<int64_t>(nq, 16384);
-    qb = std::min<int64_t>(qb, std::max<int64_t>(1, (int64_t)6e9 / (24 * cap)));
+    // the survivor scratch is sized for the worst case (every candidate of the nprobe
+    // largest lists); give it up to a quarter of the free device memory (at least 6 GB,
+    // at most 64 GB) so that indexes with very uneven lists still run large batches
+    size_t free_b = 0, total_b = 0;
+    if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) {
+      cudaGetLastError();
+      free_b = 0;
+    }
+    int64_t budget =
+        std::min<int64_t>((int64_t)64 << 30, std::max<int64_t>((int64_t)6e9, (int64_t)(free_b / 4)));
+    // scratch this index already holds counts as available (the batch size stays put)
+    budget = std::max<int64_t>(budget, (int64_t)idx->ws.spos.n * 24);
+    qb = std::min<int64_t>(qb, std::max<int64_t>(1, budget / (24 * cap)));
     qb = std::min<int64_t>(qb, std::max<int64_t>(1, (int64_t)1e9 / (4 * (int64_t)idx->nlist)));
     auto& ws = idx->ws;
     ws.stats.reserve((size_t)nq * 3);
