@@ -446,7 +446,7 @@ __global__ void k_split_bf16(const float* __restrict__ X, int M, int K, int ld,
   __nv_bfloat16* lo = out + ((int64_t)M + m) * K;
   if (vec) {
     const int k4 = K >> 2;
-#pragma unroll 2
+#pragma unroll 8
     for (int c = lane; c < k4; c += 32) {
       float4 v = __ldg(reinterpret_cast<const float4*>(x) + c);
       if (shift) {
