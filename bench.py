@@ -140,12 +140,12 @@ class ClockSampler:
 
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of kernels
 # captured with ncu at the calibrated GIST-like configuration; see
-# profiles/dram_gist-1M-d960_batched-bf16_nprobe3.md.  Used only when the timed
+# profiles/dram_gist-1M-d960_tuned-bf16_nprobe3.md.  Used only when the timed
 # run matches that configuration exactly.
 NCU_TRAFFIC = {
-    ("k_fin_exact_r", "gist-like-1M-d960", "tuned_bf16_q4", 3, 1.0, 1.0): 1346369280,
-    ("k_fin_stage2", "gist-like-1M-d960", "tuned_bf16_q4", 3, 1.0, 1.0): 529527040,
-    ("k_scan_q", "gist-like-1M-d960", "tuned_bf16_q4", 3, 1.0, 1.0): 41773824,
+    ("k_fin_exact_r", "gist-like-1M-d960", "tuned_bf16_q4", 3, 1.0, 1.0): 1346259456,
+    ("k_fin_stage2", "gist-like-1M-d960", "tuned_bf16_q4", 3, 1.0, 1.0): 529399040,
+    ("k_scan_q", "gist-like-1M-d960", "tuned_bf16_q4", 3, 1.0, 1.0): 41613824,
 }
 
 
