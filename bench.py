@@ -606,8 +606,8 @@ def main(argv=None):
     value = whole_job_qps(w.n_query, world, ms_step)
 
     # clocks during a second timed pass of the best form
-    clk = ClockSampler(local, os.path.join(ROOT, "gpurun_out", f"clocks_rank{rank}.csv")) \
-        if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else ClockSampler(local, "/tmp/mrq_clocks.csv")
+    import tempfile
+    clk = ClockSampler(local, os.path.join(tempfile.gettempdir(), f"mrq_clocks_rank{rank}.csv"))
     # about 2.5 s of steps so that the 200 ms samples see the load
     timed(forms[best], B["nprobe"],
           max(args.steps, int(1000 * args.clock_seconds / max(B["ms_per_step"], 0.05))), 1, False)

@@ -278,7 +278,10 @@ int mrq_server_reset_stats(mrq_server* server);
 /* Finish queued and running batches, stop the scheduler, free the server. */
 int mrq_server_stop(mrq_server* server);
 
-/* Save / load the index file (format version 1, documented in the design doc). */
+/* Save / load the index file: magic "MRQINDEX", version 1, header (n, D, d, bits,
+ * nlist), then tagged sections MU__, LAM_, W___, CENT, LOFF, IDS_, CODE (one u8 level
+ * per dimension), FADD, FRES, FERR, XD__, XR__, XN2_ (list-major, unpadded).  A
+ * malformed or other-version file gives MRQ_EFORMAT, an unreadable path MRQ_EIO. */
 int mrq_save(const mrq_index* index, const char* path);
 int mrq_load(const char* path, mrq_index** out);
 
