@@ -9,9 +9,10 @@ Format (little-endian), version 1:
     i64 n; i32 D; i32 d; i32 bits; i32 nlist;
     n_sections x { char[4] tag; u32 dtype; u64 count; count elements; zero pad to 8 B }
 dtype: 1 = f32, 2 = f64, 3 = i64, 4 = u8.
-Sections (all required): MU__ f32[D], LAM_ f32[D], W___ f32[D*D] (row-major),
+Sections (required): MU__ f32[D], LAM_ f32[D], W___ f32[D*D] (row-major),
 CENT f32[nlist*d], LOFF i64[nlist+1], IDS_ i64[n], CODE u8[n*d] (unsigned level
-per dimension), FADD/FRES/FERR f32[n], XD__ f32[n*d], XR__ f32[n*(D-d)], XN2_ f32[n].
+per dimension), FADD/FRES/FERR f32[n], XD__ f32[n*d], XR__ f32[n*(D-d)], XN2_ f32[n];
+optional, B > 1: FRE1/FER1 f32[n], the sign plane's factors (1 bit + refinement).
 Vector arrays are in list-major order (list j holds rows LOFF[j]..LOFF[j+1]-1).
 """
 from __future__ import annotations
@@ -36,7 +37,8 @@ def _sections(idx):
         (b"CODE", np.ascontiguousarray(idx.u, dtype=np.uint8).ravel()),
         (b"FADD", f32(idx.f_add)), (b"FRES", f32(idx.f_rescale)), (b"FERR", f32(idx.f_err)),
         (b"XD__", f32(idx.xd)), (b"XR__", f32(idx.xr)), (b"XN2_", f32(idx.xnorm2)),
-    ]
+    ] + ([(b"FRE1", f32(idx.f_rescale1)), (b"FER1", f32(idx.f_err1))]
+         if getattr(idx, "f_rescale1", None) is not None else [])
 
 
 def write_index(idx, path: str) -> None:

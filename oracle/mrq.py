@@ -163,6 +163,10 @@ class OracleIndex:
     f_err: np.ndarray       # n, 2 |x_d - c| sqrt((1 - a^2)/a^2)/sqrt(d - 1), a = <v,o'>/|v|
     ip_vo: np.ndarray       # n, <v, o'>
     resid_norm: np.ndarray  # n, |x_d - c|
+    # 1-bit factors of the sign plane (B > 1 only; None for B = 1): the factors the
+    # sign code v1 = 2*(u >> (B-1)) - 1 -- exactly the 1-bit code of o' -- would have
+    f_rescale1: np.ndarray | None = None
+    f_err1: np.ndarray | None = None
 
     @property
     def n(self) -> int:
@@ -175,10 +179,12 @@ class OracleIndex:
         """The index as the file format stores it: every real array rounded to
         float32 (then held in float64 for arithmetic)."""
         r = lambda a: np.asarray(a, dtype=np.float32).astype(np.float64)
+        r1 = lambda a: None if a is None else r(a)
         return dataclasses.replace(
             self, mu=r(self.mu), lam=r(self.lam), W=r(self.W), centroids=r(self.centroids),
             xd=r(self.xd), xr=r(self.xr), xnorm2=r(self.xnorm2), f_add=r(self.f_add),
-            f_rescale=r(self.f_rescale), f_err=r(self.f_err))
+            f_rescale=r(self.f_rescale), f_err=r(self.f_err),
+            f_rescale1=r1(self.f_rescale1), f_err1=r1(self.f_err1))
 
 
 def factors(resid_norm: np.ndarray, xr2: np.ndarray, v: np.ndarray, o: np.ndarray, d: int):
@@ -232,6 +238,10 @@ def build_index(S, d: int, bits: int, nlist: int, G: np.ndarray, *,
     u, v = encode(o, bits)                           # quantize with P_r
     xr2 = np.sum(xr * xr, axis=1)
     f_add, f_rescale, f_err, ip = factors(rn, xr2, v, o, d)
+    fr1 = fe1 = None
+    if bits > 1:                                     # factors of the sign plane (refinement)
+        v1 = 2.0 * (u >> (bits - 1)).astype(np.float64) - 1.0
+        _, fr1, fe1, _ = factors(rn, xr2, v1, o, d)
     order = np.lexsort((np.arange(n), assign))      # list-major, ids ascending inside a list
     counts = np.bincount(assign, minlength=nlist)
     offs = np.zeros(nlist + 1, dtype=np.int64)
@@ -242,7 +252,9 @@ def build_index(S, d: int, bits: int, nlist: int, G: np.ndarray, *,
                        centroids=C_rot, list_offsets=offs, ids=order.astype(np.int64),
                        xd=xd_rot[order], xr=xr[order], xnorm2=xn2[order], u=u[order], v=v[order],
                        f_add=f_add[order], f_rescale=f_rescale[order], f_err=f_err[order],
-                       ip_vo=ip[order], resid_norm=rn[order])
+                       ip_vo=ip[order], resid_norm=rn[order],
+                       f_rescale1=None if fr1 is None else fr1[order],
+                       f_err1=None if fe1 is None else fe1[order])
 
 
 # -------------------------------------------------------------------------- search
@@ -288,7 +300,7 @@ def quantize_query(qprime: np.ndarray, qbits: int):
 
 
 def estimate_list(idx: OracleIndex, j: int, qd, g_j, qr2, sigma, eps0, m,
-                  qbits: int = 0):
+                  qbits: int = 0, sign_plane: bool = False):
     """Stage (1) for every member of list j (Eq. 4 and the bounds of Algorithm 2).
 
     ip = <v, q'> with q' = (q_d' - c_j')/sqrt(g_j), exactly (qbits = 0) or through
@@ -299,23 +311,35 @@ def estimate_list(idx: OracleIndex, j: int, qd, g_j, qr2, sigma, eps0, m,
     eps_b = eps0 * sqrt(g_j) * f_err  (Eq. 5),  eps_r = m * sigma  (Chebyshev, Eq. 6)
     LB = dis' - eps_b - eps_r, UB = dis' + eps_b + eps_r.
     Returns dict with ip, dis, lb, ub (and the integer dot when quantized).
+
+    sign_plane: the first level of the 1-bit + refinement scan of a B > 1 code: the
+    same estimate from the sign plane alone (u1 = u >> (B-1), v1 = 2 u1 - 1, the
+    1-bit code of o') with its own factors f_rescale1, f_err1.
     """
     sl = idx.list_slice(j)
     sg = math.sqrt(g_j)
     qprime = (qd - idx.centroids[j]) / sg if g_j > 0 else np.zeros(idx.d)
     out = {}
-    if qbits > 0:
-        qbar, vl, delta = quantize_query(qprime, qbits)
+    if sign_plane:
+        u = (idx.u[sl] >> (idx.bits - 1)).astype(np.int64)
+        top = 1
+        vcode = 2.0 * u - 1.0
+        fres, ferr = idx.f_rescale1[sl], idx.f_err1[sl]
+    else:
         u = idx.u[sl].astype(np.int64)
         top = (1 << idx.bits) - 1
+        vcode = idx.v[sl]
+        fres, ferr = idx.f_rescale[sl], idx.f_err[sl]
+    if qbits > 0:
+        qbar, vl, delta = quantize_query(qprime, qbits)
         dot = u @ qbar
         su = u.sum(axis=1)
         ip = delta * (2.0 * dot - top * float(qbar.sum())) + vl * (2.0 * su - idx.d * top)
         out.update(int_dot=dot, qbar=qbar, vl=vl, delta=delta)
     else:
-        ip = idx.v[sl] @ qprime
-    dis = idx.f_add[sl] + g_j + qr2 + idx.f_rescale[sl] * sg * ip
-    eps = eps0 * sg * idx.f_err[sl] + m * sigma
+        ip = vcode @ qprime
+    dis = idx.f_add[sl] + g_j + qr2 + fres * sg * ip
+    eps = eps0 * sg * ferr + m * sigma
     out.update(ip=ip, dis=dis, lb=dis - eps, ub=dis + eps, scale=idx.f_add[sl] + g_j + qr2)
     return out
 
@@ -349,7 +373,8 @@ class SearchResult:
 
 
 def search_contract(idx: OracleIndex, Q, k: int, nprobe: int, *, eps0: float = 1.9,
-                    m: float = 4.0, mode: int = MODE_MRQ_PLUS, qbits: int = 0) -> SearchResult:
+                    m: float = 4.0, mode: int = MODE_MRQ_PLUS, qbits: int = 0,
+                    refine: bool = False) -> SearchResult:
     """Algorithm 2 under the order-independent threshold contract.
 
     The paper's loop prunes against the running k-th exact distance, which
@@ -360,6 +385,10 @@ def search_contract(idx: OracleIndex, Q, k: int, nprobe: int, *, eps0: float = 1
       LB2/UB2 = dis_o' -+ m*sigma, tau_B = min(tau_A, k-th smallest UB2 over S1),
       S2 = {i in S1 : LB2 <= tau_B};  MRQ (no stage 2): S2 = S1.
     The answer is the k smallest exact |x_p - q_p|^2 over S2, ties by id.
+    refine (B > 1: 1 bit + refinement): stage 1 runs in two levels, the sign plane
+    first (LB1a/UB1a with the 1-bit factors), then the full code on its survivors:
+      tau_A' = k-th smallest UB1a,  S1a = {LB1a <= tau_A'},
+      tau_A = min(tau_A', k-th smallest UB1b over S1a),  S1 = {i in S1a : LB1b <= tau_A}.
     Whenever every bound holds, the answer equals the exact top-k of the probed
     lists (and so does the paper's sequential loop).
 
@@ -386,19 +415,32 @@ def search_contract(idx: OracleIndex, Q, k: int, nprobe: int, *, eps0: float = 1
         mg = math.inf
         if nprobe < idx.nlist:
             mg = (gs[nprobe] - gs[nprobe - 1]) / max(gs[nprobe], 1e-30)
-        pos, lb, ub, sc = [], [], [], []
+        two = refine and idx.bits > 1
+        pos, lb, ub, sc, la, ua, sca = [], [], [], [], [], [], []
         for j in lists:
             e = estimate_list(idx, int(j), qd, float(g[j]), qr2_all[qi], sig_all[qi], eps0, m, qbits)
             sl = idx.list_slice(int(j))
             pos.append(np.arange(sl.start, sl.stop))
             lb.append(e["lb"]); ub.append(e["ub"]); sc.append(np.maximum(np.abs(e["dis"]), e["scale"]))
+            if two:
+                e1 = estimate_list(idx, int(j), qd, float(g[j]), qr2_all[qi], sig_all[qi], eps0, m,
+                                   qbits, sign_plane=True)
+                la.append(e1["lb"]); ua.append(e1["ub"])
+                sca.append(np.maximum(np.abs(e1["dis"]), e1["scale"]))
         pos = np.concatenate(pos) if pos else np.zeros(0, dtype=np.int64)
         lb = np.concatenate(lb) if lb else np.zeros(0)
         ub = np.concatenate(ub) if ub else np.zeros(0)
         sc = np.concatenate(sc) if sc else np.zeros(0)
         n_cand[qi] = pos.size
-        tau_a = _kth(ub, k)
-        s1 = lb <= tau_a                                    # stage-1 survivors
+        if two:                                             # 1 bit + refinement
+            la, ua, sca = np.concatenate(la), np.concatenate(ua), np.concatenate(sca)
+            tau_a1 = _kth(ua, k)
+            s1a = la <= tau_a1
+            tau_a = min(tau_a1, _kth(ub[s1a], k)) if s1a.any() else tau_a1
+            s1 = s1a & (lb <= tau_a)                        # stage-1 survivors
+        else:
+            tau_a = _kth(ub, k)
+            s1 = lb <= tau_a                                # stage-1 survivors
         # stage-2 quantities (Eq. 7) of every candidate, used on S1 only
         diso = idx.xnorm2[pos] + qp2_all[qi] - 2.0 * (idx.xd[pos] @ qd)
         lb2 = diso - m * sig_all[qi]
@@ -434,7 +476,16 @@ def search_contract(idx: OracleIndex, Q, k: int, nprobe: int, *, eps0: float = 1
         in_ans = np.isin(idx.ids[pos], ids[qi, :min(k, p2.size)])
         near = in_ans | (ex_all <= dk * (1 + 1e-6))
         rel1 = near | ((mode == MODE_MRQ_PLUS) & (ub2 <= kth_ub2 * (1 + 1e-6)))
-        if pos.size and math.isfinite(tau_a) and rel1.any():
+        if two:
+            # the sign-plane level: its test of an answer-relevant candidate, and the
+            # candidates whose upper bounds set tau_A' or tau_A
+            rel1a = rel1 | (ua <= tau_a1 * (1 + 1e-6)) | (ub <= tau_a * (1 + 1e-6))
+            if pos.size and math.isfinite(tau_a1) and rel1a.any():
+                mg = min(mg, _decision_margin(la, ua, sca, tau_a1, k, rel1a))
+            rel1 = rel1 & s1a
+            if rel1.any() and math.isfinite(tau_a):
+                mg = min(mg, _decision_margin(lb[s1a], ub[s1a], sc[s1a], tau_a, k, rel1[s1a]))
+        elif pos.size and math.isfinite(tau_a) and rel1.any():
             mg = min(mg, _decision_margin(lb, ub, sc, tau_a, k, rel1))
         rel2 = near & s1
         if mode == MODE_MRQ_PLUS and math.isfinite(tau_b) and rel2.any():

@@ -123,3 +123,31 @@ def test_quantized_inner_product_offset_term_wrong(monkeypatch):
         return qbar, -lo, delta                             # sign of v_l flipped
     monkeypatch.setattr(mrq, "quantize_query", wrong)
     _fails(pins.test_quantize_query_golden_and_grid_identity)
+
+
+def test_sign_plane_with_full_code_factors(monkeypatch):
+    orig = mrq.build_index
+
+    def wrong(*a, **k):
+        idx = orig(*a, **k)
+        if idx.f_rescale1 is not None:                     # stage 1a rescaled like the B-bit code
+            idx.f_rescale1 = idx.f_rescale.copy()
+        return idx
+    monkeypatch.setattr(mrq, "build_index", wrong)
+    _fails(pins.test_sign_plane_is_the_one_bit_code, pins.refine_pair.__wrapped__())
+
+
+def test_sign_plane_from_lowest_plane(monkeypatch):
+    orig = mrq.estimate_list
+
+    def wrong(idx, j, *a, sign_plane=False, **k):
+        if not sign_plane:
+            return orig(idx, j, *a, **k)
+        saved = idx.u
+        idx.u = (saved & 1) << (idx.bits - 1)              # the least significant plane
+        try:
+            return orig(idx, j, *a, sign_plane=True, **k)
+        finally:
+            idx.u = saved
+    monkeypatch.setattr(mrq, "estimate_list", wrong)
+    _fails(pins.test_sign_plane_is_the_one_bit_code, pins.refine_pair.__wrapped__())

@@ -390,3 +390,95 @@ def test_contract_thresholds_by_definition(small_workload, small_oracle_index):
         lb, ub = np.concatenate(lb), np.concatenate(ub)
         tau = np.sort(ub)[w.k - 1]
         assert r.n_s1[i] == int(np.sum(lb <= tau)) == r.n_s2[i]
+
+
+# ------------------------------------------------- 1 bit + refinement (stage 1a/1b)
+
+@pytest.fixture(scope="module")
+def refine_pair():
+    """The same data, rotation and IVF encoded with 1 and with 3 bits."""
+    w = datagen.workload("small", n=8000, n_comp=24, nlist=24, n_query=60)
+    base, queries = datagen.base_and_queries(w)
+    G = datagen.rotation_gaussian(w.d, 11)
+    init = datagen.kmeans_init_indices(w.n, w.nlist, 12)
+    one = mrq.build_index(base, w.d, 1, w.nlist, G, init_idx=init, kmeans_iters=6)
+    three = mrq.build_index(base, w.d, 3, w.nlist, G, init_idx=init, kmeans_iters=6)
+    return w, base, queries, one, three
+
+
+def test_sign_plane_is_the_one_bit_code(refine_pair):
+    """Stage 1a of a B-bit code is the 1-bit method: its top plane equals the code a
+    1-bit build writes for the same o', and its sign-plane estimate and bounds (with
+    the 1-bit factors) equal that build's estimate and bounds, float and quantized."""
+    w, base, queries, one, three = refine_pair
+    assert one.f_rescale1 is None and three.f_rescale1 is not None
+    np.testing.assert_array_equal(three.ids, one.ids)
+    np.testing.assert_array_equal(three.u >> 2, one.u)
+    np.testing.assert_allclose(three.f_rescale1, one.f_rescale, rtol=1e-12)
+    np.testing.assert_allclose(three.f_err1, one.f_err, rtol=1e-12)
+    assert not np.allclose(three.f_rescale1, three.f_rescale, rtol=1e-3)
+    qd, qr, qr2, sigma, qp2 = mrq.project_queries(three, queries[:8])
+    for i in range(8):
+        lists, g = mrq.probe(three, qd[i], 3)
+        for j in lists:
+            for qb in (0, 4):
+                a = mrq.estimate_list(three, int(j), qd[i], float(g[j]), qr2[i], sigma[i],
+                                      1.9, 4.0, qb, sign_plane=True)
+                b = mrq.estimate_list(one, int(j), qd[i], float(g[j]), qr2[i], sigma[i],
+                                      1.9, 4.0, qb)
+                for key in ("dis", "lb", "ub"):
+                    np.testing.assert_allclose(a[key], b[key], rtol=1e-10, atol=1e-9)
+
+
+def test_refine_without_pruning_is_brute_force(refine_pair):
+    w, base, queries, one, three = refine_pair
+    Q = queries[:10]
+    ref_ids, ref_d = mrq.exact_knn(base, Q, w.k)
+    for qb in (0, 4):
+        r = mrq.search_contract(three, Q, w.k, three.nlist, eps0=1e9, m=1e9, qbits=qb, refine=True)
+        np.testing.assert_array_equal(r.ids, ref_ids)
+        np.testing.assert_allclose(r.dists, ref_d, rtol=1e-9)
+    # a 1-bit code has no refinement: the flag changes nothing
+    a = mrq.search_contract(one, Q, w.k, 4, refine=True)
+    b = mrq.search_contract(one, Q, w.k, 4)
+    np.testing.assert_array_equal(a.ids, b.ids)
+    np.testing.assert_array_equal(a.n_s1, b.n_s1)
+
+
+def test_refine_equals_exact_when_bounds_hold(refine_pair):
+    """When every probed candidate satisfies LB <= exact <= UB at both stage-1 levels and
+    at stage 2, every threshold is at least the k-th exact distance and no true member is
+    pruned, so the two-level contract returns the exact top-k of the probed lists."""
+    w, base, queries, one, three = refine_pair
+    eps0, m, nprobe = 4.0, 16.0, 4
+    Q = queries[:60]
+    r = mrq.search_contract(three, Q, w.k, nprobe, eps0=eps0, m=m, refine=True)
+    plain = mrq.search_contract(three, Q, w.k, nprobe, eps0=eps0, m=m)
+    qd, qr, qr2, sigma, qp2 = mrq.project_queries(three, Q)
+    checked = 0
+    for i in range(Q.shape[0]):
+        lists, g = mrq.probe(three, qd[i], nprobe)
+        p, lo, hi = [], [], []
+        for j in lists:
+            sl = three.list_slice(int(j))
+            p.append(np.arange(sl.start, sl.stop))
+            for sp in (True, False):
+                e = mrq.estimate_list(three, int(j), qd[i], float(g[j]), qr2[i], sigma[i],
+                                      eps0, m, sign_plane=sp)
+                lo.append((sp, e["lb"])); hi.append((sp, e["ub"]))
+        p = np.concatenate(p)
+        lba = np.concatenate([a for sp, a in lo if sp]); uba = np.concatenate([a for sp, a in hi if sp])
+        lbb = np.concatenate([a for sp, a in lo if not sp]); ubb = np.concatenate([a for sp, a in hi if not sp])
+        ex = np.sum((three.xd[p] - qd[i]) ** 2, axis=1) + np.sum((three.xr[p] - qr[i]) ** 2, axis=1)
+        diso = three.xnorm2[p] + qp2[i] - 2 * three.xd[p] @ qd[i]
+        ok = all(np.all((lb_ <= ex) & (ex <= ub_)) for lb_, ub_ in
+                 ((lba, uba), (lbb, ubb), (diso - m * sigma[i], diso + m * sigma[i])))
+        if ok:
+            checked += 1
+            top = np.lexsort((three.ids[p], ex))[:w.k]
+            assert r.ids[i].tolist() == three.ids[p][top].tolist()
+            assert plain.ids[i].tolist() == r.ids[i].tolist()
+    assert checked >= 30
+    # the sign plane's wider interval lets more candidates through stage 1a than the
+    # full code passes in one stage, and the refinement removes most of them again
+    assert r.n_s1.sum() <= 1.5 * plain.n_s1.sum()
