@@ -77,6 +77,15 @@ typedef struct {
   int graph;        /* 1 = replay a captured CUDA graph when queries, ids and dists are device
                        memory and every argument equals the previous graph call's (the first
                        such call runs normally, then captures); ignored with profile = 1 */
+  int refine;       /* 1 = "1 bit + refinement" stage 1 for codes of bits > 1: the sign plane
+                       of every code (the 1-bit code of o', with its own Eq. 4 / Eq. 5
+                       factors) is scanned first, tau_A' = k-th smallest of its upper bounds,
+                       S1a = {LB1a <= tau_A'}; the full B-bit estimate is then computed for
+                       S1a only, tau_A = min(tau_A', k-th smallest UB1b over S1a),
+                       S1 = {i in S1a : LB1b <= tau_A}.  Needs query_bits >= 1, k <= 128 and
+                       an index holding the sign-plane factors (built by this library, or a
+                       file with FRE1/FER1 sections); the scan then runs pair by pair
+                       (batched is ignored).  With bits = 1 it changes nothing.  Default 0 */
   void* cuda_stream;/* cudaStream_t, or NULL */
 } mrq_search_opts;
 
@@ -280,15 +289,19 @@ int mrq_server_stop(mrq_server* server);
 
 /* Save / load the index file: magic "MRQINDEX", version 1, header (n, D, d, bits,
  * nlist), then tagged sections MU__, LAM_, W___, CENT, LOFF, IDS_, CODE (one u8 level
- * per dimension), FADD, FRES, FERR, XD__, XR__, XN2_ (list-major, unpadded).  A
- * malformed or other-version file gives MRQ_EFORMAT, an unreadable path MRQ_EIO. */
+ * per dimension), FADD, FRES, FERR, XD__, XR__, XN2_ (list-major, unpadded), and, for
+ * bits > 1, the optional FRE1, FER1 (f32[n]: Eq. 4 / Eq. 5 factors of the sign plane,
+ * used by refine = 1; written when the index holds them, both or neither).  Unknown
+ * sections are skipped.  A malformed or other-version file gives MRQ_EFORMAT, an
+ * unreadable path MRQ_EIO. */
 int mrq_save(const mrq_index* index, const char* path);
 int mrq_load(const char* path, mrq_index** out);
 
 int mrq_index_info(const mrq_index* index, mrq_index_info_t* info);
 
 /* Copy one index array to host memory in the file's canonical layout (list-major,
- * unpadded).  field: 4-character tag of the file format (e.g. "CODE", "XD__"). */
+ * unpadded).  field: 4-character tag of the file format (e.g. "CODE", "XD__"; "FRE1" and
+ * "FER1" only when the index holds them, else MRQ_EINVAL). */
 int mrq_index_export(const mrq_index* index, const char* field, void* host_dst,
                      size_t bytes);
 

@@ -50,7 +50,8 @@ class BuildOpts(C.Structure):
 class SearchOpts(C.Structure):
     _fields_ = [("eps0", C.c_float), ("m", C.c_float), ("mode", C.c_int),
                 ("precision", C.c_int), ("query_bits", C.c_int), ("batched", C.c_int),
-                ("profile", C.c_int), ("graph", C.c_int), ("cuda_stream", C.c_void_p)]
+                ("profile", C.c_int), ("graph", C.c_int), ("refine", C.c_int),
+                ("cuda_stream", C.c_void_p)]
 
 
 class ServerOpts(C.Structure):
@@ -169,11 +170,12 @@ def mrq_build_opts(seed: int = 1, kmeans_iters: int = 20, init_centroids=None, i
 
 def mrq_search_opts(eps0: float = 1.9, m: float = 4.0, mode: int = MODE_MRQ_PLUS,
                     precision: int = PREC_FP32, query_bits: int = 0, batched: int = 0,
-                    profile: int = 0, graph: int = 0, stream=None) -> SearchOpts:
+                    profile: int = 0, graph: int = 0, stream=None, refine: int = 0) -> SearchOpts:
     o = SearchOpts()
     _lib.mrq_search_opts_default(C.byref(o))
     o.eps0, o.m, o.mode, o.precision = eps0, m, mode, precision
     o.query_bits, o.batched, o.profile, o.graph = query_bits, batched, profile, graph
+    o.refine = refine
     if stream is not None:
         o.cuda_stream = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
     return o
@@ -319,6 +321,7 @@ _FIELD_SHAPES = {
     "FRES": (np.float32, lambda i: (i.n,)), "FERR": (np.float32, lambda i: (i.n,)),
     "XD__": (np.float32, lambda i: (i.n, i.d)), "XR__": (np.float32, lambda i: (i.n, i.D - i.d)),
     "XN2_": (np.float32, lambda i: (i.n,)),
+    "FRE1": (np.float32, lambda i: (i.n,)), "FER1": (np.float32, lambda i: (i.n,)),
 }
 
 

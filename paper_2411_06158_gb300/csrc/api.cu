@@ -74,7 +74,19 @@ mrq_search_opts resolve(const mrq_search_opts* opt) {
   MRQ_REQUIRE(o.query_bits >= 0 && o.query_bits <= 8, "query_bits must be in [0, 8]");
   MRQ_REQUIRE(o.batched >= MRQ_SCAN_PAIRS && o.batched <= MRQ_SCAN_BATCHED_TC,
               "batched must be MRQ_SCAN_PAIRS, MRQ_SCAN_BATCHED, MRQ_SCAN_AUTO or MRQ_SCAN_BATCHED_TC");
+  MRQ_REQUIRE(o.refine == 0 || o.refine == 1, "refine must be 0 or 1");
   return o;
+}
+
+// the 1 bit + refinement scan's own requirements (a 1-bit code has no refinement and
+// searches as usual)
+void check_refine(const mrq_index* idx, const mrq_search_opts& o, int k, int nprobe) {
+  if (!mrq::refine_active(idx, o)) return;
+  MRQ_REQUIRE(idx->fres1.p != nullptr,
+              "refine needs the sign-plane factors (FRE1/FER1), which this index does not hold");
+  MRQ_REQUIRE(o.query_bits > 0, "refine needs a quantized query (query_bits >= 1)");
+  MRQ_REQUIRE(k <= 128, "refine needs k <= 128");
+  MRQ_REQUIRE(nprobe <= mrq::REFINE_MAX_NPROBE, "refine needs nprobe <= 4096");
 }
 
 // ---------------------------------------------------------------- file format
@@ -175,6 +187,7 @@ int mrq_search(mrq_index* idx, const float* queries, int64_t nq, int k, int npro
     if (nq == 0) return;
     MRQ_REQUIRE(queries && ids && dists, "queries, ids and dists must not be NULL");
     const mrq_search_opts o = resolve(opt);
+    check_refine(idx, o, k, nprobe);
     use_device(idx);
     cudaStream_t st = stream_of(o);
     const bool qdev = on_device(queries);
@@ -214,7 +227,7 @@ int mrq_search(mrq_index* idx, const float* queries, int64_t nq, int k, int npro
     const bool use_graph = o.graph && !o.profile && (qdev || pinned_host(queries)) &&
                            (odev || (pinned_host(ids) && pinned_host(dists)));
     mrq_index::GraphKey key{queries, ids, dists, nq, k, nprobe, o.mode, o.precision,
-                            o.query_bits, o.batched, o.eps0, o.m};
+                            o.query_bits, o.batched, o.refine, o.eps0, o.m};
     // tensor-core forms read each query once (the bf16 split), so page-locked host
     // queries are read in place through their device mapping instead of copied first
     const float* qmap = nullptr;
@@ -363,12 +376,13 @@ int mrq_autotune(mrq_index* idx, const float* queries, int64_t nq, int k, int np
       cands.push_back({MRQ_SCAN_PAIRS, chunk, 16});
     }
     const int wds = idx->words, nch = idx->d / 32;
-    const bool can_batch = o.query_bits > 0 && wds <= 16 && (wds & (wds - 1)) == 0 &&
+    const bool refine = mrq::refine_active(idx, o);  // scans pair by pair
+    const bool can_batch = !refine && o.query_bits > 0 && wds <= 16 && (wds & (wds - 1)) == 0 &&
                            (idx->bits & (idx->bits - 1)) == 0 && (nch & (nch - 1)) == 0 &&
                            !(wds == 16 && idx->d == 32);
     if (can_batch)
       for (int g : {4, 8, 16}) cands.push_back({MRQ_SCAN_BATCHED, 4096, g});
-    if (mrq::tc_available() && mrq::scan_tc_supported(idx->d, idx->bits, o.query_bits))
+    if (!refine && mrq::tc_available() && mrq::scan_tc_supported(idx->d, idx->bits, o.query_bits))
       cands.push_back({MRQ_SCAN_BATCHED_TC, 4096, mrq::TC_SCAN_GROUP});
     const mrq::ScanConfig dflt = mrq::scan_config(idx, o, nq, k, nprobe);
     result->consistent = 1;
@@ -398,7 +412,7 @@ int mrq_autotune(mrq_index* idx, const float* queries, int64_t nq, int k, int np
     result->n_tried = (int)cands.size();
     {
       std::lock_guard<std::mutex> lk(idx->tune_mu);
-      idx->tuned[std::make_tuple(mrq::scan_kclass(k), nprobe, o.query_bits)] = pick;
+      idx->tuned[std::make_tuple(mrq::scan_kclass(k), nprobe, o.query_bits, refine ? 1 : 0)] = pick;
     }
     idx->graph_valid = false;  // a captured graph may hold the old configuration
   });
@@ -520,7 +534,8 @@ int mrq_index_info(const mrq_index* idx, mrq_index_info_t* info) {
                                    idx->W2.bytes() + idx->cent2.bytes() + idx->cent.bytes() +
                                    idx->cent_n2.bytes() + idx->loff.bytes() + idx->ploff.bytes() +
                                    idx->ids.bytes() + idx->codes.bytes() + idx->fadd.bytes() +
-                                   idx->fres.bytes() + idx->ferr.bytes() + idx->xd.bytes() +
+                                   idx->fres.bytes() + idx->ferr.bytes() + idx->fres1.bytes() +
+                                   idx->ferr1.bytes() + idx->xd.bytes() +
                                    idx->xr.bytes() + idx->xn2.bytes());
   });
 }
@@ -547,8 +562,10 @@ static void export_field(const mrq_index* idx, const std::string& f, std::vector
     out = d2h_bytes(lv.p, (size_t)n * d, st);
     MRQ_CUDA(cudaStreamSynchronize(st));
     dtype = DT_U8;
-  } else if (f == "FADD" || f == "FRES" || f == "FERR") {
-    const float* src = f == "FADD" ? idx->fadd.p : f == "FRES" ? idx->fres.p : idx->ferr.p;
+  } else if (f == "FADD" || f == "FRES" || f == "FERR" ||
+             ((f == "FRE1" || f == "FER1") && idx->fres1.p)) {
+    const float* src = f == "FADD" ? idx->fadd.p : f == "FRES" ? idx->fres.p
+                     : f == "FERR" ? idx->ferr.p : f == "FRE1" ? idx->fres1.p : idx->ferr1.p;
     mrq::DevBuf<float> t((size_t)std::max<int64_t>(n, 1));
     mrq::export_padded(idx, src, t.p, st);
     out = d2h_bytes(t.p, n, st);
@@ -574,7 +591,8 @@ int mrq_index_export(const mrq_index* idx, const char* field, void* host_dst, si
 }
 
 static const char* kTags[] = {"MU__", "LAM_", "W___", "CENT", "LOFF", "IDS_", "CODE",
-                              "FADD", "FRES", "FERR", "XD__", "XR__", "XN2_"};
+                              "FADD", "FRES", "FERR", "XD__", "XR__", "XN2_", "FRE1", "FER1"};
+constexpr uint32_t kRequiredTags = 13;  // FRE1 / FER1: written when the index holds them
 
 int mrq_save(const mrq_index* idx, const char* path) {
   return guarded([&] {
@@ -586,14 +604,15 @@ int mrq_save(const mrq_index* idx, const char* path) {
     auto put = [&](const void* p, size_t b) {
       if (b && std::fwrite(p, 1, b, f) != b) mrq::fail(MRQ_EIO, "write failed");
     };
-    const uint32_t nsec = sizeof(kTags) / sizeof(kTags[0]);
+    const uint32_t nsec = kRequiredTags + (idx->fres1.p ? 2 : 0);
     put(kMagic, 8);
     put(&kVersion, 4);
     put(&nsec, 4);
     const int32_t hdr[4] = {idx->D, idx->d, idx->bits, idx->nlist};
     put(&idx->n, 8);
     put(hdr, 16);
-    for (const char* tag : kTags) {
+    for (uint32_t t = 0; t < nsec; ++t) {
+      const char* tag = kTags[t];
       std::vector<uint8_t> data;
       uint32_t dt = 0;
       export_field(idx, tag, data, dt, nullptr);
@@ -645,9 +664,11 @@ int mrq_load(const char* path, mrq_index** out) {
         {"CODE", DT_U8, (uint64_t)n * d}, {"FADD", DT_F32, (uint64_t)n},
         {"FRES", DT_F32, (uint64_t)n}, {"FERR", DT_F32, (uint64_t)n},
         {"XD__", DT_F32, (uint64_t)n * d}, {"XR__", DT_F32, (uint64_t)n * r},
-        {"XN2_", DT_F32, (uint64_t)n}};
-    std::vector<std::vector<uint8_t>> sec(13);
-    std::vector<bool> seen(13, false);
+        {"XN2_", DT_F32, (uint64_t)n}, {"FRE1", DT_F32, (uint64_t)n},
+        {"FER1", DT_F32, (uint64_t)n}};
+    constexpr int kWant = 15;
+    std::vector<std::vector<uint8_t>> sec(kWant);
+    std::vector<bool> seen(kWant, false);
     for (uint32_t s = 0; s < nsec; ++s) {
       char tag[4];
       uint32_t dt;
@@ -658,7 +679,7 @@ int mrq_load(const char* path, mrq_index** out) {
       if (dt < DT_F32 || dt > DT_U8) mrq::fail(MRQ_EFORMAT, "bad section dtype");
       if (count > (uint64_t(1) << 40)) mrq::fail(MRQ_EFORMAT, "section too large");
       int which = -1;
-      for (int w = 0; w < 13; ++w)
+      for (int w = 0; w < kWant; ++w)
         if (std::memcmp(tag, want[w].tag, 4) == 0) which = w;
       size_t bytes = count * dt_size(dt);
       std::vector<uint8_t> data(bytes);
@@ -671,8 +692,10 @@ int mrq_load(const char* path, mrq_index** out) {
       sec[which] = std::move(data);
       seen[which] = true;
     }
-    for (int w = 0; w < 13; ++w)
+    for (int w = 0; w < (int)kRequiredTags; ++w)
       if (!seen[w]) mrq::fail(MRQ_EFORMAT, std::string("missing section ") + want[w].tag);
+    if (seen[13] != seen[14]) mrq::fail(MRQ_EFORMAT, "FRE1 and FER1 come together");
+    const bool sign_factors = seen[13] && bits > 1;
     idx->h_loff.resize(nlist + 1);
     std::memcpy(idx->h_loff.data(), sec[4].data(), 8 * (nlist + 1));
     if (idx->h_loff[0] != 0 || idx->h_loff[nlist] != n) mrq::fail(MRQ_EFORMAT, "bad list offsets");
@@ -700,12 +723,16 @@ int mrq_load(const char* path, mrq_index** out) {
     up(idx->xr, sec[11], (size_t)n * r);
     up(idx->xn2, sec[12], n);
     mrq::DevBuf<uint8_t> lv;
-    mrq::DevBuf<float> fa, fr, fe;
+    mrq::DevBuf<float> fa, fr, fe, fr1, fe1;
     up(lv, sec[6], (size_t)n * d);
     up(fa, sec[7], n);
     up(fr, sec[8], n);
     up(fe, sec[9], n);
-    mrq::finalize_layout(idx.get(), lv.p, fa.p, fr.p, fe.p, st);
+    if (sign_factors) {
+      up(fr1, sec[13], n);
+      up(fe1, sec[14], n);
+    }
+    mrq::finalize_layout(idx.get(), lv.p, fa.p, fr.p, fe.p, st, fr1.p, fe1.p);
     MRQ_CUDA(cudaStreamSynchronize(st));
     *out = idx.release();
   });

@@ -362,13 +362,29 @@ __global__ void k_rownorm2(const float* __restrict__ X, int64_t n, int w, float*
   if ((threadIdx.x & 31) == 0) out[p] = s;
 }
 
+// Eq. 4 / Eq. 5 factors of a code v with <v, o'> = ip and |v|^2 = vn2
+__device__ __forceinline__ void code_factors(double rn, double ip, double vn2, int d, float& fr,
+                                             float& fe) {
+  if (rn > 0.0 && ip > 0.0) {
+    const double a = ip / sqrt(vn2);
+    fr = (float)(-2.0 * rn / ip);
+    fe = (float)(2.0 * rn * sqrt(fmax(1.0 - a * a, 0.0) / (a * a)) / sqrt((double)(d - 1)));
+  } else {
+    fr = 0.f;
+    fe = 0.f;
+  }
+}
+
 // Quantization (Algorithm 1, quantize step) and factors (Eq. 4, Eq. 5), one warp per vector.
+// With bits > 1 and fres1 != NULL it also writes the factors of the sign plane, the 1-bit
+// code v1_i = sign(o'_i) (the top bit of the level), for the 1 bit + refinement scan.
 __global__ void k_quantize(const float* __restrict__ xd, const float* __restrict__ xr2,
                            const float* __restrict__ cent, const int32_t* __restrict__ assign,
                            const int64_t* __restrict__ ids, int64_t n, int d, int bits,
                            uint8_t* __restrict__ levels, float* __restrict__ fadd,
                            float* __restrict__ fres, float* __restrict__ ferr,
-                           float* __restrict__ xn2) {
+                           float* __restrict__ xn2, float* __restrict__ fres1,
+                           float* __restrict__ ferr1) {
   int64_t p = (int64_t)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
   if (p >= n) return;
   const int lane = threadIdx.x & 31;
@@ -393,7 +409,7 @@ __global__ void k_quantize(const float* __restrict__ xd, const float* __restrict
   }
   mx = warp_max(mx);
   const float t = mx > 0.f ? (float)top / mx : 0.f;
-  double ip = 0.0, vn2 = 0.0;
+  double ip = 0.0, vn2 = 0.0, ip1 = 0.0;
   for (int c = 0; c < nc; ++c) {
     const float o = r[c];
     float lev = 1.f;
@@ -406,22 +422,18 @@ __global__ void k_quantize(const float* __restrict__ xd, const float* __restrict
     levels[p * d + c * 32 + lane] = (uint8_t)((int)(v + top) / 2);
     ip += (double)v * (double)o;
     vn2 += (double)v * (double)v;
+    ip1 += v > 0.f ? (double)o : -(double)o;
   }
   ip = warp_sum_d(ip);
   vn2 = warp_sum_d(vn2);
+  if (fres1) ip1 = warp_sum_d(ip1);
   if (lane == 0) {
     const double rn = (double)nr;
     const double tail = (double)xr2[p];
     fadd[p] = (float)(rn * rn + tail);
     xn2[p] = (float)((double)xx + tail);
-    if (rn > 0.0 && ip > 0.0) {
-      double a = ip / sqrt(vn2);
-      fres[p] = (float)(-2.0 * rn / ip);
-      ferr[p] = (float)(2.0 * rn * sqrt(fmax(1.0 - a * a, 0.0) / (a * a)) / sqrt((double)(d - 1)));
-    } else {
-      fres[p] = 0.f;
-      ferr[p] = 0.f;
-    }
+    code_factors(rn, ip, vn2, d, fres[p], ferr[p]);
+    if (fres1) code_factors(rn, ip1, (double)d, d, fres1[p], ferr1[p]);
   }
 }
 
@@ -444,10 +456,12 @@ __device__ __forceinline__ int64_t code_word(int64_t pp, int w, int words, int v
 
 __global__ void k_pack(const uint8_t* __restrict__ levels, const float* __restrict__ fa,
                        const float* __restrict__ fr, const float* __restrict__ fe,
+                       const float* __restrict__ fr1, const float* __restrict__ fe1,
                        const int64_t* __restrict__ loff, const int64_t* __restrict__ ploff,
                        int nlist, int64_t n, int d, int bits, int words, int vw,
                        uint32_t* __restrict__ codes, float* __restrict__ pa,
-                       float* __restrict__ pr, float* __restrict__ pe) {
+                       float* __restrict__ pr, float* __restrict__ pe, float* __restrict__ pr1,
+                       float* __restrict__ pe1) {
   int64_t p = (int64_t)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
   if (p >= n) return;
   const int lane = threadIdx.x & 31;
@@ -465,6 +479,10 @@ __global__ void k_pack(const uint8_t* __restrict__ levels, const float* __restri
     pa[pp] = fa[p];
     pr[pp] = fr[p];
     pe[pp] = fe[p];
+    if (pr1) {
+      pr1[pp] = fr1[p];
+      pe1[pp] = fe1[p];
+    }
   }
 }
 
@@ -519,7 +537,7 @@ inline int warps_grid(int64_t n, int wpb = 8) { return ceil_div(n, wpb); }
 // ================================================================== host side
 
 void finalize_layout(mrq_index* idx, const uint8_t* levels, const float* fa, const float* fr,
-                     const float* fe, cudaStream_t st) {
+                     const float* fe, cudaStream_t st, const float* fr1, const float* fe1) {
   const int nlist = idx->nlist;
   idx->words = idx->bits * idx->d / 32;
   idx->vw = (idx->words % 4 == 0) ? 4 : (idx->words % 2 == 0) ? 2 : 1;
@@ -550,10 +568,21 @@ void finalize_layout(mrq_index* idx, const uint8_t* levels, const float* fa, con
   MRQ_CUDA(cudaMemsetAsync(idx->fadd.p, 0, idx->fadd.bytes(), st));
   MRQ_CUDA(cudaMemsetAsync(idx->fres.p, 0, idx->fres.bytes(), st));
   MRQ_CUDA(cudaMemsetAsync(idx->ferr.p, 0, idx->ferr.bytes(), st));
+  const bool sign_factors = idx->bits > 1 && fr1 && fe1;
+  if (sign_factors) {
+    idx->fres1.alloc(np);
+    idx->ferr1.alloc(np);
+    MRQ_CUDA(cudaMemsetAsync(idx->fres1.p, 0, idx->fres1.bytes(), st));
+    MRQ_CUDA(cudaMemsetAsync(idx->ferr1.p, 0, idx->ferr1.bytes(), st));
+  } else {
+    idx->fres1.release();
+    idx->ferr1.release();
+  }
   if (idx->n > 0) {
-    k_pack<<<warps_grid(idx->n), 256, 0, st>>>(levels, fa, fr, fe, idx->loff.p, idx->ploff.p, nlist,
-                                               idx->n, idx->d, idx->bits, idx->words, idx->vw,
-                                               idx->codes.p, idx->fadd.p, idx->fres.p, idx->ferr.p);
+    k_pack<<<warps_grid(idx->n), 256, 0, st>>>(
+        levels, fa, fr, fe, sign_factors ? fr1 : nullptr, sign_factors ? fe1 : nullptr,
+        idx->loff.p, idx->ploff.p, nlist, idx->n, idx->d, idx->bits, idx->words, idx->vw,
+        idx->codes.p, idx->fadd.p, idx->fres.p, idx->ferr.p, idx->fres1.p, idx->ferr1.p);
     MRQ_CHECK_LAUNCH();
   }
   make_bf16_split(idx, st);
@@ -794,8 +823,12 @@ void build_index(mrq_index* idx, const float* X, const mrq_build_opts& o, cudaSt
   perm.release();
 
   // ---- quantization and factors
-  DevBuf<float> xr2(n), fa(n), fr(n), fe(n);
+  DevBuf<float> xr2(n), fa(n), fr(n), fe(n), fr1, fe1;
   DevBuf<uint8_t> levels((size_t)n * d);
+  if (idx->bits > 1) {
+    fr1.alloc(n);
+    fe1.alloc(n);
+  }
   idx->xn2.alloc(n);
   if (r > 0) {
     k_rownorm2<<<warps_grid(n), 256, 0, st>>>(idx->xr.p, n, r, xr2.p);
@@ -804,9 +837,10 @@ void build_index(mrq_index* idx, const float* X, const mrq_build_opts& o, cudaSt
     MRQ_CUDA(cudaMemsetAsync(xr2.p, 0, 4 * n, st));
   }
   k_quantize<<<warps_grid(n), 256, 0, st>>>(idx->xd.p, xr2.p, idx->cent.p, assign.p, idx->ids.p, n,
-                                            d, idx->bits, levels.p, fa.p, fr.p, fe.p, idx->xn2.p);
+                                            d, idx->bits, levels.p, fa.p, fr.p, fe.p, idx->xn2.p,
+                                            fr1.p, fe1.p);
   MRQ_CHECK_LAUNCH();
-  finalize_layout(idx, levels.p, fa.p, fr.p, fe.p, st);
+  finalize_layout(idx, levels.p, fa.p, fr.p, fe.p, st, fr1.p, fe1.p);
   MRQ_CUDA(cudaStreamSynchronize(st));
 }
 

@@ -179,13 +179,16 @@ struct mrq_index {
   mrq::DevBuf<int64_t> ids;               // n, list-major
   mrq::DevBuf<uint32_t> codes;            // padded bit-plane layout
   mrq::DevBuf<float> fadd, fres, ferr;    // padded
+  // padded factors of the sign plane (the 1-bit code of o'), held when bits > 1: the
+  // first level of the 1 bit + refinement scan
+  mrq::DevBuf<float> fres1, ferr1;
   mrq::DevBuf<float> xd, xr, xn2;         // list-major, unpadded
   mrq::Workspace ws;
   int64_t last_nq = 0;
   mutable bool last_stats_dev = false;
-  // autotuned scan configurations, keyed by (k class, nprobe, query bits)
+  // autotuned scan configurations, keyed by (k class, nprobe, query bits, refinement)
   std::mutex tune_mu;
-  std::map<std::tuple<int, int, int>, mrq::ScanConfig> tuned;  // last search's counters still in ws.stats (device)
+  std::map<std::tuple<int, int, int, int>, mrq::ScanConfig> tuned;  // last search's counters still in ws.stats (device)
   mutable std::vector<int64_t> last_stats;        // nq x 3 host copy of the last search's counters
   // profiling of the last search: MRQ_NSTAGES + 1 events per batch
   std::vector<cudaEvent_t> prof_ev;
@@ -199,12 +202,13 @@ struct mrq_index {
     void* ids;
     void* dists;
     int64_t nq;
-    int k, nprobe, mode, precision, query_bits, batched;
+    int k, nprobe, mode, precision, query_bits, batched, refine;
     float eps0, m;
     bool operator==(const GraphKey& o) const {
       return q == o.q && ids == o.ids && dists == o.dists && nq == o.nq && k == o.k &&
              nprobe == o.nprobe && mode == o.mode && precision == o.precision &&
-             query_bits == o.query_bits && batched == o.batched && eps0 == o.eps0 && m == o.m;
+             query_bits == o.query_bits && batched == o.batched && refine == o.refine &&
+             eps0 == o.eps0 && m == o.m;
     }
   };
   bool graph_valid = false;
@@ -227,8 +231,10 @@ namespace mrq {
 // ---- build-side launchers (build.cu) ----
 void build_index(mrq_index* idx, const float* base_dev, const mrq_build_opts& o, cudaStream_t st);
 // code levels (n x d, u8, list-major) + unpadded factors -> padded device layout
+// fres1_dev / ferr1_dev: the sign plane's factors (bits > 1), or NULL
 void finalize_layout(mrq_index* idx, const uint8_t* levels_dev, const float* fadd_dev,
-                     const float* fres_dev, const float* ferr_dev, cudaStream_t st);
+                     const float* fres_dev, const float* ferr_dev, cudaStream_t st,
+                     const float* fres1_dev = nullptr, const float* ferr1_dev = nullptr);
 void export_levels(const mrq_index* idx, uint8_t* levels_dev, cudaStream_t st);
 void export_padded(const mrq_index* idx, const float* padded_dev, float* out_dev, cudaStream_t st);
 void make_bf16_split(mrq_index* idx, cudaStream_t st);
@@ -274,6 +280,12 @@ void search_batch(mrq_index* idx, Workspace& ws, const float* q_dev, int64_t nq,
                   int64_t* stats_dev, cudaStream_t st);
 void project_batch(mrq_index* idx, Workspace& ws, const float* q_dev, int64_t nq, int precision,
                    float* qd, float* qr, cudaStream_t st, __nv_bfloat16* probe_bf = nullptr);
+// the search runs the 1 bit + refinement stage 1 (bits > 1 and refine = 1)
+constexpr int REFINE_MAX_NPROBE = 4096;  // stage 1b's probe table: 12 B of shared memory each
+inline bool refine_active(const mrq_index* idx, const mrq_search_opts& o) {
+  return o.refine != 0 && idx->bits > 1;
+}
+
 // the scan configuration a search uses; a ScopedScanConfig forces one on this thread
 ScanConfig scan_config(mrq_index* idx, const mrq_search_opts& o, int64_t nq, int k, int nprobe);
 int scan_kclass(int k);

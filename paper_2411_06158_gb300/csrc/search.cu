@@ -414,6 +414,8 @@ struct ScanParams {
   const float* fres;
   const float* ferr;
   int d, bits, words, vw, nprobe, k, qbits;
+  int plane0;             // first code plane scanned: 0 = the full code, bits - 1 = the sign
+                          // plane alone (stage 1a of 1 bit + refinement, 1-bit factors)
   float eps0, m;
   int64_t npairs;
   int64_t cap;
@@ -455,7 +457,7 @@ __global__ void __launch_bounds__(SCAN_WARPS * 32) k_scan(ScanParams P) {
   float* qp = smem + wid * (5 * d);  // q' (d)
   float* lut = qp + d;               // 4d: nibble tables (float32 mode)
   uint32_t* qw = reinterpret_cast<uint32_t*>(lut);  // qbits x nch words (quantized mode)
-  const int topc = (1 << P.bits) - 1;
+  const int topc = (1 << (P.bits - P.plane0)) - 1;  // of the planes scanned
   const int topq = (1 << P.qbits) - 1;
 
   const int lvw = P.vw == 4 ? 2 : P.vw == 2 ? 1 : 0;
@@ -551,7 +553,7 @@ __global__ void __launch_bounds__(SCAN_WARPS * 32) k_scan(ScanParams P) {
       int idot = 0;
       if (!QUANT) {
         float acc = 0.f;
-        for (int a = 0; a < P.bits; ++a) {
+        for (int a = P.plane0; a < P.bits; ++a) {
           float pacc = 0.f;
           for (int c = 0; c < nch; ++c) {
             const int w = a * nch + c;
@@ -560,12 +562,12 @@ __global__ void __launch_bounds__(SCAN_WARPS * 32) k_scan(ScanParams P) {
 #pragma unroll
             for (int s = 0; s < 8; ++s) pacc += L[s * 16 + ((word >> (4 * s)) & 15)];
           }
-          acc = fmaf((float)(1 << a), pacc, acc);
+          acc = fmaf((float)(1 << (a - P.plane0)), pacc, acc);
         }
         ip = acc;
       } else {
         int dot = 0, su = 0;
-        for (int a = 0; a < P.bits; ++a) {
+        for (int a = P.plane0; a < P.bits; ++a) {
           int pd = 0, ps = 0;
           for (int c = 0; c < nch; ++c) {
             const int w = a * nch + c;
@@ -573,8 +575,8 @@ __global__ void __launch_bounds__(SCAN_WARPS * 32) k_scan(ScanParams P) {
             ps += __popc(word);
             for (int bq = 0; bq < P.qbits; ++bq) pd += __popc(word & qw[bq * nch + c]) << bq;
           }
-          dot += pd << a;
-          su += ps << a;
+          dot += pd << (a - P.plane0);
+          su += ps << (a - P.plane0);
         }
         idot = dot;
         ip = qdelta * (float)(2 * dot - topc * qsum) + ql * (float)(2 * su - d * topc);
@@ -657,10 +659,14 @@ __global__ void __launch_bounds__(SCAN_WARPS * 32) k_scan(ScanParams P) {
 // words), the candidate's code words fetched with VW-wide loads and every loop
 // unrolled; no shared memory.  The insertion into the warp's top-k list (KM 0) skips
 // upper bounds not below the query's published bound, which cannot lower tau.
-template <int KM, int NCH, int BITS, int QB>
+// LB: code planes stored (LB > BITS: only the top BITS planes are read, so LB = bits,
+// BITS = 1 scans the sign plane of a multi-bit code: stage 1a of 1 bit + refinement).
+template <int KM, int NCH, int BITS, int QB, int LB = BITS>
 __global__ void __launch_bounds__(SCAN_WARPS * 32) k_scan_q(ScanParams P) {
-  constexpr int W = BITS * NCH;
-  constexpr int VW = (W % 4 == 0) ? 4 : (W % 2 == 0) ? 2 : 1;
+  constexpr int W = BITS * NCH;                                 // words read per candidate
+  constexpr int WL = LB * NCH;                                  // words stored per candidate
+  constexpr int VW = (WL % 4 == 0) ? 4 : (WL % 2 == 0) ? 2 : 1; // the layout's vector width
+  constexpr int OFF = (LB - BITS) * NCH;                        // first word read
   constexpr int topc = (1 << BITS) - 1;
   constexpr int topq = (1 << QB) - 1;
   constexpr int d = NCH * 32;
@@ -732,10 +738,18 @@ __global__ void __launch_bounds__(SCAN_WARPS * 32) k_scan_q(ScanParams P) {
     // a block's code words and factors (its 32 candidates' padded positions)
     auto fetch = [&](int64_t b0, uint32_t (&cw)[W], float& fa, float& fr, float& fe) {
       const int64_t pp = pb0 + b0 + lane;
-      const uint32_t* cbase = P.codes + (pp >> 5) * (int64_t)(W * 32) + (pp & 31) * VW;
+      const uint32_t* cbase = P.codes + (pp >> 5) * (int64_t)(WL * 32) + (pp & 31) * VW;
+      if constexpr (OFF % VW != 0 || W % VW != 0) {
+        // the planes read do not fill whole vector groups: one word at a time
+#pragma unroll
+        for (int t = 0; t < W; ++t) {
+          const int wl = OFF + t;
+          cw[t] = __ldg(cbase + (wl / VW) * 32 * VW + wl % VW);
+        }
+      } else {
 #pragma unroll
       for (int gq = 0; gq < W / VW; ++gq) {
-        const uint32_t* src = cbase + gq * 32 * VW;
+        const uint32_t* src = cbase + (OFF / VW + gq) * 32 * VW;
         if (VW == 4) {
           const uint4 v = __ldg(reinterpret_cast<const uint4*>(src));
           cw[gq * 4] = v.x; cw[gq * 4 + 1] = v.y; cw[gq * 4 + 2] = v.z; cw[gq * 4 + 3] = v.w;
@@ -745,6 +759,7 @@ __global__ void __launch_bounds__(SCAN_WARPS * 32) k_scan_q(ScanParams P) {
         } else {
           cw[gq] = __ldg(src);
         }
+      }
       }
       fa = __ldg(P.fadd + pp);
       fr = __ldg(P.fres + pp);
@@ -1623,6 +1638,90 @@ __global__ void __launch_bounds__(FW_WARPS * 32) k_fin_s1(FinParams P) {
   }
 }
 
+// 1 bit + refinement, stage 1b: the full B-bit estimate (Eq. 4) and bounds (Eq. 5 plus
+// the Chebyshev term) of every stage-1a survivor (S1a, in s2pos), UB1b -> s2a,
+// LB1b -> s2b.  One CTA per query.  A survivor's pair (its probed list) is found by a
+// binary search over the query's probed lists sorted by list id (list starts ascend with
+// the id, and an empty list never holds a candidate, so the last probed list starting
+// at or before the position holds it); its quantized query (the same grid as the scan
+// of stage 1a) comes from k_pair_prep.
+struct RefineParams {
+  const int32_t* plist;
+  const int64_t* loff;
+  const int64_t* ploff;
+  const uint32_t* codes;
+  const float* fadd;
+  const float* fres;
+  const float* ferr;
+  const PairQ* pq;
+  const uint32_t* qplanes;
+  const int* qm1;
+  const int32_t* s2pos;
+  float* s2a;
+  float* s2b;
+  int d, bits, words, vw, nprobe, qbits;
+  int64_t cap;
+};
+
+__global__ void __launch_bounds__(256) k_refine1b(RefineParams P) {
+  extern __shared__ int rsm[];
+  int* jraw = rsm;                     // the query's probed lists in probe order
+  int* jsort = rsm + P.nprobe;         // ascending list ids
+  int* start = rsm + 2 * P.nprobe;     // their first positions
+  const int64_t q = blockIdx.x;
+  const int np = P.nprobe;
+  for (int r = threadIdx.x; r < np; r += 256) jraw[r] = P.plist[q * np + r];
+  __syncthreads();
+  for (int r = threadIdx.x; r < np; r += 256) {  // rank of a distinct id = its sorted slot
+    const int j = jraw[r];
+    int rank = 0;
+    for (int t = 0; t < np; ++t) rank += jraw[t] < j;
+    jsort[rank] = r;
+    start[rank] = (int)P.loff[j];
+  }
+  __syncthreads();
+  const int M = P.qm1[q];
+  const int64_t base = q * P.cap;
+  const int nch = P.d >> 5;
+  const int topc = (1 << P.bits) - 1;
+  const int lvw = P.vw == 4 ? 2 : P.vw == 2 ? 1 : 0;
+  for (int i = threadIdx.x; i < M; i += 256) {
+    const int p = P.s2pos[base + i];
+    int lo = 0, hi = np - 1;  // last t with start[t] <= p
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (start[mid] <= p) lo = mid; else hi = mid - 1;
+    }
+    const int r = jsort[lo];
+    const int j = jraw[r];
+    const int64_t w = q * np + r;
+    const int64_t pp = P.ploff[j] + (p - P.loff[j]);
+    const float4 pa = __ldg(reinterpret_cast<const float4*>(P.pq + w));      // sg, a0, e0, em
+    const float4 pb = __ldg(reinterpret_cast<const float4*>(P.pq + w) + 1);  // ql, qdelta, qsum
+    const int qsum = __float_as_int(pb.z);
+    const uint32_t* qw = P.qplanes + w * (int64_t)(P.qbits * nch);
+    const uint32_t* cbase = P.codes + (pp >> 5) * (int64_t)P.words * 32 + (pp & 31) * P.vw;
+    int dot = 0, su = 0;
+    for (int a = 0; a < P.bits; ++a) {
+      int pd = 0, ps = 0;
+      for (int c = 0; c < nch; ++c) {
+        const int wd = a * nch + c;
+        const uint32_t word = __ldg(cbase + ((wd >> lvw) << (5 + lvw)) + (wd & (P.vw - 1)));
+        ps += __popc(word);
+        for (int bq = 0; bq < P.qbits; ++bq) pd += __popc(word & __ldg(qw + bq * nch + c)) << bq;
+      }
+      dot += pd << a;
+      su += ps << a;
+    }
+    const float ip = pb.y * (float)(2 * dot - topc * qsum) + pb.x * (float)(2 * su - P.d * topc);
+    const float fa = __ldg(P.fadd + pp), fr = __ldg(P.fres + pp), fe = __ldg(P.ferr + pp);
+    const float dis = fa + pa.y + fr * pa.x * ip;  // Eq. 4
+    const float eps = pa.z * fe + pa.w;            // Eq. 5 + Chebyshev
+    P.s2a[base + i] = dis + eps;
+    P.s2b[base + i] = dis - eps;
+  }
+}
+
 // phase 2 (MRQ+): dis_o' = |x_p|^2 + |q_p|^2 - 2 <x_d', q_d'> (Eq. 7), UB2/LB2 = dis_o' -+ m sigma.
 // The same pass over x_d' also sums |x_d' - q_d'|^2 directly, the leading part of the
 // exact distance, into sub (free once tau_A is known), so that the exact rerank
@@ -1667,6 +1766,39 @@ __global__ void __launch_bounds__(256) k_fin_stage2(FinParams P) {
       P.s2b[base + b + lane] = diso - em;
       P.sub[base + b + lane] = myd2;
     }
+  }
+}
+
+// 1 bit + refinement, end of stage 1: tau_A = min(tau_A', k-th smallest UB1b over S1a),
+// S1 = {i in S1a : LB1b <= tau_A} (ordered compaction, s2pos -> spos); qtau and qm1 then
+// hold tau_A and |S1|
+__global__ void __launch_bounds__(FW_WARPS * 32) k_fin_s1b(FinParams P) {
+  __shared__ int hist_all[FW_WARPS][256];
+  __shared__ float filt_all[FW_WARPS][FW_FILT];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int64_t q = (int64_t)blockIdx.x * FW_WARPS + wid;
+  if (q >= P.nq) return;
+  const int64_t base = q * P.cap;
+  const int M = P.qm1[q];
+  const float tauA1 = P.qtau[q];
+  float tauA = tauA1;
+  if (M >= P.k) {
+    if (P.k <= 32) {
+      // fewer than k upper bounds <= tau_A': the k-th exceeds it, tau_A = tau_A'
+      const uint32_t kt = warp_kth_small(P.s2a + base, M, P.k, tauA1);
+      if (kt != 0xffffffffu) tauA = fminf(tauA1, fkey_inv(kt));
+    } else {
+      tauA = fminf(tauA1, fkey_inv(warp_kth_filtered(P.s2a + base, M, P.k, tauA1, filt_all[wid],
+                                                     FW_FILT, hist_all[wid])));
+    }
+  }
+  const float* lb = P.s2b + base;
+  const int M1 = warp_compact(P.s2pos + base, M, P.spos + base,
+                              [&](int i) { return lb[i] <= tauA; });
+  if (lane == 0) {
+    P.qtau[q] = tauA;
+    P.qm1[q] = M1;
+    if (P.stats) P.stats[q * 3 + 1] = M1;
   }
 }
 
@@ -1893,9 +2025,9 @@ void launch_scan_t(const ScanParams& p, int64_t grid_warps, size_t smem, cudaStr
   MRQ_CHECK_LAUNCH();
 }
 
-template <int KM, int NCH, int BITS, int QB>
+template <int KM, int NCH, int BITS, int QB, int LB = BITS>
 void launch_scan_q(const ScanParams& p, int64_t grid_warps, cudaStream_t st) {
-  auto kern = k_scan_q<KM, NCH, BITS, QB>;
+  auto kern = k_scan_q<KM, NCH, BITS, QB, LB>;
   const int per_sm = occupancy((const void*)kern, SCAN_WARPS * 32, 0);
   int64_t want = (grid_warps + SCAN_WARPS - 1) / SCAN_WARPS;
   int blocks = (int)std::min<int64_t>(want, (int64_t)num_sms() * per_sm);
@@ -1907,6 +2039,18 @@ void launch_scan_q(const ScanParams& p, int64_t grid_warps, cudaStream_t st) {
 bool launch_scan_fixed(const ScanParams& p, int64_t npairs, cudaStream_t st) {
   if (p.qbits != 4 || p.k > 128) return false;
   const int nch = p.d >> 5;
+  if (p.plane0 > 0) {  // the sign plane of a multi-bit code
+    if (p.plane0 != p.bits - 1) return false;
+#define MRQ_SQ1(B, N)                                                       \
+    if (p.bits == B && nch == N) {                                           \
+      if (p.k <= 32) launch_scan_q<0, N, 1, 4, B>(p, npairs, st);            \
+      else launch_scan_q<1, N, 1, 4, B>(p, npairs, st);                      \
+      return true;                                                           \
+    }
+    MRQ_SQ1(2, 2) MRQ_SQ1(2, 4) MRQ_SQ1(2, 8) MRQ_SQ1(4, 1) MRQ_SQ1(4, 4) MRQ_SQ1(4, 8)
+#undef MRQ_SQ1
+    return false;
+  }
 #define MRQ_SQ(B, N)                                                        \
   if (p.bits == B && nch == N) {                                             \
     if (p.k <= 32) launch_scan_q<0, N, B, 4>(p, npairs, st);                 \
@@ -2022,7 +2166,8 @@ ScanConfig scan_config(mrq_index* idx, const mrq_search_opts& o, int64_t nq, int
   if (o.batched != MRQ_SCAN_AUTO) return c;
   {
     std::lock_guard<std::mutex> lk(idx->tune_mu);
-    auto it = idx->tuned.find(std::make_tuple(scan_kclass(k), nprobe, o.query_bits));
+    auto it = idx->tuned.find(std::make_tuple(scan_kclass(k), nprobe, o.query_bits,
+                                              refine_active(idx, o) ? 1 : 0));
     if (it != idx->tuned.end()) return it->second;
   }
   // untuned rule: batch when each probed list is shared by many queries of the batch
@@ -2134,6 +2279,13 @@ void search_batch(mrq_index* idx, Workspace& ws, const float* q, int64_t nq, int
   sp.spos = ws.spos.p; sp.slb = ws.slb.p; sp.sub = ws.sub.p;
   // scan configuration: forced (autotuner), tuned for this (k, nprobe), or the rule
   const ScanConfig cfg = scan_config(idx, o, nq, k, nprobe);
+  // 1 bit + refinement: stage 1a scans the sign plane pair by pair with the 1-bit factors
+  const bool refine = refine_active(idx, o);
+  if (refine) {
+    sp.plane0 = idx->bits - 1;
+    sp.fres = idx->fres1.p;
+    sp.ferr = idx->ferr1.p;
+  }
   // per-pair work items (w = i * stride, i < n), long lists split into cfg.chunk chunks
   auto build_items = [&](int64_t n, int stride) {
     const int64_t max_items = n + (nq * idx->cap_by_nprobe[nprobe]) / cfg.chunk + 1;
@@ -2163,9 +2315,10 @@ void search_batch(mrq_index* idx, Workspace& ws, const float* q, int64_t nq, int
   const bool pop_ok = o.query_bits > 0 && wds <= BATCH_MAXW && (wds & (wds - 1)) == 0 &&
                       (idx->bits & (idx->bits - 1)) == 0 && ((d / 32) & (d / 32 - 1)) == 0 &&
                       !(wds == 16 && d == 32);
-  const bool use_tc = cfg.scan == MRQ_SCAN_BATCHED_TC && tc_available() &&
+  const bool use_tc = !refine && cfg.scan == MRQ_SCAN_BATCHED_TC && tc_available() &&
                       scan_tc_supported(d, idx->bits, o.query_bits);
-  const bool batched = use_tc || ((cfg.scan == MRQ_SCAN_BATCHED || cfg.scan == MRQ_SCAN_BATCHED_TC) && pop_ok);
+  const bool batched = !refine && (use_tc || ((cfg.scan == MRQ_SCAN_BATCHED ||
+                                                cfg.scan == MRQ_SCAN_BATCHED_TC) && pop_ok));
   if (batched) {
     const int64_t np_ = nq * nprobe;
     const int nch = d / 32;
@@ -2255,6 +2408,16 @@ void search_batch(mrq_index* idx, Workspace& ws, const float* q, int64_t nq, int
   }
   int64_t grid_items = nq * nprobe;
   if (!batched && idx->max_list > cfg.chunk) grid_items = build_items(nq * nprobe, 1);
+  if (refine) {  // the pairs' quantized queries, for stage 1b
+    const int64_t np_ = nq * nprobe;
+    ws.pq.reserve(np_ * sizeof(PairQ));
+    ws.qplanes.reserve(np_ * o.query_bits * (d / 32));
+    k_pair_prep<<<ceil_div(np_, 8), 256, 0, st>>>(ws.qd.p, ws.qstat.p, ws.plist.p, ws.pg.p,
+                                                  idx->cent.p, np_, nprobe, d, o.query_bits,
+                                                  o.eps0, o.m, reinterpret_cast<PairQ*>(ws.pq.p),
+                                                  ws.qplanes.p, nullptr);
+    MRQ_CHECK_LAUNCH();
+  }
   if (!batched) launch_scan(sp, grid_items, st, false);
   // 5. finalize
   mark(idx, MRQ_STAGE_TAU_A, st);
@@ -2274,6 +2437,22 @@ void search_batch(mrq_index* idx, Workspace& ws, const float* q, int64_t nq, int
     const unsigned gw = ceil_div(nq, FW_WARPS);
     k_fin_s1<<<gw, FW_WARPS * 32, 0, st>>>(fp);
     MRQ_CHECK_LAUNCH();
+    if (refine) {
+      RefineParams rp{};
+      rp.plist = ws.plist.p; rp.loff = idx->loff.p; rp.ploff = idx->ploff.p;
+      rp.codes = idx->codes.p; rp.fadd = idx->fadd.p; rp.fres = idx->fres.p; rp.ferr = idx->ferr.p;
+      rp.pq = reinterpret_cast<const PairQ*>(ws.pq.p); rp.qplanes = ws.qplanes.p;
+      rp.qm1 = ws.qm1.p; rp.s2pos = ws.s2pos.p; rp.s2a = ws.s2a.p; rp.s2b = ws.s2b.p;
+      rp.d = d; rp.bits = idx->bits; rp.words = idx->words; rp.vw = idx->vw;
+      rp.nprobe = nprobe; rp.qbits = o.query_bits; rp.cap = cap;
+      k_refine1b<<<(unsigned)nq, 256, (size_t)12 * nprobe, st>>>(rp);
+      MRQ_CHECK_LAUNCH();
+      k_fin_s1b<<<gw, FW_WARPS * 32, 0, st>>>(fp);
+      MRQ_CHECK_LAUNCH();
+      // S1 now sits in spos: the later phases read it from there and compact into s2pos
+      std::swap(fp.spos, fp.s2pos);
+      idx->launches += 3;
+    }
     mark(idx, MRQ_STAGE_STAGE2, st);
     if (o.mode == MRQ_MODE_MRQ_PLUS) {
       k_fin_stage2<<<(unsigned)nq, 256, (size_t)((d + 3) & ~3) * 4, st>>>(fp);

@@ -266,6 +266,12 @@ int mrq_server_start(mrq_index* idx, const mrq_server_opts* opt, mrq_server** ou
     MRQ_REQUIRE(o.max_inflight >= 1 && o.max_inflight <= 64, "max_inflight must be in [1, 64]");
     MRQ_REQUIRE(o.max_k >= 1 && o.max_k <= 1024, "max_k must be in [1, 1024]");
     MRQ_REQUIRE(o.max_wait_us >= 0, "max_wait_us must be >= 0");
+    MRQ_REQUIRE(o.search.refine == 0 || o.search.refine == 1, "refine must be 0 or 1");
+    if (mrq::refine_active(idx, o.search)) {
+      MRQ_REQUIRE(idx->fres1.p != nullptr, "refine needs the sign-plane factors (FRE1/FER1)");
+      MRQ_REQUIRE(o.search.query_bits > 0, "refine needs a quantized query (query_bits >= 1)");
+      MRQ_REQUIRE(o.max_k <= 128, "refine needs max_k <= 128");
+    }
     MRQ_CUDA(cudaSetDevice(idx->device));
     std::unique_ptr<mrq_server> sv(new mrq_server());
     idx->prof_on = false;  // the scheduler thread never records profiling events
@@ -292,6 +298,8 @@ int mrq_submit(mrq_server* sv, const float* q, int k, int nprobe, uint64_t* tick
     MRQ_REQUIRE(sv && q && ticket, "NULL argument");
     MRQ_REQUIRE(k >= 1 && k <= sv->opt.max_k, "k must be in [1, max_k]");
     MRQ_REQUIRE(nprobe >= 1 && nprobe <= sv->idx->nlist && nprobe <= 16384, "nprobe out of range");
+    MRQ_REQUIRE(!mrq::refine_active(sv->idx, sv->opt.search) || nprobe <= mrq::REFINE_MAX_NPROBE,
+                "refine needs nprobe <= 4096");
     Req r;
     r.k = k;
     r.nprobe = nprobe;
@@ -345,6 +353,9 @@ int mrq_submit_many(mrq_server* sv, int64_t n, const float* q, const int* k, con
       MRQ_REQUIRE(k[i] >= 1 && k[i] <= sv->opt.max_k, "k must be in [1, max_k]");
       MRQ_REQUIRE(nprobe[i] >= 1 && nprobe[i] <= sv->idx->nlist && nprobe[i] <= 16384,
                   "nprobe out of range");
+      MRQ_REQUIRE(!mrq::refine_active(sv->idx, sv->opt.search) ||
+                      nprobe[i] <= mrq::REFINE_MAX_NPROBE,
+                  "refine needs nprobe <= 4096");
       rs[i].k = k[i];
       rs[i].nprobe = nprobe[i];
       rs[i].q.assign(q + i * D, q + (i + 1) * D);
