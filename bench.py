@@ -492,12 +492,17 @@ def main(argv=None):
         "tuned_bf16_q4": mrq.mrq_search_opts(query_bits=4, precision=mrq.PREC_BF16,
                                              batched=mrq.SCAN_AUTO, graph=1, stream=stream),
     }
+    if w.bits > 1:
+        # 1 bit + refinement: the sign plane first, the full code for its survivors only
+        forms["refine_bf16_q4"] = mrq.mrq_search_opts(query_bits=4, precision=mrq.PREC_BF16,
+                                                      graph=1, refine=1, stream=stream)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
     def with_m(opts, m, eps0=None):
         return mrq.mrq_search_opts(eps0=opts.eps0 if eps0 is None else eps0, m=m, mode=opts.mode,
                                    precision=opts.precision, query_bits=opts.query_bits,
-                                   batched=opts.batched, graph=opts.graph, stream=stream)
+                                   batched=opts.batched, graph=opts.graph, refine=opts.refine,
+                                   stream=stream)
 
     def calibrate(opts):
         """Smallest nprobe reaching the recall target for each bound setting -- the
@@ -526,7 +531,7 @@ def main(argv=None):
     def timed(opts, npb, steps, warmup, profile):
         o = mrq.mrq_search_opts(eps0=opts.eps0, m=opts.m, mode=opts.mode, precision=opts.precision,
                                 query_bits=opts.query_bits, batched=opts.batched,
-                                graph=0 if profile else opts.graph,
+                                graph=0 if profile else opts.graph, refine=opts.refine,
                                 profile=1 if profile else 0, stream=stream)
         ids = torch.empty((w.n_query, w.k), dtype=torch.int64, device=dev)
         dists = torch.empty((w.n_query, w.k), dtype=torch.float32, device=dev)
