@@ -143,9 +143,9 @@ class ClockSampler:
 # profiles/dram_gist-1M-d960_tuned-bf16_nprobe3.md.  Used only when the timed
 # run matches that configuration exactly.
 NCU_TRAFFIC = {
-    ("k_fin_exact_r", "gist-like-1M-d960", "tuned_bf16_q4", 3, 1.0, 1.0): 1346259456,
-    ("k_fin_stage2", "gist-like-1M-d960", "tuned_bf16_q4", 3, 1.0, 1.0): 529399040,
-    ("k_scan_q", "gist-like-1M-d960", "tuned_bf16_q4", 3, 1.0, 1.0): 41613824,
+    ("k_fin_exact_r", "gist-like-1M-d960", 128, 1, "tuned_bf16_q4", 3, 1.0, 1.0): 1346259456,
+    ("k_fin_stage2", "gist-like-1M-d960", 128, 1, "tuned_bf16_q4", 3, 1.0, 1.0): 529399040,
+    ("k_scan_q", "gist-like-1M-d960", 128, 1, "tuned_bf16_q4", 3, 1.0, 1.0): 41613824,
 }
 
 
@@ -650,7 +650,7 @@ def main(argv=None):
         scan_mode = (B.get("autotune") or {}).get("scan", mrq.SCAN_PAIRS)
     fixed = (o_best.query_bits == 4 and w.k <= 128 and
              (w.bits, w.d // 32) in {(1, 1), (1, 2), (1, 4), (1, 8), (2, 2), (2, 4), (2, 8),
-                                     (4, 1), (4, 4), (4, 8)})
+                                     (4, 1), (4, 4), (4, 8), (1, 30), (1, 32)})
     scan_kernel = ("k_scan_tc" if scan_mode == mrq.SCAN_BATCHED_TC
                    else "k_scan_batched" if scan_mode == mrq.SCAN_BATCHED
                    else "k_scan_q" if fixed else "k_scan")
@@ -664,7 +664,7 @@ def main(argv=None):
     launch_ms = B["stage_ms"][dom] / n_batches
     alg_bytes = bpq * w.n_query / n_batches
     achieved = alg_bytes / (launch_ms / 1000.0) / 1e9
-    tkey = (kname, w.name, best, B["nprobe"], round(B["m"], 3), round(B["eps0"], 3))
+    tkey = (kname, w.name, w.d, w.bits, best, B["nprobe"], round(B["m"], 3), round(B["eps0"], 3))
     traffic = NCU_TRAFFIC.get(tkey) if w.n_query == 10_000 else None
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
             "frac": achieved / peak, "traffic": traffic, "kernel": kname,

@@ -114,6 +114,8 @@ typedef struct {
   int64_t device_bytes; /* device memory held by the index */
 } mrq_index_info_t;
 
+#define MRQ_MAX_D 1024 /* largest quantized dimension d */
+
 /* Fill *opt with the defaults listed above. */
 void mrq_build_opts_default(mrq_build_opts* opt);
 void mrq_search_opts_default(mrq_search_opts* opt);
@@ -121,7 +123,8 @@ void mrq_search_opts_default(mrq_search_opts* opt);
 /*
  * Build an IVF-MRQ index on the GPU (Algorithm 1).
  *  base: n x D float32 (host or device).  d: number of leading PCA coordinates
- *  that are quantized, 0 < d <= D, d % 32 == 0, d >= 32.  bits: code bits per
+ *  that are quantized, 32 <= d <= min(D, MRQ_MAX_D), d % 32 == 0; d = D leaves no
+ *  residual tail (sigma = 0, Eq. 6), i.e. IVF-RaBitQ (Section 6.1).  bits: code bits per
  *  quantized coordinate, 1..8 (1 = the paper's sign code).  nlist: IVF lists,
  *  1 <= nlist <= n.  n must be < 2^31.  opt may be NULL (defaults).
  * Steps: float64 mean/covariance and float64 Jacobi eigendecomposition (PCA,

@@ -149,7 +149,8 @@ int mrq_build(const float* base, int64_t n, int D, int d, int bits, int nlist,
     MRQ_REQUIRE(base != nullptr, "base is NULL");
     MRQ_REQUIRE(n >= 1 && n < (int64_t(1) << 31), "n must be in [1, 2^31)");
     MRQ_REQUIRE(D >= 32 && D <= 16384, "D must be in [32, 16384]");
-    MRQ_REQUIRE(d >= 32 && d <= D && d % 32 == 0 && d <= 512, "d must be a multiple of 32 in [32, min(D, 512)]");
+    MRQ_REQUIRE(d >= 32 && d <= D && d % 32 == 0 && d <= MRQ_MAX_D,
+                "d must be a multiple of 32 in [32, min(D, 1024)]");
     MRQ_REQUIRE(bits >= 1 && bits <= 8, "bits must be in [1, 8]");
     MRQ_REQUIRE(nlist >= 1 && nlist <= n && nlist <= (1 << 20), "nlist must be in [1, min(n, 2^20)]");
     mrq_build_opts o;
@@ -650,7 +651,7 @@ int mrq_load(const char* path, mrq_index** out) {
     get(hdr, 16);
     const int D = hdr[0], d = hdr[1], bits = hdr[2], nlist = hdr[3];
     if (!(n >= 1 && n < (int64_t(1) << 31) && D >= 32 && D <= 16384 && d >= 32 && d <= D &&
-          d % 32 == 0 && d <= 512 && bits >= 1 && bits <= 8 && nlist >= 1 && nlist <= n))
+          d % 32 == 0 && d <= MRQ_MAX_D && bits >= 1 && bits <= 8 && nlist >= 1 && nlist <= n))
       mrq::fail(MRQ_EFORMAT, "index header out of range");
     const int r = D - d;
     std::unique_ptr<mrq_index> idx(new mrq_index());

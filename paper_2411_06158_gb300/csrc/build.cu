@@ -391,7 +391,7 @@ __global__ void k_quantize(const float* __restrict__ xd, const float* __restrict
   const int j = assign[ids[p]];
   const int top = (1 << bits) - 1;
   const int nc = d / 32;
-  float r[16];  // d <= 512
+  float r[MRQ_MAX_D / 32];
   float ss = 0.f, xx = 0.f;
   for (int c = 0; c < nc; ++c) {
     float x = xd[p * d + c * 32 + lane];

@@ -454,7 +454,9 @@ __global__ void __launch_bounds__(SCAN_WARPS * 32) k_scan(ScanParams P) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int d = P.d;
   const int nch = d >> 5;  // 32-dim chunks
-  float* qp = smem + wid * (5 * d);  // q' (d)
+  // per warp: q' (d) then 4d floats of nibble tables (float32 mode) or the query's
+  // qbits x d/32 plane words (quantized mode, at most d/4 words)
+  float* qp = smem + wid * ((QUANT ? 2 : 5) * d);
   float* lut = qp + d;               // 4d: nibble tables (float32 mode)
   uint32_t* qw = reinterpret_cast<uint32_t*>(lut);  // qbits x nch words (quantized mode)
   const int topc = (1 << (P.bits - P.plane0)) - 1;  // of the planes scanned
@@ -2059,6 +2061,7 @@ bool launch_scan_fixed(const ScanParams& p, int64_t npairs, cudaStream_t st) {
   }
   MRQ_SQ(1, 1) MRQ_SQ(1, 2) MRQ_SQ(1, 4) MRQ_SQ(1, 8)
   MRQ_SQ(2, 2) MRQ_SQ(2, 4) MRQ_SQ(2, 8) MRQ_SQ(4, 1) MRQ_SQ(4, 4) MRQ_SQ(4, 8)
+  MRQ_SQ(1, 30) MRQ_SQ(1, 32)  // d = D = 960, 1024 (no tail: IVF-RaBitQ)
 #undef MRQ_SQ
   return false;
 }
@@ -2067,7 +2070,7 @@ void launch_scan(const ScanParams& p, int64_t npairs, cudaStream_t st, bool dbg)
   const bool quant = p.qbits > 0;
   const int km = p.k <= 32 ? 0 : (p.k <= 128 ? 1 : 2);
   if (!dbg && quant && launch_scan_fixed(p, npairs, st)) return;
-  size_t smem = (size_t)SCAN_WARPS * 5 * p.d * sizeof(float);
+  size_t smem = (size_t)SCAN_WARPS * (quant ? 2 : 5) * p.d * sizeof(float);
   if (dbg) {
     if (quant) launch_scan_t<2, true, true>(p, 1, smem, st);
     else launch_scan_t<2, false, true>(p, 1, smem, st);
