@@ -24,7 +24,7 @@ import math
 import numpy as np
 
 __all__ = [
-    "OracleIndex", "pca_train", "orthogonal_from_gaussian", "kmeans", "encode",
+    "OracleIndex", "choose_d", "pca_train", "orthogonal_from_gaussian", "kmeans", "encode",
     "build_index", "project_queries", "probe", "quantize_query", "estimate_list",
     "search_contract", "search_literal", "exact_knn", "SearchResult",
 ]
@@ -34,6 +34,27 @@ MODE_MRQ_PLUS = 1
 
 
 # --------------------------------------------------------------------------- build
+
+def choose_d(lam, D: int, target: float = 0.8, max_d: int = 1024) -> int:
+    """Eq. 8 (Section 5, parameter setting): d = the smallest power of two 2^i >= 128
+    whose leading PCA coordinates hold at least `target` of the total variance.
+
+    Reading (the printed formula is garbled): the sums run over the variances
+    lam_j = sigma_j^2 (the prose speaks of captured variance), the denominator over all
+    D coordinates.  d is a multiple of 32 no larger than D (nor than the library's
+    largest quantized dimension): when no power of two below that cap reaches the
+    target, d is the cap itself.
+    """
+    lam = np.maximum(np.asarray(lam, dtype=np.float64)[:D], 0.0)
+    total = float(lam.sum())
+    cap = min((D // 32) * 32, max_d)
+    p = 128
+    while p < cap:
+        if float(lam[:p].sum()) >= target * total:
+            return p
+        p *= 2
+    return cap
+
 
 def pca_train(S: np.ndarray):
     """PCA of the base set (Algorithm 1, first two steps; residual variances of Eq. 6).

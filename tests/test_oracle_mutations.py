@@ -151,3 +151,28 @@ def test_sign_plane_from_lowest_plane(monkeypatch):
             idx.u = saved
     monkeypatch.setattr(mrq, "estimate_list", wrong)
     _fails(pins.test_sign_plane_is_the_one_bit_code, pins.refine_pair.__wrapped__())
+
+
+def test_eq8_denominator_over_the_lead_only(monkeypatch):
+    def wrong(lam, D, target=0.8, max_d=1024):
+        # the garbled formula taken literally: the denominator runs over the leading
+        # coordinates only, so every candidate "captures" all of its own variance
+        lam = np.maximum(np.asarray(lam, dtype=np.float64)[:D], 0.0)
+        cap = min((D // 32) * 32, max_d)
+        p = 128
+        while p < cap:
+            if lam[:p].sum() >= target * lam[:p].sum():
+                return p
+            p *= 2
+        return cap
+    monkeypatch.setattr(mrq, "choose_d", wrong)
+    _fails(pins.test_choose_d_hand_examples)
+
+
+def test_eq8_on_standard_deviations(monkeypatch):
+    orig = mrq.choose_d
+
+    def wrong(lam, D, target=0.8, max_d=1024):
+        return orig(np.sqrt(np.maximum(np.asarray(lam, dtype=np.float64), 0.0)), D, target, max_d)
+    monkeypatch.setattr(mrq, "choose_d", wrong)
+    _fails(pins.test_choose_d_on_a_closed_form_spectrum)

@@ -482,3 +482,41 @@ def test_refine_equals_exact_when_bounds_hold(refine_pair):
     # the sign plane's wider interval lets more candidates through stage 1a than the
     # full code passes in one stage, and the refinement removes most of them again
     assert r.n_s1.sum() <= 1.5 * plain.n_s1.sum()
+
+
+# ------------------------------------------------------ Eq. 8: automatic d selection
+
+def test_choose_d_hand_examples():
+    # one unit of variance on each of the first 200 coordinates, 0.1 on the other 824
+    # (D = 1024): total 282.4; the first 128 hold 128 / 282.4 = 0.453, the first 256
+    # hold (200 + 56 * 0.1) / 282.4 = 0.728, the first 512 (200 + 312 * 0.1) / 282.4 = 0.819
+    lam = np.r_[np.ones(200), np.full(824, 0.1)]
+    assert mrq.choose_d(lam, 1024) == 512
+    assert mrq.choose_d(lam, 1024, target=0.7) == 256
+    assert mrq.choose_d(lam, 1024, target=0.45) == 128      # at least 128 even when fewer do
+    # the denominator is the whole spectrum: ten coordinates of variance 1 and 950 of
+    # 0.001 (D = 960) leave 10 / 10.95 = 0.913 in the first 128
+    assert mrq.choose_d(np.r_[np.ones(10), np.full(950, 1e-3)], 960) == 128
+    # flat spectrum (D = 960): 512 / 960 = 0.53 < 0.8, the next power of two passes D, so
+    # d = D, no tail (IVF-RaBitQ)
+    assert mrq.choose_d(np.ones(960), 960) == 960
+    # D below 128 (DEEP's 96): d = D; D not a multiple of 32: d rounds down
+    assert mrq.choose_d(np.ones(96), 96) == 96
+    assert mrq.choose_d(np.ones(100), 100) == 96
+    # no power of two above the library's largest d: d = 1024 for a flat D = 1536
+    assert mrq.choose_d(np.ones(1536), 1536) == 1024
+
+
+def test_choose_d_on_a_closed_form_spectrum():
+    """lam_i = i^-1 (i = 1..D, D = 960): the captured fraction at p is H_p / H_960 with
+    H the harmonic number; H_128 / H_960 = 5.4384 / 7.4425 = 0.731, H_256 / H_960 = 6.1312 /
+    7.4425 = 0.824, so Eq. 8 picks 256.  Also run through the oracle's own PCA on data with
+    that spectrum (a random orthogonal basis times scaled Gaussians)."""
+    D = 960
+    lam = 1.0 / np.arange(1, D + 1)
+    assert mrq.choose_d(lam, D) == 256
+    rng = np.random.default_rng(4)
+    U, _ = np.linalg.qr(rng.standard_normal((D, D)))
+    X = (rng.standard_normal((20_000, D)) * np.sqrt(lam)) @ U.T
+    _, lam_hat, _ = mrq.pca_train(X)
+    assert mrq.choose_d(lam_hat, D) == 256
