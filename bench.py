@@ -56,6 +56,8 @@ def parse_args(argv=None):
     p.add_argument("--eps0", type=float, default=None, help="fixed eps0 with --nprobe")
     p.add_argument("--clock-seconds", type=float, default=2.5,
                    help="length of the clock-sampling pass (0: one short pass)")
+    p.add_argument("--variance-report", action="store_true",
+                   help="PCA variance capture per workload and the d chosen by Eq. 8")
     p.add_argument("--precision-report", action="store_true",
                    help="precision form: projection error of each precision against a float64 "
                         "projection with the index's own W and mu, and recall@10 (one JSON line "
@@ -376,6 +378,37 @@ def run_serving(args):
 
 # --------------------------------------------------------------- GPU arm
 
+def run_variance_report(args):
+    """Variance capture of the PCA spectrum (the long tail that motivates the split,
+    Section 3) for each workload shape, and the d that the rule of Eq. 8 picks: a
+    build with d = 0 on a sample of the base (PCA on the GPU, the spectrum exported)."""
+    import numpy as np
+    import torch
+
+    import datagen
+    import paper_2411_06158_gb300 as mrq
+
+    dev = torch.device("cuda", 0)
+    out = {}
+    for name in ("gist", "embed", "deep", "serve"):
+        w = datagen.workload(name, n=min(args.n or 200_000, 200_000), n_query=1)
+        base, _ = datagen.base_and_queries(w)
+        bt = torch.from_numpy(base).to(dev)
+        row = {"D": w.D, "n_sample": w.n}
+        for target in (0.8, 0.9):
+            gi = mrq.mrq_build(bt, 0, 1, 16, mrq.mrq_build_opts(kmeans_iters=0,
+                                                               auto_d_variance=target))
+            row[f"eq8_d_at_{target}"] = gi.info().d
+        lam = np.maximum(mrq.mrq_index_export(gi, "LAM_").astype(np.float64), 0.0)
+        tot = lam.sum()
+        row["captured"] = {p: round(float(lam[:p].sum() / tot), 4)
+                           for p in (32, 64, 128, 256, 512, 1024) if p <= w.D}
+        out[w.name] = row
+        del gi, bt
+        torch.cuda.empty_cache()
+    print(json.dumps({"report": "variance", "rule": "Eq. 8", "workloads": out}))
+
+
 def run_precision_report(args):
     """Precision form: for d in {64, 128, 256} and each projection precision (float32
     CUDA cores, bf16 and split hi+lo bf16 tensor cores), the max and mean relative error
@@ -440,6 +473,8 @@ def main(argv=None):
         return run_serving(args)
     if args.precision_report:
         return run_precision_report(args)
+    if args.variance_report:
+        return run_variance_report(args)
     import numpy as np
     import torch
 

@@ -58,6 +58,8 @@ typedef struct {
   const float* init_centroids;  /* nlist x D raw-space initial centroids, or NULL */
   const int64_t* init_ids;      /* nlist base rows used as initial centroids, or NULL */
   const double* rotation_gauss; /* d x d Gaussian draw behind P_r (Algorithm 1), or NULL */
+  double auto_d_variance;       /* with d = 0: the fraction of the total PCA variance the
+                                   chosen d must hold (Eq. 8); default 0.8 */
 } mrq_build_opts;
 
 typedef struct {
@@ -124,7 +126,12 @@ void mrq_search_opts_default(mrq_search_opts* opt);
  * Build an IVF-MRQ index on the GPU (Algorithm 1).
  *  base: n x D float32 (host or device).  d: number of leading PCA coordinates
  *  that are quantized, 32 <= d <= min(D, MRQ_MAX_D), d % 32 == 0; d = D leaves no
- *  residual tail (sigma = 0, Eq. 6), i.e. IVF-RaBitQ (Section 6.1).  bits: code bits per
+ *  residual tail (sigma = 0, Eq. 6), i.e. IVF-RaBitQ (Section 6.1).  d = 0 chooses d
+ *  by the rule of Eq. 8 once the PCA spectrum is known: the smallest power of two
+ *  >= 128 whose leading coordinates hold opt->auto_d_variance of the total variance
+ *  (eigenvalues; denominator over all D), capped at the largest multiple of 32 not
+ *  above min(D, MRQ_MAX_D); mrq_index_info reports it.  d = 0 with rotation_gauss is
+ *  MRQ_EINVAL (the draw's size depends on d).  bits: code bits per
  *  quantized coordinate, 1..8 (1 = the paper's sign code).  nlist: IVF lists,
  *  1 <= nlist <= n.  n must be < 2^31.  opt may be NULL (defaults).
  * Steps: float64 mean/covariance and float64 Jacobi eigendecomposition (PCA,

@@ -44,7 +44,7 @@ class MRQError(RuntimeError):
 class BuildOpts(C.Structure):
     _fields_ = [("seed", C.c_uint64), ("kmeans_iters", C.c_int),
                 ("init_centroids", C.c_void_p), ("init_ids", C.c_void_p),
-                ("rotation_gauss", C.c_void_p)]
+                ("rotation_gauss", C.c_void_p), ("auto_d_variance", C.c_double)]
 
 
 class SearchOpts(C.Structure):
@@ -147,11 +147,11 @@ def _f32(x):
 
 
 def mrq_build_opts(seed: int = 1, kmeans_iters: int = 20, init_centroids=None, init_ids=None,
-                   rotation_gauss=None):
+                   rotation_gauss=None, auto_d_variance: float = 0.8):
     """Build options plus the arrays that must stay alive during the call."""
     o = BuildOpts()
     _lib.mrq_build_opts_default(C.byref(o))
-    o.seed, o.kmeans_iters = seed, kmeans_iters
+    o.seed, o.kmeans_iters, o.auto_d_variance = seed, kmeans_iters, auto_d_variance
     keep = []
     if init_centroids is not None:
         a = np.ascontiguousarray(init_centroids, dtype=np.float32)

@@ -127,6 +127,7 @@ void mrq_build_opts_default(mrq_build_opts* opt) {
   std::memset(opt, 0, sizeof(*opt));
   opt->seed = 1;
   opt->kmeans_iters = 20;
+  opt->auto_d_variance = 0.8;
 }
 
 void mrq_search_opts_default(mrq_search_opts* opt) {
@@ -149,14 +150,18 @@ int mrq_build(const float* base, int64_t n, int D, int d, int bits, int nlist,
     MRQ_REQUIRE(base != nullptr, "base is NULL");
     MRQ_REQUIRE(n >= 1 && n < (int64_t(1) << 31), "n must be in [1, 2^31)");
     MRQ_REQUIRE(D >= 32 && D <= 16384, "D must be in [32, 16384]");
-    MRQ_REQUIRE(d >= 32 && d <= D && d % 32 == 0 && d <= MRQ_MAX_D,
-                "d must be a multiple of 32 in [32, min(D, 1024)]");
+    MRQ_REQUIRE(d == 0 || (d >= 32 && d <= D && d % 32 == 0 && d <= MRQ_MAX_D),
+                "d must be 0 (Eq. 8) or a multiple of 32 in [32, min(D, 1024)]");
     MRQ_REQUIRE(bits >= 1 && bits <= 8, "bits must be in [1, 8]");
     MRQ_REQUIRE(nlist >= 1 && nlist <= n && nlist <= (1 << 20), "nlist must be in [1, min(n, 2^20)]");
     mrq_build_opts o;
     mrq_build_opts_default(&o);
     if (opt) o = *opt;
     MRQ_REQUIRE(o.kmeans_iters >= 0 && o.kmeans_iters <= 1000, "kmeans_iters must be in [0, 1000]");
+    MRQ_REQUIRE(o.auto_d_variance > 0.0 && o.auto_d_variance <= 1.0,
+                "auto_d_variance must be in (0, 1]");
+    MRQ_REQUIRE(d != 0 || o.rotation_gauss == nullptr,
+                "d = 0 (chosen by Eq. 8) cannot take a rotation_gauss draw");
     std::unique_ptr<mrq_index> idx(new mrq_index());
     MRQ_CUDA(cudaGetDevice(&idx->device));
     idx->n = n;

@@ -667,9 +667,24 @@ static void eigen_pca(const double* Cdev, int D, double inv_n, std::vector<doubl
   MRQ_CUDA(cudaStreamSynchronize(st));
 }
 
+// Eq. 8: the smallest power of two p >= 128 whose leading p eigenvalues hold `target` of
+// their total (all D), capped at the largest multiple of 32 not above min(D, MRQ_MAX_D)
+static int choose_d(const std::vector<double>& lam, int D, double target) {
+  double total = 0.0;
+  for (int i = 0; i < D; ++i) total += std::max(lam[i], 0.0);
+  const int cap = std::min((D / 32) * 32, MRQ_MAX_D);
+  double lead = 0.0;
+  int i = 0;
+  for (int p = 128; p < cap; p *= 2) {
+    for (; i < p; ++i) lead += std::max(lam[i], 0.0);
+    if (lead >= target * total) return p;
+  }
+  return cap;
+}
+
 void build_index(mrq_index* idx, const float* X, const mrq_build_opts& o, cudaStream_t st) {
   const int64_t n = idx->n;
-  const int D = idx->D, d = idx->d, nlist = idx->nlist, r = D - d;
+  const int D = idx->D, nlist = idx->nlist;
   const uint64_t seed = o.seed ? o.seed : 1;
 
   // ---- PCA: float64 mean and covariance
@@ -702,6 +717,8 @@ void build_index(mrq_index* idx, const float* X, const mrq_build_opts& o, cudaSt
   DevBuf<double> Pp;
   eigen_pca(C.p, D, 1.0 / (double)n, lam_h, Pp, st);
   C.release();
+  if (idx->d == 0) idx->d = choose_d(lam_h, D, o.auto_d_variance);  // Eq. 8
+  const int d = idx->d, r = D - d;
 
   // ---- random rotation P_r (d x d): Q of the Gaussian draw
   std::vector<double> G((size_t)d * d);
