@@ -26,7 +26,8 @@ import numpy as np
 __all__ = [
     "OracleIndex", "choose_d", "pca_train", "orthogonal_from_gaussian", "kmeans", "encode",
     "build_index", "project_queries", "probe", "quantize_query", "estimate_list",
-    "search_contract", "search_literal", "exact_knn", "SearchResult",
+    "search_contract", "search_literal", "exact_knn", "SearchResult", "sq8_train",
+    "sq8_estimate", "search_mrsq8",
 ]
 
 MODE_MRQ = 0
@@ -513,6 +514,107 @@ def search_contract(idx: OracleIndex, Q, k: int, nprobe: int, *, eps0: float = 1
             mg = min(mg, _decision_margin(lb2[s1], ub2[s1], sc2[s1], tau_b, k, rel2[s1]))
         margin[qi] = mg
     return SearchResult(ids, dists, n_cand, n_s1, n_s2, margin)
+
+
+def sq8_train(xd):
+    """MR-SQ (Appendix A.2, Exp-5): 8-bit scalar quantization of the projected lead
+    coordinates (the stored x_d' rows) instead of RaBitQ codes.
+
+    Reading (the paper only names "8-bit SQ"): per dimension a uniform grid of 256 levels
+    from the column's minimum to its maximum over the base, delta = (hi - lo) / 255;
+    code c = floor((x - lo) / delta + 1/2) clamped to [0, 255], reconstruction
+    x_hat = lo + c * delta.  A constant column (delta = 0) gets code 0.  The grid and
+    the code decision are taken in float32 (the GPU kernel's precision).
+    Returns lo (float32 [d]), delta (float32 [d]), codes (uint8 [n x d]).
+    """
+    X = np.asarray(xd, dtype=np.float32)
+    lo = X.min(axis=0)
+    hi = X.max(axis=0)
+    delta = ((hi - lo) / np.float32(255)).astype(np.float32)
+    safe = np.where(delta > 0, delta, np.float32(1))
+    t = ((X - lo) / safe).astype(np.float32)
+    c = np.floor(t + np.float32(0.5))
+    c = np.where(delta > 0, np.clip(c, 0, 255), 0).astype(np.uint8)
+    return lo, delta, c
+
+
+def sq8_estimate(idx: OracleIndex, sq, qd, qr2, pos=None):
+    """MR-SQ estimate (Exp-5) of the rows ``pos`` (all rows when None) for one projected
+    query: dis'' = |q_d' - x_hat|^2 + |x_r|^2 + |q_r|^2 with x_hat the SQ8
+    reconstruction; the residual inner product is dropped, as in Eq. 4."""
+    lo, delta, codes = sq
+    sel = slice(None) if pos is None else pos
+    xhat = lo.astype(np.float64) + codes[sel].astype(np.float64) * delta.astype(np.float64)
+    xr = idx.xr[sel]
+    return np.sum((qd - xhat) ** 2, axis=1) + np.sum(xr * xr, axis=1) + qr2
+
+
+def search_mrsq8(idx: OracleIndex, Q, k: int, nprobe: int, rerank: int = 500,
+                 sq=None) -> SearchResult:
+    """MR-SQ search (Exp-5): SQ8 estimates over the probed lists, then a fixed rerank
+    range instead of an error bound.
+
+    Per query (after the projection and probe of Algorithm 2):
+      dis'' = |q_d' - x_hat|^2 + |x_r|^2 + |q_r|^2   (the residual inner product
+              -2<x_r, q_r> is dropped, as Eq. 4 drops it),
+      the `rerank` candidates with the smallest dis'' (ties by id) get their exact
+      distance, and the answer is the k smallest exact distances (ties by id).
+    n_s1 = n_s2 = the number reranked.  ``margin``: the probe boundary, how far each
+    answer-relevant candidate (exact distance within the k-th) sits from the rerank cut
+    in dis'', and consecutive answer distances around rank k.
+    """
+    sq = sq if sq is not None else sq8_train(idx.xd)
+    qd_all, qr_all, qr2_all, _, _ = project_queries(idx, Q)
+    nq = qd_all.shape[0]
+    ids = np.full((nq, k), -1, dtype=np.int64)
+    dists = np.full((nq, k), np.inf)
+    n_cand = np.zeros(nq, dtype=np.int64)
+    n_rr = np.zeros(nq, dtype=np.int64)
+    margin = np.full(nq, np.inf)
+    for qi in range(nq):
+        qd, qr = qd_all[qi], qr_all[qi]
+        lists, g = probe(idx, qd, nprobe)
+        gs = np.sort(g)
+        mg = math.inf
+        if nprobe < idx.nlist:
+            mg = (gs[nprobe] - gs[nprobe - 1]) / max(gs[nprobe], 1e-30)
+        pos = (np.concatenate([np.arange(idx.list_offsets[j], idx.list_offsets[j + 1])
+                               for j in lists]) if len(lists) else np.zeros(0, dtype=np.int64))
+        n_cand[qi] = pos.size
+        if pos.size == 0:
+            margin[qi] = mg
+            continue
+        est = sq8_estimate(idx, sq, qd, qr2_all[qi], pos)
+        order = np.lexsort((idx.ids[pos], est))
+        R = min(rerank, pos.size)
+        sel = order[:R]
+        n_rr[qi] = R
+        ex_all = (np.sum((idx.xd[pos] - qd) ** 2, axis=1)
+                  + np.sum((idx.xr[pos] - qr) ** 2, axis=1))
+        ex = ex_all[sel]
+        oid = idx.ids[pos[sel]]
+        o = np.lexsort((oid, ex))
+        kk = min(k, R)
+        ids[qi, :kk] = oid[o[:kk]]
+        dists[qi, :kk] = ex[o[:kk]]
+        srt = ex[o]
+        if srt.size > 1:
+            lim = min(k + 1, srt.size)
+            gaps = np.diff(srt[:lim]) / np.maximum(srt[1:lim], 1e-30)
+            mg = min(mg, float(np.min(gaps)))
+        if R < pos.size:
+            dk = srt[kk - 1]
+            rel = ex_all <= dk * (1 + 1e-6)           # could be in the answer
+            inside = np.zeros(pos.size, dtype=bool)
+            inside[sel] = True
+            t_in, t_out = est[order[R - 1]], est[order[R]]
+            for i in np.nonzero(rel)[0]:
+                if inside[i]:
+                    mg = min(mg, (t_out - est[i]) / max(t_out, 1e-30))
+                else:
+                    mg = min(mg, (est[i] - t_in) / max(est[i], 1e-30))
+        margin[qi] = mg
+    return SearchResult(ids, dists, n_cand, n_rr, n_rr.copy(), margin)
 
 
 def search_literal(idx: OracleIndex, Q, k: int, nprobe: int, *, eps0: float = 1.9,

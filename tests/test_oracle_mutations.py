@@ -176,3 +176,37 @@ def test_eq8_on_standard_deviations(monkeypatch):
         return orig(np.sqrt(np.maximum(np.asarray(lam, dtype=np.float64), 0.0)), D, target, max_d)
     monkeypatch.setattr(mrq, "choose_d", wrong)
     _fails(pins.test_choose_d_on_a_closed_form_spectrum)
+
+
+def test_sq8_truncating_codes(monkeypatch):
+    def wrong(xd):
+        X = np.asarray(xd, dtype=np.float32)
+        lo, hi = X.min(axis=0), X.max(axis=0)
+        delta = ((hi - lo) / np.float32(255)).astype(np.float32)
+        safe = np.where(delta > 0, delta, np.float32(1))
+        c = np.floor((X - lo) / safe)                        # no rounding to nearest
+        return lo, delta, np.where(delta > 0, np.clip(c, 0, 255), 0).astype(np.uint8)
+    monkeypatch.setattr(mrq, "sq8_train", wrong)
+    _fails(pins.test_sq8_reconstruction_bound)
+
+
+def test_mrsq8_grid_off_by_one_level(monkeypatch):
+    orig = mrq.sq8_train
+
+    def shifted(xd):
+        lo, delta, c = orig(xd)
+        return lo + delta, delta, c                          # reconstruction one level up
+    monkeypatch.setattr(mrq, "sq8_train", shifted)
+    wk, idx = _small()
+    _fails(pins.test_mrsq8_estimate_within_its_bound, wk, idx)
+
+
+def test_mrsq8_dropped_tail_norm(monkeypatch):
+    orig = mrq.sq8_estimate
+
+    def wrong(idx, sq, qd, qr2, pos=None):
+        sel = slice(None) if pos is None else pos
+        return orig(idx, sq, qd, qr2, pos) - np.sum(idx.xr[sel] ** 2, axis=1)
+    monkeypatch.setattr(mrq, "sq8_estimate", wrong)
+    wk, idx = _small()
+    _fails(pins.test_mrsq8_estimate_within_its_bound, wk, idx)

@@ -520,3 +520,75 @@ def test_choose_d_on_a_closed_form_spectrum():
     X = (rng.standard_normal((20_000, D)) * np.sqrt(lam)) @ U.T
     _, lam_hat, _ = mrq.pca_train(X)
     assert mrq.choose_d(lam_hat, D) == 256
+
+
+# ------------------------------------------------------------ MR-SQ (Exp-5), 8-bit SQ
+
+def test_sq8_hand_example():
+    # column 0: 0 .. 255 integers, so lo = 0, delta = 1 and the codes are the values;
+    # column 1: -1, 1, 0.5, 0: lo = -1, delta = 2/255, (0.5 + 1) / (2/255) = 191.25 -> 191;
+    # 0 sits exactly on a half level in exact arithmetic (127.5), but the decision is taken
+    # in float32: delta = fl(2/255) = 0.0078431377 > 2/255, 1 / delta = 127.49999, and
+    # floor(127.49999 + 0.5) = 127; column 2 is constant -> 0
+    X = np.array([[0, -1, 3], [255, 1, 3], [17, 0.5, 3], [100, 0, 3]], dtype=np.float32)
+    lo, delta, c = mrq.sq8_train(X)
+    np.testing.assert_array_equal(lo, np.float32([0, -1, 3]))
+    np.testing.assert_array_equal(delta, np.float32([1, 2 / 255, 0]))
+    np.testing.assert_array_equal(c, np.array([[0, 0, 0], [255, 255, 0], [17, 191, 0],
+                                               [100, 127, 0]], dtype=np.uint8))
+
+
+def test_sq8_reconstruction_bound():
+    """Round to nearest on a uniform grid: |x - x_hat| <= delta / 2 per coordinate (up to
+    float32 rounding of the grid), and the extremes reconstruct exactly."""
+    rng = np.random.default_rng(7)
+    X = (rng.standard_normal((4000, 48)) * rng.uniform(0.1, 5, 48)).astype(np.float32)
+    lo, delta, c = mrq.sq8_train(X)
+    xhat = lo.astype(np.float64) + c.astype(np.float64) * delta.astype(np.float64)
+    err = np.abs(xhat - X.astype(np.float64))
+    assert np.all(err <= delta.astype(np.float64) / 2 * (1 + 1e-4) + 1e-6)
+    assert np.all(c[np.argmin(X, axis=0), np.arange(48)] == 0)
+    assert np.all(c[np.argmax(X, axis=0), np.arange(48)] == 255)
+
+
+def test_mrsq8_estimate_within_its_bound(small_workload, small_oracle_index):
+    """dis'' - |x_r|^2 - |q_r|^2 is |q_d' - x_hat|^2, within |x_hat - x_d'| of |q_d' - x_d'|
+    (triangle inequality): | sqrt(dis'' - |x_r|^2 - |q_r|^2) - |q_d' - x_d'| | <= |delta|/2."""
+    w, base, queries = small_workload
+    idx = small_oracle_index
+    sq = mrq.sq8_train(idx.xd)
+    qd, qr, qr2, _, _ = mrq.project_queries(idx, queries[:20])
+    bound = np.linalg.norm(sq[1].astype(np.float64)) / 2 * (1 + 1e-4) + 1e-9
+    xr2 = np.linalg.norm(idx.xr, axis=1) ** 2
+    for i in range(20):
+        est = mrq.sq8_estimate(idx, sq, qd[i], qr2[i])
+        lead = np.sqrt(np.maximum(est - xr2 - qr2[i], 0))
+        true_lead = np.linalg.norm(idx.xd - qd[i], axis=1)
+        assert np.all(np.abs(lead - true_lead) <= bound)
+        # and the dropped term is exactly the residual cross term
+        full = np.sum((idx.xd - qd[i]) ** 2, axis=1) + np.sum((idx.xr - qr[i]) ** 2, axis=1)
+        assert np.allclose(full - (true_lead ** 2 + xr2 + qr2[i]), -2 * idx.xr @ qr[i], atol=1e-8)
+
+
+def test_mrsq8_full_rerank_is_brute_force(small_workload, small_oracle_index):
+    w, base, queries = small_workload
+    idx = small_oracle_index
+    Q = queries[:12]
+    ref_ids, ref_d = mrq.exact_knn(base, Q, w.k)
+    r = mrq.search_mrsq8(idx, Q, w.k, idx.nlist, rerank=idx.xd.shape[0])
+    np.testing.assert_array_equal(r.ids, ref_ids)
+    np.testing.assert_allclose(r.dists, ref_d, rtol=1e-9)
+
+
+def test_mrsq8_rerank_range(small_workload, small_oracle_index):
+    """The answer is the exact top-k of the rerank range, and with enough range the
+    recall matches the exact top-k of the probed lists (8-bit codes are fine-grained)."""
+    w, base, queries = small_workload
+    idx = small_oracle_index
+    Q = queries[:40]
+    r = mrq.search_mrsq8(idx, Q, w.k, w.nprobe, rerank=200)
+    assert np.all(r.n_s1 == np.minimum(200, r.n_cand))
+    full = mrq.search_contract(idx, Q, w.k, w.nprobe, eps0=1e9, m=1e9)   # exact over probed
+    assert mrq.recall_at_k(r.ids, full.ids) > 0.99
+    r10 = mrq.search_mrsq8(idx, Q, w.k, w.nprobe, rerank=w.k)
+    assert mrq.recall_at_k(r10.ids, full.ids) < mrq.recall_at_k(r.ids, full.ids)
