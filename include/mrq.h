@@ -44,6 +44,14 @@ extern "C" {
 /* search modes (Section 6.1, algorithm list) */
 #define MRQ_MODE_MRQ 0      /* IVF-MRQ: stage 1 then exact rerank (no stage 2) */
 #define MRQ_MODE_MRQ_PLUS 1 /* IVF-MRQ+: stage 1, stage 2 (Eq. 7), exact rerank */
+#define MRQ_MODE_SQ8 2      /* MR-SQ (Appendix A.2, Exp-5): 8-bit scalar quantization of
+                               the projected lead coordinates x_d' (per dimension, 256 levels
+                               from the base's min to max, round to nearest) instead of the
+                               RaBitQ code; estimate |q_d' - x_hat|^2 + |x_r|^2 + |q_r|^2; the
+                               `rerank` smallest estimates (ties by id) are reranked exactly.
+                               No error bound: eps0, m, query_bits, batched and refine are
+                               ignored.  The codes are made from the index's x_d' on first use
+                               (n * d bytes, not saved).  k <= 128. */
 
 /* query-projection precision (the first step of Algorithm 2) */
 #define MRQ_PREC_FP32 0   /* float32 CUDA-core GEMM */
@@ -88,6 +96,7 @@ typedef struct {
                        an index holding the sign-plane factors (built by this library, or a
                        file with FRE1/FER1 sections); the scan then runs pair by pair
                        (batched is ignored).  With bits = 1 it changes nothing.  Default 0 */
+  int rerank;       /* MRQ_MODE_SQ8: the rerank range R, k <= R <= 65536; default 500 */
   void* cuda_stream;/* cudaStream_t, or NULL */
 } mrq_search_opts;
 
@@ -311,7 +320,9 @@ int mrq_index_info(const mrq_index* index, mrq_index_info_t* info);
 
 /* Copy one index array to host memory in the file's canonical layout (list-major,
  * unpadded).  field: 4-character tag of the file format (e.g. "CODE", "XD__"; "FRE1" and
- * "FER1" only when the index holds them, else MRQ_EINVAL). */
+ * "FER1" only when the index holds them, else MRQ_EINVAL), or one of the MR-SQ arrays
+ * (made on demand): "SQ8C" u8[n*d] codes, "SQ8L" f32[d] grid start, "SQ8S" f32[d] grid
+ * step. */
 int mrq_index_export(const mrq_index* index, const char* field, void* host_dst,
                      size_t bytes);
 

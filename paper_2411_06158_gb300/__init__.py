@@ -20,7 +20,7 @@ LIB_PATH = os.path.join(_HERE, "libmrq.so")
 
 MRQ_OK = 0
 MRQ_EINVAL, MRQ_ENOMEM, MRQ_ECUDA, MRQ_EFORMAT, MRQ_EIO, MRQ_ETIMEDOUT = -1, -2, -3, -4, -5, -6
-MODE_MRQ, MODE_MRQ_PLUS = 0, 1
+MODE_MRQ, MODE_MRQ_PLUS, MODE_SQ8 = 0, 1, 2
 PREC_FP32, PREC_BF16, PREC_BF16X3 = 0, 1, 2
 SCAN_PAIRS, SCAN_BATCHED, SCAN_AUTO, SCAN_BATCHED_TC = 0, 1, 2, 3
 
@@ -51,7 +51,7 @@ class SearchOpts(C.Structure):
     _fields_ = [("eps0", C.c_float), ("m", C.c_float), ("mode", C.c_int),
                 ("precision", C.c_int), ("query_bits", C.c_int), ("batched", C.c_int),
                 ("profile", C.c_int), ("graph", C.c_int), ("refine", C.c_int),
-                ("cuda_stream", C.c_void_p)]
+                ("rerank", C.c_int), ("cuda_stream", C.c_void_p)]
 
 
 class ServerOpts(C.Structure):
@@ -170,12 +170,13 @@ def mrq_build_opts(seed: int = 1, kmeans_iters: int = 20, init_centroids=None, i
 
 def mrq_search_opts(eps0: float = 1.9, m: float = 4.0, mode: int = MODE_MRQ_PLUS,
                     precision: int = PREC_FP32, query_bits: int = 0, batched: int = 0,
-                    profile: int = 0, graph: int = 0, stream=None, refine: int = 0) -> SearchOpts:
+                    profile: int = 0, graph: int = 0, stream=None, refine: int = 0,
+                    rerank: int = 500) -> SearchOpts:
     o = SearchOpts()
     _lib.mrq_search_opts_default(C.byref(o))
     o.eps0, o.m, o.mode, o.precision = eps0, m, mode, precision
     o.query_bits, o.batched, o.profile, o.graph = query_bits, batched, profile, graph
-    o.refine = refine
+    o.refine, o.rerank = refine, rerank
     if stream is not None:
         o.cuda_stream = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
     return o
@@ -322,6 +323,8 @@ _FIELD_SHAPES = {
     "XD__": (np.float32, lambda i: (i.n, i.d)), "XR__": (np.float32, lambda i: (i.n, i.D - i.d)),
     "XN2_": (np.float32, lambda i: (i.n,)),
     "FRE1": (np.float32, lambda i: (i.n,)), "FER1": (np.float32, lambda i: (i.n,)),
+    "SQ8C": (np.uint8, lambda i: (i.n, i.d)), "SQ8L": (np.float32, lambda i: (i.d,)),
+    "SQ8S": (np.float32, lambda i: (i.d,)),
 }
 
 

@@ -69,7 +69,10 @@ mrq_search_opts resolve(const mrq_search_opts* opt) {
   mrq_search_opts_default(&o);
   if (opt) o = *opt;
   MRQ_REQUIRE(o.eps0 >= 0.f && o.m >= 0.f, "eps0 and m must be >= 0");
-  MRQ_REQUIRE(o.mode == MRQ_MODE_MRQ || o.mode == MRQ_MODE_MRQ_PLUS, "mode must be MRQ_MODE_MRQ or MRQ_MODE_MRQ_PLUS");
+  MRQ_REQUIRE(o.mode == MRQ_MODE_MRQ || o.mode == MRQ_MODE_MRQ_PLUS || o.mode == MRQ_MODE_SQ8,
+              "mode must be MRQ_MODE_MRQ, MRQ_MODE_MRQ_PLUS or MRQ_MODE_SQ8");
+  MRQ_REQUIRE(o.mode != MRQ_MODE_SQ8 || (o.rerank >= 1 && o.rerank <= 65536),
+              "rerank must be in [1, 65536]");
   MRQ_REQUIRE(o.precision >= MRQ_PREC_FP32 && o.precision <= MRQ_PREC_BF16X3, "unknown precision");
   MRQ_REQUIRE(o.query_bits >= 0 && o.query_bits <= 8, "query_bits must be in [0, 8]");
   MRQ_REQUIRE(o.batched >= MRQ_SCAN_PAIRS && o.batched <= MRQ_SCAN_BATCHED_TC,
@@ -139,6 +142,7 @@ void mrq_search_opts_default(mrq_search_opts* opt) {
   opt->precision = MRQ_PREC_FP32;
   opt->query_bits = 0;
   opt->batched = 0;
+  opt->rerank = 500;
   opt->cuda_stream = nullptr;
 }
 
@@ -194,8 +198,12 @@ int mrq_search(mrq_index* idx, const float* queries, int64_t nq, int k, int npro
     MRQ_REQUIRE(queries && ids && dists, "queries, ids and dists must not be NULL");
     const mrq_search_opts o = resolve(opt);
     check_refine(idx, o, k, nprobe);
+    if (o.mode == MRQ_MODE_SQ8) {
+      MRQ_REQUIRE(k <= 128 && k <= o.rerank, "MRQ_MODE_SQ8 needs k <= 128 and k <= rerank");
+    }
     use_device(idx);
     cudaStream_t st = stream_of(o);
+    if (o.mode == MRQ_MODE_SQ8) mrq::ensure_sq8(idx, st);  // before any graph capture
     const bool qdev = on_device(queries);
     const bool odev = on_device(ids);
     MRQ_REQUIRE(odev == on_device(dists), "ids and dists must both be host or both be device memory");
@@ -233,7 +241,8 @@ int mrq_search(mrq_index* idx, const float* queries, int64_t nq, int k, int npro
     const bool use_graph = o.graph && !o.profile && (qdev || pinned_host(queries)) &&
                            (odev || (pinned_host(ids) && pinned_host(dists)));
     mrq_index::GraphKey key{queries, ids, dists, nq, k, nprobe, o.mode, o.precision,
-                            o.query_bits, o.batched, o.refine, o.eps0, o.m};
+                            o.query_bits, o.batched, o.refine,
+                            o.mode == MRQ_MODE_SQ8 ? o.rerank : 0, o.eps0, o.m};
     // tensor-core forms read each query once (the bf16 split), so page-locked host
     // queries are read in place through their device mapping instead of copied first
     const float* qmap = nullptr;
@@ -383,12 +392,14 @@ int mrq_autotune(mrq_index* idx, const float* queries, int64_t nq, int k, int np
     }
     const int wds = idx->words, nch = idx->d / 32;
     const bool refine = mrq::refine_active(idx, o);  // scans pair by pair
-    const bool can_batch = !refine && o.query_bits > 0 && wds <= 16 && (wds & (wds - 1)) == 0 &&
+    const bool sq8 = o.mode == MRQ_MODE_SQ8;          // so does MR-SQ
+    const bool can_batch = !refine && !sq8 && o.query_bits > 0 && wds <= 16 && (wds & (wds - 1)) == 0 &&
                            (idx->bits & (idx->bits - 1)) == 0 && (nch & (nch - 1)) == 0 &&
                            !(wds == 16 && idx->d == 32);
     if (can_batch)
       for (int g : {4, 8, 16}) cands.push_back({MRQ_SCAN_BATCHED, 4096, g});
-    if (!refine && mrq::tc_available() && mrq::scan_tc_supported(idx->d, idx->bits, o.query_bits))
+    if (!refine && !sq8 && mrq::tc_available() &&
+        mrq::scan_tc_supported(idx->d, idx->bits, o.query_bits))
       cands.push_back({MRQ_SCAN_BATCHED_TC, 4096, mrq::TC_SCAN_GROUP});
     const mrq::ScanConfig dflt = mrq::scan_config(idx, o, nq, k, nprobe);
     result->consistent = 1;
@@ -418,7 +429,8 @@ int mrq_autotune(mrq_index* idx, const float* queries, int64_t nq, int k, int np
     result->n_tried = (int)cands.size();
     {
       std::lock_guard<std::mutex> lk(idx->tune_mu);
-      idx->tuned[std::make_tuple(mrq::scan_kclass(k), nprobe, o.query_bits, refine ? 1 : 0)] = pick;
+      idx->tuned[std::make_tuple(mrq::scan_kclass(k), nprobe, o.query_bits, mrq::scan_variant(idx, o))] =
+          pick;
     }
     idx->graph_valid = false;  // a captured graph may hold the old configuration
   });
@@ -568,6 +580,10 @@ static void export_field(const mrq_index* idx, const std::string& f, std::vector
     out = d2h_bytes(lv.p, (size_t)n * d, st);
     MRQ_CUDA(cudaStreamSynchronize(st));
     dtype = DT_U8;
+  } else if (f == "SQ8C" || f == "SQ8L" || f == "SQ8S") {
+    mrq::ensure_sq8(idx, st);
+    if (f == "SQ8C") { out = d2h_bytes(idx->sq_codes.p, (size_t)n * d, st); dtype = DT_U8; }
+    else { out = d2h_bytes(f == "SQ8L" ? idx->sq_lo.p : idx->sq_delta.p, d, st); dtype = DT_F32; }
   } else if (f == "FADD" || f == "FRES" || f == "FERR" ||
              ((f == "FRE1" || f == "FER1") && idx->fres1.p)) {
     const float* src = f == "FADD" ? idx->fadd.p : f == "FRES" ? idx->fres.p

@@ -182,11 +182,16 @@ struct mrq_index {
   // padded factors of the sign plane (the 1-bit code of o'), held when bits > 1: the
   // first level of the 1 bit + refinement scan
   mrq::DevBuf<float> fres1, ferr1;
+  // MR-SQ (MRQ_MODE_SQ8), made on first use from xd / xr: 8-bit codes of x_d' (n x d,
+  // list-major), the per-dimension grid (lo, delta) and |x_r|^2 (n)
+  mutable std::mutex sq_mu;
+  mutable mrq::DevBuf<uint8_t> sq_codes;
+  mutable mrq::DevBuf<float> sq_lo, sq_delta, sq_xr2;
   mrq::DevBuf<float> xd, xr, xn2;         // list-major, unpadded
   mrq::Workspace ws;
   int64_t last_nq = 0;
   mutable bool last_stats_dev = false;
-  // autotuned scan configurations, keyed by (k class, nprobe, query bits, refinement)
+  // autotuned scan configurations, keyed by (k class, nprobe, query bits, scan_variant)
   std::mutex tune_mu;
   std::map<std::tuple<int, int, int, int>, mrq::ScanConfig> tuned;  // last search's counters still in ws.stats (device)
   mutable std::vector<int64_t> last_stats;        // nq x 3 host copy of the last search's counters
@@ -202,12 +207,13 @@ struct mrq_index {
     void* ids;
     void* dists;
     int64_t nq;
-    int k, nprobe, mode, precision, query_bits, batched, refine;
+    int k, nprobe, mode, precision, query_bits, batched, refine, rerank;
     float eps0, m;
     bool operator==(const GraphKey& o) const {
       return q == o.q && ids == o.ids && dists == o.dists && nq == o.nq && k == o.k &&
              nprobe == o.nprobe && mode == o.mode && precision == o.precision &&
              query_bits == o.query_bits && batched == o.batched && refine == o.refine &&
+             rerank == o.rerank &&
              eps0 == o.eps0 && m == o.m;
     }
   };
@@ -280,10 +286,18 @@ void search_batch(mrq_index* idx, Workspace& ws, const float* q_dev, int64_t nq,
                   int64_t* stats_dev, cudaStream_t st);
 void project_batch(mrq_index* idx, Workspace& ws, const float* q_dev, int64_t nq, int precision,
                    float* qd, float* qr, cudaStream_t st, __nv_bfloat16* probe_bf = nullptr);
+// MR-SQ arrays of the index (made once, on the given stream, then synchronised)
+void ensure_sq8(const mrq_index* idx, cudaStream_t st);
+
 // the search runs the 1 bit + refinement stage 1 (bits > 1 and refine = 1)
 constexpr int REFINE_MAX_NPROBE = 4096;  // stage 1b's probe table: 12 B of shared memory each
 inline bool refine_active(const mrq_index* idx, const mrq_search_opts& o) {
-  return o.refine != 0 && idx->bits > 1;
+  return o.refine != 0 && idx->bits > 1 && o.mode != MRQ_MODE_SQ8;
+}
+
+// which scan a search runs, for the autotuner's key: 0 one-stage, 1 refinement, 2 MR-SQ
+inline int scan_variant(const mrq_index* idx, const mrq_search_opts& o) {
+  return o.mode == MRQ_MODE_SQ8 ? 2 : refine_active(idx, o) ? 1 : 0;
 }
 
 // the scan configuration a search uses; a ScopedScanConfig forces one on this thread

@@ -2000,6 +2000,204 @@ __global__ void __launch_bounds__(FW_WARPS * 32) k_fin_topk(FinParams P) {
   }
 }
 
+// ------------------------------------------------------------------ MR-SQ (Exp-5)
+//
+// 8-bit scalar quantization of x_d' (per dimension: 256 levels from the base's min to
+// max, round to nearest, decided in float32), the estimate
+// |q_d' - x_hat|^2 + |x_r|^2 + |q_r|^2, a fixed rerank range instead of error bounds.
+
+// column min / max of X (n x d) as order-preserving keys: mm[c] = min, mm[d + c] = max
+__global__ void k_sq8_minmax(const float* __restrict__ X, int64_t n, int d, int64_t rows_per,
+                             unsigned int* __restrict__ mm) {
+  const int c = blockIdx.x * 32 + (threadIdx.x & 31);
+  const int64_t r0 = (int64_t)blockIdx.y * rows_per + (threadIdx.x >> 5);
+  const int64_t r1 = min(n, (int64_t)(blockIdx.y + 1) * rows_per);
+  if (c >= d) return;
+  uint32_t lo = 0xffffffffu, hi = 0u;
+  for (int64_t r = r0; r < r1; r += blockDim.x >> 5) {
+    const uint32_t k = fkey(X[r * d + c]);
+    lo = min(lo, k);
+    hi = max(hi, k);
+  }
+  atomicMin(mm + c, lo);
+  atomicMax(mm + d + c, hi);
+}
+
+__global__ void k_sq8_grid(const unsigned int* __restrict__ mm, int d, float* __restrict__ lo,
+                           float* __restrict__ delta) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= d) return;
+  const float a = fkey_inv(mm[c]), b = fkey_inv(mm[d + c]);
+  lo[c] = a;
+  delta[c] = (b - a) / 255.f;
+}
+
+__global__ void k_sq8_encode(const float* __restrict__ X, int64_t n, int d,
+                             const float* __restrict__ lo, const float* __restrict__ delta,
+                             uint8_t* __restrict__ codes) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n * d) return;
+  const int c = (int)(i % d);
+  const float dl = delta[c];
+  int v = 0;
+  if (dl > 0.f) {
+    const float t = (X[i] - lo[c]) / dl;
+    v = (int)floorf(t + 0.5f);
+    v = min(max(v, 0), 255);
+  }
+  codes[i] = (uint8_t)v;
+}
+
+__global__ void k_sq8_rownorm(const float* __restrict__ X, int64_t n, int r, float* __restrict__ out) {
+  const int64_t p = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (p >= n) return;
+  float s = 0.f;
+  for (int c = threadIdx.x & 31; c < r; c += 32) s = fmaf(X[p * r + c], X[p * r + c], s);
+  s = warp_sum(s);
+  if ((threadIdx.x & 31) == 0) out[p] = s;
+}
+
+struct Sq8Params {
+  const float* qd;       // nq x d
+  const float* qstat;    // nq x 4 (|q_r|^2 first)
+  const int32_t* plist;  // nq x nprobe
+  const int64_t* loff;
+  const uint8_t* codes;  // n x d, list-major
+  const float* lo;
+  const float* delta;
+  const float* xr2;
+  int d, nprobe;
+  int64_t npairs, cap;
+  const int64_t* items;  // (pair << 32 | chunk) work items, or NULL: one per pair
+  const int* nitems;
+  int chunk;
+  unsigned int* work;
+  unsigned int* qcnt;
+  int32_t* spos;
+  float* slb;
+};
+
+// one warp per (query, list) work item, one lane per candidate: the candidate's d code
+// bytes in 16-byte loads, (q_d'_i - lo_i) and delta_i from shared memory; every
+// candidate's (position, estimate) is appended to the query's region
+__global__ void __launch_bounds__(SCAN_WARPS * 32) k_scan_sq8(Sq8Params P) {
+  extern __shared__ float2 sqa[];  // per warp: d x (q_d'_i - lo_i, delta_i)
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int d = P.d;
+  float2* a = sqa + (int64_t)wid * d;
+  const int64_t n_items = P.items ? (int64_t)*P.nitems : P.npairs;
+  while (true) {
+    unsigned int it = 0;
+    if (lane == 0) it = atomicAdd(P.work, 1u);
+    it = __shfl_sync(0xffffffffu, it, 0);
+    if ((int64_t)it >= n_items) break;
+    int64_t w = it, c_lo = 0, c_hi = -1;
+    if (P.items) {
+      const int64_t v = P.items[it];
+      w = v >> 32;
+      c_lo = (v & 0xffffffffll) * P.chunk;
+      c_hi = c_lo + P.chunk;
+    }
+    const int64_t q = w / P.nprobe;
+    const int j = P.plist[w];
+    __syncwarp();
+    for (int i = lane; i < d; i += 32) a[i] = make_float2(P.qd[q * d + i] - P.lo[i], P.delta[i]);
+    __syncwarp();
+    const float qr2 = P.qstat[q * 4 + 0];
+    const int64_t lb0 = P.loff[j];
+    const int64_t lsize = P.loff[j + 1] - lb0;
+    const int64_t size = c_hi < 0 ? lsize : min(lsize, c_hi);
+    for (int64_t b0 = c_lo; b0 < size; b0 += 32) {
+      const int64_t idx = b0 + lane;
+      const bool valid = idx < size;
+      float est = 0.f;
+      int64_t p = lb0 + idx;
+      if (valid) {
+        const uint4* row = reinterpret_cast<const uint4*>(P.codes + p * d);
+        float s = 0.f;
+        for (int g = 0; g < d / 16; ++g) {
+          const uint4 v = __ldg(row + g);
+          const uint32_t wds[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+#pragma unroll
+            for (int t = 0; t < 4; ++t) {
+              const float2 av = a[g * 16 + e * 4 + t];
+              const float x = av.x - (float)((wds[e] >> (8 * t)) & 255u) * av.y;
+              s = fmaf(x, x, s);
+            }
+          }
+        }
+        est = s + __ldg(P.xr2 + p) + qr2;
+      }
+      const unsigned vm = __ballot_sync(0xffffffffu, valid);
+      unsigned base = 0;
+      if (lane == 0 && vm) base = atomicAdd(P.qcnt + q, (unsigned)__popc(vm));
+      base = __shfl_sync(0xffffffffu, base, 0);
+      if (valid) {
+        const int64_t at = q * P.cap + base + __popc(vm & ((1u << lane) - 1));
+        P.spos[at] = (int32_t)p;
+        P.slb[at] = est;
+      }
+    }
+  }
+}
+
+// the rerank range: the R smallest estimates of each query by (estimate, id), compacted
+// (positions) into s2pos; qm2 = their number
+__global__ void __launch_bounds__(FW_WARPS * 32) k_sq8_select(FinParams P, int R) {
+  __shared__ int hist_all[FW_WARPS][256];
+  __shared__ float filt_all[FW_WARPS][FW_FILT];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int64_t q = (int64_t)blockIdx.x * FW_WARPS + wid;
+  if (q >= P.nq) return;
+  const int64_t base = q * P.cap;
+  const int M = (int)min((int64_t)P.qcnt[q], P.cap);
+  const float* est = P.slb + base;
+  const int32_t* pos = P.spos + base;
+  int32_t* out = P.s2pos + base;
+  int n;
+  if (M <= R) {
+    n = warp_compact(pos, M, out, [&](int) { return true; });
+  } else {
+    const uint32_t T = warp_kth_filtered(est, M, R, FINF, filt_all[wid], FW_FILT, hist_all[wid]);
+    n = warp_compact(pos, M, out, [&](int i) { return fkey(est[i]) < T; });
+    // estimates equal to the R-th: the lowest ids first
+    uint32_t last = 0u;
+    bool first = true;
+    while (n < R) {
+      uint32_t best = 0xffffffffu;
+      int bpos = -1;
+      for (int i = lane; i < M; i += 32) {
+        if (fkey(est[i]) == T) {
+          const uint32_t id = (uint32_t)P.ids[pos[i]];
+          if ((first || id > last) && id < best) { best = id; bpos = pos[i]; }
+        }
+      }
+#pragma unroll
+      for (int o = 16; o; o >>= 1) {
+        const uint32_t ob = __shfl_xor_sync(0xffffffffu, best, o);
+        const int op = __shfl_xor_sync(0xffffffffu, bpos, o);
+        if (ob < best) { best = ob; bpos = op; }
+      }
+      if (best == 0xffffffffu) break;
+      if (lane == 0) out[n] = bpos;
+      ++n;
+      last = best;
+      first = false;
+    }
+    __syncwarp();
+  }
+  if (lane == 0) {
+    P.qm2[q] = n;
+    if (P.stats) {
+      P.stats[q * 3 + 0] = (int64_t)M;
+      P.stats[q * 3 + 1] = n;
+      P.stats[q * 3 + 2] = n;
+    }
+  }
+}
+
 int g_num_sms = 0;
 int num_sms() {
   if (!g_num_sms) {
@@ -2170,7 +2368,7 @@ ScanConfig scan_config(mrq_index* idx, const mrq_search_opts& o, int64_t nq, int
   {
     std::lock_guard<std::mutex> lk(idx->tune_mu);
     auto it = idx->tuned.find(std::make_tuple(scan_kclass(k), nprobe, o.query_bits,
-                                              refine_active(idx, o) ? 1 : 0));
+                                              scan_variant(idx, o)));
     if (it != idx->tuned.end()) return it->second;
   }
   // untuned rule: batch when each probed list is shared by many queries of the batch
@@ -2312,6 +2510,55 @@ void search_batch(mrq_index* idx, Workspace& ws, const float* q, int64_t nq, int
     idx->launches += 3;
     return max_items;
   };
+  if (o.mode == MRQ_MODE_SQ8) {
+    // MR-SQ: the SQ8 scan appends every probed candidate's estimate, the rerank range is
+    // selected, reranked exactly and the top-k taken
+    const int64_t np_ = nq * nprobe;
+    Sq8Params qp{};
+    qp.qd = ws.qd.p; qp.qstat = ws.qstat.p; qp.plist = ws.plist.p; qp.loff = idx->loff.p;
+    qp.codes = idx->sq_codes.p; qp.lo = idx->sq_lo.p; qp.delta = idx->sq_delta.p;
+    qp.xr2 = idx->sq_xr2.p; qp.d = d; qp.nprobe = nprobe; qp.npairs = np_; qp.cap = cap;
+    qp.work = ws.work.p; qp.qcnt = ws.qcnt.p; qp.spos = ws.spos.p; qp.slb = ws.slb.p;
+    int64_t grid_items = np_;
+    if (idx->max_list > cfg.chunk) {
+      grid_items = build_items(np_, 1);
+      qp.items = sp.items; qp.nitems = sp.nitems; qp.chunk = sp.chunk;
+    }
+    const size_t qsm = (size_t)SCAN_WARPS * d * sizeof(float2);
+    ensure_smem((const void*)k_scan_sq8, qsm);
+    const int per_sm = occupancy((const void*)k_scan_sq8, SCAN_WARPS * 32, qsm);
+    const int blocks = (int)std::max<int64_t>(
+        1, std::min<int64_t>((grid_items + SCAN_WARPS - 1) / SCAN_WARPS, (int64_t)num_sms() * per_sm));
+    k_scan_sq8<<<blocks, SCAN_WARPS * 32, qsm, st>>>(qp);
+    MRQ_CHECK_LAUNCH();
+    mark(idx, MRQ_STAGE_TAU_A, st);
+    FinParams fp{};
+    fp.qd = ws.qd.p; fp.qr = ws.qr.p; fp.qstat = ws.qstat.p; fp.plist = ws.plist.p;
+    fp.loff = idx->loff.p; fp.xd = idx->xd.p; fp.xr = idx->xr.p; fp.xn2 = idx->xn2.p;
+    fp.ids = idx->ids.p; fp.d = d; fp.r = r; fp.nprobe = nprobe; fp.k = k; fp.mode = o.mode;
+    fp.m = o.m; fp.cap = cap; fp.qcnt = ws.qcnt.p; fp.spos = ws.spos.p; fp.slb = ws.slb.p;
+    fp.sub = ws.sub.p; fp.s2pos = ws.s2pos.p; fp.s2a = ws.s2a.p; fp.s2b = ws.s2b.p;
+    fp.out_ids = out_ids; fp.out_d = out_d; fp.stats = stats;
+    ws.qm2.reserve(nq);
+    fp.qm2 = ws.qm2.p; fp.nq = nq;
+    const unsigned gw = ceil_div(nq, FW_WARPS);
+    k_sq8_select<<<gw, FW_WARPS * 32, 0, st>>>(fp, o.rerank);
+    MRQ_CHECK_LAUNCH();
+    for (int sidx = MRQ_STAGE_STAGE2; sidx <= MRQ_STAGE_EXACT; ++sidx) mark(idx, sidx, st);
+    fp.spos = ws.s2pos.p;  // the rerank range
+    const size_t esm = (size_t)(((d + 3) & ~3) + r) * 4;
+    ensure_smem((const void*)k_fin_exact, esm);
+    k_fin_exact<<<(unsigned)nq, 256, esm, st>>>(fp);
+    MRQ_CHECK_LAUNCH();
+    mark(idx, MRQ_STAGE_TOPK, st);
+    k_fin_topk<<<gw, FW_WARPS * 32, 0, st>>>(fp);
+    MRQ_CHECK_LAUNCH();
+    mark(idx, MRQ_NSTAGES, st);
+    if (idx->prof_on) idx->prof_batches++;
+    // qstats, the probe (as below), the scan, select, exact, top-k
+    idx->launches += (fused ? 4 : tc_probe ? 5 : 6) - 2 + 4;
+    return;
+  }
   // batched forms: quantized query; the popcount kernel needs code words a power of two
   // (bits in {1,2,4,8}) up to 16, the tensor-core kernel bits <= 4 and query_bits <= 4
   const int wds = idx->words;
@@ -2492,6 +2739,37 @@ void search_batch(mrq_index* idx, Workspace& ws, const float* q, int64_t nq, int
   // projection), select + refine (one kernel in the fused probe), scan, the first
   // finalize phase
   idx->launches += fused ? 4 : tc_probe ? 5 : 6;
+}
+
+void ensure_sq8(const mrq_index* idx, cudaStream_t st) {
+  std::lock_guard<std::mutex> lk(idx->sq_mu);
+  if (idx->sq_codes.p) return;
+  const int64_t n = idx->n;
+  const int d = idx->d, r = idx->D - idx->d;
+  DevBuf<unsigned int> mm(2 * (size_t)d);
+  MRQ_CUDA(cudaMemsetAsync(mm.p, 0xff, 4 * (size_t)d, st));
+  MRQ_CUDA(cudaMemsetAsync(mm.p + d, 0, 4 * (size_t)d, st));
+  const int64_t rows_per = 8192;
+  k_sq8_minmax<<<dim3(ceil_div(d, 32), ceil_div(n, rows_per)), 256, 0, st>>>(idx->xd.p, n, d,
+                                                                            rows_per, mm.p);
+  MRQ_CHECK_LAUNCH();
+  DevBuf<float> lo(d), delta(d), xr2(std::max<int64_t>(n, 1));
+  DevBuf<uint8_t> codes((size_t)n * d);
+  k_sq8_grid<<<ceil_div(d, 256), 256, 0, st>>>(mm.p, d, lo.p, delta.p);
+  MRQ_CHECK_LAUNCH();
+  k_sq8_encode<<<ceil_div(n * d, 256), 256, 0, st>>>(idx->xd.p, n, d, lo.p, delta.p, codes.p);
+  MRQ_CHECK_LAUNCH();
+  if (r > 0) {
+    k_sq8_rownorm<<<ceil_div(n, 8), 256, 0, st>>>(idx->xr.p, n, r, xr2.p);
+    MRQ_CHECK_LAUNCH();
+  } else {
+    MRQ_CUDA(cudaMemsetAsync(xr2.p, 0, 4 * (size_t)n, st));
+  }
+  MRQ_CUDA(cudaStreamSynchronize(st));
+  idx->sq_lo = std::move(lo);
+  idx->sq_delta = std::move(delta);
+  idx->sq_xr2 = std::move(xr2);
+  idx->sq_codes = std::move(codes);
 }
 
 size_t batch_scratch_bytes(const mrq_index* idx, int64_t nq, int k, int nprobe) {
