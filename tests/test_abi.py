@@ -88,3 +88,47 @@ def test_build_script_targets_sm103a():
     sys.path.insert(0, os.path.join(ROOT, "paper_2411_06158_gb300"))
     import build_lib
     assert build_lib.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]
+
+
+STRUCTS = {  # C typedef -> ctypes mirror in the binding
+    "mrq_build_opts": "BuildOpts", "mrq_search_opts": "SearchOpts",
+    "mrq_index_info_t": "IndexInfo", "mrq_tune_result_t": "TuneResult",
+    "mrq_server_opts": "ServerOpts", "mrq_server_stats_t": "ServerStats",
+}
+
+
+def test_struct_layouts_match_the_header(lib, tmp_path):
+    """Every option / result struct of include/mrq.h has the size and field offsets of its
+    ctypes mirror (a C program built against the header prints them)."""
+    import shutil
+    import subprocess
+    if shutil.which("gcc") is None:
+        pytest.skip("no C compiler")
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "mrq.h"', 'int main(void) {']
+    for cname, pyname in STRUCTS.items():
+        st = getattr(lib, pyname)
+        lines.append(f'  printf("{cname} size %zu\\n", sizeof({cname}));')
+        for f, _ in st._fields_:
+            lines.append(f'  printf("{cname} {f} %zu\\n", offsetof({cname}, {f}));')
+    lines += ['  return 0;', '}']
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)],
+                   check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {tuple(l.split()[:2]): int(l.split()[2]) for l in out if l.strip()}
+    for cname, pyname in STRUCTS.items():
+        st = getattr(lib, pyname)
+        assert got[(cname, "size")] == C.sizeof(st), cname
+        for f, _ in st._fields_:
+            assert got[(cname, f)] == getattr(st, f).offset, f"{cname}.{f}"
+
+
+def test_new_option_defaults(lib):
+    o = lib.SearchOpts()
+    lib._lib.mrq_search_opts_default(C.byref(o))
+    assert o.refine == 0 and o.rerank == 500 and o.graph == 0 and o.batched == 0
+    b = lib.BuildOpts()
+    lib._lib.mrq_build_opts_default(C.byref(b))
+    assert b.auto_d_variance == pytest.approx(0.8)
