@@ -411,7 +411,8 @@ def run_variance_report(args):
 
 def run_precision_report(args):
     """Precision form: for d in {64, 128, 256} and each projection precision (float32
-    CUDA cores, bf16 and split hi+lo bf16 tensor cores), the max and mean relative error
+    CUDA cores, bf16, split hi+lo bf16 and row-scaled e4m3 tensor cores), the max and mean
+    relative error
     of the projected query coordinates [q_d' | q_r] against a float64 projection with
     the index's exported W and mu (relative to |q - mu|), the error of the stage-1
     estimate dis' it implies, and recall@10 at a fixed nprobe."""
@@ -445,7 +446,7 @@ def run_precision_report(args):
         scale = np.linalg.norm(qc, axis=1, keepdims=True)
         ids_fp32 = None
         for name, prec in (("fp32", mrq.PREC_FP32), ("bf16", mrq.PREC_BF16),
-                           ("bf16x3", mrq.PREC_BF16X3)):
+                           ("bf16x3", mrq.PREC_BF16X3), ("fp8", mrq.PREC_FP8)):
             o = mrq.mrq_search_opts(precision=prec, query_bits=4, batched=mrq.SCAN_AUTO)
             got = mrq.mrq_project(idx, q_t, o).cpu().numpy().astype(np.float64)
             rel = np.abs(got - ref) / scale
@@ -518,6 +519,7 @@ def main(argv=None):
         "plain_q4": mrq.mrq_search_opts(query_bits=4, stream=stream),
         "bf16x3_q4": mrq.mrq_search_opts(query_bits=4, precision=mrq.PREC_BF16X3, stream=stream),
         "bf16_q4": mrq.mrq_search_opts(query_bits=4, precision=mrq.PREC_BF16, stream=stream),
+        "fp8_q4": mrq.mrq_search_opts(query_bits=4, precision=mrq.PREC_FP8, stream=stream),
         "batched_bf16_q4": mrq.mrq_search_opts(query_bits=4, precision=mrq.PREC_BF16, batched=1,
                                                graph=1, stream=stream),
         "batched_tc_bf16_q4": mrq.mrq_search_opts(query_bits=4, precision=mrq.PREC_BF16,

@@ -57,6 +57,10 @@ extern "C" {
 #define MRQ_PREC_FP32 0   /* float32 CUDA-core GEMM */
 #define MRQ_PREC_BF16 1   /* one bf16 tensor-core product, fp32 accumulate */
 #define MRQ_PREC_BF16X3 2 /* split hi+lo bf16: hi*hi + hi*lo + lo*hi, fp32 accumulate */
+#define MRQ_PREC_FP8 3    /* row-scaled e4m3: each centred query row and each row of W scaled
+                             so that its largest magnitude is 448, one kind::f8f6f4 product,
+                             fp32 accumulate, the two row scales applied in the epilogue (the
+                             probe then runs in bf16 on the projected q_d').  Needs D % 16 == 0 */
 
 typedef struct mrq_index mrq_index; /* opaque; owned by the library */
 
@@ -183,7 +187,8 @@ int mrq_project(mrq_index* index, const float* queries, int64_t nq,
 
 /* Largest scratch, in bytes, that mrq_project_noalloc may use: its bf16 copy
  * of the centred queries takes 2 * nq * D bytes at MRQ_PREC_BF16 and
- * 4 * nq * D bytes at MRQ_PREC_BF16X3 (hi and lo halves). */
+ * 4 * nq * D bytes at MRQ_PREC_BF16X3 (hi and lo halves); its e4m3 copy at
+ * MRQ_PREC_FP8 takes nq * D bytes (rounded up to 256) plus 4 * nq of row scales. */
 #define MRQ_PROJECT_NOALLOC_MAX_BYTES 8388608
 
 /*
@@ -203,8 +208,9 @@ int mrq_project(mrq_index* index, const float* queries, int64_t nq,
  * Scratch: MRQ_PREC_FP32 needs none.  The tensor-core precisions stage the
  * bf16 operand of the query in a fixed static device array of
  * MRQ_PROJECT_NOALLOC_MAX_BYTES bytes that the library owns; a request that
- * needs more (nq * D > 4194304 at MRQ_PREC_BF16, > 2097152 at MRQ_PREC_BF16X3)
- * returns MRQ_EINVAL without launching anything: split the batch.  The
+ * needs more (nq * D > 4194304 at MRQ_PREC_BF16, > 2097152 at MRQ_PREC_BF16X3,
+ * about 8.4e6 at MRQ_PREC_FP8) returns MRQ_EINVAL without launching anything: split
+ * the batch.  The
  * pipeline error word in that array is cleared at the start of every call;
  * nothing else in it has to start at zero.
  *

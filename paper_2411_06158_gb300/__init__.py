@@ -21,7 +21,7 @@ LIB_PATH = os.path.join(_HERE, "libmrq.so")
 MRQ_OK = 0
 MRQ_EINVAL, MRQ_ENOMEM, MRQ_ECUDA, MRQ_EFORMAT, MRQ_EIO, MRQ_ETIMEDOUT = -1, -2, -3, -4, -5, -6
 MODE_MRQ, MODE_MRQ_PLUS, MODE_SQ8 = 0, 1, 2
-PREC_FP32, PREC_BF16, PREC_BF16X3 = 0, 1, 2
+PREC_FP32, PREC_BF16, PREC_BF16X3, PREC_FP8 = 0, 1, 2, 3
 SCAN_PAIRS, SCAN_BATCHED, SCAN_AUTO, SCAN_BATCHED_TC = 0, 1, 2, 3
 
 EXPORTS = [

@@ -73,7 +73,7 @@ mrq_search_opts resolve(const mrq_search_opts* opt) {
               "mode must be MRQ_MODE_MRQ, MRQ_MODE_MRQ_PLUS or MRQ_MODE_SQ8");
   MRQ_REQUIRE(o.mode != MRQ_MODE_SQ8 || (o.rerank >= 1 && o.rerank <= 65536),
               "rerank must be in [1, 65536]");
-  MRQ_REQUIRE(o.precision >= MRQ_PREC_FP32 && o.precision <= MRQ_PREC_BF16X3, "unknown precision");
+  MRQ_REQUIRE(o.precision >= MRQ_PREC_FP32 && o.precision <= MRQ_PREC_FP8, "unknown precision");
   MRQ_REQUIRE(o.query_bits >= 0 && o.query_bits <= 8, "query_bits must be in [0, 8]");
   MRQ_REQUIRE(o.batched >= MRQ_SCAN_PAIRS && o.batched <= MRQ_SCAN_BATCHED_TC,
               "batched must be MRQ_SCAN_PAIRS, MRQ_SCAN_BATCHED, MRQ_SCAN_AUTO or MRQ_SCAN_BATCHED_TC");
@@ -549,7 +549,8 @@ int mrq_index_info(const mrq_index* idx, mrq_index_info_t* info) {
     info->nlist = idx->nlist;
     info->max_list = idx->max_list;
     info->device_bytes = (int64_t)(idx->mu.bytes() + idx->lam.bytes() + idx->W.bytes() +
-                                   idx->W2.bytes() + idx->cent2.bytes() + idx->cent.bytes() +
+                                   idx->W2.bytes() + idx->W8.bytes() + idx->W8s.bytes() +
+                                   idx->cent2.bytes() + idx->cent.bytes() +
                                    idx->cent_n2.bytes() + idx->loff.bytes() + idx->ploff.bytes() +
                                    idx->ids.bytes() + idx->codes.bytes() + idx->fadd.bytes() +
                                    idx->fres.bytes() + idx->ferr.bytes() + idx->fres1.bytes() +

@@ -608,6 +608,11 @@ void make_bf16_split(mrq_index* idx, cudaStream_t st) {
   idx->W2.alloc(2 * nn);
   k_bf16_split<<<ceil_div(nn, 256), 256, 0, st>>>(idx->W.p, nn, idx->W2.p);
   MRQ_CHECK_LAUNCH();
+  if (idx->D % 16 == 0) {  // the FP8 projection's operand: 16-byte e4m3 rows
+    idx->W8.alloc((size_t)nn);
+    idx->W8s.alloc(idx->D);
+    quantize_rows_fp8(idx->W.p, idx->D, idx->D, idx->D, nullptr, idx->W8.p, idx->W8s.p, st);
+  }
   int64_t nc = (int64_t)idx->nlist * idx->d;
   idx->cent2.alloc(2 * nc);
   k_bf16_split<<<ceil_div(nc, 256), 256, 0, st>>>(idx->cent.p, nc, idx->cent2.p);

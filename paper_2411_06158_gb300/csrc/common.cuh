@@ -79,6 +79,8 @@ struct Workspace {
   DevBuf<float> qd, qr;    // projected queries
   DevBuf<float> qstat;     // nq x 4: |q_r|^2, sigma, |q_p|^2, unused
   DevBuf<__nv_bfloat16> qbf;  // nq x D bf16 hi/lo split queries (tensor-core projection)
+  DevBuf<uint8_t> q8;          // nq x D row-scaled e4m3 queries (FP8 projection)
+  DevBuf<float> q8s;           // their row scales
   DevBuf<__nv_bfloat16> qbf2;  // nq x d bf16 hi/lo split q_d' (tensor-core probe operand)
   DevBuf<float> gmat;      // nq x nlist probe distances
   DevBuf<unsigned long long> ppart;  // nq x tiles x nprobe fused probe candidates
@@ -173,6 +175,8 @@ struct mrq_index {
 
   mrq::DevBuf<float> mu, lam, W;  // D, D, D x D
   mrq::DevBuf<__nv_bfloat16> W2;          // bf16 split of W: rows [0,D) hi, [D,2D) lo
+  mrq::DevBuf<uint8_t> W8;                // row-scaled e4m3 W (D x D; D % 16 == 0 only)
+  mrq::DevBuf<float> W8s;                 // its row scales
   mrq::DevBuf<__nv_bfloat16> cent2;       // bf16 split of the centroids: [0,nlist) hi, then lo
   mrq::DevBuf<float> cent, cent_n2;       // nlist x d (rotated frame), nlist
   mrq::DevBuf<int64_t> loff, ploff;       // nlist + 1
@@ -268,6 +272,14 @@ int* tc_error_mirror();  // page-locked host int for reading it back asynchronou
 int tc_check_error();  // nonzero if a bounded wait in a tensor-core kernel gave up
 // probe_bf (optional, M x d bf16, twice with split3): the projection's epilogue also
 // writes the probe's split operand of q_d', so the probe can skip its split (presplit)
+// row-scaled e4m3 rows of X (centred by shift when given) and their scales
+void quantize_rows_fp8(const float* X, int M, int K, int ld, const float* shift, uint8_t* out,
+                       float* scale, cudaStream_t st);
+// [q_d' | q_r] = W (q - mu) from e4m3 operands (MRQ_PREC_FP8); err: the pipeline error word
+// (NULL: the library's)
+void project_fp8(const float* Q, const float* mu, const uint8_t* W8, const float* W8s, int M,
+                 int D, int d, uint8_t* q8, float* q8s, float* qd, int ldd, float* qr, int ldr,
+                 cudaStream_t st, __nv_bfloat16* probe_bf, int* err);
 void project_tc(const float* Q, const float* mu, const __nv_bfloat16* W2, int M, int D, int d,
                 bool split3, __nv_bfloat16* qbf, float* qd, float* qr, cudaStream_t st,
                 __nv_bfloat16* probe_bf = nullptr);

@@ -5,7 +5,10 @@
 // C[M x N] = A[M x K] * B[N x K]^T with A, B in bf16 (K contiguous) and float32
 // accumulation in tensor memory.  The split-precision form stores each operand
 // as hi = bf16(x) and lo = bf16(x - hi) (rows [0, R) = hi, [R, 2R) = lo of one
-// tensor) and accumulates hi*hi + hi*lo + lo*hi into the same accumulator.
+// tensor) and accumulates hi*hi + hi*lo + lo*hi into the same accumulator.  The
+// row-scaled FP8 form stores both operands as e4m3 with one float32 scale per row
+// (|row|_max -> 448) and runs kind::f8f6f4 MMAs (K = 32 per instruction, the same 32
+// bytes per step), the epilogue multiplying each accumulator by its two row scales.
 //
 // One CTA computes a 128 x BN tile: warp 0 issues TMA loads (128-byte swizzled
 // 64-wide K slices) into a 4-stage shared-memory ring, warp 1 issues
@@ -128,6 +131,20 @@ __device__ __forceinline__ void tc_mma(uint32_t dtmem, uint64_t a, uint64_t b, u
       "l"(a), "l"(b), "r"(idesc), "r"(acc)
       : "memory");
 }
+// Instruction descriptor, kind::f8f6f4: D f32 (bits 4-5 = 1), A and B e4m3 (format 0 in
+// bits 7-9 and 10-12), both K-major, N >> 3 at bit 17, M >> 4 at bit 24.
+template <int N>
+__host__ __device__ constexpr uint32_t idesc_e4m3() {
+  return (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(TC_BM >> 4) << 24);
+}
+__device__ __forceinline__ void tc_mma_f8(uint32_t dtmem, uint64_t a, uint64_t b, uint32_t idesc,
+                                          uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n}" ::"r"(dtmem),
+      "l"(a), "l"(b), "r"(idesc), "r"(acc)
+      : "memory");
+}
 __device__ __forceinline__ void tc_commit(uint64_t* bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                    su32(bar))
@@ -164,19 +181,22 @@ struct TcArgs {
   int* err;
   __nv_bfloat16* pbf;  // epi 0, optional: the first `split` columns again, split into bf16
   int pbf_two;         // hi (rows 0..M-1) and, when set, lo (rows M..2M-1) for the probe
+  const float* rscale;  // FP8 form, epi 0: per-row scale of A (M) and of B (N)
+  const float* cscale;
 };
 
 constexpr int TC_PSEL = 16;  // largest nprobe selected inside the probe epilogue
 
-template <int BN, int PSEL, int STAGES>
+template <int BN, int PSEL, int STAGES, bool F8 = false>
 __global__ void __launch_bounds__(256, 1)
     k_gemm_tc(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtensorMap tb,
               TcArgs P) {
-  constexpr int A_BYTES = TC_BM * TC_BK * 2;
+  constexpr int A_BYTES = TC_BM * TC_BK * 2;  // 128-byte K slices: 64 bf16 or 128 e4m3
   constexpr int B_BYTES = BN * TC_BK * 2;
   constexpr int STAGE = A_BYTES + B_BYTES;
+  constexpr int KBE = F8 ? 2 * TC_BK : TC_BK;  // elements per K slice
   constexpr uint32_t NCOLS = BN <= 32 ? 32 : BN <= 64 ? 64 : BN <= 128 ? 128 : 256;
-  constexpr uint32_t IDESC = idesc_bf16<BN>();
+  constexpr uint32_t IDESC = F8 ? idesc_e4m3<BN>() : idesc_bf16<BN>();
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                              ~static_cast<uintptr_t>(1023));
@@ -187,7 +207,7 @@ __global__ void __launch_bounds__(256, 1)
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int m0 = blockIdx.x * TC_BM, n0 = blockIdx.y * BN;
-  const int kpp = (P.K + TC_BK - 1) / TC_BK;  // k-blocks per phase
+  const int kpp = (P.K + KBE - 1) / KBE;  // k-blocks per phase
   const int nkb = kpp * P.phases;
 
   if (threadIdx.x == 0) {
@@ -218,7 +238,7 @@ __global__ void __launch_bounds__(256, 1)
     for (int kb = 0; kb < nkb; ++kb) {
       if (!mbar_wait(&empty[stage], phase ^ 1u, &s_abort, P.err, 1)) break;
       const int ph = kb / kpp;
-      const int k0 = (kb % kpp) * TC_BK;
+      const int k0 = (kb % kpp) * KBE;
       const int ay = m0 + (ph == 2 ? P.a_lo : 0);
       const int by = n0 + (ph == 1 ? P.b_lo : 0);
       uint8_t* sa = smem + stage * STAGE;
@@ -236,9 +256,14 @@ __global__ void __launch_bounds__(256, 1)
       tc_fence_after();
       const uint32_t sa = su32(smem + stage * STAGE);
       const uint64_t ad = sdesc(sa), bd = sdesc(sa + A_BYTES);
+      // four MMAs of 32 bytes of K each (16 bf16 or 32 e4m3)
 #pragma unroll
-      for (int kk = 0; kk < TC_BK / 16; ++kk)
-        tc_mma(tmem, ad + 2ull * kk, bd + 2ull * kk, IDESC, (kb | kk) != 0 ? 1u : 0u);
+      for (int kk = 0; kk < TC_BK / 16; ++kk) {
+        if constexpr (F8)
+          tc_mma_f8(tmem, ad + 2ull * kk, bd + 2ull * kk, IDESC, (kb | kk) != 0 ? 1u : 0u);
+        else
+          tc_mma(tmem, ad + 2ull * kk, bd + 2ull * kk, IDESC, (kb | kk) != 0 ? 1u : 0u);
+      }
       tc_commit(&empty[stage]);
       if (++stage == STAGES) { stage = 0; phase ^= 1u; }
     }
@@ -266,6 +291,14 @@ __global__ void __launch_bounds__(256, 1)
       tc_ld32(trow + (uint32_t)c, r);
       const int col0 = n0 + c;
       if (row >= P.M || col0 >= P.N) continue;
+      if constexpr (F8) {  // the two row scales of the e4m3 operands
+        const float rs = P.rscale[row];
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+          const float cs = col0 + j < P.N ? P.cscale[col0 + j] : 0.f;
+          r[j] = __float_as_uint(__uint_as_float(r[j]) * rs * cs);
+        }
+      }
       if (P.epi == 0) {
         if (P.pbf && col0 + 32 <= P.split) {
           // the probe's bf16 operand (hi, and lo = x - hi) of these 32 q_d' coordinates,
@@ -491,6 +524,28 @@ void split_bf16(const float* X, int M, int K, int ld, const float* shift, bool t
   MRQ_CHECK_LAUNCH();
 }
 
+// Row-scaled e4m3 of an M x K block of X (row stride ld), centred by `shift` when given
+// (one warp per row): scale[m] = max_k |x_mk - shift_k| / 448 (1 for a zero row) and
+// out[m * K + k] = e4m3((x_mk - shift_k) / scale[m]), rounded to nearest, saturating.
+__global__ void k_quant_fp8(const float* __restrict__ X, int M, int K, int ld,
+                            const float* __restrict__ shift, uint8_t* __restrict__ out,
+                            float* __restrict__ scale) {
+  const int64_t m = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (m >= M) return;
+  const int lane = threadIdx.x & 31;
+  const float* x = X + m * (int64_t)ld;
+  float amax = 0.f;
+  for (int k = lane; k < K; k += 32) amax = fmaxf(amax, fabsf(x[k] - (shift ? shift[k] : 0.f)));
+#pragma unroll
+  for (int o = 16; o; o >>= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+  const float sc = amax > 0.f ? amax / 448.f : 1.f;
+  uint8_t* o8 = out + m * (int64_t)K;
+  for (int k = lane; k < K; k += 32)
+    o8[k] = (uint8_t)__nv_cvt_float_to_fp8((x[k] - (shift ? shift[k] : 0.f)) / sc, __NV_SATFINITE,
+                                           __NV_E4M3);
+  if (lane == 0) scale[m] = sc;
+}
+
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
   if (!fn) {
@@ -503,13 +558,15 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   return fn;
 }
 
-CUtensorMap make_map(const void* base, uint64_t rows, uint64_t K, uint32_t box_rows) {
+// K-major operand of `rows` rows, 128-byte swizzled slices of K (bf16, or e4m3 bytes)
+CUtensorMap make_map(const void* base, uint64_t rows, uint64_t K, uint32_t box_rows, bool f8 = false) {
   CUtensorMap m;
   cuuint64_t dims[2] = {K, rows};
-  cuuint64_t strides[1] = {K * 2};
-  cuuint32_t box[2] = {TC_BK, box_rows};
+  cuuint64_t strides[1] = {K * (f8 ? 1 : 2)};
+  cuuint32_t box[2] = {f8 ? 2 * TC_BK : TC_BK, box_rows};
   cuuint32_t es[2] = {1, 1};
-  CUresult r = encode_fn()(&m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims,
+  CUresult r = encode_fn()(&m, f8 ? CU_TENSOR_MAP_DATA_TYPE_UINT8 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16,
+                           2, const_cast<void*>(base), dims,
                            strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
                            CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
@@ -519,18 +576,26 @@ CUtensorMap make_map(const void* base, uint64_t rows, uint64_t K, uint32_t box_r
 
 int* g_err = nullptr;
 
-template <int BN, int PSEL, int STAGES>
-void launch_tc(const __nv_bfloat16* A2, const __nv_bfloat16* B2, const TcArgs& a, cudaStream_t st) {
+template <int BN, int PSEL, int STAGES, bool F8 = false>
+void launch_tc(const void* A2, const void* B2, const TcArgs& a, cudaStream_t st) {
   constexpr int STAGE = TC_BM * TC_BK * 2 + BN * TC_BK * 2;
   const size_t smem = (size_t)STAGES * STAGE + 1024;
   const uint64_t arows = (uint64_t)a.M * (a.phases == 3 ? 2 : 1);
   const uint64_t brows = (uint64_t)a.N * (a.phases == 3 ? 2 : 1);
-  CUtensorMap ta = make_map(A2, arows, a.K, TC_BM);
-  CUtensorMap tb = make_map(B2, brows, a.K, BN);
-  ensure_smem((const void*)k_gemm_tc<BN, PSEL, STAGES>, smem);
+  CUtensorMap ta = make_map(A2, arows, a.K, TC_BM, F8);
+  CUtensorMap tb = make_map(B2, brows, a.K, BN, F8);
+  ensure_smem((const void*)k_gemm_tc<BN, PSEL, STAGES, F8>, smem);
   dim3 grid(ceil_div(a.M, TC_BM), ceil_div(a.N, BN));
-  k_gemm_tc<BN, PSEL, STAGES><<<grid, 256, smem, st>>>(ta, tb, a);
+  k_gemm_tc<BN, PSEL, STAGES, F8><<<grid, 256, smem, st>>>(ta, tb, a);
   MRQ_CHECK_LAUNCH();
+}
+
+// the row-scaled FP8 projection (epi 0, one phase): e4m3 A (M x K) and B (N x K)
+void run_tc_f8(const uint8_t* A8, const uint8_t* B8, TcArgs a, cudaStream_t st) {
+  if (!a.err) a.err = tc_error_word();
+  if (a.N <= 64) launch_tc<64, 4, 4, true>(A8, B8, a, st);
+  else if (a.N <= 128) launch_tc<128, 4, 4, true>(A8, B8, a, st);
+  else launch_tc<256, 4, 4, true>(A8, B8, a, st);
 }
 
 void run_tc(const __nv_bfloat16* A2, const __nv_bfloat16* B2, TcArgs a, cudaStream_t st) {
@@ -600,6 +665,29 @@ void project_tc(const float* Q, const float* mu, const __nv_bfloat16* W2, int M,
   a.pbf = (d % 32 == 0) ? probe_bf : nullptr;
   a.pbf_two = split3 ? 1 : 0;
   run_tc(qbf, W2, a, st);
+}
+
+void quantize_rows_fp8(const float* X, int M, int K, int ld, const float* shift, uint8_t* out,
+                       float* scale, cudaStream_t st) {
+  if (M <= 0) return;
+  k_quant_fp8<<<ceil_div(M, 8), 256, 0, st>>>(X, M, K, ld, shift, out, scale);
+  MRQ_CHECK_LAUNCH();
+}
+
+void project_fp8(const float* Q, const float* mu, const uint8_t* W8, const float* W8s, int M,
+                 int D, int d, uint8_t* q8, float* q8s, float* qd, int ldd, float* qr, int ldr,
+                 cudaStream_t st, __nv_bfloat16* probe_bf, int* err) {
+  quantize_rows_fp8(Q, M, D, D, mu, q8, q8s, st);
+  TcArgs a{};
+  a.M = M; a.N = D; a.K = D;
+  a.phases = 1;
+  a.epi = 0;
+  a.out0 = qd; a.ld0 = ldd; a.out1 = qr; a.ld1 = ldr; a.split = d;
+  a.pbf = (d % 32 == 0) ? probe_bf : nullptr;
+  a.pbf_two = 0;
+  a.rscale = q8s; a.cscale = W8s;
+  a.err = err;
+  run_tc_f8(q8, W8, a, st);
 }
 
 void probe_tc(const float* qd, const float* qstat, const __nv_bfloat16* C2, const float* cn2,
@@ -685,6 +773,30 @@ void project_noalloc(mrq_index* idx, const float* q, int64_t nq, int precision, 
     MRQ_CUDA(cudaStreamSynchronize(st));
     return;
   }
+  if (precision == MRQ_PREC_FP8) {
+    // scratch: [0, 256) error word, then the e4m3 queries (nq x D bytes, rounded up to
+    // 256), then their row scales
+    const int64_t qbytes = (nq * D + 255) / 256 * 256;
+    const int64_t need = qbytes + 4 * nq;
+    if (need > MRQ_PROJECT_NOALLOC_MAX_BYTES)
+      fail(MRQ_EINVAL, "mrq_project_noalloc: nq * D = " + std::to_string(nq * D) + " needs " +
+                           std::to_string(need) + " bytes of scratch at FP8, more than its fixed " +
+                           std::to_string(MRQ_PROJECT_NOALLOC_MAX_BYTES) + "; split the batch");
+    MRQ_REQUIRE(tc_available(), "tensor-core projection needs an sm_103 device");
+    MRQ_REQUIRE(idx->W8.p != nullptr, "FP8 projection needs D to be a multiple of 16");
+    unsigned char* base = project_scratch();
+    int* err = reinterpret_cast<int*>(base);
+    uint8_t* q8 = base + 256;
+    float* q8s = reinterpret_cast<float*>(base + 256 + qbytes);
+    MRQ_CUDA(cudaMemsetAsync(err, 0, sizeof(int), st));
+    project_fp8(q, idx->mu.p, idx->W8.p, idx->W8s.p, (int)nq, D, d, q8, q8s, qp, D, qp + d, D,
+                st, nullptr, err);
+    int h = 0;
+    MRQ_CUDA(cudaMemcpyAsync(&h, err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    MRQ_CUDA(cudaStreamSynchronize(st));
+    if (h) fail(MRQ_ETIMEDOUT, "a tensor-core kernel gave up waiting on its pipeline");
+    return;
+  }
   const bool split3 = precision == MRQ_PREC_BF16X3;
   const int64_t need = nq * D * 2 * (split3 ? 2 : 1);
   if (need > MRQ_PROJECT_NOALLOC_MAX_BYTES)
@@ -740,20 +852,6 @@ __device__ __forceinline__ uint32_t sw128_off8(int rows, int row, int k) {
                     ((((kin >> 4) ^ (row & 7)) << 4) | (kin & 15)));
 }
 
-// Instruction descriptor, kind::f8f6f4: D f32 (bits 4-5 = 1), A and B e4m3 (format 0 in
-// bits 7-9 and 10-12), both K-major, N >> 3 at bit 17, M >> 4 at bit 24.
-template <int N>
-__host__ __device__ constexpr uint32_t idesc_e4m3() {
-  return (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(TC_BM >> 4) << 24);
-}
-__device__ __forceinline__ void tc_mma_f8(uint32_t dtmem, uint64_t a, uint64_t b, uint32_t idesc,
-                                          uint32_t acc) {
-  asm volatile(
-      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-      " tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n}" ::"r"(dtmem),
-      "l"(a), "l"(b), "r"(idesc), "r"(acc)
-      : "memory");
-}
 
 // e4m3 bytes of two small non-negative integers (exact up to 16)
 __device__ __forceinline__ uint32_t e4m3x2(int v0, int v1) {

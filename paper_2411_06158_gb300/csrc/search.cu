@@ -2335,6 +2335,13 @@ void project_batch(mrq_index* idx, Workspace& ws, const float* q, int64_t nq, in
   const int D = idx->D, d = idx->d, r = D - d;
   if (precision == MRQ_PREC_FP32) {
     gemm_nt_f32(q, D, idx->mu.p, idx->W.p, D, (int)nq, D, D, qd, d, qr, r, d, st);
+  } else if (precision == MRQ_PREC_FP8) {
+    MRQ_REQUIRE(tc_available(), "tensor-core projection needs an sm_103 device");
+    MRQ_REQUIRE(idx->W8.p != nullptr, "FP8 projection needs D to be a multiple of 16 (16-byte e4m3 rows)");
+    ws.q8.reserve((size_t)nq * D);
+    ws.q8s.reserve((size_t)nq);
+    project_fp8(q, idx->mu.p, idx->W8.p, idx->W8s.p, (int)nq, D, d, ws.q8.p, ws.q8s.p, qd, d, qr, r,
+                st, probe_bf, nullptr);
   } else {
     MRQ_REQUIRE(tc_available(), "tensor-core projection needs an sm_103 device");
     MRQ_REQUIRE(D % 8 == 0, "tensor-core precisions need D to be a multiple of 8 (16-byte bf16 rows)");

@@ -35,8 +35,8 @@ def _rel_err(got, ref, q, mu):
     return float(((got - ref).abs() / scale).max())
 
 
-@pytest.mark.parametrize("prec", [mrq.PREC_FP32, mrq.PREC_BF16, mrq.PREC_BF16X3],
-                         ids=["fp32", "bf16", "bf16x3"])
+@pytest.mark.parametrize("prec", [mrq.PREC_FP32, mrq.PREC_BF16, mrq.PREC_BF16X3, mrq.PREC_FP8],
+                         ids=["fp32", "bf16", "bf16x3", "fp8"])
 def test_two_calls_match_mrq_project(index, prec):
     D, gi, queries, mu = index
     q = queries[:333].contiguous()                       # ragged: not a multiple of 128 rows
@@ -94,7 +94,7 @@ def test_device_memory_unchanged_across_calls(index):
     D, gi, queries, mu = index
     q = queries[:512].contiguous()
     outs = {p: torch.empty((512, D), device="cuda")
-            for p in (mrq.PREC_FP32, mrq.PREC_BF16, mrq.PREC_BF16X3)}
+            for p in (mrq.PREC_FP32, mrq.PREC_BF16, mrq.PREC_BF16X3, mrq.PREC_FP8)}
     for p, out in outs.items():                          # set-up calls
         mrq.mrq_project_noalloc(gi, q, out, mrq.mrq_search_opts(precision=p))
     torch.cuda.synchronize()
