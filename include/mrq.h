@@ -126,7 +126,8 @@ typedef struct {
   int64_t n;
   int D, d, bits, nlist;
   int64_t max_list;     /* largest list size */
-  int64_t device_bytes; /* device memory held by the index */
+  int64_t device_bytes; /* device memory held by the index (its arrays, including the
+                           MR-SQ codes once made; not the search workspace) */
 } mrq_index_info_t;
 
 #define MRQ_MAX_D 1024 /* largest quantized dimension d */

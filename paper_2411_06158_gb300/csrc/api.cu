@@ -554,7 +554,9 @@ int mrq_index_info(const mrq_index* idx, mrq_index_info_t* info) {
                                    idx->cent_n2.bytes() + idx->loff.bytes() + idx->ploff.bytes() +
                                    idx->ids.bytes() + idx->codes.bytes() + idx->fadd.bytes() +
                                    idx->fres.bytes() + idx->ferr.bytes() + idx->fres1.bytes() +
-                                   idx->ferr1.bytes() + idx->xd.bytes() +
+                                   idx->ferr1.bytes() + idx->sq_codes.bytes() +
+                                   idx->sq_lo.bytes() + idx->sq_delta.bytes() +
+                                   idx->sq_xr2.bytes() + idx->xd.bytes() +
                                    idx->xr.bytes() + idx->xn2.bytes());
   });
 }
