@@ -203,7 +203,7 @@ def recall(found, truth):
 
 # ------------------------------------------------------------- CPU oracle
 
-def oracle_sample_setup(w, nprobe, n_queries):
+def oracle_sample_setup(w, nprobe, n_queries, n_timed=None):
     """The CPU baseline's bounded sample: the same mixture at 1/16 of the base and
     1/16 of the lists (so the mean list size and the candidates per query at the
     same nprobe match the full workload), ``n_queries`` of the workload's queries."""
@@ -220,28 +220,65 @@ def oracle_sample_setup(w, nprobe, n_queries):
     npr = min(nprobe, nlist_s)
     desc = (f"oracle (numpy float64, 1 thread) on a 1/{scale} sample: N={n_s}, nlist={nlist_s}, "
             f"nprobe={npr} (same mean list size and candidates per query as the full "
-            f"workload), D={w.D}, d={w.d}, bits={w.bits}, {n_queries} queries")
+            f"workload), D={w.D}, d={w.d}, bits={w.bits}, "
+            f"{n_queries if n_timed is None else n_timed} queries")
     return idx, queries, npr, desc
 
 
-def _oracle_worker(wname, over, nprobe, nq, steps, point, conn):
+_ORACLE_SHARED = {}  # the all-core leg's index and queries, inherited by forked workers
+
+
+def _oracle_chunk(span):
+    from oracle import mrq as omrq
+    sh = _ORACLE_SHARED
+    lo, hi = span
+    omrq.search_contract(sh["idx"], sh["queries"][lo:hi], sh["k"], sh["npr"], **sh["point"])
+    return hi - lo
+
+
+def _oracle_worker(wname, over, nprobe, nq, steps, point, conn, procs=1):
+    """Times the oracle single-threaded on nq queries; with procs > 1 also on all cores:
+    procs single-threaded processes forked from this one (which never touches the GPU)
+    search procs * nq queries, nq each."""
+    import multiprocessing as mp
+
     import datagen
     from oracle import mrq as omrq
     w = datagen.workload(wname, **over)
-    idx, queries, npr, desc = oracle_sample_setup(w, nprobe, nq)
+    idx, queries, npr, desc = oracle_sample_setup(w, nprobe, nq * max(1, procs), n_timed=nq)
     desc += ", eps0={eps0}, m={m}, query_bits={qbits}".format(**point)
     times = []
     for _ in range(steps):
         t0 = time.perf_counter()
-        omrq.search_contract(idx, queries, w.k, npr, **point)
+        omrq.search_contract(idx, queries[:nq], w.k, npr, **point)
         times.append(time.perf_counter() - t0)
-    conn.send((times, desc))
+    all_times = []
+    if procs > 1:
+        _ORACLE_SHARED.update(idx=idx, queries=queries, k=w.k, npr=npr, point=point)
+        spans = [(i * nq, (i + 1) * nq) for i in range(procs)]
+        with mp.get_context("fork").Pool(procs) as pool:
+            pool.map(_oracle_chunk, spans)                 # warm-up
+            for _ in range(steps):
+                t0 = time.perf_counter()
+                pool.map(_oracle_chunk, spans)
+                all_times.append(time.perf_counter() - t0)
+    conn.send((times, desc, all_times))
     conn.close()
 
 
-def time_oracle(args, w, nprobe, steps, eps0=1.9, m=4.0, qbits=0):
+def host_cores():
+    """Host cores this process may use (the all-core oracle leg's process count)."""
+    try:
+        return max(1, len(os.sched_getaffinity(0)))
+    except AttributeError:  # pragma: no cover
+        return max(1, os.cpu_count() or 1)
+
+
+def time_oracle(args, w, nprobe, steps, eps0=1.9, m=4.0, qbits=0, procs=1):
     """Run the oracle in a spawned single-threaded process at the operating point
-    (nprobe, eps0, m, query bits); returns (qps, desc, times)."""
+    (nprobe, eps0, m, query bits); returns (qps, desc, times, all_cores) where all_cores
+    is None or, with procs > 1, {"value", "cores", "queries"} of the same oracle run as
+    procs single-threaded processes on procs times as many queries."""
     import multiprocessing as mp
     env_keys = ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS")
     old = {k: os.environ.get(k) for k in env_keys}
@@ -253,9 +290,10 @@ def time_oracle(args, w, nprobe, steps, eps0=1.9, m=4.0, qbits=0):
         over = {f: getattr(w, f) for f in ("n", "n_query", "d", "bits", "nlist")}
         p = ctx.Process(target=_oracle_worker,
                         args=(args.workload, over, nprobe, args.cpu_queries, steps,
-                              {"eps0": float(eps0), "m": float(m), "qbits": int(qbits)}, b))
+                              {"eps0": float(eps0), "m": float(m), "qbits": int(qbits)}, b,
+                              procs))
         p.start()
-        times, desc = a.recv()
+        times, desc, all_times = a.recv()
         p.join()
     finally:
         for k, v in old.items():
@@ -264,7 +302,12 @@ def time_oracle(args, w, nprobe, steps, eps0=1.9, m=4.0, qbits=0):
             else:
                 os.environ[k] = v
     per = sorted(times)[len(times) // 2]
-    return args.cpu_queries / per, desc, times
+    allc = None
+    if all_times:
+        t_all = sorted(all_times)[len(all_times) // 2]
+        allc = {"value": procs * args.cpu_queries / t_all, "cores": procs,
+                "queries": procs * args.cpu_queries}
+    return args.cpu_queries / per, desc, times, allc
 
 
 def run_reference(args):
@@ -281,8 +324,9 @@ def run_reference(args):
         pt["m"] = args.m
     nprobe = pt["nprobe"]
     steps = max(1, args.steps)
-    qps, desc, times = time_oracle(args, w, nprobe, steps + max(0, args.warmup),
-                                   eps0=pt["eps0"], m=pt["m"], qbits=pt["query_bits"])
+    qps, desc, times, allc = time_oracle(args, w, nprobe, steps + max(0, args.warmup),
+                                         eps0=pt["eps0"], m=pt["m"], qbits=pt["query_bits"],
+                                         procs=host_cores())
     times = times[max(0, args.warmup):]
     ms = 1000.0 * sum(times) / len(times)
     value = args.cpu_queries * len(times) / sum(times)
@@ -294,7 +338,7 @@ def run_reference(args):
                                             "eps0": pt["eps0"], "m": pt["m"],
                                             "query_bits": pt["query_bits"], "k": w.k},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": desc},
+                             "sample": desc, "all_cores": allc},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
@@ -723,9 +767,10 @@ def main(argv=None):
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         try:
-            cq, desc, _ = time_oracle(args, w, B["nprobe"], 2, eps0=B["eps0"], m=B["m"],
-                                      qbits=B["query_bits"])
-            cpu = {"value": cq, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc}
+            cq, desc, _, allc = time_oracle(args, w, B["nprobe"], 2, eps0=B["eps0"], m=B["m"],
+                                            qbits=B["query_bits"], procs=host_cores())
+            cpu = {"value": cq, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc,
+                   "all_cores": allc}
         except Exception as e:  # keep the GPU line even if the CPU leg fails
             cpu = {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle", "error": str(e)}
 

@@ -24,7 +24,9 @@ def test_reference_arm_json_line():
     assert line["value"] > 0 and line["higher_is_better"] is True
     assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["value"] == line["value"]
     cb = line["cpu_baseline"]
-    assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == line["value"]
+    assert cb["kind"] == "oracle" and cb["cores"] == 1 and cb["value"] == line["value"]
+    ac = cb["all_cores"]                  # the same oracle on every host core, when several
+    assert ac is None or (ac["cores"] >= 2 and ac["value"] > 0 and ac["queries"] == 8 * ac["cores"])
     assert line["config"]["workload"] == "small-20k-d128"
 
 
