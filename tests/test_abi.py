@@ -132,3 +132,21 @@ def test_new_option_defaults(lib):
     b = lib.BuildOpts()
     lib._lib.mrq_build_opts_default(C.byref(b))
     assert b.auto_d_variance == pytest.approx(0.8)
+
+
+def test_build_option_rejections_before_any_gpu_call(lib):
+    """Eq. 8's d = 0 cannot take a rotation draw (its size depends on d), its variance
+    target must lie in (0, 1], and d may not exceed MRQ_MAX_D = 1024; all rejected by
+    argument checks, on a machine without a GPU too."""
+    base = np.zeros((2000, 1088), dtype=np.float32)
+    h = C.c_void_p()
+    o, keep = lib.mrq_build_opts(rotation_gauss=np.zeros((32, 32)))
+    rc = lib._lib.mrq_build(base.ctypes.data, 2000, 1088, 0, 1, 8, C.byref(o), C.byref(h))
+    assert rc == lib.MRQ_EINVAL and "rotation_gauss" in lib.mrq_last_error()
+    for bad in (0.0, -0.5, 1.01):
+        o, keep = lib.mrq_build_opts(auto_d_variance=bad)
+        rc = lib._lib.mrq_build(base.ctypes.data, 2000, 1088, 0, 1, 8, C.byref(o), C.byref(h))
+        assert rc == lib.MRQ_EINVAL and "auto_d_variance" in lib.mrq_last_error()
+    rc = lib._lib.mrq_build(base.ctypes.data, 2000, 1088, 1056, 1, 8, None, C.byref(h))
+    assert rc == lib.MRQ_EINVAL and "1024" in lib.mrq_last_error()
+    assert h.value is None
