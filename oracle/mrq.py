@@ -27,7 +27,7 @@ __all__ = [
     "OracleIndex", "choose_d", "pca_train", "orthogonal_from_gaussian", "kmeans", "encode",
     "build_index", "project_queries", "probe", "quantize_query", "estimate_list",
     "search_contract", "search_literal", "exact_knn", "SearchResult", "sq8_train",
-    "sq8_estimate", "search_mrsq8",
+    "sq8_estimate", "search_mrsq8", "opq_train", "pq_decode", "pq_estimate", "search_mrpq",
 ]
 
 MODE_MRQ = 0
@@ -549,21 +549,15 @@ def sq8_estimate(idx: OracleIndex, sq, qd, qr2, pos=None):
     return np.sum((qd - xhat) ** 2, axis=1) + np.sum(xr * xr, axis=1) + qr2
 
 
-def search_mrsq8(idx: OracleIndex, Q, k: int, nprobe: int, rerank: int = 500,
-                 sq=None) -> SearchResult:
-    """MR-SQ search (Exp-5): SQ8 estimates over the probed lists, then a fixed rerank
-    range instead of an error bound.
-
-    Per query (after the projection and probe of Algorithm 2):
-      dis'' = |q_d' - x_hat|^2 + |x_r|^2 + |q_r|^2   (the residual inner product
-              -2<x_r, q_r> is dropped, as Eq. 4 drops it),
-      the `rerank` candidates with the smallest dis'' (ties by id) get their exact
-      distance, and the answer is the k smallest exact distances (ties by id).
-    n_s1 = n_s2 = the number reranked.  ``margin``: the probe boundary, how far each
-    answer-relevant candidate (exact distance within the k-th) sits from the rerank cut
-    in dis'', and consecutive answer distances around rank k.
-    """
-    sq = sq if sq is not None else sq8_train(idx.xd)
+def _search_rerank(idx: OracleIndex, Q, k: int, nprobe: int, rerank: int,
+                   estimate) -> SearchResult:
+    """The fixed-rerank-range search of Exp-5 (MR-SQ, MR-PQ): after the projection and
+    probe of Algorithm 2, the `rerank` probed candidates with the smallest estimate
+    ``estimate(qd, qr2, pos)`` (ties by id) get their exact distance, and the answer is
+    the k smallest exact distances (ties by id).  n_s1 = n_s2 = the number reranked.
+    ``margin``: the probe boundary, how far each answer-relevant candidate (exact
+    distance within the k-th) sits from the rerank cut in the estimate, and
+    consecutive answer distances around rank k."""
     qd_all, qr_all, qr2_all, _, _ = project_queries(idx, Q)
     nq = qd_all.shape[0]
     ids = np.full((nq, k), -1, dtype=np.int64)
@@ -584,7 +578,7 @@ def search_mrsq8(idx: OracleIndex, Q, k: int, nprobe: int, rerank: int = 500,
         if pos.size == 0:
             margin[qi] = mg
             continue
-        est = sq8_estimate(idx, sq, qd, qr2_all[qi], pos)
+        est = estimate(qd, qr2_all[qi], pos)
         order = np.lexsort((idx.ids[pos], est))
         R = min(rerank, pos.size)
         sel = order[:R]
@@ -615,6 +609,83 @@ def search_mrsq8(idx: OracleIndex, Q, k: int, nprobe: int, rerank: int = 500,
                     mg = min(mg, (est[i] - t_in) / max(est[i], 1e-30))
         margin[qi] = mg
     return SearchResult(ids, dists, n_cand, n_rr, n_rr.copy(), margin)
+
+
+
+
+def search_mrsq8(idx: OracleIndex, Q, k: int, nprobe: int, rerank: int = 500,
+                 sq=None) -> SearchResult:
+    """MR-SQ search (Exp-5): SQ8 estimates over the probed lists, then a fixed rerank
+    range instead of an error bound (``_search_rerank``), with
+      dis'' = |q_d' - x_hat|^2 + |x_r|^2 + |q_r|^2   (the residual inner product
+              -2<x_r, q_r> is dropped, as Eq. 4 drops it).
+    """
+    sq = sq if sq is not None else sq8_train(idx.xd)
+    return _search_rerank(idx, Q, k, nprobe, rerank,
+                          lambda qd, qr2, pos: sq8_estimate(idx, sq, qd, qr2, pos))
+
+
+def opq_train(X, M: int, K: int, init_idx, opq_iters: int = 4, km_iters: int = 6):
+    """MR-PQ (Appendix A.2, Exp-5): optimized product quantization of the projected lead
+    coordinates (rows of X, n x d).
+
+    Reading (the paper names OPQ only): the non-parametric OPQ of Ge et al. (2013) --
+    alternate, ``opq_iters`` times, (a) Lloyd k-means (``km_iters`` rounds, warm
+    started) of each of the M subspaces of d/M consecutive coordinates of X R into K
+    centroids, and (b) the orthogonal R minimising |X R - Y|_F for the decoded Y, which
+    is U V^T for the SVD X^T Y = U S V^T (orthogonal Procrustes); then a final k-means
+    round set and the codes.  R starts at the identity; the initial centroids of every
+    subspace are the rows ``init_idx`` (K of them).
+    Returns R (d x d), codebooks (M x K x d/M), codes (uint8 n x M).
+    """
+    X = np.asarray(X, dtype=np.float64)
+    n, d = X.shape
+    if d % M or K > n or K > 256:
+        raise ValueError("invalid PQ shape")
+    ds = d // M
+    R = np.eye(d)
+    Xr = X @ R
+    C = np.stack([Xr[np.asarray(init_idx), m * ds:(m + 1) * ds] for m in range(M)])
+    codes = np.zeros((n, M), dtype=np.int64)
+    for _ in range(opq_iters):
+        Xr = X @ R
+        for m in range(M):
+            C[m], codes[:, m] = kmeans(Xr[:, m * ds:(m + 1) * ds], C[m], km_iters)
+        Y = pq_decode(C, codes)
+        U, _, Vt = np.linalg.svd(X.T @ Y)
+        R = U @ Vt
+    Xr = X @ R
+    for m in range(M):
+        C[m], codes[:, m] = kmeans(Xr[:, m * ds:(m + 1) * ds], C[m], km_iters)
+    return R, C, codes.astype(np.uint8)
+
+
+def pq_decode(C, codes):
+    """Concatenated centroids of the codes (n x d, in the rotated frame X R)."""
+    return np.concatenate([C[m][codes[:, m]] for m in range(C.shape[0])], axis=1)
+
+
+def pq_estimate(idx: OracleIndex, pq, qd, qr2, pos=None):
+    """MR-PQ estimate (asymmetric distance computation): with q' = q_d' R and the
+    lookup table T[m][j] = |q'_m - C[m][j]|^2 of each subspace m,
+    dis'' = sum_m T[m][code_m] + |x_r|^2 + |q_r|^2 (the residual cross term dropped)."""
+    R, C, codes = pq
+    sel = slice(None) if pos is None else pos
+    M, K, ds = C.shape
+    qp = np.asarray(qd, dtype=np.float64) @ R
+    T = np.stack([np.sum((qp[m * ds:(m + 1) * ds][None, :] - C[m]) ** 2, axis=1)
+                  for m in range(M)])                       # M x K
+    cs = codes[sel].astype(np.int64)
+    lead = np.sum(T[np.arange(M)[None, :], cs], axis=1)
+    xr = idx.xr[sel]
+    return lead + np.sum(xr * xr, axis=1) + qr2
+
+
+def search_mrpq(idx: OracleIndex, Q, k: int, nprobe: int, pq, rerank: int = 500) -> SearchResult:
+    """MR-PQ search (Exp-5): OPQ estimates (``pq`` from ``opq_train`` on idx.xd) over the
+    probed lists and the fixed rerank range of ``_search_rerank``."""
+    return _search_rerank(idx, Q, k, nprobe, rerank,
+                          lambda qd, qr2, pos: pq_estimate(idx, pq, qd, qr2, pos))
 
 
 def search_literal(idx: OracleIndex, Q, k: int, nprobe: int, *, eps0: float = 1.9,

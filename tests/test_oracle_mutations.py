@@ -210,3 +210,33 @@ def test_mrsq8_dropped_tail_norm(monkeypatch):
     monkeypatch.setattr(mrq, "sq8_estimate", wrong)
     wk, idx = _small()
     _fails(pins.test_mrsq8_estimate_within_its_bound, wk, idx)
+
+
+def test_pq_query_rotated_by_the_transpose(monkeypatch):
+    orig = mrq.pq_estimate
+
+    def wrong(idx, pq, qd, qr2, pos=None):
+        R, C, codes = pq
+        return orig(idx, (R.T, C, codes), qd, qr2, pos)
+    monkeypatch.setattr(mrq, "pq_estimate", wrong)
+    fx = pins.pq_setup.__wrapped__(*pins_small())
+    _fails(pins.test_pq_estimate_is_the_rotated_decoded_distance, fx)
+
+
+def test_procrustes_factors_swapped(monkeypatch):
+    real_svd = np.linalg.svd
+
+    def swapped(a, *args, **kw):
+        U, S, Vt = real_svd(a, *args, **kw)
+        return Vt.T, S, U.T                      # the rotation becomes V U^T, not U V^T
+    wk, idx = _small()
+    init = datagen.kmeans_init_indices(idx.xd.shape[0], 16, 21)
+    pq = mrq.opq_train(idx.xd, M=16, K=16, init_idx=init, opq_iters=4, km_iters=4)
+    monkeypatch.setattr(np.linalg, "svd", swapped)
+    _fails(pins.test_opq_rotation_is_orthogonal_and_procrustes_optimal,
+           (wk[0], wk[1], wk[2], idx, pq, init))
+
+
+def pins_small():
+    wk, idx = _small()
+    return wk, idx

@@ -592,3 +592,89 @@ def test_mrsq8_rerank_range(small_workload, small_oracle_index):
     assert mrq.recall_at_k(r.ids, full.ids) > 0.99
     r10 = mrq.search_mrsq8(idx, Q, w.k, w.nprobe, rerank=w.k)
     assert mrq.recall_at_k(r10.ids, full.ids) < mrq.recall_at_k(r.ids, full.ids)
+
+
+# -------------------------------------------------------- MR-PQ (Exp-5), OPQ codes
+
+@pytest.fixture(scope="module")
+def pq_setup(small_workload, small_oracle_index):
+    w, base, queries = small_workload
+    idx = small_oracle_index
+    init = datagen.kmeans_init_indices(idx.xd.shape[0], 16, 21)
+    pq = mrq.opq_train(idx.xd, M=16, K=16, init_idx=init, opq_iters=4, km_iters=4)
+    return w, base, queries, idx, pq, init
+
+
+def test_opq_rotation_is_orthogonal_and_procrustes_optimal(pq_setup):
+    """R is orthogonal, and for the final codes no other orthogonal matrix (the identity,
+    random rotations, R itself perturbed) brings X closer to their decoded rows."""
+    w, base, queries, idx, pq, init = pq_setup
+    R, C, codes = pq
+    d = R.shape[0]
+    np.testing.assert_allclose(R.T @ R, np.eye(d), atol=1e-10)
+    X = idx.xd.astype(np.float64)
+    Y = mrq.pq_decode(C, codes.astype(np.int64))
+    # the Procrustes step for these codes (one more alternation) cannot do worse than R
+    U, _, Vt = np.linalg.svd(X.T @ Y)
+    best = np.linalg.norm(X @ (U @ Vt) - Y)
+    rng = np.random.default_rng(3)
+    for Q in [np.eye(d), R] + [np.linalg.qr(rng.standard_normal((d, d)))[0] for _ in range(5)]:
+        assert best <= np.linalg.norm(X @ Q - Y) + 1e-9
+    # one alternation from the identity: R is the orthogonal polar factor of X^T Y0 for the
+    # codes Y0 of plain PQ, A (A^T A)^(-1/2) with A = X^T Y0 (computed by an eigensolver,
+    # not an SVD)
+    R1, _, _ = mrq.opq_train(X, M=16, K=16, init_idx=init, opq_iters=1, km_iters=4)
+    _, C0, codes0 = mrq.opq_train(X, M=16, K=16, init_idx=init, opq_iters=0, km_iters=4)
+    A = X.T @ mrq.pq_decode(C0, codes0.astype(np.int64))
+    lam, V = np.linalg.eigh(A.T @ A)
+    polar = A @ (V / np.sqrt(lam)[None, :]) @ V.T
+    np.testing.assert_allclose(R1, polar, atol=1e-8)
+
+
+def test_opq_lowers_distortion_against_plain_pq(pq_setup):
+    """The learned rotation never raises the quantization distortion over the alternations
+    (each step minimises it over its own variable), so it ends at most at plain PQ's."""
+    w, base, queries, idx, pq, init = pq_setup
+    X = idx.xd.astype(np.float64)
+    dist = []
+    for it in (0, 1, 2, 4):
+        R, C, codes = mrq.opq_train(X, M=16, K=16, init_idx=init, opq_iters=it, km_iters=4)
+        dist.append(np.sum((X @ R - mrq.pq_decode(C, codes.astype(np.int64))) ** 2))
+    assert all(b <= a * (1 + 1e-9) for a, b in zip(dist, dist[1:]))
+    assert dist[-1] < dist[0]
+
+
+def test_pq_estimate_is_the_rotated_decoded_distance(pq_setup):
+    """The lookup-table sum equals |q_d' - y R^T|^2 for the decoded row y (R orthogonal:
+    |q R - y| = |q - y R^T|), plus |x_r|^2 + |q_r|^2 -- a transposed R or a wrong
+    subspace slice breaks it."""
+    w, base, queries, idx, pq, init = pq_setup
+    R, C, codes = pq
+    Y = mrq.pq_decode(C, codes.astype(np.int64)) @ R.T      # back in the x_d' frame
+    qd, qr, qr2, _, _ = mrq.project_queries(idx, queries[:10])
+    xr2 = np.linalg.norm(idx.xr, axis=1) ** 2
+    for i in range(10):
+        est = mrq.pq_estimate(idx, pq, qd[i], qr2[i])
+        want = np.linalg.norm(Y - qd[i], axis=1) ** 2 + xr2 + qr2[i]
+        np.testing.assert_allclose(est, want, rtol=1e-9, atol=1e-9)
+
+
+def test_pq_with_one_centroid_per_point_is_exact():
+    """K = n: every point is its own centroid, the codes reconstruct X R exactly and the
+    MR-PQ estimate is |q_d' - x_d'|^2 + |x_r|^2 + |q_r|^2."""
+    rng = np.random.default_rng(5)
+    X = rng.standard_normal((16, 8))
+    R, C, codes = mrq.opq_train(X, M=2, K=16, init_idx=np.arange(16), opq_iters=2, km_iters=2)
+    np.testing.assert_allclose(mrq.pq_decode(C, codes.astype(np.int64)), X @ R, atol=1e-10)
+
+
+def test_mrpq_full_rerank_is_brute_force(pq_setup):
+    w, base, queries, idx, pq, init = pq_setup
+    Q = queries[:10]
+    ref_ids, ref_d = mrq.exact_knn(base, Q, w.k)
+    r = mrq.search_mrpq(idx, Q, w.k, idx.nlist, pq, rerank=idx.xd.shape[0])
+    np.testing.assert_array_equal(r.ids, ref_ids)
+    np.testing.assert_allclose(r.dists, ref_d, rtol=1e-9)
+    r2 = mrq.search_mrpq(idx, queries[:40], w.k, w.nprobe, pq, rerank=300)
+    full = mrq.search_contract(idx, queries[:40], w.k, w.nprobe, eps0=1e9, m=1e9)
+    assert mrq.recall_at_k(r2.ids, full.ids) > 0.97
