@@ -678,3 +678,16 @@ def test_mrpq_full_rerank_is_brute_force(pq_setup):
     r2 = mrq.search_mrpq(idx, queries[:40], w.k, w.nprobe, pq, rerank=300)
     full = mrq.search_contract(idx, queries[:40], w.k, w.nprobe, eps0=1e9, m=1e9)
     assert mrq.recall_at_k(r2.ids, full.ids) > 0.97
+
+
+def test_index_file_optional_sign_plane_sections(tmp_path, refine_pair):
+    """The writer adds FRE1/FER1 for a multi-bit index (and only then); the reader returns
+    them unchanged (float32)."""
+    w, base, queries, one, three = refine_pair
+    p1, p3 = str(tmp_path / "b1.mrq"), str(tmp_path / "b3.mrq")
+    index_file.write_index(one, p1)
+    index_file.write_index(three, p3)
+    f1, f3 = index_file.read_index(p1), index_file.read_index(p3)
+    assert "FRE1" not in f1 and "FER1" not in f1
+    np.testing.assert_array_equal(f3["FRE1"], three.f_rescale1.astype(np.float32))
+    np.testing.assert_array_equal(f3["FER1"], three.f_err1.astype(np.float32))
