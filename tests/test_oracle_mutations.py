@@ -115,7 +115,7 @@ def test_threshold_from_too_few_upper_bounds(monkeypatch):
     _fails(pins.test_contract_thresholds_by_definition, wk, idx)
 
 
-def test_quantized_inner_product_offset_term_wrong(monkeypatch):
+def test_query_grid_offset_sign_flipped(monkeypatch):
     orig = mrq.quantize_query
 
     def wrong(qprime, qbits):
@@ -123,6 +123,82 @@ def test_quantized_inner_product_offset_term_wrong(monkeypatch):
         return qbar, -lo, delta                             # sign of v_l flipped
     monkeypatch.setattr(mrq, "quantize_query", wrong)
     _fails(pins.test_quantize_query_golden_and_grid_identity)
+
+
+def _estimate_with_ip(orig, change):
+    """estimate_list whose quantized inner product is replaced by change(e, top, d),
+    with dis', LB and UB moved consistently (a mistake inside the Eq. 4 identity)."""
+    def wrong(idx, j, qd, g_j, qr2, sigma, eps0, m, qbits=0, sign_plane=False):
+        e = dict(orig(idx, j, qd, g_j, qr2, sigma, eps0, m, qbits, sign_plane=sign_plane))
+        if qbits > 0:
+            sl = idx.list_slice(j)
+            top = 1 if sign_plane else (1 << idx.bits) - 1
+            fres = idx.f_rescale1[sl] if sign_plane else idx.f_rescale[sl]
+            ip = change(e, top, idx.d, idx.u[sl] >> (idx.bits - 1) if sign_plane else idx.u[sl])
+            dd = fres * math.sqrt(g_j) * (ip - e["ip"])
+            e.update(ip=ip, dis=e["dis"] + dd, lb=e["lb"] + dd, ub=e["ub"] + dd)
+        return e
+    return wrong
+
+
+@pytest.mark.parametrize("pin", ["test_quantized_estimate_hand_example", "on_grid"])
+def test_quantized_inner_product_drops_qbar_sum(monkeypatch, pin):
+    # ip = delta*(2<u,qbar>) + v_l*(2 sum u - d*top): the -top*sum(qbar) term dropped
+    wrong = _estimate_with_ip(mrq.estimate_list,
+                              lambda e, top, d, u: e["ip"] + e["delta"] * top * float(e["qbar"].sum()))
+    monkeypatch.setattr(mrq, "estimate_list", wrong)
+    if pin == "on_grid":
+        _fails(pins.test_quantized_estimate_on_grid_is_exact,
+               pins.multibit_indices.__wrapped__(), 1, 4)
+    else:
+        _fails(pins.test_quantized_estimate_hand_example)
+
+
+@pytest.mark.parametrize("pin", ["test_quantized_estimate_hand_example", "on_grid"])
+def test_quantized_inner_product_offset_without_top(monkeypatch, pin):
+    # the v_l term with d where d*(2^B - 1) belongs (invisible at B = 1)
+    def change(e, top, d, u):
+        return e["ip"] + e["vl"] * (d * top - d)
+    monkeypatch.setattr(mrq, "estimate_list", _estimate_with_ip(mrq.estimate_list, change))
+    if pin == "on_grid":
+        _fails(pins.test_quantized_estimate_on_grid_is_exact,
+               pins.multibit_indices.__wrapped__(), 4, 4)
+    else:
+        _fails(pins.test_quantized_estimate_hand_example)
+
+
+def test_quantized_inner_product_offset_sign(monkeypatch):
+    # v_l*(d*top - 2 sum u): the offset term with its sign flipped
+    def change(e, top, d, u):
+        su = u.astype(np.int64).sum(axis=1)
+        return e["ip"] - 2.0 * e["vl"] * (2.0 * su - d * top)
+    monkeypatch.setattr(mrq, "estimate_list", _estimate_with_ip(mrq.estimate_list, change))
+    _fails(pins.test_quantized_estimate_hand_example)
+    _fails(pins.test_quantized_estimate_off_grid_is_the_dequantized_query,
+           pins.multibit_indices.__wrapped__(), 4)
+
+
+def _margin_variant(kind):
+    def wrong(lb, ub, sc, tau, k, rel):
+        srt = np.sort(ub)
+        if kind == "gap_ranks":                               # gap of ranks k-1, k-2
+            gap_k = ((srt[k - 1] - srt[k - 2]) / max(abs(srt[k - 1]), 1e-30)
+                     if srt.size > k and k >= 2 else math.inf)
+        else:
+            gap_k = (srt[k] - srt[k - 1]) / max(abs(srt[k]), 1e-30) if srt.size > k else math.inf
+        m = np.abs(lb - tau) / sc
+        if kind != "no_zero_width":
+            m = np.where(ub <= tau, np.maximum(m, gap_k), m)
+        return float(np.max(m[rel]) if kind == "max" else np.min(m[rel]))
+    return wrong
+
+
+@pytest.mark.parametrize("kind,pin", [("max", "test_decision_margin_hand_example"),
+                                      ("gap_ranks", "test_decision_margin_hand_example"),
+                                      ("no_zero_width", "test_decision_margin_zero_width_bounds")])
+def test_decision_margin_mistakes(monkeypatch, kind, pin):
+    monkeypatch.setattr(mrq, "_decision_margin", _margin_variant(kind))
+    _fails(getattr(pins, pin))
 
 
 def test_sign_plane_with_full_code_factors(monkeypatch):

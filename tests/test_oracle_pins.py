@@ -134,6 +134,205 @@ def test_quantize_query_golden_and_grid_identity():
         np.testing.assert_allclose(formula, direct, rtol=0, atol=1e-12)
 
 
+def _tiny_list_index(u, bits, f_add, f_rescale, f_err, centroid):
+    """A one-list OracleIndex holding just what Eq. 4 / Eq. 5 read (hand examples)."""
+    u = np.asarray(u, dtype=np.uint8)
+    n, d = u.shape
+    top = (1 << bits) - 1
+    z = np.zeros(n)
+    return mrq.OracleIndex(
+        D=d, d=d, bits=bits, nlist=1, mu=np.zeros(d), lam=np.zeros(d), Pp=np.eye(d),
+        Pr=np.eye(d), W=np.eye(d), centroids=np.asarray(centroid, dtype=np.float64)[None, :],
+        list_offsets=np.array([0, n]), ids=np.arange(n), xd=np.zeros((n, d)),
+        xr=np.zeros((n, 0)), xnorm2=z, u=u, v=2.0 * u.astype(np.float64) - top,
+        f_add=np.asarray(f_add, dtype=np.float64), f_rescale=np.asarray(f_rescale, dtype=np.float64),
+        f_err=np.asarray(f_err, dtype=np.float64), ip_vo=z, resid_norm=z)
+
+
+def test_quantized_estimate_hand_example():
+    """Eq. 4 / Eq. 5 through a 2-bit quantized query, every value worked by hand
+    (tests/golden/quantized_estimate_example.txt)."""
+    g = _load_golden("quantized_estimate_example.txt")
+    idx = _tiny_list_index(g["u"].reshape(2, 4), 2, g["f_add"], g["f_rescale"], g["f_err"],
+                           np.zeros(4))
+    args = (idx, 0, g["qd"], float(g["g"][0]), float(g["qr2"][0]), float(g["sigma"][0]),
+            float(g["eps0"][0]), float(g["m"][0]))
+    for qbits in (2, 0):                        # on the grid both branches agree exactly
+        e = mrq.estimate_list(*args, qbits=qbits)
+        np.testing.assert_allclose(e["ip"], g["ip"], rtol=0, atol=1e-15)
+        np.testing.assert_allclose(e["dis"], g["dis"], rtol=0, atol=1e-14)
+        np.testing.assert_allclose(e["lb"], g["lb"], rtol=0, atol=1e-14)
+        np.testing.assert_allclose(e["ub"], g["ub"], rtol=0, atol=1e-14)
+        if qbits:
+            np.testing.assert_array_equal(e["qbar"], g["qbar"])
+            np.testing.assert_array_equal(e["int_dot"], g["int_dot"])
+            assert e["vl"] == g["vl"][0] and e["delta"] == g["delta"][0]
+
+
+@pytest.fixture(scope="module")
+def multibit_indices():
+    """One small workload encoded with 1, 2 and 4 bits per dimension (same rotation, IVF)."""
+    w = datagen.workload("small", n=4000, n_comp=16, nlist=8, n_query=20)
+    base, queries = datagen.base_and_queries(w)
+    G = datagen.rotation_gaussian(w.d, 17)
+    init = datagen.kmeans_init_indices(w.n, w.nlist, 18)
+    out = {b: mrq.build_index(base, w.d, b, w.nlist, G, init_idx=init, kmeans_iters=4)
+           for b in (1, 2, 4)}
+    return w, queries, out
+
+
+@pytest.mark.parametrize("bits", [1, 2, 4])
+@pytest.mark.parametrize("qbits", [2, 4])
+def test_quantized_estimate_on_grid_is_exact(multibit_indices, bits, qbits):
+    """When q' lies on the query grid (v_l and delta exact in binary), the quantized
+    branch of Eq. 4 must give <v, q'> itself: the code values of the stored levels
+    (v = 2u - (2^B - 1)) against q', summed directly here; the integer dot is <u, qbar>."""
+    w, queries, idxs = multibit_indices
+    idx = idxs[bits]
+    top_q = (1 << qbits) - 1
+    rng = np.random.default_rng(100 * bits + qbits)
+    for j in range(idx.nlist):
+        sl = idx.list_slice(j)
+        if sl.stop == sl.start:
+            continue
+        qb = rng.integers(0, top_q + 1, size=idx.d)
+        qb[rng.integers(idx.d)] = 0
+        qb[(rng.integers(idx.d - 1) + 1 + int(np.argmin(qb))) % idx.d] = top_q
+        vl, dl = -0.625, 2.0 ** -(qbits + 1)          # exact in binary
+        qgrid = vl + dl * qb
+        gj = 0.25                                     # sqrt(g) = 0.5, exact
+        qd = idx.centroids[j] + 0.5 * qgrid
+        e = mrq.estimate_list(idx, j, qd, gj, 0.3, 0.2, 1.9, 4.0, qbits=qbits)
+        np.testing.assert_array_equal(e["qbar"], qb)
+        assert e["vl"] == vl and e["delta"] == dl
+        u = idx.u[sl].astype(np.int64)
+        np.testing.assert_array_equal(e["int_dot"], u @ qb)
+        top = (1 << bits) - 1
+        v = 2 * u - top
+        direct = np.array([sum(float(v[r, i]) * qgrid[i] for i in range(idx.d))
+                           for r in range(u.shape[0])])
+        np.testing.assert_allclose(e["ip"], direct, rtol=0, atol=1e-12)
+        want = idx.f_add[sl] + gj + 0.3 + idx.f_rescale[sl] * 0.5 * direct
+        np.testing.assert_allclose(e["dis"], want, rtol=1e-12, atol=1e-12)
+
+
+@pytest.mark.parametrize("bits", [1, 4])
+def test_quantized_estimate_off_grid_is_the_dequantized_query(multibit_indices, bits):
+    """Off the grid, the quantized branch equals <v, q_hat'> for the dequantized query
+    q_hat' = v_l + delta*qbar, and q_hat' is within delta/2 of q' in every coordinate
+    (round to nearest on a min/max grid with 2^B_q levels)."""
+    w, queries, idxs = multibit_indices
+    idx = idxs[bits]
+    qd, qr, qr2, sigma, qp2 = mrq.project_queries(idx, queries[:6])
+    top = (1 << bits) - 1
+    for i in range(6):
+        lists, g = mrq.probe(idx, qd[i], 3)
+        for j in lists:
+            j = int(j)
+            sl = idx.list_slice(j)
+            e = mrq.estimate_list(idx, j, qd[i], float(g[j]), qr2[i], sigma[i], 1.9, 4.0, qbits=4)
+            qprime = (qd[i] - idx.centroids[j]) / math.sqrt(g[j])
+            qhat = e["vl"] + e["delta"] * e["qbar"].astype(np.float64)
+            assert e["qbar"].min() == 0 and e["qbar"].max() == 15
+            assert np.max(np.abs(qhat - qprime)) <= 0.5 * e["delta"] * (1 + 1e-5) + 1e-7
+            v = 2.0 * idx.u[sl].astype(np.float64) - top
+            np.testing.assert_allclose(e["ip"], v @ qhat, rtol=0,
+                                       atol=1e-12 * (1 + np.abs(v).sum(axis=1).max()))
+
+
+# ------------------------------------------- decision margin (which queries are strict)
+
+def test_decision_margin_hand_example():
+    """k = 2, four candidates with scale 10: tau = 2.0 (2nd smallest UB).
+    |lb - tau|/10 = .15 .05 .09 .2; the 2nd/3rd UB gap is (3 - 2)/3 = 1/3, which
+    protects the two candidates inside the k smallest UBs (lb <= ub <= tau), so their
+    margins are 1/3, 1/3; the others keep .09 and .2."""
+    lb = np.array([0.5, 1.5, 2.9, 4.0])
+    ub = np.array([1.0, 2.0, 3.0, 5.0])
+    sc = np.full(4, 10.0)
+    allrel = np.ones(4, dtype=bool)
+    assert mrq._decision_margin(lb, ub, sc, 2.0, 2, allrel) == pytest.approx(0.09, rel=1e-12)
+    assert mrq._decision_margin(lb, ub, sc, 2.0, 2, np.array([1, 1, 0, 1], bool)) == \
+        pytest.approx(0.2, rel=1e-12)
+    assert mrq._decision_margin(lb, ub, sc, 2.0, 2, np.array([1, 1, 0, 0], bool)) == \
+        pytest.approx(1.0 / 3.0, rel=1e-12)
+    # per-candidate scales divide each candidate's own gap: (2.9 - 2)/... at scale 1
+    sc2 = np.array([10.0, 10.0, 1.0, 10.0])
+    assert mrq._decision_margin(lb, ub, sc2, 2.0, 2, allrel) == pytest.approx(0.2, rel=1e-12)
+
+
+def test_decision_margin_zero_width_bounds():
+    """d = D: lb = ub.  k = 1, bounds 1, 1.001, 4 and tau = 1: the first candidate sits
+    exactly on tau (|lb - tau| = 0), yet it stays selected until the 1st/2nd upper-bound
+    gap (0.001/1.001) closes, so the margin is that gap, not 0."""
+    b = np.array([1.0, 1.001, 4.0])
+    mg = mrq._decision_margin(b, b, np.ones(3), 1.0, 1, np.ones(3, dtype=bool))
+    assert mg == pytest.approx(0.001 / 1.001, rel=1e-12)
+    # fewer than k + 1 candidates: no (k+1)-th bound can displace them
+    assert mrq._decision_margin(b[:1], b[:1], np.ones(1), 1.0, 1, np.ones(1, bool)) == math.inf
+
+
+def test_margin_covers_bound_perturbations(small_workload, small_oracle_index, monkeypatch):
+    """The margin is the promise the GPU parity tests rely on: moving every bound (and
+    every estimate) of a query by less than a fraction of its margin must leave that
+    query's answer unchanged.  Two kinds of move: random ones (estimates, bound widths,
+    sigma), and an adversarial one that pushes every stage-1 lower bound toward
+    tau_A (up when selected, capped at the candidate's own upper bound; down when not),
+    the move that flips the closest stage-1 decision first."""
+    w, base, queries = small_workload
+    idx = small_oracle_index
+    Q = queries[:30]
+    k, nprobe, kw = w.k, w.nprobe, dict(eps0=1.0, m=1.0, qbits=4)
+    ref = mrq.search_contract(idx, Q, k, nprobe, **kw)
+    qd, qr, qr2, sigma, qp2 = mrq.project_queries(idx, Q)
+    orig_est = mrq.estimate_list
+    orig_proj = mrq.project_queries
+    rng = np.random.default_rng(7)
+    st = {"a": 0.0, "tau": None}
+
+    def noisy_est(*a, **kk):
+        e = dict(orig_est(*a, **kk))
+        n = e["dis"].shape[0]
+        if st["tau"] is not None:                    # adversarial: toward tau_A
+            up = e["lb"] <= st["tau"]
+            e["lb"] = np.where(up, np.minimum(e["lb"] + st["a"], e["ub"]), e["lb"] - st["a"])
+            return e
+        shift = rng.uniform(-0.5, 0.5, n) * st["a"]
+        widen = rng.uniform(-0.5, 0.5, n) * st["a"]
+        e["dis"] = e["dis"] + shift
+        e["lb"] = e["lb"] + shift - widen
+        e["ub"] = e["ub"] + shift + widen
+        return e
+
+    def noisy_proj(idx_, Q_):
+        qd_, qr_, qr2_, sig_, qp2_ = orig_proj(idx_, Q_)
+        if st["tau"] is not None:
+            return qd_, qr_, qr2_, sig_, qp2_
+        # moves every stage-2 bound (and stage-1 eps_r) by m * d_sigma <= a/4
+        return qd_, qr_, qr2_, sig_ + st["a"] * 0.25 * rng.uniform(-1, 1, sig_.shape), qp2_
+
+    checked = 0
+    for i in range(Q.shape[0]):
+        if not math.isfinite(ref.margin[i]):
+            continue
+        lists, g = mrq.probe(idx, qd[i], nprobe)
+        pos = np.concatenate([np.arange(*idx.list_slice(int(j)).indices(idx.n)) for j in lists])
+        ub = np.concatenate([orig_est(idx, int(j), qd[i], float(g[j]), qr2[i], sigma[i], 1.0, 1.0,
+                                      qbits=4)["ub"] for j in lists])
+        tau_a = float(np.sort(ub)[k - 1])
+        s_min = min(float(np.min(idx.f_add[pos])) + float(g[lists].min()) + qr2[i],
+                    float(np.min(idx.xnorm2[pos])) + qp2[i], float(ref.dists[i, k - 1]))
+        monkeypatch.setattr(mrq, "estimate_list", noisy_est)
+        monkeypatch.setattr(mrq, "project_queries", noisy_proj)
+        for trial in range(3):
+            st["a"] = 0.1 * ref.margin[i] * s_min
+            st["tau"] = tau_a if trial == 0 else None
+            r = mrq.search_contract(idx, Q[i:i + 1], k, nprobe, **kw)
+            assert r.ids[0].tolist() == ref.ids[i].tolist(), (i, trial, ref.margin[i])
+        monkeypatch.undo()
+        checked += 1
+    assert checked >= 25
+
 # --------------------------------------------- decomposition identities (Eq. 1-3)
 
 def test_eq3_decomposition_exact(small_workload, small_oracle_index):
