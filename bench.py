@@ -62,6 +62,13 @@ def parse_args(argv=None):
                    help="precision form: projection error of each precision against a float64 "
                         "projection with the index's own W and mu, and recall@10 (one JSON line "
                         "per (d, precision); embedding-like workload unless --workload is given)")
+    p.add_argument("--sweep", action="store_true",
+                   help="QPS-vs-recall curve: nprobe ladder (default 16..256) at d in {128, 256} "
+                        "and 1 and 4 bits per dimension, scan GB/s per point (one JSON line "
+                        "per point)")
+    p.add_argument("--sweep-nprobe", default="16,32,64,128,256")
+    p.add_argument("--sweep-shapes", default="128:1,128:4,256:1,256:4",
+                   help="d:bits pairs of the sweep")
     p.add_argument("--serve", action="store_true",
                    help="serving form: Poisson arrivals at swept rates, p50/p99 latency")
     p.add_argument("--rates", default="20000,100000,500000,2000000",
@@ -144,11 +151,36 @@ class ClockSampler:
 # captured with ncu at the calibrated GIST-like configuration; see
 # profiles/dram_gist-1M-d960_tuned-bf16_nprobe3.md.  Used only when the timed
 # run matches that configuration exactly.
+NCU_TRAFFIC_SOURCE = "profiles/dram_gist-1M-d960_tuned-bf16_nprobe3.md"
 NCU_TRAFFIC = {
     ("k_fin_exact_r", "gist-like-1M-d960", 128, 1, "tuned_bf16_q4", 3, 1.0, 1.0): 1346259456,
     ("k_fin_stage2", "gist-like-1M-d960", 128, 1, "tuned_bf16_q4", 3, 1.0, 1.0): 529399040,
     ("k_scan_q", "gist-like-1M-d960", 128, 1, "tuned_bf16_q4", 3, 1.0, 1.0): 41613824,
 }
+
+
+PREC_NAMES = {0: "f32", 1: "bf16", 2: "bf16x3", 3: "e4m3"}
+
+
+def form_dtype(opts) -> str:
+    """Arithmetic of a search form: the projection's operand type (tensor-core forms
+    accumulate in f32), the query code width of the stage-1 scan (u4: 4-bit integer
+    query against the integer code levels; f32: float query), and f32 for estimates,
+    bounds and exact distances."""
+    proj = PREC_NAMES.get(int(opts.precision), "f32")
+    scan = f"u{opts.query_bits}" if opts.query_bits else "f32"
+    return f"{proj}-proj/{scan}-scan/f32-dist"
+
+
+def form_summary(results, forms, names):
+    """The fastest of ``names`` that reached the recall target, as a small object."""
+    got = [(results[n]["qps"], n) for n in names if results.get(n, {}).get("qps")]
+    if not got:
+        return None
+    q, n = max(got)
+    r = results[n]
+    return {"form": n, "value": q, "unit": UNIT, "dtype": form_dtype(forms[n]),
+            "ms_per_step": r["ms_per_step"], "nprobe": r["nprobe"], "recall@10": r["recall"]}
 
 
 # ------------------------------------------------------------ multi-rank
@@ -510,12 +542,108 @@ def run_precision_report(args):
     return 0
 
 
+def run_sweep(args):
+    """QPS-vs-recall curve of the GIST-like configuration (Exp-1's methodology, Fig. 5):
+    for each (d, bits) of --sweep-shapes and each nprobe of --sweep-nprobe, recall@10
+    against exact ground truth, queries/s of the plain float32 per-query form, of the
+    float32 projection with a 4-bit query (per-pair scan) and of the autotuned bf16 form,
+    and the stage-1 scan's algorithmic bytes per second (candidates x (B*d/8 code bytes +
+    12 factor bytes) over the scan's CUDA-event time).  eps0 and m stay at the library's
+    defaults (1.9, 4).  One JSON line per point, then a summary line."""
+    import numpy as np
+    import torch
+
+    import datagen
+    import paper_2411_06158_gb300 as mrq
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    w0 = workload_of(args)
+    base, queries = datagen.base_and_queries(w0)
+    base_t = torch.from_numpy(base).to(dev)
+    q_t = torch.from_numpy(queries).to(dev)
+    truth = ground_truth(base_t, q_t, w0.k)
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    peak, peak_kind = load_peaks()
+    forms = {
+        "plain_fp32": dict(query_bits=0),
+        "plain_q4": dict(query_bits=4),
+        "tuned_bf16_q4": dict(query_bits=4, precision=mrq.PREC_BF16, batched=mrq.SCAN_AUTO,
+                              graph=1),
+    }
+    ids = torch.empty((w0.n_query, w0.k), dtype=torch.int64, device=dev)
+    dists = torch.empty((w0.n_query, w0.k), dtype=torch.float32, device=dev)
+
+    def run(idx, npb, kw, steps, profile):
+        o = mrq.mrq_search_opts(stream=stream, profile=int(profile),
+                                **{**kw, "graph": 0 if profile else kw.get("graph", 0)})
+        for _ in range(2):
+            mrq.mrq_search(idx, q_t, w0.k, npb, o, out=(ids, dists))
+        per, scan = [], []
+        for _ in range(steps):
+            flush.zero_()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            mrq.mrq_search(idx, q_t, w0.k, npb, o, out=(ids, dists))
+            b.record(stream)
+            b.synchronize()
+            per.append(a.elapsed_time(b))
+            if profile:
+                scan.append(mrq.mrq_last_search_profile(idx)[0]["scan"])
+        return sorted(per)[len(per) // 2], (sorted(scan)[len(scan) // 2] if scan else None)
+
+    curve = []
+    for shape in args.sweep_shapes.split(","):
+        d, bits = (int(t) for t in shape.split(":"))
+        w = w0.scaled(d=d, bits=bits)
+        t0 = time.time()
+        idx = mrq.mrq_build(base_t, d, bits, w.nlist, mrq.mrq_build_opts(seed=w.seed("method")))
+        torch.cuda.synchronize()
+        t_build = time.time() - t0
+        for npb in [int(t) for t in args.sweep_nprobe.split(",")]:
+            if npb > w.nlist:
+                continue
+            for name, kw in forms.items():
+                tune = None
+                if kw.get("batched") == mrq.SCAN_AUTO:
+                    tune = mrq.mrq_autotune(idx, q_t, w.k, npb,
+                                            mrq.mrq_search_opts(stream=stream, **kw))
+                ms, _ = run(idx, npb, kw, args.steps, False)
+                pms, scan_ms = run(idx, npb, kw, args.steps, True)
+                r = recall(ids.cpu().numpy(), truth)
+                st = mrq.mrq_last_search_stats(idx, w.n_query)
+                cand = float(st["n_cand"].mean())
+                scan_bytes = cand * w.n_query * (bits * d / 8 + 12)
+                gbs = scan_bytes / (scan_ms / 1000.0) / 1e9 if scan_ms else None
+                pt = {"metric": "QPS-vs-recall", "workload": w.name, "n": w.n, "D": w.D, "d": d,
+                      "bits": bits, "nlist": w.nlist, "k": w.k, "queries": w.n_query,
+                      "nprobe": npb, "eps0": 1.9, "m": 4.0, "form": name,
+                      "dtype": form_dtype(mrq.mrq_search_opts(**kw)), "recall@10": r,
+                      "qps": w.n_query / (ms / 1000.0), "ms_per_step": ms,
+                      "scan_ms": scan_ms, "scan_GBps_algorithmic": gbs,
+                      "scan_frac_of_peak": (gbs / peak) if gbs else None, "peak_kind": peak_kind,
+                      "cand_per_query": cand, "s1_per_query": float(st["n_s1"].mean()),
+                      "exact_per_query": float(st["n_exact"].mean()),
+                      "scan_form": None if tune is None else tune["scan"], "build_s": t_build,
+                      "l2": "256 MB buffer written between timed steps"}
+                curve.append(pt)
+                print(json.dumps(pt), flush=True)
+        del idx
+        torch.cuda.empty_cache()
+    print(json.dumps({"report": "sweep", "points": len(curve)}))
+    return 0
+
+
 def main(argv=None):
     args = parse_args(argv)
     if args.impl == "reference":
         return run_reference(args)
     if args.serve:
         return run_serving(args)
+    if args.sweep:
+        return run_sweep(args)
     if args.precision_report:
         return run_precision_report(args)
     if args.variance_report:
@@ -756,7 +884,11 @@ def main(argv=None):
     tkey = (kname, w.name, w.d, w.bits, best, B["nprobe"], round(B["m"], 3), round(B["eps0"], 3))
     traffic = NCU_TRAFFIC.get(tkey) if w.n_query == 10_000 else None
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-            "frac": achieved / peak, "traffic": traffic, "kernel": kname,
+            "frac": achieved / peak, "traffic": traffic,
+            "traffic_source": (f"ncu capture recorded in {NCU_TRAFFIC_SOURCE} (same kernel, "
+                               "workload and operating point; not measured in this run)"
+                               if traffic is not None else None),
+            "kernel": kname,
             "peak_kind": peak_kind, "algorithmic_bytes_per_launch": alg_bytes,
             "launch_ms": launch_ms,
             "others": {s_: {"kernel": per_q[s_][0],
@@ -777,7 +909,8 @@ def main(argv=None):
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "scaling": "weak", "vs_baseline": None, "dtype": form_dtype(forms[best]),
+        "data": "synthetic",
         "config": {"workload": w.name, "n": w.n, "D": w.D, "d": w.d, "bits": w.bits,
                    "nlist": w.nlist, "k": w.k, "queries_per_step": w.n_query,
                    "nprobe": B["nprobe"], "m": B["m"], "eps0": B["eps0"], "recall@10": B["recall"],
@@ -786,6 +919,9 @@ def main(argv=None):
         "e2e": {"value": e2e_qps, "unit": UNIT, "h2d_bytes_per_step": w.n_query * w.D * 4,
                 "d2h_bytes_per_step": w.n_query * w.k * 12},
         "gpu_launches": B["launches_per_step"] * args.steps,
+        # the same metric for the forms whose projection error is at float32 level
+        "fp32_equivalent": form_summary(results, forms, ("bf16x3_q4", "plain_q4", "plain_fp32")),
+        "plain_fp32": form_summary(results, forms, ("plain_fp32",)),
         "roofline": roof, "cpu_baseline": cpu, "clocks": clocks,
         "forms": {k: {kk: vv for kk, vv in v.items() if kk != "per_step_ms"} for k, v in results.items()},
         "build_s": t_build, "datagen_s": t_gen,

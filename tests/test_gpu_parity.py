@@ -29,8 +29,7 @@ if not torch.cuda.is_available():  # pragma: no cover
 
 import paper_2411_06158_gb300 as mrq  # noqa: E402
 
-STRICT = 1e-5       # oracle margin above which answers must be identical
-DIST_RTOL = 2e-5    # float32 distance vs float64 oracle
+from parity_helpers import DIST_RTOL, STRICT, check_answers  # noqa: E402
 
 
 def _setup(tmp_path_factory, name, **over):
@@ -62,19 +61,9 @@ def fullrank(tmp_path_factory):
     return _setup(tmp_path_factory, "fr", D=64, d=64, n=8000, n_comp=32, nlist=40, n_query=80)
 
 
-def _check_answers(S, ids, dists, ref, k):
-    base, queries = S["base"], S["queries"]
-    strict = ref.margin > STRICT
-    assert strict.mean() > 0.8, "too few decisive queries for a meaningful comparison"
-    np.testing.assert_array_equal(ids[strict], ref.ids[strict])
-    np.testing.assert_allclose(dists[strict], ref.dists[strict], rtol=DIST_RTOL, atol=1e-6)
-    for qi in np.nonzero(~strict)[0]:
-        got = ids[qi][ids[qi] >= 0]
-        true = np.sum((base[got].astype(np.float64) - queries[qi]) ** 2, axis=1)
-        np.testing.assert_allclose(dists[qi][:got.size], true, rtol=1e-4, atol=1e-5)
-        assert np.all(np.diff(dists[qi][:got.size]) >= 0)
-        assert len(set(got.tolist()) & set(ref.ids[qi].tolist())) >= k - 1
-    return int(strict.sum())
+def _check_answers(S, ids, dists, ref, k, min_strict=0.9, label=""):
+    return check_answers(S["base"], S["queries"], np.asarray(ids), np.asarray(dists), ref, k,
+                         min_strict=min_strict, label=label)
 
 
 @pytest.mark.parametrize("qbits", [0, 4])
@@ -86,14 +75,14 @@ def test_same_index_search(small, qbits, mode):
     opts = mrq.mrq_search_opts(mode=mode, query_bits=qbits)
     ids, dists = mrq.mrq_search(S["gidx"], q, w.k, w.nprobe, opts)
     ref = omrq.search_contract(S["stored"], S["queries"], w.k, w.nprobe, mode=mode, qbits=qbits)
-    n = _check_answers(S, ids.cpu().numpy(), dists.cpu().numpy(), ref, w.k)
+    n = _check_answers(S, ids.cpu().numpy(), dists.cpu().numpy(), ref, w.k, min_strict=0.95,
+                       label=f"small mode={mode} qbits={qbits}")
     st = mrq.mrq_last_search_stats(S["gidx"], len(S["queries"]))
     np.testing.assert_array_equal(st["n_cand"], ref.n_cand)
     strict = ref.margin > STRICT
     # survivor counts agree up to float32 decisions on irrelevant candidates
     assert np.abs(st["n_s1"] - ref.n_s1)[strict].max() <= max(3, 0.01 * ref.n_s1.max())
     assert np.abs(st["n_exact"] - ref.n_s2)[strict].max() <= max(3, 0.01 * ref.n_s2.max())
-    assert n >= 0.8 * len(S["queries"])
 
 
 @pytest.mark.parametrize("fixture", ["multibit", "fullrank"])
