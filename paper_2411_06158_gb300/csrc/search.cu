@@ -659,12 +659,29 @@ __global__ void __launch_bounds__(SCAN_WARPS * 32) k_scan(ScanParams P) {
 // BITS code planes, QB query planes.  The same arithmetic, in the same order, as
 // k_scan<KM, true, false>, with the query planes in registers (warp-uniform ballot
 // words), the candidate's code words fetched with VW-wide loads and every loop
-// unrolled; no shared memory.  The insertion into the warp's top-k list (KM 0) skips
-// upper bounds not below the query's published bound, which cannot lower tau.
+// unrolled.  The insertion into the warp's top-k list (KM 0) skips upper bounds not
+// below the query's published bound, which cannot lower tau.
 // LB: code planes stored (LB > BITS: only the top BITS planes are read, so LB = bits,
 // BITS = 1 scans the sign plane of a multi-bit code: stage 1a of 1 bit + refinement).
+// Per 32-candidate block the loop keeps only what each block needs: the next block's
+// loads are issued before this one is scored (short codes), the query's published bound
+// is read one block ahead, survivors go to a per-warp staging buffer in shared memory
+// that is appended to the query's survivor list with one atomic per SCAN_STAGE entries,
+// and the next work item is claimed while the current one is scanned.
+constexpr int SCAN_STAGE = 64;
+
+// resident CTAs per SM the register budget is cut for, from the registers a lane needs:
+// the query planes (qb x nch words), the code words (twice for the software pipeline of
+// short codes) and about 30 for the rest
+constexpr int scan_q_min_ctas(int nch, int words, int qb) {
+  return (qb * nch + (words <= 16 ? 2 * words : words) + 30) <= 64 ? 4
+         : (qb * nch + (words <= 16 ? 2 * words : words) + 30) <= 80 ? 3
+         : (qb * nch + (words <= 16 ? 2 * words : words) + 30) <= 128 ? 2 : 1;
+}
+
 template <int KM, int NCH, int BITS, int QB, int LB = BITS>
-__global__ void __launch_bounds__(SCAN_WARPS * 32) k_scan_q(ScanParams P) {
+__global__ void __launch_bounds__(SCAN_WARPS * 32, scan_q_min_ctas(NCH, BITS * NCH, QB))
+    k_scan_q(ScanParams P) {
   constexpr int W = BITS * NCH;                                 // words read per candidate
   constexpr int WL = LB * NCH;                                  // words stored per candidate
   constexpr int VW = (WL % 4 == 0) ? 4 : (WL % 2 == 0) ? 2 : 1; // the layout's vector width
@@ -672,13 +689,20 @@ __global__ void __launch_bounds__(SCAN_WARPS * 32) k_scan_q(ScanParams P) {
   constexpr int topc = (1 << BITS) - 1;
   constexpr int topq = (1 << QB) - 1;
   constexpr int d = NCH * 32;
-  const int lane = threadIdx.x & 31;
+  __shared__ int32_t stg_pos[SCAN_WARPS][SCAN_STAGE];
+  __shared__ float stg_lb[SCAN_WARPS][SCAN_STAGE];
+  __shared__ float stg_ub[SCAN_WARPS][SCAN_STAGE];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  int32_t* s_pos = stg_pos[wid];
+  float* s_lb = stg_lb[wid];
+  float* s_ub = stg_ub[wid];
   const int64_t n_items = P.items ? (int64_t)*P.nitems : P.npairs;
+  unsigned int it_next = 0;
+  if (lane == 0) it_next = atomicAdd(P.work, 1u);
   while (true) {
-    unsigned int it = 0;
-    if (lane == 0) it = atomicAdd(P.work, 1u);
-    it = __shfl_sync(0xffffffffu, it, 0);
+    const unsigned int it = __shfl_sync(0xffffffffu, it_next, 0);
     if ((int64_t)it >= n_items) break;
+    if (lane == 0) it_next = atomicAdd(P.work, 1u);   // claimed now, used next round
     int64_t w = it, c_lo = 0, c_hi = -1;
     if (P.items) {
       const int64_t v = P.items[it];
@@ -731,41 +755,61 @@ __global__ void __launch_bounds__(SCAN_WARPS * 32) k_scan_q(ScanParams P) {
     const int64_t lsize = P.loff[j + 1] - lb0;
     const int64_t size = c_hi < 0 ? lsize : min(lsize, c_hi);
     const int64_t pb0 = P.ploff[j];
-    float lst = FINF;
+    float lst = FINF, kth = FINF;
     float top4[4] = {FINF, FINF, FINF, FINF};
     const int mper = (P.k + 31) >> 5;
     float tau = FINF;
     float gt = KM != 2 ? fkey_inv(__ldcg(P.gtau + q)) : FINF;
+    uint32_t gnext = 0;           // lane 0: the published bound, read one block ahead
+    if (KM != 2 && lane == 0) gnext = __ldcg(P.gtau + q);
+    int fill = 0;                 // staged survivors of this warp
+    // one append of the staged survivors to the query's list
+    auto flush = [&]() {
+      __syncwarp();
+      unsigned base = 0;
+      if (lane == 0) base = atomicAdd(P.qcnt + q, (unsigned)fill);
+      base = __shfl_sync(0xffffffffu, base, 0);
+      const int64_t at = q * P.cap + base;
+      for (int i = lane; i < fill; i += 32) {
+        P.spos[at + i] = s_pos[i];
+        P.slb[at + i] = s_lb[i];
+        P.sub[at + i] = s_ub[i];
+      }
+      __syncwarp();
+      fill = 0;
+    };
 
-    // a block's code words and factors (its 32 candidates' padded positions)
-    auto fetch = [&](int64_t b0, uint32_t (&cw)[W], float& fa, float& fr, float& fe) {
-      const int64_t pp = pb0 + b0 + lane;
-      const uint32_t* cbase = P.codes + (pp >> 5) * (int64_t)(WL * 32) + (pp & 31) * VW;
+    // the lane's padded position, advanced one 32-candidate block at a time (blocks
+    // start at multiples of 32: list starts are padded, chunks are multiples of 32)
+    int64_t pp = pb0 + c_lo + lane;
+    auto fetch = [&](uint32_t (&cw)[W], float& fa, float& fr, float& fe) {
+      const uint32_t* cptr = P.codes + (pp >> 5) * (int64_t)(WL * 32) + lane * VW;
       if constexpr (OFF % VW != 0 || W % VW != 0) {
         // the planes read do not fill whole vector groups: one word at a time
 #pragma unroll
         for (int t = 0; t < W; ++t) {
           const int wl = OFF + t;
-          cw[t] = __ldg(cbase + (wl / VW) * 32 * VW + wl % VW);
+          cw[t] = __ldg(cptr + (wl / VW) * 32 * VW + wl % VW);
         }
       } else {
 #pragma unroll
-      for (int gq = 0; gq < W / VW; ++gq) {
-        const uint32_t* src = cbase + (OFF / VW + gq) * 32 * VW;
-        if (VW == 4) {
-          const uint4 v = __ldg(reinterpret_cast<const uint4*>(src));
-          cw[gq * 4] = v.x; cw[gq * 4 + 1] = v.y; cw[gq * 4 + 2] = v.z; cw[gq * 4 + 3] = v.w;
-        } else if (VW == 2) {
-          const uint2 v = __ldg(reinterpret_cast<const uint2*>(src));
-          cw[gq * 2] = v.x; cw[gq * 2 + 1] = v.y;
-        } else {
-          cw[gq] = __ldg(src);
+        for (int gq = 0; gq < W / VW; ++gq) {
+          const uint32_t* src = cptr + (OFF / VW + gq) * 32 * VW;
+          if (VW == 4) {
+            const uint4 v = __ldg(reinterpret_cast<const uint4*>(src));
+            cw[gq * 4] = v.x; cw[gq * 4 + 1] = v.y; cw[gq * 4 + 2] = v.z; cw[gq * 4 + 3] = v.w;
+          } else if (VW == 2) {
+            const uint2 v = __ldg(reinterpret_cast<const uint2*>(src));
+            cw[gq * 2] = v.x; cw[gq * 2 + 1] = v.y;
+          } else {
+            cw[gq] = __ldg(src);
+          }
         }
-      }
       }
       fa = __ldg(P.fadd + pp);
       fr = __ldg(P.fres + pp);
       fe = __ldg(P.ferr + pp);
+      pp += 32;
     };
     // software pipeline (short codes): the next block's loads are in flight while this
     // one is scored; long codes (W > 16) are popcount-bound and keep the registers
@@ -773,7 +817,7 @@ __global__ void __launch_bounds__(SCAN_WARPS * 32) k_scan_q(ScanParams P) {
     uint32_t nw[W];
     float nfa = 0.f, nfr = 0.f, nfe = 0.f;
     if constexpr (PF) {
-      if (c_lo < size) fetch(c_lo, nw, nfa, nfr, nfe);
+      if (c_lo < size) fetch(nw, nfa, nfr, nfe);
     }
     for (int64_t b0 = c_lo; b0 < size; b0 += 32) {
       const int64_t idx = b0 + lane;
@@ -784,9 +828,9 @@ __global__ void __launch_bounds__(SCAN_WARPS * 32) k_scan_q(ScanParams P) {
 #pragma unroll
         for (int t = 0; t < W; ++t) cw[t] = nw[t];
         fa = nfa; fr = nfr; fe = nfe;
-        if (b0 + 32 < size) fetch(b0 + 32, nw, nfa, nfr, nfe);
+        if (b0 + 32 < size) fetch(nw, nfa, nfr, nfe);
       } else {
-        fetch(b0, cw, fa, fr, fe);
+        fetch(cw, fa, fr, fe);
       }
       int dot = 0, su = 0;
 #pragma unroll
@@ -808,49 +852,50 @@ __global__ void __launch_bounds__(SCAN_WARPS * 32) k_scan_q(ScanParams P) {
       float lb = dis - eps, ub = dis + eps;
       if (!valid) { lb = FINF; ub = FINF; }
       if (KM != 2 && b0 > c_lo) {
-        float g2 = 0.f;
-        if (lane == 0) g2 = fkey_inv(__ldcg(P.gtau + q));
-        gt = fminf(gt, __shfl_sync(0xffffffffu, g2, 0));
+        gt = fminf(gt, fkey_inv(__shfl_sync(0xffffffffu, gnext, 0)));
+        if (lane == 0) gnext = __ldcg(P.gtau + q);
       }
       if (KM == 0) {
-        float kth = __shfl_sync(0xffffffffu, lst, P.k - 1);
         const bool in = ub < kth && ub < gt;
         unsigned mask = __ballot_sync(0xffffffffu, in);
-        if (__popc(mask) > 6) {
-          // many: sort this block's bounds across the lanes and merge the two ascending
-          // lists (the k smallest of the union are the same values in any order)
-          float v = in ? ub : FINF;
+        if (mask) {
+          if (__popc(mask) > 6) {
+            // many: sort this block's bounds across the lanes and merge the two ascending
+            // lists (the k smallest of the union are the same values in any order)
+            float v = in ? ub : FINF;
 #pragma unroll
-          for (int size2 = 2; size2 <= 32; size2 <<= 1) {
+            for (int size2 = 2; size2 <= 32; size2 <<= 1) {
 #pragma unroll
-            for (int stride = size2 >> 1; stride > 0; stride >>= 1) {
-              const float o = __shfl_xor_sync(0xffffffffu, v, stride);
-              const bool up = (lane & size2) == 0, lower = (lane & stride) == 0;
-              v = (lower == up) ? fminf(v, o) : fmaxf(v, o);
+              for (int stride = size2 >> 1; stride > 0; stride >>= 1) {
+                const float o = __shfl_xor_sync(0xffffffffu, v, stride);
+                const bool up = (lane & size2) == 0, lower = (lane & stride) == 0;
+                v = (lower == up) ? fminf(v, o) : fmaxf(v, o);
+              }
+            }
+            // min(lst[i], v[31 - i]) are the 32 smallest of both, a bitonic sequence
+            float mg = fminf(lst, __shfl_sync(0xffffffffu, v, 31 - lane));
+#pragma unroll
+            for (int stride = 16; stride > 0; stride >>= 1) {
+              const float o = __shfl_xor_sync(0xffffffffu, mg, stride);
+              mg = (lane & stride) == 0 ? fminf(mg, o) : fmaxf(mg, o);
+            }
+            lst = lane < P.k ? mg : FINF;
+            mask = 0;
+          }
+          while (mask) {
+            int src = __ffs(mask) - 1;
+            mask &= mask - 1;
+            float v = __shfl_sync(0xffffffffu, ub, src);
+            float cur = __shfl_sync(0xffffffffu, lst, P.k - 1);
+            if (v < cur) {
+              float prev = __shfl_up_sync(0xffffffffu, lst, 1);
+              float nl = (lst <= v) ? lst : ((lane == 0 || prev <= v) ? v : prev);
+              lst = lane < P.k ? nl : FINF;
             }
           }
-          // min(lst[i], v[31 - i]) are the 32 smallest of both, a bitonic sequence
-          float mg = fminf(lst, __shfl_sync(0xffffffffu, v, 31 - lane));
-#pragma unroll
-          for (int stride = 16; stride > 0; stride >>= 1) {
-            const float o = __shfl_xor_sync(0xffffffffu, mg, stride);
-            mg = (lane & stride) == 0 ? fminf(mg, o) : fmaxf(mg, o);
-          }
-          lst = lane < P.k ? mg : FINF;
-          mask = 0;
+          kth = __shfl_sync(0xffffffffu, lst, P.k - 1);
         }
-        while (mask) {
-          int src = __ffs(mask) - 1;
-          mask &= mask - 1;
-          float v = __shfl_sync(0xffffffffu, ub, src);
-          float cur = __shfl_sync(0xffffffffu, lst, P.k - 1);
-          if (v < cur) {
-            float prev = __shfl_up_sync(0xffffffffu, lst, 1);
-            float nl = (lst <= v) ? lst : ((lane == 0 || prev <= v) ? v : prev);
-            lst = lane < P.k ? nl : FINF;
-          }
-        }
-        tau = fminf(gt, __shfl_sync(0xffffffffu, lst, P.k - 1));
+        tau = fminf(gt, kth);
       } else if (KM == 1) {
         float v = ub;
 #pragma unroll
@@ -865,17 +910,18 @@ __global__ void __launch_bounds__(SCAN_WARPS * 32) k_scan_q(ScanParams P) {
       const bool surv = valid && lb <= tau;
       const unsigned sm = __ballot_sync(0xffffffffu, surv);
       if (sm) {
-        unsigned base = 0;
-        if (lane == 0) base = atomicAdd(P.qcnt + q, (unsigned)__popc(sm));
-        base = __shfl_sync(0xffffffffu, base, 0);
+        const int cnt = __popc(sm);
+        if (fill + cnt > SCAN_STAGE) flush();
         if (surv) {
-          const int64_t at = q * P.cap + base + __popc(sm & ((1u << lane) - 1));
-          P.spos[at] = (int32_t)(lb0 + idx);
-          P.slb[at] = lb;
-          P.sub[at] = ub;
+          const int at = fill + __popc(sm & ((1u << lane) - 1));
+          s_pos[at] = (int32_t)(lb0 + idx);
+          s_lb[at] = lb;
+          s_ub[at] = ub;
         }
+        fill += cnt;
       }
     }
+    if (fill) flush();
     __syncwarp();
   }
 }
