@@ -574,7 +574,20 @@ CUtensorMap make_map(const void* base, uint64_t rows, uint64_t K, uint32_t box_r
   return m;
 }
 
-int* g_err = nullptr;
+// The pipeline error word (and a page-locked host copy for asynchronous readback) of
+// each device, made on first use with that device current: a kernel only ever writes
+// the word of the device it runs on.
+constexpr int TC_MAX_DEVICES = 64;
+std::mutex g_err_mu;
+int* g_err_dev[TC_MAX_DEVICES] = {};
+int* g_err_host[TC_MAX_DEVICES] = {};
+
+int current_device_slot() {
+  int dev = 0;
+  MRQ_CUDA(cudaGetDevice(&dev));
+  MRQ_REQUIRE(dev >= 0 && dev < TC_MAX_DEVICES, "device ordinal too large for the error-word table");
+  return dev;
+}
 
 template <int BN, int PSEL, int STAGES, bool F8 = false>
 void launch_tc(const void* A2, const void* B2, const TcArgs& a, cudaStream_t st) {
@@ -631,24 +644,39 @@ bool tc_available() {
 }
 
 int* tc_error_word() {
-  if (!g_err) {
-    MRQ_CUDA(cudaMalloc(&g_err, sizeof(int)));
-    MRQ_CUDA(cudaMemset(g_err, 0, sizeof(int)));
+  const int dev = current_device_slot();
+  std::lock_guard<std::mutex> lk(g_err_mu);
+  if (!g_err_dev[dev]) {
+    int* p = nullptr;
+    MRQ_CUDA(cudaMalloc(&p, sizeof(int)));
+    MRQ_CUDA(cudaMemset(p, 0, sizeof(int)));
+    g_err_dev[dev] = p;
   }
-  return g_err;
+  return g_err_dev[dev];
 }
 
 int* tc_error_mirror() {
-  static int* h = nullptr;
-  if (!h) MRQ_CUDA(cudaHostAlloc(reinterpret_cast<void**>(&h), sizeof(int), cudaHostAllocDefault));
-  return h;
+  const int dev = current_device_slot();
+  std::lock_guard<std::mutex> lk(g_err_mu);
+  if (!g_err_host[dev]) {
+    int* h = nullptr;
+    MRQ_CUDA(cudaHostAlloc(reinterpret_cast<void**>(&h), sizeof(int), cudaHostAllocDefault));
+    g_err_host[dev] = h;
+  }
+  return g_err_host[dev];
 }
 
 int tc_check_error() {
-  if (!g_err) return 0;
+  const int dev = current_device_slot();
+  int* w = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(g_err_mu);
+    w = g_err_dev[dev];
+  }
+  if (!w) return 0;
   int h = 0;
-  MRQ_CUDA(cudaMemcpy(&h, g_err, sizeof(int), cudaMemcpyDeviceToHost));
-  if (h) MRQ_CUDA(cudaMemset(g_err, 0, sizeof(int)));
+  MRQ_CUDA(cudaMemcpy(&h, w, sizeof(int), cudaMemcpyDeviceToHost));
+  if (h) MRQ_CUDA(cudaMemset(w, 0, sizeof(int)));
   return h;
 }
 
