@@ -703,12 +703,19 @@ __global__ void __launch_bounds__(SCAN_WARPS * 32, scan_q_min_ctas(NCH, BITS * N
     const unsigned int it = __shfl_sync(0xffffffffu, it_next, 0);
     if ((int64_t)it >= n_items) break;
     if (lane == 0) it_next = atomicAdd(P.work, 1u);   // claimed now, used next round
-    int64_t w = it, c_lo = 0, c_hi = -1;
+    int64_t w, c_lo = 0, c_hi = -1;
     if (P.items) {
       const int64_t v = P.items[it];
       w = v >> 32;
       c_lo = (v & 0xffffffffll) * P.chunk;
       c_hi = c_lo + P.chunk;
+    } else {
+      // probe-rank-major order: every query's nearest list first, then every query's
+      // second list, ...; a query's later lists then start from the bound its nearest
+      // list published instead of an empty top-k list
+      const uint32_t nqr = (uint32_t)(P.npairs / P.nprobe);
+      const uint32_t r = it / nqr;
+      w = (int64_t)(it - r * nqr) * P.nprobe + r;
     }
     const int64_t q = (int64_t)((uint32_t)w / (uint32_t)P.nprobe);  // pairs < 2^31
     const int j = P.plist[w];
@@ -779,10 +786,10 @@ __global__ void __launch_bounds__(SCAN_WARPS * 32, scan_q_min_ctas(NCH, BITS * N
       fill = 0;
     };
 
-    // the lane's padded position, advanced one 32-candidate block at a time (blocks
-    // start at multiples of 32: list starts are padded, chunks are multiples of 32)
-    int64_t pp = pb0 + c_lo + lane;
-    auto fetch = [&](uint32_t (&cw)[W], float& fa, float& fr, float& fe) {
+    // the lane's codes and factors of the 32-candidate block starting at candidate b
+    // (blocks start at multiples of 32: list starts are padded, chunks are multiples of 64)
+    auto fetch = [&](int64_t b, uint32_t (&cw)[W], float& fa, float& fr, float& fe) {
+      const int64_t pp = pb0 + b + lane;
       const uint32_t* cptr = P.codes + (pp >> 5) * (int64_t)(WL * 32) + lane * VW;
       if constexpr (OFF % VW != 0 || W % VW != 0) {
         // the planes read do not fill whole vector groups: one word at a time
@@ -809,116 +816,152 @@ __global__ void __launch_bounds__(SCAN_WARPS * 32, scan_q_min_ctas(NCH, BITS * N
       fa = __ldg(P.fadd + pp);
       fr = __ldg(P.fres + pp);
       fe = __ldg(P.ferr + pp);
-      pp += 32;
     };
-    // software pipeline (short codes): the next block's loads are in flight while this
-    // one is scored; long codes (W > 16) are popcount-bound and keep the registers
+    // software pipeline (short codes): the next U blocks' loads are in flight while these
+    // are scored; long codes (W > 16) are popcount-bound and keep the registers.  Short
+    // codes (W <= 4) score two blocks per iteration: two independent dots to overlap, and
+    // the bound refresh, threshold and survivor bookkeeping once per 64 candidates.
     constexpr bool PF = W <= 16;
-    uint32_t nw[W];
-    float nfa = 0.f, nfr = 0.f, nfe = 0.f;
+    constexpr int U = W <= 4 ? 2 : 1;
+    uint32_t nw[U][W];
+    float nfa[U], nfr[U], nfe[U];
     if constexpr (PF) {
-      if (c_lo < size) fetch(nw, nfa, nfr, nfe);
+#pragma unroll
+      for (int u = 0; u < U; ++u)
+        if (c_lo + 32 * u < size) fetch(c_lo + 32 * u, nw[u], nfa[u], nfr[u], nfe[u]);
     }
-    for (int64_t b0 = c_lo; b0 < size; b0 += 32) {
-      const int64_t idx = b0 + lane;
-      const bool valid = idx < size;
-      uint32_t cw[W];
-      float fa, fr, fe;
+    for (int64_t b0 = c_lo; b0 < size; b0 += 32 * U) {
+      uint32_t cw[U][W];
+      float fa[U], fr[U], fe[U];
       if constexpr (PF) {
 #pragma unroll
-        for (int t = 0; t < W; ++t) cw[t] = nw[t];
-        fa = nfa; fr = nfr; fe = nfe;
-        if (b0 + 32 < size) fetch(nw, nfa, nfr, nfe);
-      } else {
-        fetch(cw, fa, fr, fe);
-      }
-      int dot = 0, su = 0;
+        for (int u = 0; u < U; ++u) {
 #pragma unroll
-      for (int a = 0; a < BITS; ++a) {
-        int pd = 0, ps = 0;
-#pragma unroll
-        for (int c = 0; c < NCH; ++c) {
-          const uint32_t word = cw[a * NCH + c];
-          ps += __popc(word);
-#pragma unroll
-          for (int bq = 0; bq < QB; ++bq) pd += __popc(word & qw[bq][c]) << bq;
+          for (int t = 0; t < W; ++t) cw[u][t] = nw[u][t];
+          fa[u] = nfa[u]; fr[u] = nfr[u]; fe[u] = nfe[u];
         }
-        dot += pd << a;
-        su += ps << a;
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+          if (b0 + 32 * (U + u) < size) fetch(b0 + 32 * (U + u), nw[u], nfa[u], nfr[u], nfe[u]);
+      } else {
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+          if (b0 + 32 * u < size) fetch(b0 + 32 * u, cw[u], fa[u], fr[u], fe[u]);
       }
-      const float ip = qdelta * (float)(2 * dot - topc * qsum) + ql * (float)(2 * su - d * topc);
-      const float dis = fa + a0 + fr * sg * ip;  // Eq. 4
-      const float eps = e0 * fe + em;             // Eq. 5 + Chebyshev
-      float lb = dis - eps, ub = dis + eps;
-      if (!valid) { lb = FINF; ub = FINF; }
+      float lb[U], ub[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        // <u, qbar> = sum_a 2^a sum_bq 2^bq popc(plane_a & qplane_bq): per query plane
+        // the popcounts of all chunks are summed first, the planes weighted after
+        int dot = 0, su = 0;
+#pragma unroll
+        for (int a = 0; a < BITS; ++a) {
+          int pl[QB];
+          int ps = 0;
+#pragma unroll
+          for (int bq = 0; bq < QB; ++bq) pl[bq] = 0;
+#pragma unroll
+          for (int c = 0; c < NCH; ++c) {
+            const uint32_t word = cw[u][a * NCH + c];
+            ps += __popc(word);
+#pragma unroll
+            for (int bq = 0; bq < QB; ++bq) pl[bq] += __popc(word & qw[bq][c]);
+          }
+          int pd = pl[QB - 1];
+#pragma unroll
+          for (int bq = QB - 2; bq >= 0; --bq) pd = 2 * pd + pl[bq];
+          dot += pd << a;
+          su += ps << a;
+        }
+        const float ip =
+            qdelta * (float)(2 * dot - topc * qsum) + ql * (float)(2 * su - d * topc);
+        const float dis = fa[u] + a0 + fr[u] * sg * ip;  // Eq. 4
+        const float eps = e0 * fe[u] + em;                // Eq. 5 + Chebyshev
+        const bool valid = b0 + 32 * u + lane < size;
+        lb[u] = valid ? dis - eps : FINF;
+        ub[u] = valid ? dis + eps : FINF;
+      }
       if (KM != 2 && b0 > c_lo) {
         gt = fminf(gt, fkey_inv(__shfl_sync(0xffffffffu, gnext, 0)));
         if (lane == 0) gnext = __ldcg(P.gtau + q);
       }
       if (KM == 0) {
-        const bool in = ub < kth && ub < gt;
-        unsigned mask = __ballot_sync(0xffffffffu, in);
-        if (mask) {
-          if (__popc(mask) > 6) {
-            // many: sort this block's bounds across the lanes and merge the two ascending
-            // lists (the k smallest of the union are the same values in any order)
-            float v = in ? ub : FINF;
 #pragma unroll
-            for (int size2 = 2; size2 <= 32; size2 <<= 1) {
+        for (int u = 0; u < U; ++u) {
+          const bool in = ub[u] < kth && ub[u] < gt;
+          unsigned mask = __ballot_sync(0xffffffffu, in);
+          if (mask) {
+            if (__popc(mask) > 6) {
+              // many: sort this block's bounds across the lanes and merge the two ascending
+              // lists (the k smallest of the union are the same values in any order)
+              float v = in ? ub[u] : FINF;
 #pragma unroll
-              for (int stride = size2 >> 1; stride > 0; stride >>= 1) {
-                const float o = __shfl_xor_sync(0xffffffffu, v, stride);
-                const bool up = (lane & size2) == 0, lower = (lane & stride) == 0;
-                v = (lower == up) ? fminf(v, o) : fmaxf(v, o);
+              for (int size2 = 2; size2 <= 32; size2 <<= 1) {
+#pragma unroll
+                for (int stride = size2 >> 1; stride > 0; stride >>= 1) {
+                  const float o = __shfl_xor_sync(0xffffffffu, v, stride);
+                  const bool up = (lane & size2) == 0, lower = (lane & stride) == 0;
+                  v = (lower == up) ? fminf(v, o) : fmaxf(v, o);
+                }
+              }
+              // min(lst[i], v[31 - i]) are the 32 smallest of both, a bitonic sequence
+              float mg = fminf(lst, __shfl_sync(0xffffffffu, v, 31 - lane));
+#pragma unroll
+              for (int stride = 16; stride > 0; stride >>= 1) {
+                const float o = __shfl_xor_sync(0xffffffffu, mg, stride);
+                mg = (lane & stride) == 0 ? fminf(mg, o) : fmaxf(mg, o);
+              }
+              lst = lane < P.k ? mg : FINF;
+              mask = 0;
+            }
+            while (mask) {
+              int src = __ffs(mask) - 1;
+              mask &= mask - 1;
+              float v = __shfl_sync(0xffffffffu, ub[u], src);
+              float cur = __shfl_sync(0xffffffffu, lst, P.k - 1);
+              if (v < cur) {
+                float prev = __shfl_up_sync(0xffffffffu, lst, 1);
+                float nl = (lst <= v) ? lst : ((lane == 0 || prev <= v) ? v : prev);
+                lst = lane < P.k ? nl : FINF;
               }
             }
-            // min(lst[i], v[31 - i]) are the 32 smallest of both, a bitonic sequence
-            float mg = fminf(lst, __shfl_sync(0xffffffffu, v, 31 - lane));
-#pragma unroll
-            for (int stride = 16; stride > 0; stride >>= 1) {
-              const float o = __shfl_xor_sync(0xffffffffu, mg, stride);
-              mg = (lane & stride) == 0 ? fminf(mg, o) : fmaxf(mg, o);
-            }
-            lst = lane < P.k ? mg : FINF;
-            mask = 0;
+            kth = __shfl_sync(0xffffffffu, lst, P.k - 1);
           }
-          while (mask) {
-            int src = __ffs(mask) - 1;
-            mask &= mask - 1;
-            float v = __shfl_sync(0xffffffffu, ub, src);
-            float cur = __shfl_sync(0xffffffffu, lst, P.k - 1);
-            if (v < cur) {
-              float prev = __shfl_up_sync(0xffffffffu, lst, 1);
-              float nl = (lst <= v) ? lst : ((lane == 0 || prev <= v) ? v : prev);
-              lst = lane < P.k ? nl : FINF;
-            }
-          }
-          kth = __shfl_sync(0xffffffffu, lst, P.k - 1);
         }
         tau = fminf(gt, kth);
       } else if (KM == 1) {
-        float v = ub;
 #pragma unroll
-        for (int t = 0; t < 4; ++t) {
-          if (t < mper && v < top4[t]) { float x = top4[t]; top4[t] = v; v = x; }
+        for (int u = 0; u < U; ++u) {
+          float v = ub[u];
+#pragma unroll
+          for (int t = 0; t < 4; ++t) {
+            if (t < mper && v < top4[t]) { float x = top4[t]; top4[t] = v; v = x; }
+          }
         }
         float mine = mper == 1 ? top4[0] : mper == 2 ? top4[1] : mper == 3 ? top4[2] : top4[3];
         tau = fminf(gt, warp_max(mine));
       }
       if (KM != 2 && lane == 0 && tau < gt) atomicMin(P.gtau + q, fkey(tau));
       if (KM != 2) gt = fminf(gt, tau);
-      const bool surv = valid && lb <= tau;
-      const unsigned sm = __ballot_sync(0xffffffffu, surv);
-      if (sm) {
-        const int cnt = __popc(sm);
-        if (fill + cnt > SCAN_STAGE) flush();
-        if (surv) {
-          const int at = fill + __popc(sm & ((1u << lane) - 1));
-          s_pos[at] = (int32_t)(lb0 + idx);
-          s_lb[at] = lb;
-          s_ub[at] = ub;
+      unsigned sm[U], any = 0;
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        sm[u] = __ballot_sync(0xffffffffu, lb[u] <= tau);   // invalid lanes hold +inf
+        any |= sm[u];
+      }
+      if (any) {
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          const int cnt = __popc(sm[u]);
+          if (fill + cnt > SCAN_STAGE) flush();
+          if ((sm[u] >> lane) & 1u) {
+            const int at = fill + __popc(sm[u] & ((1u << lane) - 1));
+            s_pos[at] = (int32_t)(lb0 + b0 + 32 * u + lane);
+            s_lb[at] = lb[u];
+            s_ub[at] = ub[u];
+          }
+          fill += cnt;
         }
-        fill += cnt;
       }
     }
     if (fill) flush();
