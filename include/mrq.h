@@ -209,8 +209,9 @@ int mrq_project(mrq_index* index, const float* queries, int64_t nq,
  * Scratch: MRQ_PREC_FP32 needs none.  The tensor-core precisions stage the
  * bf16 operand of the query in a fixed static device array of
  * MRQ_PROJECT_NOALLOC_MAX_BYTES bytes that the library owns; a request that
- * needs more (nq * D > 4194304 at MRQ_PREC_BF16, > 2097152 at MRQ_PREC_BF16X3,
- * about 8.4e6 at MRQ_PREC_FP8) returns MRQ_EINVAL without launching anything: split
+ * needs more (nq * D > 4194304 at MRQ_PREC_BF16, > 2097152 at MRQ_PREC_BF16X3; at
+ * MRQ_PREC_FP8 whenever 256 * ceil(nq * D / 256) + 4 * nq > 8388608, e.g.
+ * nq > 63550 at D = 128) returns MRQ_EINVAL without launching anything: split
  * the batch.  The
  * pipeline error word in that array is cleared at the start of every call;
  * nothing else in it has to start at zero.

@@ -51,11 +51,37 @@ def test_two_calls_match_mrq_project(index, prec):
         assert _rel_err(out, ref, q, mu) <= TOL
 
 
-@pytest.mark.parametrize("prec,per", [(mrq.PREC_BF16, 2), (mrq.PREC_BF16X3, 4)],
-                         ids=["bf16", "bf16x3"])
-def test_largest_batch_and_rejection(index, prec, per):
+def _scratch_bytes(prec, nq, D):
+    """Scratch one call needs (include/mrq.h): 2 or 4 bytes per element of the bf16
+    operand; at FP8 one byte per element rounded up to 256, plus 4 bytes per row scale."""
+    if prec == mrq.PREC_FP8:
+        return (nq * D + 255) // 256 * 256 + 4 * nq
+    return nq * D * (2 if prec == mrq.PREC_BF16 else 4)
+
+
+def _largest_batch(prec, D):
+    lo, hi = 1, MAX_BYTES                      # scratch need grows with nq
+    while lo < hi:
+        mid = (lo + hi + 1) // 2
+        if _scratch_bytes(prec, mid, D) <= MAX_BYTES:
+            lo = mid
+        else:
+            hi = mid - 1
+    return lo
+
+
+def test_fp8_bound_stated_in_the_header():
+    assert _largest_batch(mrq.PREC_FP8, 128) == 63550
+    assert _largest_batch(mrq.PREC_BF16, 128) * 128 == 4194304
+    assert _largest_batch(mrq.PREC_BF16X3, 128) * 128 == 2097152
+
+
+@pytest.mark.parametrize("prec", [mrq.PREC_BF16, mrq.PREC_BF16X3, mrq.PREC_FP8],
+                         ids=["bf16", "bf16x3", "fp8"])
+def test_largest_batch_and_rejection(index, prec):
     D, gi, queries, mu = index
-    nmax = MAX_BYTES // (per * D)
+    nmax = _largest_batch(prec, D)
+    assert _scratch_bytes(prec, nmax + 1, D) > MAX_BYTES
     opts = mrq.mrq_search_opts(precision=prec)
     reps = (nmax + 1 + queries.shape[0] - 1) // queries.shape[0]
     big = queries.repeat(reps, 1)[: nmax + 1].contiguous()
