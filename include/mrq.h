@@ -72,6 +72,13 @@ typedef struct {
   const double* rotation_gauss; /* d x d Gaussian draw behind P_r (Algorithm 1), or NULL */
   double auto_d_variance;       /* with d = 0: the fraction of the total PCA variance the
                                    chosen d must hold (Eq. 8); default 0.8 */
+  const int64_t* pca_rows;      /* host array of pca_n base rows (each in [0, n)) whose mean
+                                   and 1/pca_n covariance define the PCA and the residual
+                                   variances instead of the whole base: the sampled global
+                                   statistics Section 5 suggests when the data is spread over
+                                   many machines; every row is still projected, clustered and
+                                   encoded.  NULL (default) = all rows */
+  int64_t pca_n;                /* rows in pca_rows, >= 2 when pca_rows is given */
 } mrq_build_opts;
 
 typedef struct {
@@ -333,6 +340,40 @@ int mrq_index_info(const mrq_index* index, mrq_index_info_t* info);
  * step. */
 int mrq_index_export(const mrq_index* index, const char* field, void* host_dst,
                      size_t bytes);
+
+/*
+ * List-sharded search (Section 5, distributed deployment: MRQ inside a distributed
+ * IVF system).  The IVF lists are partitioned over nshards shards; every shard keeps
+ * the global statistics (mu, lambda, W, all centroids) so that it probes the same
+ * lists as the whole index, but holds only the members of its own lists.  A query
+ * is searched on every shard (same k, nprobe and options), each shard returns its
+ * top k under the threshold contract of its own candidates, and one exchange plus
+ * mrq_merge_topk gives the answer.  Whenever every estimate's bounds hold, each
+ * shard's answer is the exact top k of its probed candidates, so the merged answer
+ * is the exact top k of all probed candidates: the single index's answer.
+ */
+
+/* Partition plan (host only, no GPU call): lists in decreasing size (ties: lower list
+ * id first) each go to the shard holding the fewest vectors so far (ties: lower shard).
+ *  list_sizes: int64[nlist] (host).  owner: int32[nlist] (host, caller-owned) receives
+ *  each list's shard.  1 <= nshards <= nlist, else MRQ_EINVAL. */
+int mrq_shard_plan(const int64_t* list_sizes, int nlist, int nshards, int32_t* owner);
+
+/* A new index (on the current device) holding shard `shard` of `index` under
+ * mrq_shard_plan: the same header, mu, lambda, W and centroids, and the members
+ * (codes, factors, x_d', x_r, norms, ids) of the lists the plan gives it; the other
+ * lists are empty.  *out is released with mrq_free.  0 <= shard < nshards <= nlist;
+ * MRQ_EINVAL also when the shard would hold no vector. */
+int mrq_index_shard(const mrq_index* index, int nshards, int shard, mrq_index** out);
+
+/* Merge per-shard answers: ids / dists are nparts x nq x k (part-major, each part's rows
+ * sorted by (dist, id), id -1 / dist +inf padding), out_ids / out_dists nq x k receive
+ * the k smallest (dist, id) of each query over all parts, -1 / +inf padded.  All four
+ * arrays host or all four device memory (the device merge runs on cuda_stream, NULL =
+ * the legacy default stream, and returns after it completes); caller-owned.  Host merges
+ * make no GPU call.  1 <= nparts <= 64, 1 <= k <= 1024, nq >= 0, else MRQ_EINVAL. */
+int mrq_merge_topk(const int64_t* ids, const float* dists, int nparts, int64_t nq, int k,
+                   void* cuda_stream, int64_t* out_ids, float* out_dists);
 
 void mrq_free(mrq_index* index);
 

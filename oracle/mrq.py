@@ -28,6 +28,7 @@ __all__ = [
     "build_index", "project_queries", "probe", "quantize_query", "estimate_list",
     "search_contract", "search_literal", "exact_knn", "SearchResult", "sq8_train",
     "sq8_estimate", "search_mrsq8", "opq_train", "pq_decode", "pq_estimate", "search_mrpq",
+    "restrict_lists", "merge_answers",
 ]
 
 MODE_MRQ = 0
@@ -232,18 +233,22 @@ def factors(resid_norm: np.ndarray, xr2: np.ndarray, v: np.ndarray, o: np.ndarra
 
 def build_index(S, d: int, bits: int, nlist: int, G: np.ndarray, *,
                 init_idx: np.ndarray | None = None, init_centroids: np.ndarray | None = None,
-                kmeans_iters: int = 20) -> OracleIndex:
+                kmeans_iters: int = 20, pca_rows: np.ndarray | None = None) -> OracleIndex:
     """Algorithm 1: PCA, rotate, split, IVF on x_d, quantize with P_r, precompute.
 
     ``G`` is the d x d Gaussian draw behind P_r.  The initial centroids are the
     base points ``init_idx`` (projected) or the raw-space points
     ``init_centroids`` (projected); one of the two is required.
+    ``pca_rows``: the PCA (mean, covariance, eigenvalues) is taken over these base
+    rows only -- the sampled global statistics Section 5 suggests for data spread over
+    many machines; every row is still projected, clustered and encoded.
     """
     S = np.asarray(S, dtype=np.float64)
     n, D = S.shape
     if not (0 < d <= D and d % 32 == 0 and 1 <= bits <= 8 and 1 <= nlist <= n and d >= 2):
         raise ValueError("invalid build parameters")
-    mu, lam, Pp = pca_train(S)                       # PCA matrix and residual variances
+    # PCA matrix and residual variances
+    mu, lam, Pp = pca_train(S if pca_rows is None else S[np.asarray(pca_rows)])
     Xp = (S - mu) @ Pp.T                             # x_p = P_p x (centred)
     xd, xr = Xp[:, :d], Xp[:, d:]                    # split
     if init_centroids is not None:
@@ -277,6 +282,39 @@ def build_index(S, d: int, bits: int, nlist: int, G: np.ndarray, *,
                        ip_vo=ip[order], resid_norm=rn[order],
                        f_rescale1=None if fr1 is None else fr1[order],
                        f_err1=None if fe1 is None else fe1[order])
+
+
+def restrict_lists(idx: OracleIndex, lists) -> OracleIndex:
+    """One shard of a list-sharded index (Section 5, distributed deployment): the same
+    statistics, rotation and centroids (so it probes the same lists), holding only the
+    members of ``lists``; every other list is empty.  Row order inside a list is kept."""
+    keep = np.zeros(idx.nlist, dtype=bool)
+    keep[np.asarray(lists, dtype=np.int64)] = True
+    sizes = np.where(keep, np.diff(idx.list_offsets), 0)
+    rows = np.concatenate([np.arange(idx.list_offsets[j], idx.list_offsets[j + 1])
+                           for j in range(idx.nlist) if keep[j]] or [np.zeros(0, np.int64)])
+    offs = np.zeros(idx.nlist + 1, dtype=np.int64)
+    offs[1:] = np.cumsum(sizes)
+    sel = lambda a: None if a is None else a[rows]
+    return dataclasses.replace(
+        idx, list_offsets=offs, ids=idx.ids[rows], xd=idx.xd[rows], xr=idx.xr[rows],
+        xnorm2=idx.xnorm2[rows], u=idx.u[rows], v=idx.v[rows], f_add=idx.f_add[rows],
+        f_rescale=idx.f_rescale[rows], f_err=idx.f_err[rows], ip_vo=idx.ip_vo[rows],
+        resid_norm=idx.resid_norm[rows], f_rescale1=sel(idx.f_rescale1), f_err1=sel(idx.f_err1))
+
+
+def merge_answers(parts, k: int):
+    """The k smallest (distance, id) of each query over several answers (the shards'),
+    padding (id -1) ignored; returns (ids, dists) padded with -1 / +inf."""
+    nq = parts[0][0].shape[0]
+    ids = np.full((nq, k), -1, dtype=np.int64)
+    dists = np.full((nq, k), np.inf)
+    for q in range(nq):
+        pairs = sorted((float(d_), int(i_)) for pi, pd in parts
+                       for i_, d_ in zip(pi[q], pd[q]) if i_ >= 0)[:k]
+        for t, (d_, i_) in enumerate(pairs):
+            ids[q, t], dists[q, t] = i_, d_
+    return ids, dists
 
 
 # -------------------------------------------------------------------------- search

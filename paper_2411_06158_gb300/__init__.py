@@ -31,7 +31,7 @@ EXPORTS = [
     "mrq_index_info", "mrq_index_export", "mrq_free", "mrq_last_error",
     "mrq_server_opts_default", "mrq_server_start", "mrq_submit", "mrq_submit_many", "mrq_poll",
     "mrq_poll_many", "mrq_poll_completed", "mrq_server_stats", "mrq_server_reset_stats",
-    "mrq_server_stop",
+    "mrq_server_stop", "mrq_shard_plan", "mrq_index_shard", "mrq_merge_topk",
 ]
 
 
@@ -44,7 +44,8 @@ class MRQError(RuntimeError):
 class BuildOpts(C.Structure):
     _fields_ = [("seed", C.c_uint64), ("kmeans_iters", C.c_int),
                 ("init_centroids", C.c_void_p), ("init_ids", C.c_void_p),
-                ("rotation_gauss", C.c_void_p), ("auto_d_variance", C.c_double)]
+                ("rotation_gauss", C.c_void_p), ("auto_d_variance", C.c_double),
+                ("pca_rows", C.c_void_p), ("pca_n", C.c_int64)]
 
 
 class SearchOpts(C.Structure):
@@ -107,6 +108,9 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
     lib.mrq_server_stats.argtypes = [vp, C.POINTER(ServerStats)]
     lib.mrq_server_reset_stats.argtypes = [vp]
     lib.mrq_server_stop.argtypes = [vp]
+    lib.mrq_shard_plan.argtypes = [vp, i32, i32, vp]
+    lib.mrq_index_shard.argtypes = [vp, i32, i32, C.POINTER(vp)]
+    lib.mrq_merge_topk.argtypes = [vp, vp, i32, i64, i32, vp, vp, vp]
     lib.mrq_last_error.restype = C.c_char_p
     for name in EXPORTS:
         if name not in ("mrq_free", "mrq_last_error", "mrq_build_opts_default",
@@ -147,12 +151,16 @@ def _f32(x):
 
 
 def mrq_build_opts(seed: int = 1, kmeans_iters: int = 20, init_centroids=None, init_ids=None,
-                   rotation_gauss=None, auto_d_variance: float = 0.8):
+                   rotation_gauss=None, auto_d_variance: float = 0.8, pca_rows=None):
     """Build options plus the arrays that must stay alive during the call."""
     o = BuildOpts()
     _lib.mrq_build_opts_default(C.byref(o))
     o.seed, o.kmeans_iters, o.auto_d_variance = seed, kmeans_iters, auto_d_variance
     keep = []
+    if pca_rows is not None:
+        a = np.ascontiguousarray(pca_rows, dtype=np.int64)
+        keep.append(a)
+        o.pca_rows, o.pca_n = a.ctypes.data, a.shape[0]
     if init_centroids is not None:
         a = np.ascontiguousarray(init_centroids, dtype=np.float32)
         keep.append(a)
@@ -333,6 +341,43 @@ def mrq_index_export(index: Index, field: str) -> np.ndarray:
     dt, shp = _FIELD_SHAPES[field]
     out = np.empty(shp(info), dtype=dt)
     _check(_lib.mrq_index_export(index.handle, field.encode(), _ptr(out), out.nbytes))
+    return out
+
+
+def mrq_shard_plan(list_sizes, nshards: int) -> np.ndarray:
+    """Shard of every IVF list under the library's partition plan (host only)."""
+    sizes = np.ascontiguousarray(list_sizes, dtype=np.int64)
+    owner = np.empty(sizes.shape[0], dtype=np.int32)
+    _check(_lib.mrq_shard_plan(_ptr(sizes), sizes.shape[0], nshards, _ptr(owner)))
+    return owner
+
+
+def mrq_index_shard(index: Index, nshards: int, shard: int) -> Index:
+    """The index of shard `shard` of `nshards` (every centroid, its own lists' members)."""
+    h = C.c_void_p()
+    _check(_lib.mrq_index_shard(index.handle, nshards, shard, C.byref(h)))
+    return Index(h.value)
+
+
+def mrq_merge_topk(ids, dists, k: int, out=None, stream=None):
+    """Merge per-part answers: ids / dists are (nparts, nq, k), numpy arrays or CUDA
+    tensors; returns (ids, dists) of shape (nq, k) in the same kind of memory."""
+    nparts, nq = int(ids.shape[0]), int(ids.shape[1])
+    if out is None:
+        if _is_torch(ids):
+            import torch
+            out = (torch.empty((nq, k), dtype=torch.int64, device=ids.device),
+                   torch.empty((nq, k), dtype=torch.float32, device=ids.device))
+        else:
+            out = (np.empty((nq, k), dtype=np.int64), np.empty((nq, k), dtype=np.float32))
+    if not _is_torch(ids):
+        ids = np.ascontiguousarray(ids, dtype=np.int64)
+        dists = np.ascontiguousarray(dists, dtype=np.float32)
+    st = None
+    if stream is not None:
+        st = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+    _check(_lib.mrq_merge_topk(_ptr(ids), _ptr(dists), nparts, nq, k, st, _ptr(out[0]),
+                               _ptr(out[1])))
     return out
 
 

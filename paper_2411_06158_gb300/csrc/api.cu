@@ -166,6 +166,11 @@ int mrq_build(const float* base, int64_t n, int D, int d, int bits, int nlist,
                 "auto_d_variance must be in (0, 1]");
     MRQ_REQUIRE(d != 0 || o.rotation_gauss == nullptr,
                 "d = 0 (chosen by Eq. 8) cannot take a rotation_gauss draw");
+    if (o.pca_rows) {
+      MRQ_REQUIRE(o.pca_n >= 2 && o.pca_n <= n, "pca_n must be in [2, n] with pca_rows");
+      for (int64_t i = 0; i < o.pca_n; ++i)
+        MRQ_REQUIRE(o.pca_rows[i] >= 0 && o.pca_rows[i] < n, "pca_rows out of range");
+    }
     std::unique_ptr<mrq_index> idx(new mrq_index());
     MRQ_CUDA(cudaGetDevice(&idx->device));
     idx->n = n;
@@ -652,6 +657,58 @@ int mrq_save(const mrq_index* idx, const char* path) {
   });
 }
 
+// An index on the current device from the canonical (file) arrays: sections in the order
+// MU__ LAM_ W___ CENT LOFF IDS_ CODE FADD FRES FERR XD__ XR__ XN2_ [FRE1 FER1], validated
+// for sizes by the caller; the offsets, ids and code levels are checked here.
+static std::unique_ptr<mrq_index> index_from_sections(int64_t n, int D, int d, int bits,
+                                                      int nlist,
+                                                      const std::vector<std::vector<uint8_t>>& sec,
+                                                      bool sign_factors) {
+  const int r = D - d;
+  std::unique_ptr<mrq_index> idx(new mrq_index());
+  MRQ_CUDA(cudaGetDevice(&idx->device));
+  idx->n = n; idx->D = D; idx->d = d; idx->bits = bits; idx->nlist = nlist;
+  idx->h_loff.resize(nlist + 1);
+  std::memcpy(idx->h_loff.data(), sec[4].data(), 8 * (nlist + 1));
+  if (idx->h_loff[0] != 0 || idx->h_loff[nlist] != n) mrq::fail(MRQ_EFORMAT, "bad list offsets");
+  for (int j = 0; j < nlist; ++j)
+    if (idx->h_loff[j + 1] < idx->h_loff[j]) mrq::fail(MRQ_EFORMAT, "bad list offsets");
+  {
+    const int64_t* ids = reinterpret_cast<const int64_t*>(sec[5].data());
+    for (int64_t i = 0; i < n; ++i)
+      if (ids[i] < 0 || ids[i] >= (int64_t(1) << 31)) mrq::fail(MRQ_EFORMAT, "id out of range");
+    const uint8_t* lv = sec[6].data();
+    for (size_t i = 0; i < sec[6].size(); ++i)
+      if (lv[i] >> bits) mrq::fail(MRQ_EFORMAT, "code level exceeds 2^bits - 1");
+  }
+  cudaStream_t st = nullptr;
+  auto up = [&](auto& buf, const std::vector<uint8_t>& data, size_t count) {
+    buf.alloc(std::max<size_t>(count, 1));
+    if (count) MRQ_CUDA(cudaMemcpyAsync(buf.p, data.data(), data.size(), cudaMemcpyHostToDevice, st));
+  };
+  up(idx->mu, sec[0], D);
+  up(idx->lam, sec[1], D);
+  up(idx->W, sec[2], (size_t)D * D);
+  up(idx->cent, sec[3], (size_t)nlist * d);
+  up(idx->ids, sec[5], n);
+  up(idx->xd, sec[10], (size_t)n * d);
+  up(idx->xr, sec[11], (size_t)n * r);
+  up(idx->xn2, sec[12], n);
+  mrq::DevBuf<uint8_t> lv;
+  mrq::DevBuf<float> fa, fr, fe, fr1, fe1;
+  up(lv, sec[6], (size_t)n * d);
+  up(fa, sec[7], n);
+  up(fr, sec[8], n);
+  up(fe, sec[9], n);
+  if (sign_factors) {
+    up(fr1, sec[13], n);
+    up(fe1, sec[14], n);
+  }
+  mrq::finalize_layout(idx.get(), lv.p, fa.p, fr.p, fe.p, st, fr1.p, fe1.p);
+  MRQ_CUDA(cudaStreamSynchronize(st));
+  return idx;
+}
+
 int mrq_load(const char* path, mrq_index** out) {
   return guarded([&] {
     MRQ_REQUIRE(path && out, "NULL argument");
@@ -675,12 +732,10 @@ int mrq_load(const char* path, mrq_index** out) {
     get(hdr, 16);
     const int D = hdr[0], d = hdr[1], bits = hdr[2], nlist = hdr[3];
     if (!(n >= 1 && n < (int64_t(1) << 31) && D >= 32 && D <= 16384 && d >= 32 && d <= D &&
-          d % 32 == 0 && d <= MRQ_MAX_D && bits >= 1 && bits <= 8 && nlist >= 1 && nlist <= n))
+          d % 32 == 0 && d <= MRQ_MAX_D && bits >= 1 && bits <= 8 && nlist >= 1 &&
+          nlist <= (1 << 20)))
       mrq::fail(MRQ_EFORMAT, "index header out of range");
     const int r = D - d;
-    std::unique_ptr<mrq_index> idx(new mrq_index());
-    MRQ_CUDA(cudaGetDevice(&idx->device));
-    idx->n = n; idx->D = D; idx->d = d; idx->bits = bits; idx->nlist = nlist;
     struct Want { const char* tag; uint32_t dt; uint64_t count; };
     const Want want[] = {
         {"MU__", DT_F32, (uint64_t)D}, {"LAM_", DT_F32, (uint64_t)D},
@@ -721,45 +776,68 @@ int mrq_load(const char* path, mrq_index** out) {
       if (!seen[w]) mrq::fail(MRQ_EFORMAT, std::string("missing section ") + want[w].tag);
     if (seen[13] != seen[14]) mrq::fail(MRQ_EFORMAT, "FRE1 and FER1 come together");
     const bool sign_factors = seen[13] && bits > 1;
-    idx->h_loff.resize(nlist + 1);
-    std::memcpy(idx->h_loff.data(), sec[4].data(), 8 * (nlist + 1));
-    if (idx->h_loff[0] != 0 || idx->h_loff[nlist] != n) mrq::fail(MRQ_EFORMAT, "bad list offsets");
-    for (int j = 0; j < nlist; ++j)
-      if (idx->h_loff[j + 1] < idx->h_loff[j]) mrq::fail(MRQ_EFORMAT, "bad list offsets");
-    {
-      const int64_t* ids = reinterpret_cast<const int64_t*>(sec[5].data());
-      for (int64_t i = 0; i < n; ++i)
-        if (ids[i] < 0 || ids[i] >= (int64_t(1) << 31)) mrq::fail(MRQ_EFORMAT, "id out of range");
-      const uint8_t* lv = sec[6].data();
-      for (size_t i = 0; i < sec[6].size(); ++i)
-        if (lv[i] >> bits) mrq::fail(MRQ_EFORMAT, "code level exceeds 2^bits - 1");
+    std::unique_ptr<mrq_index> built = index_from_sections(n, D, d, bits, nlist, sec, sign_factors);
+    *out = built.release();
+  });
+}
+
+int mrq_shard_plan(const int64_t* list_sizes, int nlist, int nshards, int32_t* owner) {
+  return guarded([&] { mrq::shard_plan(list_sizes, nlist, nshards, owner); });
+}
+
+int mrq_index_shard(const mrq_index* idx, int nshards, int shard, mrq_index** out) {
+  return guarded([&] {
+    MRQ_REQUIRE(idx && out, "NULL argument");
+    *out = nullptr;
+    MRQ_REQUIRE(nshards >= 1 && nshards <= idx->nlist, "need 1 <= nshards <= nlist");
+    MRQ_REQUIRE(shard >= 0 && shard < nshards, "need 0 <= shard < nshards");
+    use_device(idx);
+    const int nlist = idx->nlist, D = idx->D, d = idx->d, r = D - d;
+    std::vector<int64_t> sizes(nlist), loff(nlist + 1, 0), keep;
+    for (int j = 0; j < nlist; ++j) sizes[j] = idx->h_loff[j + 1] - idx->h_loff[j];
+    std::vector<int32_t> owner(nlist);
+    mrq::shard_plan(sizes.data(), nlist, nshards, owner.data());
+    for (int j = 0; j < nlist; ++j) {
+      if (owner[j] == shard)
+        for (int64_t i = idx->h_loff[j]; i < idx->h_loff[j + 1]; ++i) keep.push_back(i);
+      loff[j + 1] = (int64_t)keep.size();
     }
-    cudaStream_t st = nullptr;
-    auto up = [&](auto& buf, const std::vector<uint8_t>& data, size_t count) {
-      buf.alloc(std::max<size_t>(count, 1));
-      if (count) MRQ_CUDA(cudaMemcpyAsync(buf.p, data.data(), data.size(), cudaMemcpyHostToDevice, st));
-    };
-    up(idx->mu, sec[0], D);
-    up(idx->lam, sec[1], D);
-    up(idx->W, sec[2], (size_t)D * D);
-    up(idx->cent, sec[3], (size_t)nlist * d);
-    up(idx->ids, sec[5], n);
-    up(idx->xd, sec[10], (size_t)n * d);
-    up(idx->xr, sec[11], (size_t)n * r);
-    up(idx->xn2, sec[12], n);
-    mrq::DevBuf<uint8_t> lv;
-    mrq::DevBuf<float> fa, fr, fe, fr1, fe1;
-    up(lv, sec[6], (size_t)n * d);
-    up(fa, sec[7], n);
-    up(fr, sec[8], n);
-    up(fe, sec[9], n);
-    if (sign_factors) {
-      up(fr1, sec[13], n);
-      up(fe1, sec[14], n);
+    const int64_t m = (int64_t)keep.size();
+    MRQ_REQUIRE(m >= 1, "the shard would hold no vector");
+    const bool sign = idx->fres1.p != nullptr;
+    const int nsec = sign ? 15 : 13;
+    // bytes per row of the list-major arrays (0: a global array, copied whole)
+    const size_t row_bytes[15] = {0, 0, 0, 0, 0, 8, (size_t)d, 4, 4, 4, 4 * (size_t)d,
+                                  4 * (size_t)r, 4, 4, 4};
+    std::vector<std::vector<uint8_t>> sec(15);
+    for (int t = 0; t < nsec; ++t) {
+      if (t == 4) {  // LOFF
+        sec[4].resize(8 * loff.size());
+        std::memcpy(sec[4].data(), loff.data(), sec[4].size());
+        continue;
+      }
+      std::vector<uint8_t> data;
+      uint32_t dt = 0;
+      export_field(idx, kTags[t], data, dt, nullptr);
+      const size_t rb = row_bytes[t];
+      if (rb == 0) {
+        sec[t] = std::move(data);
+        continue;
+      }
+      sec[t].resize(rb * (size_t)m);
+      for (int64_t i = 0; i < m; ++i)
+        std::memcpy(sec[t].data() + rb * i, data.data() + rb * keep[i], rb);
     }
-    mrq::finalize_layout(idx.get(), lv.p, fa.p, fr.p, fe.p, st, fr1.p, fe1.p);
-    MRQ_CUDA(cudaStreamSynchronize(st));
-    *out = idx.release();
+    std::unique_ptr<mrq_index> built =
+        index_from_sections(m, D, d, idx->bits, nlist, sec, sign && idx->bits > 1);
+    *out = built.release();
+  });
+}
+
+int mrq_merge_topk(const int64_t* ids, const float* dists, int nparts, int64_t nq, int k,
+                   void* cuda_stream, int64_t* out_ids, float* out_dists) {
+  return guarded([&] {
+    mrq::merge_topk(ids, dists, nparts, nq, k, (cudaStream_t)cuda_stream, out_ids, out_dists);
   });
 }
 

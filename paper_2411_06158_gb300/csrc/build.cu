@@ -66,6 +66,15 @@ struct SplitMix64 {
 
 // ------------------------------------------------------------ mean / covariance
 
+// rows[i] of X (n x D) into row i of out (one CTA per row)
+__global__ void k_gather_rows(const float* __restrict__ X, int D, const int64_t* __restrict__ rows,
+                              int64_t nrows, float* __restrict__ out) {
+  const int64_t i = blockIdx.x;
+  if (i >= nrows) return;
+  const float* src = X + rows[i] * (int64_t)D;
+  for (int c = threadIdx.x; c < D; c += blockDim.x) out[i * D + c] = src[c];
+}
+
 __global__ void k_colsum(const float* __restrict__ X, int64_t n, int D, int64_t rows_per,
                          double* __restrict__ sum) {
   int c = blockIdx.x * blockDim.x + threadIdx.x;
@@ -692,15 +701,28 @@ void build_index(mrq_index* idx, const float* X, const mrq_build_opts& o, cudaSt
   const int D = idx->D, nlist = idx->nlist;
   const uint64_t seed = o.seed ? o.seed : 1;
 
-  // ---- PCA: float64 mean and covariance
+  // ---- PCA: float64 mean and covariance, over all rows or over the sampled rows
+  DevBuf<float> Xs;
+  const float* XP = X;
+  int64_t npca = n;
+  if (o.pca_rows) {
+    npca = o.pca_n;
+    DevBuf<int64_t> rows(npca);
+    MRQ_CUDA(cudaMemcpyAsync(rows.p, o.pca_rows, 8 * npca, cudaMemcpyHostToDevice, st));
+    Xs.alloc((size_t)npca * D);
+    k_gather_rows<<<(unsigned)npca, 128, 0, st>>>(X, D, rows.p, npca, Xs.p);
+    MRQ_CHECK_LAUNCH();
+    MRQ_CUDA(cudaStreamSynchronize(st));
+    XP = Xs.p;
+  }
   DevBuf<double> mu_d(D), C((size_t)D * D);
   MRQ_CUDA(cudaMemsetAsync(mu_d.p, 0, 8 * D, st));
   {
     int64_t rows_per = 4096;
-    dim3 g(ceil_div(D, 128), ceil_div(n, rows_per));
-    k_colsum<<<g, 128, 0, st>>>(X, n, D, rows_per, mu_d.p);
+    dim3 g(ceil_div(D, 128), ceil_div(npca, rows_per));
+    k_colsum<<<g, 128, 0, st>>>(XP, npca, D, rows_per, mu_d.p);
     MRQ_CHECK_LAUNCH();
-    k_scale_d<<<ceil_div(D, 256), 256, 0, st>>>(mu_d.p, D, 1.0 / (double)n);
+    k_scale_d<<<ceil_div(D, 256), 256, 0, st>>>(mu_d.p, D, 1.0 / (double)npca);
     MRQ_CHECK_LAUNCH();
   }
   MRQ_CUDA(cudaMemsetAsync(C.p, 0, C.bytes(), st));
@@ -711,16 +733,17 @@ void build_index(mrq_index* idx, const float* X, const mrq_build_opts& o, cudaSt
       for (int j = i; j < T; ++j) tl.push_back(make_int2(i, j));
     DevBuf<int2> tiles(tl.size());
     MRQ_CUDA(cudaMemcpyAsync(tiles.p, tl.data(), sizeof(int2) * tl.size(), cudaMemcpyHostToDevice, st));
-    int64_t rows_per = std::max<int64_t>(CR, ((n + 255) / 256 + CR - 1) / CR * CR);
+    int64_t rows_per = std::max<int64_t>(CR, ((npca + 255) / 256 + CR - 1) / CR * CR);
     rows_per = std::max<int64_t>(rows_per, 2048);
-    dim3 g((unsigned)tl.size(), ceil_div(n, rows_per));
-    k_cov<<<g, 256, 0, st>>>(X, n, D, mu_d.p, tiles.p, rows_per, C.p);
+    dim3 g((unsigned)tl.size(), ceil_div(npca, rows_per));
+    k_cov<<<g, 256, 0, st>>>(XP, npca, D, mu_d.p, tiles.p, rows_per, C.p);
     MRQ_CHECK_LAUNCH();
     MRQ_CUDA(cudaStreamSynchronize(st));
   }
+  Xs.release();
   std::vector<double> lam_h;
   DevBuf<double> Pp;
-  eigen_pca(C.p, D, 1.0 / (double)n, lam_h, Pp, st);
+  eigen_pca(C.p, D, 1.0 / (double)npca, lam_h, Pp, st);
   C.release();
   if (idx->d == 0) idx->d = choose_d(lam_h, D, o.auto_d_variance);  // Eq. 8
   const int d = idx->d, r = D - d;

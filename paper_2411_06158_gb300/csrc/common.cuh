@@ -267,6 +267,10 @@ void nearest_f32(const float* A, int lda, const float* B, int ldb, int M, int N,
 bool tc_available();
 void project_noalloc(mrq_index* idx, const float* q, int64_t nq, int precision, float* qp,
                      cudaStream_t st);  // static scratch only, no allocation
+// list-sharded search (shard.cu): the partition plan and the merge of per-shard answers
+void shard_plan(const int64_t* sizes, int nlist, int nshards, int32_t* owner);
+void merge_topk(const int64_t* ids, const float* dists, int nparts, int64_t nq, int k,
+                cudaStream_t st, int64_t* out_ids, float* out_dists);
 int* tc_error_word();    // device word the tensor-core kernels set when a wait gives up
 int* tc_error_mirror();  // page-locked host int for reading it back asynchronously
 int tc_check_error();  // nonzero if a bounded wait in a tensor-core kernel gave up

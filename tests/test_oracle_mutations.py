@@ -316,3 +316,47 @@ def test_procrustes_factors_swapped(monkeypatch):
 def pins_small():
     wk, idx = _small()
     return wk, idx
+
+
+def _shard_fixture():
+    import test_shard as ts
+    wk, idx = _small()
+    return ts.sharded.__wrapped__(wk, idx)
+
+
+def test_merge_keeps_the_largest(monkeypatch):
+    def wrong(parts, k):
+        nq = parts[0][0].shape[0]
+        ids = np.full((nq, k), -1, dtype=np.int64)
+        dists = np.full((nq, k), np.inf)
+        for q in range(nq):
+            pairs = sorted(((float(d_), int(i_)) for pi, pd in parts
+                            for i_, d_ in zip(pi[q], pd[q]) if i_ >= 0), reverse=True)[:k]
+            for t, (d_, i_) in enumerate(sorted(pairs)):
+                ids[q, t], dists[q, t] = i_, d_
+        return ids, dists
+    monkeypatch.setattr(mrq, "merge_answers", wrong)
+    import test_shard as ts
+    _fails(ts.test_sharded_without_pruning_is_exact_over_probed_lists, _shard_fixture())
+
+
+def test_shard_rows_off_by_one(monkeypatch):
+    orig = mrq.restrict_lists
+
+    def wrong(idx, lists):
+        sh = orig(idx, lists)
+        sh.ids = np.roll(sh.ids, 1)                              # rows one slot off their lists
+        return sh
+    monkeypatch.setattr(mrq, "restrict_lists", wrong)
+    import test_shard as ts
+    _fails(ts.test_shards_partition_the_index, _shard_fixture())
+
+
+def test_sampled_pca_ignores_the_sample(monkeypatch):
+    orig = mrq.build_index
+
+    def wrong(*a, pca_rows=None, **k):
+        return orig(*a, **k)                                        # full-base PCA
+    monkeypatch.setattr(mrq, "build_index", wrong)
+    import test_shard as ts
+    _fails(ts.test_sampled_pca_is_the_pca_of_the_sample)
