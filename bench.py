@@ -76,6 +76,10 @@ def parse_args(argv=None):
     p.add_argument("--serve-seconds", type=float, default=2.0, help="arrival window per rate")
     p.add_argument("--serve-slots", type=int, default=4, help="concurrent batches (streams)")
     p.add_argument("--serve-wait-us", type=int, default=200, help="longest wait of a partial batch")
+    p.add_argument("--serve-nprobe", default="32,64,128",
+                   help="nprobe values the requests draw from (uniformly)")
+    p.add_argument("--serve-eps0", type=float, default=1.9)
+    p.add_argument("--serve-m", type=float, default=4.0)
     return p.parse_args(argv)
 
 
@@ -404,12 +408,12 @@ def run_serving(args):
     torch.cuda.empty_cache()
     rng = np.random.default_rng(7)
     ks = rng.choice([10, 50, 100], size=w.n_query).astype(np.int32)
-    nprobes = np.array([8, 16, 32], dtype=np.int32)
+    nprobes = np.array([int(t) for t in args.serve_nprobe.split(",")], dtype=np.int32)
     nps = rng.choice(nprobes, size=w.n_query).astype(np.int32)
     # the scan decomposition per batch by the library's rule (per-pair for small batches,
     # batched once each probed list is shared by many of the batch's queries)
-    search = mrq.mrq_search_opts(eps0=1.9, m=4.0, query_bits=4, precision=mrq.PREC_BF16,
-                                 batched=mrq.SCAN_AUTO)
+    search = mrq.mrq_search_opts(eps0=args.serve_eps0, m=args.serve_m, query_bits=4,
+                                 precision=mrq.PREC_BF16, batched=mrq.SCAN_AUTO)
     for rate in [float(x) for x in args.rates.split(",")]:
         srv = mrq.Server(idx, max_batch=4096, max_inflight=args.serve_slots,
                          max_wait_us=args.serve_wait_us, max_k=100, search=search)
@@ -704,6 +708,10 @@ def main(argv=None):
     # MR-SQ (Exp-5): 8-bit SQ of the projected lead coordinates, rerank range 500
     forms["mr_sq8_bf16"] = mrq.mrq_search_opts(mode=mrq.MODE_SQ8, rerank=500,
                                                precision=mrq.PREC_BF16, graph=1, stream=stream)
+    # MR-PQ (Exp-5): OPQ of the projected lead coordinates (subspaces of 2 coordinates,
+    # 16 centroids: 4-bit codes), rerank range 500; the OPQ is trained on the GPU once
+    forms["mr_pq_bf16"] = mrq.mrq_search_opts(mode=mrq.MODE_PQ, rerank=500,
+                                              precision=mrq.PREC_BF16, graph=1, stream=stream)
     if w.bits > 1:
         # 1 bit + refinement: the sign plane first, the full code for its survivors only
         forms["refine_bf16_q4"] = mrq.mrq_search_opts(query_bits=4, precision=mrq.PREC_BF16,
@@ -721,7 +729,7 @@ def main(argv=None):
         Chebyshev multiplier m (Eq. 6) and the confidence parameter eps0 (Eq. 5),
         both left tunable by the paper -- then the fastest (eps0, m, nprobe)."""
         best, last_r = None, 0.0
-        sq8 = opts.mode == mrq.MODE_SQ8      # no error bound: eps0 and m play no part
+        sq8 = opts.mode in (mrq.MODE_SQ8, mrq.MODE_PQ)  # no error bound: eps0, m play no part
         for e0 in (EPS0_LADDER[:1] if sq8 else EPS0_LADDER):
             for m in (M_LADDER[:1] if sq8 else M_LADDER):
                 o = with_m(opts, m, e0)
@@ -778,6 +786,12 @@ def main(argv=None):
 
     if args.form:
         forms = {args.form: forms[args.form]}
+    t_pq = None
+    if "mr_pq_bf16" in forms:
+        t0 = time.time()
+        mrq.mrq_pq_train(idx, w.d // 2, 16, opq_iters=4, km_iters=6, seed=w.seed("method"))
+        torch.cuda.synchronize()
+        t_pq = time.time() - t0
     results = {}
     for name, opts in list(forms.items()):
         if args.nprobe:
@@ -813,8 +827,9 @@ def main(argv=None):
                          "s1_per_query": float(st["n_s1"].mean()),
                          "exact_per_query": float(st["n_exact"].mean()), "per_step_ms": per,
                          "autotune": tune}
-    # the headline is the MRQ method's own best form; MR-SQ (Exp-5) is reported beside it
-    ok = {k: v for k, v in results.items() if v.get("qps") and forms[k].mode != mrq.MODE_SQ8}
+    # the headline is the MRQ method's own best form; MR-SQ and MR-PQ (Exp-5) beside it
+    ok = {k: v for k, v in results.items()
+          if v.get("qps") and forms[k].mode not in (mrq.MODE_SQ8, mrq.MODE_PQ)}
     if not ok and args.form:
         ok = {k: v for k, v in results.items() if v.get("qps")}
     if not ok:
@@ -924,7 +939,7 @@ def main(argv=None):
         "plain_fp32": form_summary(results, forms, ("plain_fp32",)),
         "roofline": roof, "cpu_baseline": cpu, "clocks": clocks,
         "forms": {k: {kk: vv for kk, vv in v.items() if kk != "per_step_ms"} for k, v in results.items()},
-        "build_s": t_build, "datagen_s": t_gen,
+        "build_s": t_build, "datagen_s": t_gen, "pq_train_s": t_pq,
     }
     if rank == 0:
         print(json.dumps(line))

@@ -52,6 +52,14 @@ extern "C" {
                                No error bound: eps0, m, query_bits, batched and refine are
                                ignored.  The codes are made from the index's x_d' on first use
                                (n * d bytes, not saved).  k <= 128. */
+#define MRQ_MODE_PQ 3       /* MR-PQ (Appendix A.2, Exp-5): optimized product quantization
+                               of x_d' (an orthogonal R, M subspaces of d/M coordinates of
+                               x_d' R, K centroids each) instead of the RaBitQ code; estimate
+                               sum_m |(q_d' R)_m - C[m][code_m]|^2 + |x_r|^2 + |q_r|^2 from a
+                               per-query lookup table; the `rerank` smallest estimates (ties
+                               by id) are reranked exactly.  No error bound (as MRQ_MODE_SQ8).
+                               Needs an OPQ: mrq_pq_train, or the PQR_/PQC_/PQK_ sections of
+                               an index file.  k <= 128. */
 
 /* query-projection precision (the first step of Algorithm 2) */
 #define MRQ_PREC_FP32 0   /* float32 CUDA-core GEMM */
@@ -107,8 +115,16 @@ typedef struct {
                        an index holding the sign-plane factors (built by this library, or a
                        file with FRE1/FER1 sections); the scan then runs pair by pair
                        (batched is ignored).  With bits = 1 it changes nothing.  Default 0 */
-  int rerank;       /* MRQ_MODE_SQ8: the rerank range R, k <= R <= 65536; default 500 */
+  int rerank;       /* MRQ_MODE_SQ8 / MRQ_MODE_PQ: the rerank range R, k <= R <= 65536;
+                       default 500 */
   void* cuda_stream;/* cudaStream_t, or NULL */
+  int64_t survivor_region; /* MRQ / MRQ+ modes: entries of each query's stage-1 survivor
+                       region.  0 (default) = every candidate of the nprobe largest lists
+                       when that fits the memory budget for the batch, else the largest
+                       region that does (at least 8192).  A query whose survivors overflow
+                       its region is searched again with the full region after the batch,
+                       so the answer does not depend on it; mrq_last_search_stats still
+                       reports its counters */
 } mrq_search_opts;
 
 #define MRQ_SCAN_PAIRS 0
@@ -134,7 +150,8 @@ typedef struct {
   int D, d, bits, nlist;
   int64_t max_list;     /* largest list size */
   int64_t device_bytes; /* device memory held by the index (its arrays, including the
-                           MR-SQ codes once made; not the search workspace) */
+                           MR-SQ codes once made and the OPQ; not the search workspace) */
+  int pq_M, pq_K;       /* OPQ subspaces and centroids per subspace (0, 0: none) */
 } mrq_index_info_t;
 
 #define MRQ_MAX_D 1024 /* largest quantized dimension d */
@@ -325,7 +342,9 @@ int mrq_server_stop(mrq_server* server);
  * nlist), then tagged sections MU__, LAM_, W___, CENT, LOFF, IDS_, CODE (one u8 level
  * per dimension), FADD, FRES, FERR, XD__, XR__, XN2_ (list-major, unpadded), and, for
  * bits > 1, the optional FRE1, FER1 (f32[n]: Eq. 4 / Eq. 5 factors of the sign plane,
- * used by refine = 1; written when the index holds them, both or neither).  Unknown
+ * used by refine = 1; written when the index holds them, both or neither), and the optional
+ * MR-PQ sections PQR_ (f32[d*d], R), PQC_ (f32[K*d], codebooks M x K x d/M) and PQK_
+ * (u8[n*M], codes, list-major), all three or none.  Unknown
  * sections are skipped.  A malformed or other-version file gives MRQ_EFORMAT, an
  * unreadable path MRQ_EIO. */
 int mrq_save(const mrq_index* index, const char* path);
@@ -340,6 +359,22 @@ int mrq_index_info(const mrq_index* index, mrq_index_info_t* info);
  * step. */
 int mrq_index_export(const mrq_index* index, const char* field, void* host_dst,
                      size_t bytes);
+
+/*
+ * Train the OPQ of MRQ_MODE_PQ on the GPU (Appendix A.2, Exp-5; non-parametric OPQ):
+ * R starts at the identity and the K initial centroids of every subspace are the rows
+ * init_rows (K row positions of the list-major x_d', host int64; NULL = K distinct
+ * rows drawn from `seed`); then opq_iters times: km_iters Lloyd rounds of every
+ * subspace of x_d' R (assignment ties to the lower centroid, float64 means, an empty
+ * centroid keeps its value) and a final assignment, then R = U V^T for
+ * X^T Y = U S V^T (X the rows of x_d', Y their decoded rows; computed as
+ * A (A^T A)^(-1/2) with the float64 Jacobi eigensolver); finally one more k-means of
+ * x_d' R and the codes.  Replaces any earlier OPQ of the index; saved by mrq_save.
+ *  d % M == 0, 2 <= K <= 256, K <= n, M * K <= 4096 (the per-warp lookup table of the
+ *  scan), 0 <= opq_iters, km_iters <= 100, else MRQ_EINVAL.
+ */
+int mrq_pq_train(mrq_index* index, int M, int K, int opq_iters, int km_iters,
+                 const int64_t* init_rows, uint64_t seed);
 
 /*
  * List-sharded search (Section 5, distributed deployment: MRQ inside a distributed

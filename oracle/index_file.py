@@ -12,7 +12,9 @@ dtype: 1 = f32, 2 = f64, 3 = i64, 4 = u8.
 Sections (required): MU__ f32[D], LAM_ f32[D], W___ f32[D*D] (row-major),
 CENT f32[nlist*d], LOFF i64[nlist+1], IDS_ i64[n], CODE u8[n*d] (unsigned level
 per dimension), FADD/FRES/FERR f32[n], XD__ f32[n*d], XR__ f32[n*(D-d)], XN2_ f32[n];
-optional, B > 1: FRE1/FER1 f32[n], the sign plane's factors (1 bit + refinement).
+optional, B > 1: FRE1/FER1 f32[n], the sign plane's factors (1 bit + refinement);
+optional, MR-PQ (Exp-5): PQR_ f32[d*d] the OPQ rotation R (x_d' R is quantized),
+PQC_ f32[M*K*(d/M)] the codebooks (subspace-major), PQK_ u8[n*M] the codes (list-major).
 Vector arrays are in list-major order (list j holds rows LOFF[j]..LOFF[j+1]-1).
 """
 from __future__ import annotations
@@ -41,8 +43,15 @@ def _sections(idx):
          if getattr(idx, "f_rescale1", None) is not None else [])
 
 
-def write_index(idx, path: str) -> None:
+def write_index(idx, path: str, pq=None) -> None:
+    """``pq``: optional (R, C, codes) of ``mrq.opq_train`` on idx.xd, written as the
+    PQR_ / PQC_ / PQK_ sections."""
     secs = _sections(idx)
+    if pq is not None:
+        R, C, codes = pq
+        f32 = lambda a: np.ascontiguousarray(a, dtype=np.float32).ravel()
+        secs += [(b"PQR_", f32(R)), (b"PQC_", f32(C)),
+                 (b"PQK_", np.ascontiguousarray(codes, dtype=np.uint8).ravel())]
     with open(path, "wb") as f:
         f.write(MAGIC)
         f.write(struct.pack("<II", VERSION, len(secs)))

@@ -20,7 +20,7 @@ LIB_PATH = os.path.join(_HERE, "libmrq.so")
 
 MRQ_OK = 0
 MRQ_EINVAL, MRQ_ENOMEM, MRQ_ECUDA, MRQ_EFORMAT, MRQ_EIO, MRQ_ETIMEDOUT = -1, -2, -3, -4, -5, -6
-MODE_MRQ, MODE_MRQ_PLUS, MODE_SQ8 = 0, 1, 2
+MODE_MRQ, MODE_MRQ_PLUS, MODE_SQ8, MODE_PQ = 0, 1, 2, 3
 PREC_FP32, PREC_BF16, PREC_BF16X3, PREC_FP8 = 0, 1, 2, 3
 SCAN_PAIRS, SCAN_BATCHED, SCAN_AUTO, SCAN_BATCHED_TC = 0, 1, 2, 3
 
@@ -31,7 +31,7 @@ EXPORTS = [
     "mrq_index_info", "mrq_index_export", "mrq_free", "mrq_last_error",
     "mrq_server_opts_default", "mrq_server_start", "mrq_submit", "mrq_submit_many", "mrq_poll",
     "mrq_poll_many", "mrq_poll_completed", "mrq_server_stats", "mrq_server_reset_stats",
-    "mrq_server_stop", "mrq_shard_plan", "mrq_index_shard", "mrq_merge_topk",
+    "mrq_server_stop", "mrq_shard_plan", "mrq_index_shard", "mrq_merge_topk", "mrq_pq_train",
 ]
 
 
@@ -52,7 +52,8 @@ class SearchOpts(C.Structure):
     _fields_ = [("eps0", C.c_float), ("m", C.c_float), ("mode", C.c_int),
                 ("precision", C.c_int), ("query_bits", C.c_int), ("batched", C.c_int),
                 ("profile", C.c_int), ("graph", C.c_int), ("refine", C.c_int),
-                ("rerank", C.c_int), ("cuda_stream", C.c_void_p)]
+                ("rerank", C.c_int), ("cuda_stream", C.c_void_p),
+                ("survivor_region", C.c_int64)]
 
 
 class ServerOpts(C.Structure):
@@ -73,7 +74,8 @@ class TuneResult(C.Structure):
 
 class IndexInfo(C.Structure):
     _fields_ = [("n", C.c_int64), ("D", C.c_int), ("d", C.c_int), ("bits", C.c_int),
-                ("nlist", C.c_int), ("max_list", C.c_int64), ("device_bytes", C.c_int64)]
+                ("nlist", C.c_int), ("max_list", C.c_int64), ("device_bytes", C.c_int64),
+                ("pq_M", C.c_int), ("pq_K", C.c_int)]
 
 
 def load_library(path: str = LIB_PATH) -> C.CDLL:
@@ -108,6 +110,7 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
     lib.mrq_server_stats.argtypes = [vp, C.POINTER(ServerStats)]
     lib.mrq_server_reset_stats.argtypes = [vp]
     lib.mrq_server_stop.argtypes = [vp]
+    lib.mrq_pq_train.argtypes = [vp, i32, i32, i32, i32, vp, C.c_uint64]
     lib.mrq_shard_plan.argtypes = [vp, i32, i32, vp]
     lib.mrq_index_shard.argtypes = [vp, i32, i32, C.POINTER(vp)]
     lib.mrq_merge_topk.argtypes = [vp, vp, i32, i64, i32, vp, vp, vp]
@@ -179,12 +182,12 @@ def mrq_build_opts(seed: int = 1, kmeans_iters: int = 20, init_centroids=None, i
 def mrq_search_opts(eps0: float = 1.9, m: float = 4.0, mode: int = MODE_MRQ_PLUS,
                     precision: int = PREC_FP32, query_bits: int = 0, batched: int = 0,
                     profile: int = 0, graph: int = 0, stream=None, refine: int = 0,
-                    rerank: int = 500) -> SearchOpts:
+                    rerank: int = 500, survivor_region: int = 0) -> SearchOpts:
     o = SearchOpts()
     _lib.mrq_search_opts_default(C.byref(o))
     o.eps0, o.m, o.mode, o.precision = eps0, m, mode, precision
     o.query_bits, o.batched, o.profile, o.graph = query_bits, batched, profile, graph
-    o.refine, o.rerank = refine, rerank
+    o.refine, o.rerank, o.survivor_region = refine, rerank, survivor_region
     if stream is not None:
         o.cuda_stream = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
     return o
@@ -333,6 +336,9 @@ _FIELD_SHAPES = {
     "FRE1": (np.float32, lambda i: (i.n,)), "FER1": (np.float32, lambda i: (i.n,)),
     "SQ8C": (np.uint8, lambda i: (i.n, i.d)), "SQ8L": (np.float32, lambda i: (i.d,)),
     "SQ8S": (np.float32, lambda i: (i.d,)),
+    "PQR_": (np.float32, lambda i: (i.d, i.d)),
+    "PQC_": (np.float32, lambda i: (i.pq_M, i.pq_K, i.d // max(i.pq_M, 1))),
+    "PQK_": (np.uint8, lambda i: (i.n, i.pq_M)),
 }
 
 
@@ -342,6 +348,16 @@ def mrq_index_export(index: Index, field: str) -> np.ndarray:
     out = np.empty(shp(info), dtype=dt)
     _check(_lib.mrq_index_export(index.handle, field.encode(), _ptr(out), out.nbytes))
     return out
+
+
+def mrq_pq_train(index: Index, M: int, K: int = 16, opq_iters: int = 4, km_iters: int = 6,
+                 init_rows=None, seed: int = 1) -> None:
+    """Train the OPQ of MODE_PQ on the GPU (rows of the list-major x_d' as initial
+    centroids: ``init_rows``, or K rows drawn from ``seed``)."""
+    keep = None
+    if init_rows is not None:
+        keep = np.ascontiguousarray(init_rows, dtype=np.int64)
+    _check(_lib.mrq_pq_train(index.handle, M, K, opq_iters, km_iters, _ptr(keep), seed))
 
 
 def mrq_shard_plan(list_sizes, nshards: int) -> np.ndarray:

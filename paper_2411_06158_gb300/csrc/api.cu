@@ -69,15 +69,18 @@ mrq_search_opts resolve(const mrq_search_opts* opt) {
   mrq_search_opts_default(&o);
   if (opt) o = *opt;
   MRQ_REQUIRE(o.eps0 >= 0.f && o.m >= 0.f, "eps0 and m must be >= 0");
-  MRQ_REQUIRE(o.mode == MRQ_MODE_MRQ || o.mode == MRQ_MODE_MRQ_PLUS || o.mode == MRQ_MODE_SQ8,
-              "mode must be MRQ_MODE_MRQ, MRQ_MODE_MRQ_PLUS or MRQ_MODE_SQ8");
-  MRQ_REQUIRE(o.mode != MRQ_MODE_SQ8 || (o.rerank >= 1 && o.rerank <= 65536),
+  MRQ_REQUIRE(o.mode == MRQ_MODE_MRQ || o.mode == MRQ_MODE_MRQ_PLUS || o.mode == MRQ_MODE_SQ8 ||
+                  o.mode == MRQ_MODE_PQ,
+              "mode must be MRQ_MODE_MRQ, MRQ_MODE_MRQ_PLUS, MRQ_MODE_SQ8 or MRQ_MODE_PQ");
+  MRQ_REQUIRE((o.mode != MRQ_MODE_SQ8 && o.mode != MRQ_MODE_PQ) ||
+                  (o.rerank >= 1 && o.rerank <= 65536),
               "rerank must be in [1, 65536]");
   MRQ_REQUIRE(o.precision >= MRQ_PREC_FP32 && o.precision <= MRQ_PREC_FP8, "unknown precision");
   MRQ_REQUIRE(o.query_bits >= 0 && o.query_bits <= 8, "query_bits must be in [0, 8]");
   MRQ_REQUIRE(o.batched >= MRQ_SCAN_PAIRS && o.batched <= MRQ_SCAN_BATCHED_TC,
               "batched must be MRQ_SCAN_PAIRS, MRQ_SCAN_BATCHED, MRQ_SCAN_AUTO or MRQ_SCAN_BATCHED_TC");
   MRQ_REQUIRE(o.refine == 0 || o.refine == 1, "refine must be 0 or 1");
+  MRQ_REQUIRE(o.survivor_region >= 0, "survivor_region must be >= 0");
   return o;
 }
 
@@ -120,6 +123,50 @@ void set_last_error(const std::string& m) { g_err = m; }
 }  // namespace mrq
 
 // ===================================================================== ABI
+
+// The queries of the last search whose stage-1 survivors overflowed their region
+// (listed by the scan), searched again with the full region: their rows of the
+// queries gathered, searched in batches that fit the budget, and the answers and
+// counters written back to their rows.
+static void redo_overflowed(mrq_index* idx, const float* queries, int k, int nprobe,
+                            const mrq_search_opts& o, int64_t* ids, float* dists, int64_t cap,
+                            int64_t budget, cudaStream_t st) {
+  auto& ws = idx->ws;
+  int count = 0;
+  MRQ_CUDA(cudaMemcpy(&count, ws.ovf.p, sizeof(int), cudaMemcpyDeviceToHost));
+  if (count <= 0) return;
+  std::vector<int> bad(count);
+  MRQ_CUDA(cudaMemcpy(bad.data(), ws.ovf.p + 1, sizeof(int) * count, cudaMemcpyDeviceToHost));
+  std::sort(bad.begin(), bad.end());
+  auto& rw = idx->ws_redo;
+  rw.cap_limit = 0;
+  rw.items_budget = budget / 4;
+  const int D = idx->D;
+  const int64_t qb = std::max<int64_t>(1, std::min<int64_t>(16384, budget / (24 * cap)));
+  mrq::DevBuf<float> qt((size_t)std::min<int64_t>(qb, count) * D);
+  mrq::DevBuf<int64_t> it((size_t)std::min<int64_t>(qb, count) * k), stt((size_t)std::min<int64_t>(qb, count) * 3);
+  mrq::DevBuf<float> dt((size_t)std::min<int64_t>(qb, count) * k);
+  mrq_search_opts o2 = o;
+  o2.profile = 0;
+  const bool prof = idx->prof_on;
+  idx->prof_on = false;
+  for (int64_t a = 0; a < count; a += qb) {
+    const int64_t b = std::min<int64_t>(qb, count - a);
+    for (int64_t j = 0; j < b; ++j)
+      MRQ_CUDA(cudaMemcpyAsync(qt.p + j * D, queries + (int64_t)bad[a + j] * D, 4 * (size_t)D,
+                               cudaMemcpyDefault, st));
+    mrq::search_batch(idx, rw, qt.p, b, k, nprobe, o2, it.p, dt.p, stt.p, st);
+    for (int64_t j = 0; j < b; ++j) {
+      const int64_t row = bad[a + j];
+      MRQ_CUDA(cudaMemcpyAsync(ids + row * k, it.p + j * k, 8 * (size_t)k, cudaMemcpyDefault, st));
+      MRQ_CUDA(cudaMemcpyAsync(dists + row * k, dt.p + j * k, 4 * (size_t)k, cudaMemcpyDefault, st));
+      MRQ_CUDA(cudaMemcpyAsync(ws.stats.p + row * 3, stt.p + j * 3, 24, cudaMemcpyDeviceToDevice, st));
+    }
+    MRQ_CUDA(cudaStreamSynchronize(st));
+  }
+  idx->prof_on = prof;
+  idx->last_redo = count;
+}
 
 extern "C" {
 
@@ -203,9 +250,12 @@ int mrq_search(mrq_index* idx, const float* queries, int64_t nq, int k, int npro
     MRQ_REQUIRE(queries && ids && dists, "queries, ids and dists must not be NULL");
     const mrq_search_opts o = resolve(opt);
     check_refine(idx, o, k, nprobe);
-    if (o.mode == MRQ_MODE_SQ8) {
-      MRQ_REQUIRE(k <= 128 && k <= o.rerank, "MRQ_MODE_SQ8 needs k <= 128 and k <= rerank");
+    if (o.mode == MRQ_MODE_SQ8 || o.mode == MRQ_MODE_PQ) {
+      MRQ_REQUIRE(k <= 128 && k <= o.rerank,
+                  "MRQ_MODE_SQ8 and MRQ_MODE_PQ need k <= 128 and k <= rerank");
     }
+    if (o.mode == MRQ_MODE_PQ)
+      MRQ_REQUIRE(idx->pq_M > 0, "MRQ_MODE_PQ needs an OPQ (mrq_pq_train, or PQ sections in the file)");
     use_device(idx);
     cudaStream_t st = stream_of(o);
     if (o.mode == MRQ_MODE_SQ8) mrq::ensure_sq8(idx, st);  // before any graph capture
@@ -229,9 +279,35 @@ int mrq_search(mrq_index* idx, const float* queries, int64_t nq, int k, int npro
         std::min<int64_t>((int64_t)64 << 30, std::max<int64_t>((int64_t)6e9, (int64_t)(free_b / 4)));
     // scratch this index already holds counts as available (the batch size stays put)
     budget = std::max<int64_t>(budget, (int64_t)idx->ws.spos.n * 24);
-    qb = std::min<int64_t>(qb, std::max<int64_t>(1, budget / (24 * cap)));
-    qb = std::min<int64_t>(qb, std::max<int64_t>(1, (int64_t)1e9 / (4 * (int64_t)idx->nlist)));
     auto& ws = idx->ws;
+    // the bounded modes write only stage-1 survivors, a small fraction of the candidates:
+    // when the worst-case region (every candidate of the nprobe largest lists) does not
+    // fit a large batch, each query gets a smaller region and a query that overflows it
+    // is searched again with the full region after the batch (exact either way)
+    const bool bounded = o.mode == MRQ_MODE_MRQ || o.mode == MRQ_MODE_MRQ_PLUS;
+    constexpr int64_t kMinRegion = 8192;
+    ws.cap_limit = 0;
+    if (bounded) {
+      qb = std::min<int64_t>(nq, 131072);
+      qb = std::min<int64_t>(qb, std::max<int64_t>(1, (int64_t)8e9 / (4 * (int64_t)idx->nlist)));
+      qb = std::min<int64_t>(qb, std::max<int64_t>(1, ((int64_t)1 << 30) / nprobe));
+      if (o.survivor_region > 0 && o.survivor_region < cap) {
+        ws.cap_limit = o.survivor_region;
+        qb = std::min<int64_t>(qb, std::max<int64_t>(1, budget / (24 * ws.cap_limit)));
+      } else if (24 * cap * qb > budget) {
+        int64_t c = budget / (24 * qb);
+        if (c < kMinRegion) {
+          c = std::min<int64_t>(kMinRegion, cap);
+          qb = std::max<int64_t>(1, budget / (24 * c));
+        }
+        if (c < cap) ws.cap_limit = c;
+      }
+    } else {
+      qb = std::min<int64_t>(qb, std::max<int64_t>(1, budget / (24 * cap)));
+      qb = std::min<int64_t>(qb, std::max<int64_t>(1, (int64_t)1e9 / (4 * (int64_t)idx->nlist)));
+    }
+    ws.items_budget = budget / 4;
+    if (ws.cap_limit > 0) ws.ovf.reserve((size_t)nq + 1);
     ws.stats.reserve((size_t)nq * 3);
     if (!odev) {
       ws.oids.reserve((size_t)qb * k);
@@ -247,7 +323,8 @@ int mrq_search(mrq_index* idx, const float* queries, int64_t nq, int k, int npro
                            (odev || (pinned_host(ids) && pinned_host(dists)));
     mrq_index::GraphKey key{queries, ids, dists, nq, k, nprobe, o.mode, o.precision,
                             o.query_bits, o.batched, o.refine,
-                            o.mode == MRQ_MODE_SQ8 ? o.rerank : 0, o.eps0, o.m};
+                            (o.mode == MRQ_MODE_SQ8 || o.mode == MRQ_MODE_PQ) ? o.rerank : 0,
+                            o.eps0, o.m, o.survivor_region};
     // tensor-core forms read each query once (the bf16 split), so page-locked host
     // queries are read in place through their device mapping instead of copied first
     const float* qmap = nullptr;
@@ -259,7 +336,9 @@ int mrq_search(mrq_index* idx, const float* queries, int64_t nq, int k, int npro
         cudaGetLastError();
     }
     auto run_batches = [&](cudaStream_t s_) {
+      if (ws.cap_limit > 0) MRQ_CUDA(cudaMemsetAsync(ws.ovf.p, 0, sizeof(int), s_));
       for (int64_t s = 0; s < nq; s += qb) {
+        ws.ovf_base = s;
         const int64_t b = std::min(qb, nq - s);
         const float* qp = queries + s * D;
         if (qmap) {
@@ -328,6 +407,7 @@ int mrq_search(mrq_index* idx, const float* queries, int64_t nq, int k, int npro
     MRQ_CUDA(cudaStreamSynchronize(st));
     if (herr && *herr && mrq::tc_check_error())
       mrq::fail(MRQ_ETIMEDOUT, "a tensor-core kernel gave up waiting on its pipeline");
+    if (ws.cap_limit > 0) redo_overflowed(idx, queries, k, nprobe, o, ids, dists, cap, budget, st);
     idx->last_nq = nq;
     idx->last_stats_dev = true;
     for (int s = 0; s < MRQ_NSTAGES; ++s) idx->prof_ms[s] = 0.0;
@@ -397,7 +477,7 @@ int mrq_autotune(mrq_index* idx, const float* queries, int64_t nq, int k, int np
     }
     const int wds = idx->words, nch = idx->d / 32;
     const bool refine = mrq::refine_active(idx, o);  // scans pair by pair
-    const bool sq8 = o.mode == MRQ_MODE_SQ8;          // so does MR-SQ
+    const bool sq8 = o.mode == MRQ_MODE_SQ8 || o.mode == MRQ_MODE_PQ;  // so do MR-SQ, MR-PQ
     const bool can_batch = !refine && !sq8 && o.query_bits > 0 && wds <= 16 && (wds & (wds - 1)) == 0 &&
                            (idx->bits & (idx->bits - 1)) == 0 && (nch & (nch - 1)) == 0 &&
                            !(wds == 16 && idx->d == 32);
@@ -562,7 +642,11 @@ int mrq_index_info(const mrq_index* idx, mrq_index_info_t* info) {
                                    idx->ferr1.bytes() + idx->sq_codes.bytes() +
                                    idx->sq_lo.bytes() + idx->sq_delta.bytes() +
                                    idx->sq_xr2.bytes() + idx->xd.bytes() +
-                                   idx->xr.bytes() + idx->xn2.bytes());
+                                   idx->xr.bytes() + idx->xn2.bytes() + idx->pq_R.bytes() +
+                                   idx->pq_Rt.bytes() + idx->pq_C.bytes() +
+                                   idx->pq_codes.bytes() + idx->pq_xr2.bytes());
+    info->pq_M = idx->pq_M;
+    info->pq_K = idx->pq_K;
   });
 }
 
@@ -592,6 +676,10 @@ static void export_field(const mrq_index* idx, const std::string& f, std::vector
     mrq::ensure_sq8(idx, st);
     if (f == "SQ8C") { out = d2h_bytes(idx->sq_codes.p, (size_t)n * d, st); dtype = DT_U8; }
     else { out = d2h_bytes(f == "SQ8L" ? idx->sq_lo.p : idx->sq_delta.p, d, st); dtype = DT_F32; }
+  } else if ((f == "PQR_" || f == "PQC_" || f == "PQK_") && idx->pq_M > 0) {
+    if (f == "PQR_") { out = d2h_bytes(idx->pq_R.p, (size_t)d * d, st); dtype = DT_F32; }
+    else if (f == "PQC_") { out = d2h_bytes(idx->pq_C.p, (size_t)idx->pq_K * d, st); dtype = DT_F32; }
+    else { out = d2h_bytes(idx->pq_codes.p, (size_t)n * idx->pq_M, st); dtype = DT_U8; }
   } else if (f == "FADD" || f == "FRES" || f == "FERR" ||
              ((f == "FRE1" || f == "FER1") && idx->fres1.p)) {
     const float* src = f == "FADD" ? idx->fadd.p : f == "FRES" ? idx->fres.p
@@ -634,7 +722,10 @@ int mrq_save(const mrq_index* idx, const char* path) {
     auto put = [&](const void* p, size_t b) {
       if (b && std::fwrite(p, 1, b, f) != b) mrq::fail(MRQ_EIO, "write failed");
     };
-    const uint32_t nsec = kRequiredTags + (idx->fres1.p ? 2 : 0);
+    std::vector<const char*> tags(kTags, kTags + kRequiredTags);
+    if (idx->fres1.p) { tags.push_back("FRE1"); tags.push_back("FER1"); }
+    if (idx->pq_M > 0) { tags.push_back("PQR_"); tags.push_back("PQC_"); tags.push_back("PQK_"); }
+    const uint32_t nsec = (uint32_t)tags.size();
     put(kMagic, 8);
     put(&kVersion, 4);
     put(&nsec, 4);
@@ -642,7 +733,7 @@ int mrq_save(const mrq_index* idx, const char* path) {
     put(&idx->n, 8);
     put(hdr, 16);
     for (uint32_t t = 0; t < nsec; ++t) {
-      const char* tag = kTags[t];
+      const char* tag = tags[t];
       std::vector<uint8_t> data;
       uint32_t dt = 0;
       export_field(idx, tag, data, dt, nullptr);
@@ -747,6 +838,8 @@ int mrq_load(const char* path, mrq_index** out) {
         {"XN2_", DT_F32, (uint64_t)n}, {"FRE1", DT_F32, (uint64_t)n},
         {"FER1", DT_F32, (uint64_t)n}};
     constexpr int kWant = 15;
+    std::vector<uint8_t> pq_sec[3];
+    bool pq_seen[3] = {false, false, false};
     std::vector<std::vector<uint8_t>> sec(kWant);
     std::vector<bool> seen(kWant, false);
     for (uint32_t s = 0; s < nsec; ++s) {
@@ -766,6 +859,13 @@ int mrq_load(const char* path, mrq_index** out) {
       get(data.data(), bytes);
       uint8_t pad[8];
       get(pad, (8 - bytes % 8) % 8);
+      const char* pq_tags[3] = {"PQR_", "PQC_", "PQK_"};
+      for (int t = 0; t < 3; ++t)
+        if (std::memcmp(tag, pq_tags[t], 4) == 0) {
+          if (dt != (t == 2 ? DT_U8 : DT_F32)) mrq::fail(MRQ_EFORMAT, "PQ section has the wrong type");
+          pq_sec[t] = std::move(data);
+          pq_seen[t] = true;
+        }
       if (which < 0) continue;  // unknown sections are skipped
       if (dt != want[which].dt || count != want[which].count)
         mrq::fail(MRQ_EFORMAT, std::string("section ") + want[which].tag + " has the wrong type or size");
@@ -776,8 +876,62 @@ int mrq_load(const char* path, mrq_index** out) {
       if (!seen[w]) mrq::fail(MRQ_EFORMAT, std::string("missing section ") + want[w].tag);
     if (seen[13] != seen[14]) mrq::fail(MRQ_EFORMAT, "FRE1 and FER1 come together");
     const bool sign_factors = seen[13] && bits > 1;
+    if (pq_seen[0] || pq_seen[1] || pq_seen[2]) {
+      if (!(pq_seen[0] && pq_seen[1] && pq_seen[2]))
+        mrq::fail(MRQ_EFORMAT, "PQR_, PQC_ and PQK_ come together");
+      const int64_t nr = pq_sec[0].size() / 4, nc = pq_sec[1].size() / 4, nk = pq_sec[2].size();
+      const int64_t K = nc / d, M = nk / n;
+      if (nr != (int64_t)d * d || nc % d || nk % n || M < 1 || d % M || K < 2 || K > 256 ||
+          M * K > 4096)
+        mrq::fail(MRQ_EFORMAT, "PQ sections have inconsistent sizes");
+      for (uint8_t c : pq_sec[2])
+        if (c >= K) mrq::fail(MRQ_EFORMAT, "PQ code exceeds K - 1");
+    }
     std::unique_ptr<mrq_index> built = index_from_sections(n, D, d, bits, nlist, sec, sign_factors);
+    if (pq_seen[0]) {
+      const int K = (int)(pq_sec[1].size() / 4 / d), M = (int)(pq_sec[2].size() / n);
+      mrq::pq_install(built.get(), M, K, reinterpret_cast<const float*>(pq_sec[0].data()),
+                      reinterpret_cast<const float*>(pq_sec[1].data()), pq_sec[2].data(), nullptr);
+    }
     *out = built.release();
+  });
+}
+
+int mrq_pq_train(mrq_index* idx, int M, int K, int opq_iters, int km_iters,
+                 const int64_t* init_rows, uint64_t seed) {
+  return guarded([&] {
+    MRQ_REQUIRE(idx != nullptr, "NULL index");
+    MRQ_REQUIRE(M >= 1 && idx->d % M == 0, "M must divide d");
+    MRQ_REQUIRE(K >= 2 && K <= 256 && K <= idx->n, "K must be in [2, min(256, n)]");
+    MRQ_REQUIRE((int64_t)M * K <= 4096, "M * K must be <= 4096");
+    MRQ_REQUIRE(opq_iters >= 0 && opq_iters <= 100 && km_iters >= 0 && km_iters <= 100,
+                "opq_iters and km_iters must be in [0, 100]");
+    std::vector<int64_t> rows(K);
+    if (init_rows) {
+      for (int c = 0; c < K; ++c) {
+        MRQ_REQUIRE(init_rows[c] >= 0 && init_rows[c] < idx->n, "init_rows out of range");
+        rows[c] = init_rows[c];
+      }
+    } else {  // K distinct rows: a partial Fisher-Yates shuffle driven by SplitMix64
+      uint64_t x = seed ? seed : 1;
+      auto next = [&x]() {
+        uint64_t z = (x += 0x9E3779B97F4A7C15ull);
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+        return z ^ (z >> 31);
+      };
+      std::map<int64_t, int64_t> swapped;
+      auto at = [&](int64_t i) { auto it = swapped.find(i); return it == swapped.end() ? i : it->second; };
+      for (int c = 0; c < K; ++c) {
+        const int64_t j = c + (int64_t)(next() % (uint64_t)(idx->n - c));
+        const int64_t vj = at(j), vc = at(c);
+        swapped[j] = vc;
+        swapped[c] = vj;
+        rows[c] = vj;
+      }
+    }
+    use_device(idx);
+    mrq::pq_train(idx, M, K, opq_iters, km_iters, rows.data(), nullptr);
   });
 }
 
@@ -830,6 +984,18 @@ int mrq_index_shard(const mrq_index* idx, int nshards, int shard, mrq_index** ou
     }
     std::unique_ptr<mrq_index> built =
         index_from_sections(m, D, d, idx->bits, nlist, sec, sign && idx->bits > 1);
+    if (idx->pq_M > 0) {  // the OPQ: the same rotation and codebooks, the shard's codes
+      std::vector<uint8_t> R, C, K;
+      uint32_t dt = 0;
+      export_field(idx, "PQR_", R, dt, nullptr);
+      export_field(idx, "PQC_", C, dt, nullptr);
+      export_field(idx, "PQK_", K, dt, nullptr);
+      const size_t M = (size_t)idx->pq_M;
+      std::vector<uint8_t> ks(M * (size_t)m);
+      for (int64_t i = 0; i < m; ++i) std::memcpy(ks.data() + M * i, K.data() + M * keep[i], M);
+      mrq::pq_install(built.get(), idx->pq_M, idx->pq_K, reinterpret_cast<const float*>(R.data()),
+                      reinterpret_cast<const float*>(C.data()), ks.data(), nullptr);
+    }
     *out = built.release();
   });
 }

@@ -681,6 +681,11 @@ static void eigen_pca(const double* Cdev, int D, double inv_n, std::vector<doubl
   MRQ_CUDA(cudaStreamSynchronize(st));
 }
 
+void eigen_sym(const double* Cdev, int D, std::vector<double>& lam_host, DevBuf<double>& V_dev,
+               cudaStream_t st) {
+  eigen_pca(Cdev, D, 1.0, lam_host, V_dev, st);
+}
+
 // Eq. 8: the smallest power of two p >= 128 whose leading p eigenvalues hold `target` of
 // their total (all D), capped at the largest multiple of 32 not above min(D, MRQ_MAX_D)
 static int choose_d(const std::vector<double>& lam, int D, double target) {

@@ -78,6 +78,14 @@ struct Workspace {
   DevBuf<float> q;         // nq x D staged queries (host inputs)
   DevBuf<float> qd, qr;    // projected queries
   DevBuf<float> qstat;     // nq x 4: |q_r|^2, sigma, |q_p|^2, unused
+  DevBuf<float> pqq;       // nq x d: q_d' R, the OPQ-rotated query (MR-PQ)
+  // optimistic survivor region: with cap_limit > 0 every query's stage-1 region holds at
+  // most cap_limit entries; a query whose survivors overflow it is listed in ovf
+  // ([0] = count, then query indices offset by ovf_base) and searched again in full
+  int64_t cap_limit = 0;
+  int64_t ovf_base = 0;
+  DevBuf<int> ovf;
+  int64_t items_budget = 0;  // bytes the batched scan's work items may take (0 = any)
   DevBuf<__nv_bfloat16> qbf;  // nq x D bf16 hi/lo split queries (tensor-core projection)
   DevBuf<uint8_t> q8;          // nq x D row-scaled e4m3 queries (FP8 projection)
   DevBuf<float> q8s;           // their row scales
@@ -191,8 +199,16 @@ struct mrq_index {
   mutable std::mutex sq_mu;
   mutable mrq::DevBuf<uint8_t> sq_codes;
   mutable mrq::DevBuf<float> sq_lo, sq_delta, sq_xr2;
+  // MR-PQ (MRQ_MODE_PQ), from mrq_pq_train or the index file: the OPQ rotation R and its
+  // transpose (d x d), codebooks (pq_M x pq_K x d/pq_M, subspace-major), codes (n x pq_M,
+  // list-major) and |x_r|^2 (n)
+  int pq_M = 0, pq_K = 0;
+  mrq::DevBuf<float> pq_R, pq_Rt, pq_C, pq_xr2;
+  mrq::DevBuf<uint8_t> pq_codes;
   mrq::DevBuf<float> xd, xr, xn2;         // list-major, unpadded
   mrq::Workspace ws;
+  mrq::Workspace ws_redo;  // searches again the queries whose survivors overflowed
+  int64_t last_redo = 0;   // queries the last search searched again
   int64_t last_nq = 0;
   mutable bool last_stats_dev = false;
   // autotuned scan configurations, keyed by (k class, nprobe, query bits, scan_variant)
@@ -213,8 +229,10 @@ struct mrq_index {
     int64_t nq;
     int k, nprobe, mode, precision, query_bits, batched, refine, rerank;
     float eps0, m;
+    int64_t region;
     bool operator==(const GraphKey& o) const {
       return q == o.q && ids == o.ids && dists == o.dists && nq == o.nq && k == o.k &&
+             region == o.region &&
              nprobe == o.nprobe && mode == o.mode && precision == o.precision &&
              query_bits == o.query_bits && batched == o.batched && refine == o.refine &&
              rerank == o.rerank &&
@@ -267,6 +285,14 @@ void nearest_f32(const float* A, int lda, const float* B, int ldb, int M, int N,
 bool tc_available();
 void project_noalloc(mrq_index* idx, const float* q, int64_t nq, int precision, float* qp,
                      cudaStream_t st);  // static scratch only, no allocation
+// MR-PQ (pq.cu): OPQ training on the GPU, or an OPQ given in host memory
+void pq_train(mrq_index* idx, int M, int K, int opq_iters, int km_iters, const int64_t* init_rows,
+              cudaStream_t st);
+void pq_install(mrq_index* idx, int M, int K, const float* R, const float* C,
+                const uint8_t* codes, cudaStream_t st);
+// eigenvalues (descending) and eigenvectors (rows of V) of a symmetric D x D float64 matrix
+void eigen_sym(const double* Cdev, int D, std::vector<double>& lam_host, DevBuf<double>& V_dev,
+               cudaStream_t st);
 // list-sharded search (shard.cu): the partition plan and the merge of per-shard answers
 void shard_plan(const int64_t* sizes, int nlist, int nshards, int32_t* owner);
 void merge_topk(const int64_t* ids, const float* dists, int nparts, int64_t nq, int k,
@@ -308,12 +334,12 @@ void ensure_sq8(const mrq_index* idx, cudaStream_t st);
 // the search runs the 1 bit + refinement stage 1 (bits > 1 and refine = 1)
 constexpr int REFINE_MAX_NPROBE = 4096;  // stage 1b's probe table: 12 B of shared memory each
 inline bool refine_active(const mrq_index* idx, const mrq_search_opts& o) {
-  return o.refine != 0 && idx->bits > 1 && o.mode != MRQ_MODE_SQ8;
+  return o.refine != 0 && idx->bits > 1 && o.mode != MRQ_MODE_SQ8 && o.mode != MRQ_MODE_PQ;
 }
 
 // which scan a search runs, for the autotuner's key: 0 one-stage, 1 refinement, 2 MR-SQ
 inline int scan_variant(const mrq_index* idx, const mrq_search_opts& o) {
-  return o.mode == MRQ_MODE_SQ8 ? 2 : refine_active(idx, o) ? 1 : 0;
+  return o.mode == MRQ_MODE_SQ8 ? 2 : o.mode == MRQ_MODE_PQ ? 3 : refine_active(idx, o) ? 1 : 0;
 }
 
 // the scan configuration a search uses; a ScopedScanConfig forces one on this thread

@@ -1092,8 +1092,9 @@ __global__ void __launch_bounds__(256) k_scan_tc(TcScanParams P) {
             unsigned base = 0;
             if (lane == 0) base = atomicAdd(P.qcnt + q, (unsigned)__popc(sm));
             base = __shfl_sync(0xffffffffu, base, 0);
-            if (surv) {
-              const int64_t at = q * P.cap + base + __popc(sm & ((1u << lane) - 1));
+            const int64_t rel = (int64_t)base + __popc(sm & ((1u << lane) - 1));
+            if (surv && rel < P.cap) {  // past the region: counted only (the query is redone)
+              const int64_t at = q * P.cap + rel;
               P.spos[at] = (int32_t)(lb0 + idx);
               P.slb[at] = lb;
               P.sub[at] = ub;

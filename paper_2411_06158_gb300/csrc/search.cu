@@ -642,8 +642,9 @@ __global__ void __launch_bounds__(SCAN_WARPS * 32) k_scan(ScanParams P) {
         unsigned base = 0;
         if (lane == 0) base = atomicAdd(P.qcnt + q, (unsigned)__popc(sm));
         base = __shfl_sync(0xffffffffu, base, 0);
-        if (surv) {
-          int64_t at = q * P.cap + base + __popc(sm & ((1u << lane) - 1));
+        const int64_t rel = (int64_t)base + __popc(sm & ((1u << lane) - 1));
+        if (surv && rel < P.cap) {  // past the region: counted only (the query is redone)
+          const int64_t at = q * P.cap + rel;
           P.spos[at] = (int32_t)(lb0 + idx);
           P.slb[at] = lb;
           P.sub[at] = ub;
@@ -777,7 +778,8 @@ __global__ void __launch_bounds__(SCAN_WARPS * 32, scan_q_min_ctas(NCH, BITS * N
       if (lane == 0) base = atomicAdd(P.qcnt + q, (unsigned)fill);
       base = __shfl_sync(0xffffffffu, base, 0);
       const int64_t at = q * P.cap + base;
-      for (int i = lane; i < fill; i += 32) {
+      const int64_t room = P.cap - (int64_t)base;   // past the region: counted only
+      for (int i = lane; i < fill && i < room; i += 32) {
         P.spos[at + i] = s_pos[i];
         P.slb[at + i] = s_lb[i];
         P.sub[at + i] = s_ub[i];
@@ -1209,8 +1211,9 @@ __global__ void __launch_bounds__(256) k_scan_batched(BatchParams P) {
         unsigned base = 0;
         if (lane == 0) base = atomicAdd(P.qcnt + q, (unsigned)__popc(sm));
         base = __shfl_sync(0xffffffffu, base, 0);
-        if (surv) {
-          const int64_t at = q * P.cap + base + __popc(sm & ((1u << lane) - 1));
+        const int64_t rel = (int64_t)base + __popc(sm & ((1u << lane) - 1));
+        if (surv && rel < P.cap) {  // past the region: counted only (the query is redone)
+          const int64_t at = q * P.cap + rel;
           P.spos[at] = (int32_t)(lb0 + idx);
           P.slb[at] = lb;
           P.sub[at] = ub;
@@ -2223,8 +2226,107 @@ __global__ void __launch_bounds__(SCAN_WARPS * 32) k_scan_sq8(Sq8Params P) {
       unsigned base = 0;
       if (lane == 0 && vm) base = atomicAdd(P.qcnt + q, (unsigned)__popc(vm));
       base = __shfl_sync(0xffffffffu, base, 0);
+      const int64_t rel = (int64_t)base + __popc(vm & ((1u << lane) - 1));
+      if (valid && rel < P.cap) {
+        const int64_t at = q * P.cap + rel;
+        P.spos[at] = (int32_t)p;
+        P.slb[at] = est;
+      }
+    }
+  }
+}
+
+struct PqParams {
+  const float* qrot;     // nq x d: q_d' R
+  const float* qstat;    // nq x 4 (|q_r|^2 first)
+  const int32_t* plist;  // nq x nprobe
+  const int64_t* loff;
+  const uint8_t* codes;  // n x M, list-major
+  const float* C;        // M x K x ds
+  const float* xr2;
+  int d, M, K, nprobe;
+  int64_t npairs, cap;
+  const int64_t* items;  // (pair << 32 | chunk) work items, or NULL: one per pair
+  const int* nitems;
+  int chunk;
+  unsigned int* work;
+  unsigned int* qcnt;
+  int32_t* spos;
+  float* slb;
+};
+
+// MR-PQ estimate (Exp-5): one warp per (query, list) work item builds the query's lookup
+// table T[m][c] = |q'_m - C[m][c]|^2 in shared memory (q' = q_d' R, subvectors of d/M
+// coordinates), then one lane per candidate sums T[m][code_m] over the M subspaces and
+// adds |x_r|^2 + |q_r|^2 (the residual cross term dropped, as in Eq. 4); every
+// candidate's (position, estimate) is appended to the query's region
+__global__ void __launch_bounds__(SCAN_WARPS * 32) k_scan_pq(PqParams P) {
+  extern __shared__ float pqt[];  // per warp: M x K table
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int M = P.M, K = P.K, ds = P.d / P.M;
+  float* T = pqt + (int64_t)wid * M * K;
+  const int64_t n_items = P.items ? (int64_t)*P.nitems : P.npairs;
+  int64_t last_q = -1;
+  while (true) {
+    unsigned int it = 0;
+    if (lane == 0) it = atomicAdd(P.work, 1u);
+    it = __shfl_sync(0xffffffffu, it, 0);
+    if ((int64_t)it >= n_items) break;
+    int64_t w = it, c_lo = 0, c_hi = -1;
+    if (P.items) {
+      const int64_t v = P.items[it];
+      w = v >> 32;
+      c_lo = (v & 0xffffffffll) * P.chunk;
+      c_hi = c_lo + P.chunk;
+    }
+    const int64_t q = w / P.nprobe;
+    const int j = P.plist[w];
+    if (q != last_q) {  // the table depends on the query only
+      __syncwarp();
+      const float* qv = P.qrot + q * P.d;
+      for (int e = lane; e < M * K; e += 32) {
+        const int m = e / K, c = e - m * K;
+        const float* cb = P.C + ((int64_t)m * K + c) * ds;
+        float s = 0.f;
+        for (int t = 0; t < ds; ++t) {
+          const float x = qv[m * ds + t] - cb[t];
+          s = fmaf(x, x, s);
+        }
+        T[e] = s;
+      }
+      __syncwarp();
+      last_q = q;
+    }
+    const float qr2 = P.qstat[q * 4 + 0];
+    const int64_t lb0 = P.loff[j];
+    const int64_t lsize = P.loff[j + 1] - lb0;
+    const int64_t size = c_hi < 0 ? lsize : min(lsize, c_hi);
+    for (int64_t b0 = c_lo; b0 < size; b0 += 32) {
+      const int64_t idx = b0 + lane;
+      const bool valid = idx < size;
+      float est = 0.f;
+      const int64_t p = lb0 + idx;
       if (valid) {
-        const int64_t at = q * P.cap + base + __popc(vm & ((1u << lane) - 1));
+        const uint8_t* row = P.codes + p * M;
+        float s = 0.f;
+        if ((M & 3) == 0) {
+          for (int m = 0; m < M; m += 4) {
+            const uint32_t v4 = __ldg(reinterpret_cast<const uint32_t*>(row + m));
+#pragma unroll
+            for (int t = 0; t < 4; ++t) s += T[(m + t) * K + ((v4 >> (8 * t)) & 255u)];
+          }
+        } else {
+          for (int m = 0; m < M; ++m) s += T[m * K + __ldg(row + m)];
+        }
+        est = s + __ldg(P.xr2 + p) + qr2;
+      }
+      const unsigned vm = __ballot_sync(0xffffffffu, valid);
+      unsigned base = 0;
+      if (lane == 0 && vm) base = atomicAdd(P.qcnt + q, (unsigned)__popc(vm));
+      base = __shfl_sync(0xffffffffu, base, 0);
+      const int64_t rel = (int64_t)base + __popc(vm & ((1u << lane) - 1));
+      if (valid && rel < P.cap) {
+        const int64_t at = q * P.cap + rel;
         P.spos[at] = (int32_t)p;
         P.slb[at] = est;
       }
@@ -2473,11 +2575,25 @@ ScanConfig scan_config(mrq_index* idx, const mrq_search_opts& o, int64_t nq, int
   return c;
 }
 
+// queries whose stage-1 survivors overflowed their region: listed for a second search
+__global__ void k_overflow(const unsigned int* __restrict__ qcnt, int64_t nq, int64_t cap,
+                           int64_t base, int* __restrict__ ovf) {
+  const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= nq || (int64_t)qcnt[q] <= cap) return;
+  const int slot = atomicAdd(ovf, 1);
+  ovf[1 + slot] = (int)(base + q);
+}
+
 void search_batch(mrq_index* idx, Workspace& ws, const float* q, int64_t nq, int k, int nprobe,
                   const mrq_search_opts& o, int64_t* out_ids, float* out_d, int64_t* stats,
                   cudaStream_t st) {
   const int D = idx->D, d = idx->d, r = D - d, nlist = idx->nlist;
-  const int64_t cap = std::max<int64_t>(idx->cap_by_nprobe[nprobe], 1);
+  const int64_t cap_full = std::max<int64_t>(idx->cap_by_nprobe[nprobe], 1);
+  // the bounded modes keep only stage-1 survivors, so the region may be smaller than the
+  // worst case (every candidate); MR-SQ and MR-PQ append every candidate
+  const bool limited = (o.mode == MRQ_MODE_MRQ || o.mode == MRQ_MODE_MRQ_PLUS) &&
+                       ws.cap_limit > 0 && ws.cap_limit < cap_full && ws.ovf.p != nullptr;
+  const int64_t cap = limited ? ws.cap_limit : cap_full;
   ws.qd.reserve((size_t)nq * d);
   ws.qr.reserve((size_t)nq * std::max(r, 1));
   ws.qstat.reserve((size_t)nq * 4);
@@ -2606,10 +2722,34 @@ void search_batch(mrq_index* idx, Workspace& ws, const float* q, int64_t nq, int
     idx->launches += 3;
     return max_items;
   };
-  if (o.mode == MRQ_MODE_SQ8) {
-    // MR-SQ: the SQ8 scan appends every probed candidate's estimate, the rerank range is
-    // selected, reranked exactly and the top-k taken
+  if (o.mode == MRQ_MODE_SQ8 || o.mode == MRQ_MODE_PQ) {
+    // MR-SQ / MR-PQ: the scan appends every probed candidate's estimate, the rerank range
+    // is selected, reranked exactly and the top-k taken
     const int64_t np_ = nq * nprobe;
+    if (o.mode == MRQ_MODE_PQ) {
+      ws.pqq.reserve(nq * d);
+      gemm_nt_f32(ws.qd.p, d, nullptr, idx->pq_Rt.p, d, (int)nq, d, d, ws.pqq.p, d, ws.pqq.p, d,
+                  d, st);  // q' = q_d' R
+      PqParams pp{};
+      pp.qrot = ws.pqq.p; pp.qstat = ws.qstat.p; pp.plist = ws.plist.p; pp.loff = idx->loff.p;
+      pp.codes = idx->pq_codes.p; pp.C = idx->pq_C.p; pp.xr2 = idx->pq_xr2.p; pp.d = d;
+      pp.M = idx->pq_M; pp.K = idx->pq_K; pp.nprobe = nprobe; pp.npairs = np_; pp.cap = cap;
+      pp.work = ws.work.p; pp.qcnt = ws.qcnt.p; pp.spos = ws.spos.p; pp.slb = ws.slb.p;
+      int64_t grid_items = np_;
+      if (idx->max_list > cfg.chunk) {
+        grid_items = build_items(np_, 1);
+        pp.items = sp.items; pp.nitems = sp.nitems; pp.chunk = sp.chunk;
+      }
+      const size_t tsm = (size_t)SCAN_WARPS * pp.M * pp.K * sizeof(float);
+      ensure_smem((const void*)k_scan_pq, tsm);
+      const int per_sm = occupancy((const void*)k_scan_pq, SCAN_WARPS * 32, tsm);
+      const int blocks = (int)std::max<int64_t>(
+          1, std::min<int64_t>((grid_items + SCAN_WARPS - 1) / SCAN_WARPS,
+                               (int64_t)num_sms() * std::max(per_sm, 1)));
+      k_scan_pq<<<blocks, SCAN_WARPS * 32, tsm, st>>>(pp);
+      MRQ_CHECK_LAUNCH();
+      idx->launches += 1;  // the query rotation (the scan is counted below)
+    } else {
     Sq8Params qp{};
     qp.qd = ws.qd.p; qp.qstat = ws.qstat.p; qp.plist = ws.plist.p; qp.loff = idx->loff.p;
     qp.codes = idx->sq_codes.p; qp.lo = idx->sq_lo.p; qp.delta = idx->sq_delta.p;
@@ -2627,6 +2767,7 @@ void search_batch(mrq_index* idx, Workspace& ws, const float* q, int64_t nq, int
         1, std::min<int64_t>((grid_items + SCAN_WARPS - 1) / SCAN_WARPS, (int64_t)num_sms() * per_sm));
     k_scan_sq8<<<blocks, SCAN_WARPS * 32, qsm, st>>>(qp);
     MRQ_CHECK_LAUNCH();
+    }
     mark(idx, MRQ_STAGE_TAU_A, st);
     FinParams fp{};
     fp.qd = ws.qd.p; fp.qr = ws.qr.p; fp.qstat = ws.qstat.p; fp.plist = ws.plist.p;
@@ -2663,8 +2804,14 @@ void search_batch(mrq_index* idx, Workspace& ws, const float* q, int64_t nq, int
                       !(wds == 16 && d == 32);
   const bool use_tc = !refine && cfg.scan == MRQ_SCAN_BATCHED_TC && tc_available() &&
                       scan_tc_supported(d, idx->bits, o.query_bits);
-  const bool batched = !refine && (use_tc || ((cfg.scan == MRQ_SCAN_BATCHED ||
-                                                cfg.scan == MRQ_SCAN_BATCHED_TC) && pop_ok));
+  // the batched scan's work items are sized for the worst case (every probed list's
+  // blocks for every query): beyond the budget the pairs are scanned one by one
+  const bool items_fit = ws.items_budget <= 0 ||
+      (int64_t)(2 * (nq * nprobe + (nq * idx->cap_by_nprobe[nprobe]) / 32 + 1)) * 8 <=
+          ws.items_budget;
+  const bool batched = !refine && items_fit &&
+                       (use_tc || ((cfg.scan == MRQ_SCAN_BATCHED ||
+                                    cfg.scan == MRQ_SCAN_BATCHED_TC) && pop_ok));
   if (batched) {
     const int64_t np_ = nq * nprobe;
     const int nch = d / 32;
@@ -2765,6 +2912,11 @@ void search_batch(mrq_index* idx, Workspace& ws, const float* q, int64_t nq, int
     MRQ_CHECK_LAUNCH();
   }
   if (!batched) launch_scan(sp, grid_items, st, false);
+  if (limited) {
+    k_overflow<<<ceil_div(nq, 256), 256, 0, st>>>(ws.qcnt.p, nq, cap, ws.ovf_base, ws.ovf.p);
+    MRQ_CHECK_LAUNCH();
+    idx->launches += 1;
+  }
   // 5. finalize
   mark(idx, MRQ_STAGE_TAU_A, st);
   FinParams fp{};

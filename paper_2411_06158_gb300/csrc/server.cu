@@ -267,9 +267,10 @@ int mrq_server_start(mrq_index* idx, const mrq_server_opts* opt, mrq_server** ou
     MRQ_REQUIRE(o.max_k >= 1 && o.max_k <= 1024, "max_k must be in [1, 1024]");
     MRQ_REQUIRE(o.max_wait_us >= 0, "max_wait_us must be >= 0");
     MRQ_REQUIRE(o.search.refine == 0 || o.search.refine == 1, "refine must be 0 or 1");
-    MRQ_REQUIRE(o.search.mode != MRQ_MODE_SQ8 ||
+    MRQ_REQUIRE((o.search.mode != MRQ_MODE_SQ8 && o.search.mode != MRQ_MODE_PQ) ||
                     (o.max_k <= 128 && o.max_k <= o.search.rerank && o.search.rerank <= 65536),
-                "MRQ_MODE_SQ8 needs max_k <= 128 and max_k <= rerank <= 65536");
+                "MRQ_MODE_SQ8 and MRQ_MODE_PQ need max_k <= 128 and max_k <= rerank <= 65536");
+    MRQ_REQUIRE(o.search.mode != MRQ_MODE_PQ || idx->pq_M > 0, "MRQ_MODE_PQ needs an OPQ");
     if (o.search.mode == MRQ_MODE_SQ8) mrq::ensure_sq8(idx, nullptr);
     if (mrq::refine_active(idx, o.search)) {
       MRQ_REQUIRE(idx->fres1.p != nullptr, "refine needs the sign-plane factors (FRE1/FER1)");

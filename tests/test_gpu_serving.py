@@ -97,3 +97,49 @@ def test_poll_completed_returns_each_ticket_once(index):
             np.testing.assert_array_equal(seen[t], ref[q])
     finally:
         srv.stop()
+
+
+def test_served_answers_match_the_oracle(tmp_path):
+    """Requests with mixed k and nprobe served from an index the oracle wrote, against
+    the oracle's contract search of the same index file, query by query."""
+    from oracle import index_file
+    from oracle import mrq as omrq
+    from parity_helpers import check_answers
+    w = datagen.workload("small", n=16_000, nlist=48, n_query=160)
+    base, queries = datagen.base_and_queries(w)
+    G = datagen.rotation_gaussian(w.d, w.seed("method"))
+    init = datagen.kmeans_init_indices(w.n, w.nlist, w.seed("method") + 1)
+    oidx = omrq.build_index(base, w.d, w.bits, w.nlist, G, init_idx=init, kmeans_iters=6)
+    path = str(tmp_path / "served.mrq")
+    index_file.write_index(oidx, path)
+    gidx = mrq.mrq_load(path)
+    st = oidx.as_stored()
+    rng = np.random.default_rng(4)
+    ks = rng.choice([10, 32], size=len(queries)).astype(np.int32)
+    nps = rng.choice([4, 8], size=len(queries)).astype(np.int32)
+    srv = mrq.Server(gidx, max_batch=32, max_inflight=3, max_wait_us=200, max_k=32,
+                     search=mrq.mrq_search_opts(query_bits=4))
+    try:
+        tickets = srv.submit_many(queries, ks, nps)
+        got, deadline = {}, time.time() + 60
+        while len(got) < len(tickets) and time.time() < deadline:
+            tk, ids, dists, stt = srv.poll_completed(64, 32)
+            for t, i, d in zip(tk.tolist(), ids, dists):
+                got[t] = (i, d)
+            time.sleep(0.0005)
+    finally:
+        srv.stop()
+    assert len(got) == len(tickets)
+    pos = {t: i for i, t in enumerate(tickets.tolist())}
+    for k in (10, 32):
+        for npb in (4, 8):
+            sel = np.nonzero((ks == k) & (nps == npb))[0]
+            if sel.size == 0:
+                continue
+            ref = omrq.search_contract(st, queries[sel], k, npb, qbits=4)
+            gi = np.stack([got[int(tickets[i])][0][:k] for i in sel])
+            gd = np.stack([got[int(tickets[i])][1][:k] for i in sel])
+            # groups of 30-40 queries: one near-tie is already 3 %
+            check_answers(base, queries[sel], gi, gd, ref, k, min_strict=0.9,
+                          label=f"served k={k} nprobe={npb}")
+    assert sorted(pos) == sorted(got)
