@@ -765,6 +765,8 @@ def main(argv=None):
         if world > 1:
             torch.distributed.barrier()
         torch.cuda.synchronize()
+        if not profile:
+            torch.cuda.profiler.start()        # the capture range of ncu --profile-from-start off
         for _ in range(steps):
             flush.zero_()                      # L2 flush between timed steps
             a = torch.cuda.Event(enable_timing=True)
@@ -780,6 +782,8 @@ def main(argv=None):
                     stage[s] += ms[s]
                 launches += nl
         torch.cuda.synchronize()
+        if not profile:
+            torch.cuda.profiler.stop()
         if world > 1:
             torch.distributed.barrier()
         return per, stage, launches, ids
@@ -814,6 +818,7 @@ def main(argv=None):
         # from a captured CUDA graph when the form asks for one)
         pper, stage, launches, ids = timed(opts, npb, args.steps, args.warmup, True)
         st = mrq.mrq_last_search_stats(idx, w.n_query)
+        redone = mrq.mrq_last_search_redo(idx)
         per, *_ = timed(opts, npb, args.steps, args.warmup, False)
         ms = sum(per) / len(per)
         pms = sum(pper) / len(pper)
@@ -825,7 +830,11 @@ def main(argv=None):
                          "launches_per_step": launches // max(1, len(pper)),
                          "cand_per_query": float(st["n_cand"].mean()),
                          "s1_per_query": float(st["n_s1"].mean()),
+                         "s1_p99": float(np.percentile(st["n_s1"], 99)),
+                         "s1_max": int(st["n_s1"].max()),
+                         "exact_max": int(st["n_exact"].max()),
                          "exact_per_query": float(st["n_exact"].mean()), "per_step_ms": per,
+                         "redone_queries": redone,
                          "autotune": tune}
     # the headline is the MRQ method's own best form; MR-SQ and MR-PQ (Exp-5) beside it
     ok = {k: v for k, v in results.items()

@@ -352,6 +352,11 @@ int mrq_load(const char* path, mrq_index** out);
 
 int mrq_index_info(const mrq_index* index, mrq_index_info_t* info);
 
+/* Number of queries of the last mrq_search on this index whose stage-1 survivors
+ * overflowed their region (survivor_region, or the automatic one) and were searched
+ * again with a larger region; 0 when the region held every query.  No GPU call. */
+int mrq_last_search_redo(const mrq_index* index, int64_t* redone);
+
 /* Copy one index array to host memory in the file's canonical layout (list-major,
  * unpadded).  field: 4-character tag of the file format (e.g. "CODE", "XD__"; "FRE1" and
  * "FER1" only when the index holds them, else MRQ_EINVAL), or one of the MR-SQ arrays

@@ -32,6 +32,7 @@ EXPORTS = [
     "mrq_server_opts_default", "mrq_server_start", "mrq_submit", "mrq_submit_many", "mrq_poll",
     "mrq_poll_many", "mrq_poll_completed", "mrq_server_stats", "mrq_server_reset_stats",
     "mrq_server_stop", "mrq_shard_plan", "mrq_index_shard", "mrq_merge_topk", "mrq_pq_train",
+    "mrq_last_search_redo",
 ]
 
 
@@ -111,6 +112,7 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
     lib.mrq_server_reset_stats.argtypes = [vp]
     lib.mrq_server_stop.argtypes = [vp]
     lib.mrq_pq_train.argtypes = [vp, i32, i32, i32, i32, vp, C.c_uint64]
+    lib.mrq_last_search_redo.argtypes = [vp, vp]
     lib.mrq_shard_plan.argtypes = [vp, i32, i32, vp]
     lib.mrq_index_shard.argtypes = [vp, i32, i32, C.POINTER(vp)]
     lib.mrq_merge_topk.argtypes = [vp, vp, i32, i64, i32, vp, vp, vp]
@@ -348,6 +350,13 @@ def mrq_index_export(index: Index, field: str) -> np.ndarray:
     out = np.empty(shp(info), dtype=dt)
     _check(_lib.mrq_index_export(index.handle, field.encode(), _ptr(out), out.nbytes))
     return out
+
+
+def mrq_last_search_redo(index: Index) -> int:
+    """Queries of the last search searched again with a larger survivor region."""
+    n = np.zeros(1, dtype=np.int64)
+    _check(_lib.mrq_last_search_redo(index.handle, _ptr(n)))
+    return int(n[0])
 
 
 def mrq_pq_train(index: Index, M: int, K: int = 16, opq_iters: int = 4, km_iters: int = 6,

@@ -125,47 +125,92 @@ void set_last_error(const std::string& m) { g_err = m; }
 // ===================================================================== ABI
 
 // The queries of the last search whose stage-1 survivors overflowed their region
-// (listed by the scan), searched again with the full region: their rows of the
-// queries gathered, searched in batches that fit the budget, and the answers and
-// counters written back to their rows.
+// (listed by the scan) are searched again in rounds, each with a region eight times the
+// last (the full worst case at most, which cannot overflow): their rows gathered, searched
+// in batches that fit the budget, the answers and counters written back to their rows,
+// and the queries that overflowed again kept for the next round.
 static void redo_overflowed(mrq_index* idx, const float* queries, int k, int nprobe,
                             const mrq_search_opts& o, int64_t* ids, float* dists, int64_t cap,
                             int64_t budget, cudaStream_t st) {
   auto& ws = idx->ws;
   int count = 0;
   MRQ_CUDA(cudaMemcpy(&count, ws.ovf.p, sizeof(int), cudaMemcpyDeviceToHost));
+  idx->last_redo = count;
   if (count <= 0) return;
   std::vector<int> bad(count);
   MRQ_CUDA(cudaMemcpy(bad.data(), ws.ovf.p + 1, sizeof(int) * count, cudaMemcpyDeviceToHost));
   std::sort(bad.begin(), bad.end());
+  const bool qdev = on_device(queries), odev = on_device(ids);
   auto& rw = idx->ws_redo;
-  rw.cap_limit = 0;
-  rw.items_budget = budget / 4;
   const int D = idx->D;
-  const int64_t qb = std::max<int64_t>(1, std::min<int64_t>(16384, budget / (24 * cap)));
-  mrq::DevBuf<float> qt((size_t)std::min<int64_t>(qb, count) * D);
-  mrq::DevBuf<int64_t> it((size_t)std::min<int64_t>(qb, count) * k), stt((size_t)std::min<int64_t>(qb, count) * 3);
-  mrq::DevBuf<float> dt((size_t)std::min<int64_t>(qb, count) * k);
   mrq_search_opts o2 = o;
-  o2.profile = 0;
-  const bool prof = idx->prof_on;
-  idx->prof_on = false;
-  for (int64_t a = 0; a < count; a += qb) {
-    const int64_t b = std::min<int64_t>(qb, count - a);
-    for (int64_t j = 0; j < b; ++j)
-      MRQ_CUDA(cudaMemcpyAsync(qt.p + j * D, queries + (int64_t)bad[a + j] * D, 4 * (size_t)D,
-                               cudaMemcpyDefault, st));
-    mrq::search_batch(idx, rw, qt.p, b, k, nprobe, o2, it.p, dt.p, stt.p, st);
-    for (int64_t j = 0; j < b; ++j) {
-      const int64_t row = bad[a + j];
-      MRQ_CUDA(cudaMemcpyAsync(ids + row * k, it.p + j * k, 8 * (size_t)k, cudaMemcpyDefault, st));
-      MRQ_CUDA(cudaMemcpyAsync(dists + row * k, dt.p + j * k, 4 * (size_t)k, cudaMemcpyDefault, st));
-      MRQ_CUDA(cudaMemcpyAsync(ws.stats.p + row * 3, stt.p + j * 3, 24, cudaMemcpyDeviceToDevice, st));
+  // a profiled search keeps profiling here: the rounds' stages add to the call's totals
+  int64_t region = std::max<int64_t>(ws.cap_limit, 1);
+  while (!bad.empty()) {
+    region = std::min<int64_t>(cap, region * 8);
+    rw.cap_limit = region < cap ? region : 0;
+    rw.items_budget = budget / 4;
+    const int64_t n = (int64_t)bad.size();
+    int64_t qb = std::max<int64_t>(1, budget / (24 * region));
+    qb = std::min<int64_t>({qb, n, (int64_t)131072, std::max<int64_t>(1, ((int64_t)1 << 30) / nprobe),
+                            std::max<int64_t>(1, (int64_t)8e9 / (4 * (int64_t)idx->nlist))});
+    mrq::DevBuf<float> qt((size_t)qb * D);
+    mrq::DevBuf<int64_t> it((size_t)qb * k), stt((size_t)qb * 3);
+    mrq::DevBuf<float> dt((size_t)qb * k);
+    mrq::DevBuf<int> rows((size_t)n);
+    MRQ_CUDA(cudaMemcpyAsync(rows.p, bad.data(), sizeof(int) * n, cudaMemcpyHostToDevice, st));
+    if (rw.cap_limit > 0) {
+      rw.ovf.reserve((size_t)n + 1);
+      MRQ_CUDA(cudaMemsetAsync(rw.ovf.p, 0, sizeof(int), st));
+    }
+    std::vector<float> hq;
+    std::vector<int64_t> hi;
+    std::vector<float> hd;
+    for (int64_t a = 0; a < n; a += qb) {
+      const int64_t b = std::min<int64_t>(qb, n - a);
+      if (qdev) {
+        mrq::gather_query_rows(queries, D, rows.p + a, b, qt.p, st);
+      } else {
+        hq.resize((size_t)b * D);
+        for (int64_t j = 0; j < b; ++j)
+          std::memcpy(hq.data() + j * D, queries + (int64_t)bad[a + j] * D, 4 * (size_t)D);
+        MRQ_CUDA(cudaMemcpyAsync(qt.p, hq.data(), 4 * hq.size(), cudaMemcpyHostToDevice, st));
+      }
+      rw.ovf_base = a;  // overflow entries are positions in this round's list
+      rw.seed_tau = ws.ovf_tau.p;  // bounds recorded by row when the queries overflowed
+      rw.seed_rows = rows.p + a;
+      mrq::search_batch(idx, rw, qt.p, b, k, nprobe, o2, it.p, dt.p, stt.p, st);
+      mrq::scatter_answers(it.p, dt.p, stt.p, k, rows.p + a, b, odev ? ids : nullptr,
+                           odev ? dists : nullptr, ws.stats.p, st);
+      if (!odev) {
+        hi.resize((size_t)b * k);
+        hd.resize((size_t)b * k);
+        MRQ_CUDA(cudaMemcpyAsync(hi.data(), it.p, 8 * hi.size(), cudaMemcpyDeviceToHost, st));
+        MRQ_CUDA(cudaMemcpyAsync(hd.data(), dt.p, 4 * hd.size(), cudaMemcpyDeviceToHost, st));
+        MRQ_CUDA(cudaStreamSynchronize(st));
+        for (int64_t j = 0; j < b; ++j) {
+          std::memcpy(ids + (int64_t)bad[a + j] * k, hi.data() + j * k, 8 * (size_t)k);
+          std::memcpy(dists + (int64_t)bad[a + j] * k, hd.data() + j * k, 4 * (size_t)k);
+        }
+      }
     }
     MRQ_CUDA(cudaStreamSynchronize(st));
+    std::vector<int> next;
+    if (rw.cap_limit > 0) {
+      int c2 = 0;
+      MRQ_CUDA(cudaMemcpy(&c2, rw.ovf.p, sizeof(int), cudaMemcpyDeviceToHost));
+      if (c2 > 0) {
+        std::vector<int> posl(c2);
+        MRQ_CUDA(cudaMemcpy(posl.data(), rw.ovf.p + 1, sizeof(int) * c2, cudaMemcpyDeviceToHost));
+        next.reserve(c2);
+        for (int pidx : posl) next.push_back(bad[pidx]);
+        std::sort(next.begin(), next.end());
+      }
+    }
+    bad.swap(next);
   }
-  idx->prof_on = prof;
-  idx->last_redo = count;
+  rw.seed_tau = nullptr;
+  rw.seed_rows = nullptr;
 }
 
 extern "C" {
@@ -307,7 +352,11 @@ int mrq_search(mrq_index* idx, const float* queries, int64_t nq, int k, int npro
       qb = std::min<int64_t>(qb, std::max<int64_t>(1, (int64_t)1e9 / (4 * (int64_t)idx->nlist)));
     }
     ws.items_budget = budget / 4;
-    if (ws.cap_limit > 0) ws.ovf.reserve((size_t)nq + 1);
+    if (ws.cap_limit > 0) {
+      ws.ovf.reserve((size_t)nq + 1);
+      ws.ovf_tau.reserve((size_t)nq);
+    }
+    ws.seed_out = ws.cap_limit > 0 ? ws.ovf_tau.p : nullptr;
     ws.stats.reserve((size_t)nq * 3);
     if (!odev) {
       ws.oids.reserve((size_t)qb * k);
@@ -317,6 +366,7 @@ int mrq_search(mrq_index* idx, const float* queries, int64_t nq, int k, int npro
     idx->prof_on = o.profile != 0;
     idx->prof_batches = 0;
     idx->launches = 0;
+    idx->last_redo = 0;
     // a captured graph also covers host buffers when they are page-locked (its copy
     // nodes then read and write those buffers on every replay)
     const bool use_graph = o.graph && !o.profile && (qdev || pinned_host(queries)) &&
@@ -325,25 +375,13 @@ int mrq_search(mrq_index* idx, const float* queries, int64_t nq, int k, int npro
                             o.query_bits, o.batched, o.refine,
                             (o.mode == MRQ_MODE_SQ8 || o.mode == MRQ_MODE_PQ) ? o.rerank : 0,
                             o.eps0, o.m, o.survivor_region};
-    // tensor-core forms read each query once (the bf16 split), so page-locked host
-    // queries are read in place through their device mapping instead of copied first
-    const float* qmap = nullptr;
-    if (!qdev && o.precision != MRQ_PREC_FP32 && pinned_host(queries)) {
-      void* dp = nullptr;
-      if (cudaHostGetDevicePointer(&dp, const_cast<float*>(queries), 0) == cudaSuccess)
-        qmap = static_cast<const float*>(dp);
-      else
-        cudaGetLastError();
-    }
     auto run_batches = [&](cudaStream_t s_) {
       if (ws.cap_limit > 0) MRQ_CUDA(cudaMemsetAsync(ws.ovf.p, 0, sizeof(int), s_));
       for (int64_t s = 0; s < nq; s += qb) {
         ws.ovf_base = s;
         const int64_t b = std::min(qb, nq - s);
         const float* qp = queries + s * D;
-        if (qmap) {
-          qp = qmap + s * D;
-        } else if (!qdev) {
+        if (!qdev) {  // host queries: one copy per batch into device memory
           MRQ_CUDA(cudaMemcpyAsync(ws.q.p, qp, 4 * b * D, cudaMemcpyHostToDevice, s_));
           qp = ws.q.p;
         }
@@ -362,8 +400,10 @@ int mrq_search(mrq_index* idx, const float* queries, int64_t nq, int k, int npro
         MRQ_CUDA(cudaEventCreateWithFlags(&idx->graph_ev[0], cudaEventDisableTiming));
         MRQ_CUDA(cudaEventCreateWithFlags(&idx->graph_ev[1], cudaEventDisableTiming));
       }
-      if (!(idx->graph_valid && idx->graph_key == key)) {
-        // first call with these arguments: run once (sizes scratch), then capture
+      if (!(idx->graph_valid && idx->graph_key == key &&
+            idx->graph_epoch == mrq::g_ws_epoch.load())) {
+        // first call with these arguments, or scratch that moved since the capture: run
+        // once (sizes scratch), then capture
         run_batches(st);
         MRQ_CUDA(cudaStreamSynchronize(st));
         const int64_t l0 = idx->launches;
@@ -386,6 +426,7 @@ int mrq_search(mrq_index* idx, const float* queries, int64_t nq, int k, int npro
         cudaGraphDestroy(g);
         MRQ_CUDA(ie);
         idx->graph_key = key;
+        idx->graph_epoch = mrq::g_ws_epoch.load();
         idx->graph_valid = true;
         idx->graph_launches = idx->launches - l0;
       }
@@ -621,6 +662,13 @@ int mrq_last_search_stats(const mrq_index* idx, int64_t nq, int64_t* n_cand, int
       if (n_s1) n_s1[i] = idx->last_stats[i * 3 + 1];
       if (n_exact) n_exact[i] = idx->last_stats[i * 3 + 2];
     }
+  });
+}
+
+int mrq_last_search_redo(const mrq_index* idx, int64_t* redone) {
+  return guarded([&] {
+    MRQ_REQUIRE(idx && redone, "NULL argument");
+    *redone = idx->last_redo;
   });
 }
 

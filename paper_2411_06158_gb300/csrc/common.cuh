@@ -10,6 +10,7 @@
 #include <map>
 #include <mutex>
 #include <tuple>
+#include <atomic>
 #include <vector>
 
 #include "../../include/mrq.h"
@@ -73,49 +74,72 @@ struct DevBuf {
   T* get() const { return p; }
 };
 
+// Process-wide count of search-scratch reallocations: a captured search graph holds the
+// addresses of the scratch it was captured with, so it is captured again once this moves.
+inline std::atomic<uint64_t> g_ws_epoch{0};
+
+// a DevBuf of the search scratch: its growth moves g_ws_epoch
+template <class T>
+struct WsBuf : DevBuf<T> {
+  void reserve(size_t count) {
+    if (count > this->n) {
+      this->alloc(count);
+      g_ws_epoch.fetch_add(1);
+    }
+  }
+};
+
 // Per-index search scratch, grown on demand and reused across calls.
 struct Workspace {
-  DevBuf<float> q;         // nq x D staged queries (host inputs)
-  DevBuf<float> qd, qr;    // projected queries
-  DevBuf<float> qstat;     // nq x 4: |q_r|^2, sigma, |q_p|^2, unused
-  DevBuf<float> pqq;       // nq x d: q_d' R, the OPQ-rotated query (MR-PQ)
+  WsBuf<float> q;         // nq x D staged queries (host inputs)
+  WsBuf<float> qd, qr;    // projected queries
+  WsBuf<float> qstat;     // nq x 4: |q_r|^2, sigma, |q_p|^2, unused
+  WsBuf<float> pqq;       // nq x d: q_d' R, the OPQ-rotated query (MR-PQ)
   // optimistic survivor region: with cap_limit > 0 every query's stage-1 region holds at
   // most cap_limit entries; a query whose survivors overflow it is listed in ovf
   // ([0] = count, then query indices offset by ovf_base) and searched again in full
   int64_t cap_limit = 0;
   int64_t ovf_base = 0;
-  DevBuf<int> ovf;
+  WsBuf<int> ovf;
   int64_t items_budget = 0;  // bytes the batched scan's work items may take (0 = any)
-  DevBuf<__nv_bfloat16> qbf;  // nq x D bf16 hi/lo split queries (tensor-core projection)
-  DevBuf<uint8_t> q8;          // nq x D row-scaled e4m3 queries (FP8 projection)
-  DevBuf<float> q8s;           // their row scales
-  DevBuf<__nv_bfloat16> qbf2;  // nq x d bf16 hi/lo split q_d' (tensor-core probe operand)
-  DevBuf<float> gmat;      // nq x nlist probe distances
-  DevBuf<unsigned long long> ppart;  // nq x tiles x nprobe fused probe candidates
-  DevBuf<int32_t> plist;   // nq x nprobe probed list ids
-  DevBuf<float> pg;        // nq x nprobe |q_d - c|^2 of the probed lists
-  DevBuf<uint32_t> qcnt;   // nq survivor counters
-  DevBuf<uint32_t> gtau;   // nq running stage-1 thresholds (orderable keys)
-  DevBuf<int32_t> spos;    // nq x cap survivor positions
-  DevBuf<float> slb, sub;  // nq x cap stage-1 bounds of the survivors
-  DevBuf<float> s2a, s2b;  // nq x cap stage-2 scratch
-  DevBuf<int32_t> s2pos;   // nq x cap
-  DevBuf<int64_t> oids;    // nq x k staged results
-  DevBuf<float> odist;
-  DevBuf<int64_t> stats;   // nq x 3
-  DevBuf<uint32_t> work;   // work-queue counters
-  DevBuf<float> qtau;      // nq: tau_A per query (phased finalize)
-  DevBuf<int> qm1, qm2;    // nq: stage-1 / stage-2 survivor counts
-  DevBuf<int> ccnt, coff, nitems;  // long-list chunking: per-pair chunk counts, offsets
-  DevBuf<int64_t> items;   // (pair << 32 | chunk) scan work items
-  DevBuf<uint8_t> cubtmp;  // CUB scan scratch
+  // per row of the call: the bound an overflowed query's search again starts from
+  // (written through seed_out while the call's batches run; read through seed_tau and
+  // seed_rows, the batch's rows, by the searches again)
+  WsBuf<float> ovf_tau;
+  float* seed_out = nullptr;
+  const float* seed_tau = nullptr;
+  const int* seed_rows = nullptr;
+  WsBuf<__nv_bfloat16> qbf;  // nq x D bf16 hi/lo split queries (tensor-core projection)
+  WsBuf<uint8_t> q8;          // nq x D row-scaled e4m3 queries (FP8 projection)
+  WsBuf<float> q8s;           // their row scales
+  WsBuf<__nv_bfloat16> qbf2;  // nq x d bf16 hi/lo split q_d' (tensor-core probe operand)
+  WsBuf<float> gmat;      // nq x nlist probe distances
+  WsBuf<unsigned long long> ppart;  // nq x tiles x nprobe fused probe candidates
+  WsBuf<int32_t> plist;   // nq x nprobe probed list ids
+  WsBuf<float> pg;        // nq x nprobe |q_d - c|^2 of the probed lists
+  WsBuf<uint32_t> qcnt;   // nq survivor counters
+  WsBuf<uint32_t> gtau;   // nq running stage-1 thresholds (orderable keys)
+  WsBuf<int32_t> spos;    // nq x cap survivor positions
+  WsBuf<float> slb, sub;  // nq x cap stage-1 bounds of the survivors
+  WsBuf<float> s2a, s2b;  // nq x cap stage-2 scratch
+  WsBuf<int32_t> s2pos;   // nq x cap
+  WsBuf<int64_t> oids;    // nq x k staged results
+  WsBuf<float> odist;
+  WsBuf<int64_t> stats;   // nq x 3
+  WsBuf<uint32_t> work;   // work-queue counters
+  WsBuf<float> qtau;      // nq: tau_A per query (phased finalize)
+  WsBuf<int> qm1, qm2;    // nq: stage-1 / stage-2 survivor counts
+  WsBuf<int> ccnt, coff, nitems;  // long-list chunking: per-pair chunk counts, offsets
+  WsBuf<int64_t> items;   // (pair << 32 | chunk) scan work items
+  WsBuf<int64_t> sitems;  // the seed pass's items (each query's nearest list, chunk 0)
+  WsBuf<uint8_t> cubtmp;  // CUB scan scratch
   // list-major batched scan
-  DevBuf<int32_t> lcount, loffq, lfill, lqueue;  // per-list buckets of (query, list) pairs
-  DevBuf<int32_t> icnt, ioff;              // work items per list and their offsets
-  DevBuf<int64_t> bitems;                  // int4 work items (list, block, group)
-  DevBuf<uint8_t> pq;                      // per-pair query scalars
-  DevBuf<uint8_t> qrow;                    // per-pair query codes as e4m3 bytes (tensor-core scan)
-  DevBuf<uint32_t> qplanes;                // per-pair quantized query bit planes
+  WsBuf<int32_t> lcount, loffq, lfill, lqueue;  // per-list buckets of (query, list) pairs
+  WsBuf<int32_t> icnt, ioff;              // work items per list and their offsets
+  WsBuf<int64_t> bitems;                  // int4 work items (list, block, group)
+  WsBuf<uint8_t> pq;                      // per-pair query scalars
+  WsBuf<uint8_t> qrow;                    // per-pair query codes as e4m3 bytes (tensor-core scan)
+  WsBuf<uint32_t> qplanes;                // per-pair quantized query bit planes
 };
 
 }  // namespace mrq
@@ -245,6 +269,7 @@ struct mrq_index {
   cudaStream_t graph_stream = nullptr;
   cudaEvent_t graph_ev[2] = {nullptr, nullptr};
   int64_t graph_launches = 0;
+  uint64_t graph_epoch = 0;  // g_ws_epoch when the graph was captured
   ~mrq_index() {
     for (auto e : prof_ev) cudaEventDestroy(e);
     if (graph_exec) cudaGraphExecDestroy(graph_exec);
@@ -310,9 +335,15 @@ void quantize_rows_fp8(const float* X, int M, int K, int ld, const float* shift,
 void project_fp8(const float* Q, const float* mu, const uint8_t* W8, const float* W8s, int M,
                  int D, int d, uint8_t* q8, float* q8s, float* qd, int ldd, float* qr, int ldr,
                  cudaStream_t st, __nv_bfloat16* probe_bf, int* err);
-void project_tc(const float* Q, const float* mu, const __nv_bfloat16* W2, int M, int D, int d,
-                bool split3, __nv_bfloat16* qbf, float* qd, float* qr, cudaStream_t st,
-                __nv_bfloat16* probe_bf = nullptr);
+// returns the kernels launched: 1 (the fused projection, which centres and splits the
+// float32 queries itself) or 2 (split kernel + GEMM, for unaligned rows)
+int project_tc(const float* Q, const float* mu, const __nv_bfloat16* W2, int M, int D, int d,
+               bool split3, __nv_bfloat16* qbf, float* qd, float* qr, cudaStream_t st,
+               __nv_bfloat16* probe_bf = nullptr);
+// the fused projection alone (false: operands it cannot take, nothing launched)
+bool project_fused(const float* Q, const float* mu, const __nv_bfloat16* W2, int M, int D, int d,
+                   bool split3, float* qd, int ldd, float* qr, int ldr, __nv_bfloat16* probe_bf,
+                   int* err, cudaStream_t st);
 void probe_tc(const float* qd, const float* qstat, const __nv_bfloat16* C2, const float* cn2,
               int M, int nlist, int d, bool split3, __nv_bfloat16* qbf, float* gmat,
               cudaStream_t st, bool presplit = false);
@@ -326,8 +357,15 @@ int probe_tc_topk(const float* qd, const float* qstat, const __nv_bfloat16* C2, 
 void search_batch(mrq_index* idx, Workspace& ws, const float* q_dev, int64_t nq, int k,
                   int nprobe, const mrq_search_opts& o, int64_t* ids_dev, float* dists_dev,
                   int64_t* stats_dev, cudaStream_t st);
-void project_batch(mrq_index* idx, Workspace& ws, const float* q_dev, int64_t nq, int precision,
-                   float* qd, float* qr, cudaStream_t st, __nv_bfloat16* probe_bf = nullptr);
+// the optimistic survivor region's second search: rows of the queries gathered, and the
+// answers and counters scattered back to their rows (device buffers; out_ids NULL: counters only)
+void gather_query_rows(const float* src, int D, const int* rows, int64_t n, float* dst,
+                       cudaStream_t st);
+void scatter_answers(const int64_t* ids, const float* d, const int64_t* stats, int k, const int* rows,
+                     int64_t n, int64_t* out_ids, float* out_d, int64_t* out_stats, cudaStream_t st);
+// the projection of nq device queries at a precision; returns the kernels launched
+int project_batch(mrq_index* idx, Workspace& ws, const float* q_dev, int64_t nq, int precision,
+                  float* qd, float* qr, cudaStream_t st, __nv_bfloat16* probe_bf = nullptr);
 // MR-SQ arrays of the index (made once, on the given stream, then synchronised)
 void ensure_sq8(const mrq_index* idx, cudaStream_t st);
 

@@ -379,9 +379,16 @@ __global__ void __launch_bounds__(256, 1)
     const int row = m0 + quarter * 32 + lane;
     const bool rv = row < P.M;
     const float rn = rv ? P.rown[(int64_t)row * P.rstride] : 0.f;
-    float b[PSEL];
+    // four independent networks (one per column residue mod 4) keep four dependency
+    // chains in flight; they are merged below (the PSEL smallest of the union are the
+    // same values whatever the order of insertion)
+    float b[PSEL], b4[4][PSEL];
 #pragma unroll
-    for (int t = 0; t < PSEL; ++t) b[t] = FLT_MAX_F;
+    for (int t = 0; t < PSEL; ++t) {
+      b[t] = FLT_MAX_F;
+#pragma unroll
+      for (int u = 0; u < 4; ++u) b4[u][t] = FLT_MAX_F;
+    }
     for (int c = half * HALF; c < half * HALF + HALF; c += 32) {
       uint32_t r[32];
       tc_ld32(trow + (uint32_t)c, r);
@@ -397,8 +404,9 @@ __global__ void __launch_bounds__(256, 1)
 #pragma unroll
           for (int u = 0; u < 4; ++u) {
 #pragma unroll
-            for (int t = PSEL - 1; t >= 1; --t) b[t] = fminf(b[t], fmaxf(b[t - 1], g4[u]));
-            b[0] = fminf(b[0], g4[u]);
+            for (int t = PSEL - 1; t >= 1; --t)
+              b4[u][t] = fminf(b4[u][t], fmaxf(b4[u][t - 1], g4[u]));
+            b4[u][0] = fminf(b4[u][0], g4[u]);
           }
         }
       } else {
@@ -411,6 +419,16 @@ __global__ void __launch_bounds__(256, 1)
             b[0] = fminf(b[0], g);
           }
         }
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+#pragma unroll
+      for (int v = 0; v < PSEL; ++v) {
+        const float g = b4[u][v];
+#pragma unroll
+        for (int t = PSEL - 1; t >= 1; --t) b[t] = fminf(b[t], fmaxf(b[t - 1], g));
+        b[0] = fminf(b[0], g);
       }
     }
     float thr = b[0];  // b[] is ascending: b[nsel - 1] is the largest of the first nsel
@@ -457,6 +475,302 @@ __global__ void __launch_bounds__(256, 1)
     }
     if (rv)
       for (int t = ns + ti; t < P.nsel; ++t) out[t] = ~0ull;  // fewer than nsel columns
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 2)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(NCOLS)
+                 : "memory");
+}
+
+// ------------------------------------------------------------------ fused projection
+// [q_d' | q_r] = W (q - mu) straight from the float32 queries (Algorithm 2, rotate step):
+// the centring and the bf16 split of the query operand happen inside the GEMM, so no
+// split kernel and no bf16 copy of the queries in global memory.
+//
+// Persistent CTAs (one per SM) walk the 128 x BN output tiles in row-major tile order
+// (consecutive CTAs share a block of query rows, which then comes from L2).  Warp roles:
+//   warp 0 (one lane)  TMA producer: float32 query slices (two 32-float, 128-byte
+//                      swizzled boxes per 64-wide K slice) into the staging ring, and
+//                      W's bf16 slices (hi, and lo in the split form) into the operand ring;
+//   warp 1 (one lane)  tcgen05.mma issuer (hi*hi, plus hi*lo + lo*hi in the split form),
+//                      into one of two tensor-memory accumulators;
+//   warp 2             tensor-memory allocation;
+//   warps 4-7          converters: thread t reads row t of a staged slice, subtracts mu,
+//                      rounds to bf16 hi (and lo = bf16(x - hi)), and writes the 128-byte
+//                      swizzled K-major operand rows the MMA reads;
+//   warps 8-11         epilogue: tcgen05.ld of their 32 accumulator lanes, float32 rows of
+//                      q_d' and q_r, and the probe's bf16 operand of q_d'.
+// The two accumulators let the epilogue of one tile run under the MMAs of the next.
+struct ProjArgs {
+  int M, N, K;        // queries, output columns (D), reduction length (D)
+  int b_lo;           // row offset of W's lo half in its tensor (split form)
+  const float* mu;    // centre, K floats
+  float* out0;        // columns [0, split), row stride ld0
+  int ld0;
+  float* out1;        // columns [split, N), row stride ld1
+  int ld1;
+  int split;
+  __nv_bfloat16* pbf;  // optional: the first `split` columns again as bf16 hi (rows 0..M-1)
+  int pbf_two;         // and lo (rows M..2M-1)
+  int* err;
+  int tiles_n;        // ceil(N / BN)
+  int tiles;          // ceil(M / 128) * tiles_n
+};
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* b) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(b)) : "memory");
+}
+__device__ __forceinline__ void fence_async_shared() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+constexpr int PJ_THREADS = 384;
+constexpr int PJ_F32_STAGE = TC_BM * 64 * 4;  // 128 rows x 64 float32 = two 16 KB boxes
+
+template <int BN, int SA, int SB, int S32, bool THREE>
+__global__ void __launch_bounds__(PJ_THREADS, 1)
+    k_proj_tc(const __grid_constant__ CUtensorMap tq, const __grid_constant__ CUtensorMap tw,
+              ProjArgs P) {
+  constexpr int A_BYTES = TC_BM * TC_BK * 2;
+  constexpr int B_BYTES = BN * TC_BK * 2;
+  constexpr int AST = A_BYTES * (THREE ? 2 : 1);  // one A stage: hi (and lo)
+  constexpr int BST = B_BYTES * (THREE ? 2 : 1);  // one B stage: hi (and lo)
+  // the two accumulators start at column 0 and at BSTR (BN rounded up to a power of two)
+  constexpr uint32_t BSTR = BN <= 64 ? 64 : BN <= 128 ? 128 : 256;
+  constexpr uint32_t NCOLS = 2 * BSTR;
+  constexpr uint32_t IDESC = idesc_bf16<BN>();
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* ar = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
+                                           ~static_cast<uintptr_t>(1023));
+  uint8_t* br = ar + SA * AST;
+  uint8_t* f32r = br + SB * BST;
+  __shared__ __align__(8) uint64_t f_full[S32], f_empty[S32], a_full[SA], a_empty[SA];
+  __shared__ __align__(8) uint64_t b_full[SB], b_empty[SB], c_full[2], c_empty[2];
+  __shared__ uint32_t tmem_slot;
+  __shared__ volatile int s_abort;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nkb = (P.K + TC_BK - 1) / TC_BK;
+  if (threadIdx.x == 0) {
+    s_abort = 0;
+    for (int s = 0; s < S32; ++s) { mbar_init(&f_full[s], 1); mbar_init(&f_empty[s], 4); }
+    for (int s = 0; s < SA; ++s) { mbar_init(&a_full[s], 4); mbar_init(&a_empty[s], 1); }
+    for (int s = 0; s < SB; ++s) { mbar_init(&b_full[s], 1); mbar_init(&b_empty[s], 1); }
+    for (int s = 0; s < 2; ++s) { mbar_init(&c_full[s], 1); mbar_init(&c_empty[s], 4); }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    fence_async_shared();
+  }
+  if (warp == 2) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     su32(&tmem_slot)),
+                 "r"(NCOLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_slot;
+
+  if (warp == 0) {
+    if (lane == 0) {  // query producer: float32 slices into the staging ring
+      uint32_t fs = 0, fph = 0;
+      bool ok = true;
+      for (int tile = blockIdx.x; ok && tile < P.tiles; tile += gridDim.x) {
+        const int m0 = (tile / P.tiles_n) * TC_BM;
+        for (int kb = 0; kb < nkb; ++kb) {
+          if (!mbar_wait(&f_empty[fs], fph ^ 1u, &s_abort, P.err, 11)) { ok = false; break; }
+          uint8_t* f = f32r + fs * PJ_F32_STAGE;
+          mbar_expect_tx(&f_full[fs], PJ_F32_STAGE);
+          tma_load_2d(f, &tq, kb * TC_BK, m0, &f_full[fs]);
+          tma_load_2d(f + PJ_F32_STAGE / 2, &tq, kb * TC_BK + 32, m0, &f_full[fs]);
+          if (++fs == S32) { fs = 0; fph ^= 1u; }
+        }
+      }
+    }
+  } else if (warp == 3) {
+    if (lane == 0) {  // W producer: bf16 slices (hi, and lo) into the B ring
+      uint32_t bs = 0, bph = 0;
+      bool ok = true;
+      for (int tile = blockIdx.x; ok && tile < P.tiles; tile += gridDim.x) {
+        const int n0 = (tile % P.tiles_n) * BN;
+        for (int kb = 0; kb < nkb; ++kb) {
+          if (!mbar_wait(&b_empty[bs], bph ^ 1u, &s_abort, P.err, 12)) { ok = false; break; }
+          uint8_t* b = br + bs * BST;
+          mbar_expect_tx(&b_full[bs], BST);
+          tma_load_2d(b, &tw, kb * TC_BK, n0, &b_full[bs]);
+          if constexpr (THREE) tma_load_2d(b + B_BYTES, &tw, kb * TC_BK, n0 + P.b_lo, &b_full[bs]);
+          if (++bs == SB) { bs = 0; bph ^= 1u; }
+        }
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {  // MMA issuer
+      uint32_t as = 0, aph = 0, bs = 0, bph = 0, cs = 0, cph = 0;
+      bool ok = true;
+      for (int tile = blockIdx.x; ok && tile < P.tiles; tile += gridDim.x) {
+        if (!mbar_wait(&c_empty[cs], cph ^ 1u, &s_abort, P.err, 13)) break;
+        tc_fence_after();
+        const uint32_t dt = tmem + cs * BSTR;
+        for (int kb = 0; kb < nkb; ++kb) {
+          if (!mbar_wait(&a_full[as], aph, &s_abort, P.err, 14) ||
+              !mbar_wait(&b_full[bs], bph, &s_abort, P.err, 18)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t sa = su32(ar + as * AST), sb = su32(br + bs * BST);
+          const uint64_t ah = sdesc(sa), bh = sdesc(sb);
+#pragma unroll
+          for (int kk = 0; kk < TC_BK / 16; ++kk)
+            tc_mma(dt, ah + 2ull * kk, bh + 2ull * kk, IDESC, (kb | kk) != 0 ? 1u : 0u);
+          if constexpr (THREE) {
+            const uint64_t al = sdesc(sa + A_BYTES), bl = sdesc(sb + B_BYTES);
+#pragma unroll
+            for (int kk = 0; kk < TC_BK / 16; ++kk) {
+              tc_mma(dt, ah + 2ull * kk, bl + 2ull * kk, IDESC, 1u);
+              tc_mma(dt, al + 2ull * kk, bh + 2ull * kk, IDESC, 1u);
+            }
+          }
+          tc_commit(&a_empty[as]);
+          tc_commit(&b_empty[bs]);
+          if (++as == SA) { as = 0; aph ^= 1u; }
+          if (++bs == SB) { bs = 0; bph ^= 1u; }
+        }
+        if (!ok) break;
+        tc_commit(&c_full[cs]);
+        cs ^= 1u;
+        if (cs == 0) cph ^= 1u;
+      }
+    }
+  } else if (warp >= 4 && warp < 8) {  // converters: thread t owns row t of each slice
+    const int t = threadIdx.x - 128;
+    const int sw = t & 7;
+    uint32_t fs = 0, fph = 0, as = 0, aph = 0;
+    bool ok = true;
+    for (int tile = blockIdx.x; ok && tile < P.tiles; tile += gridDim.x) {
+      for (int kb = 0; kb < nkb; ++kb) {
+        // the centre of this slice's 64 coordinates, read while the slice lands
+        const int kc = kb * TC_BK;
+        float4 mu4[16];
+#pragma unroll
+        for (int j = 0; j < 16; ++j)
+          mu4[j] = kc + 4 * j < P.K ? __ldg(reinterpret_cast<const float4*>(P.mu + kc) + j)
+                                    : make_float4(0.f, 0.f, 0.f, 0.f);
+        if (!mbar_wait(&f_full[fs], fph, &s_abort, P.err, 15) ||
+            !mbar_wait(&a_empty[as], aph ^ 1u, &s_abort, P.err, 16)) {
+          ok = false;
+          break;
+        }
+        const uint8_t* f = f32r + fs * PJ_F32_STAGE + t * 128;
+        uint8_t* ah = ar + as * AST + t * 128;
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {  // 8 consecutive k per 16-byte bf16 chunk
+          const uint8_t* fb = f + (c >> 2) * (PJ_F32_STAGE / 2);
+          const int u0 = 2 * (c & 3);
+          const float4 v0 = *reinterpret_cast<const float4*>(fb + ((u0 ^ sw) << 4));
+          const float4 v1 = *reinterpret_cast<const float4*>(fb + (((u0 + 1) ^ sw) << 4));
+          // K is a multiple of 8: a chunk is all inside or all outside (zero there)
+          const bool in = kc + 8 * c < P.K;
+          const float4 m0 = mu4[2 * c], m1 = mu4[2 * c + 1];
+          float x[8] = {v0.x - m0.x, v0.y - m0.y, v0.z - m0.z, v0.w - m0.w,
+                        v1.x - m1.x, v1.y - m1.y, v1.z - m1.z, v1.w - m1.w};
+          if (!in) {
+#pragma unroll
+            for (int j = 0; j < 8; ++j) x[j] = 0.f;
+          }
+          uint32_t hw[4], lw[4];
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            const __nv_bfloat162 h = __floats2bfloat162_rn(x[2 * j], x[2 * j + 1]);
+            hw[j] = *reinterpret_cast<const uint32_t*>(&h);
+            if constexpr (THREE) {
+              const float2 hf = __bfloat1622float2(h);
+              const __nv_bfloat162 l = __floats2bfloat162_rn(x[2 * j] - hf.x, x[2 * j + 1] - hf.y);
+              lw[j] = *reinterpret_cast<const uint32_t*>(&l);
+            }
+          }
+          const int du = (c ^ sw) << 4;
+          *reinterpret_cast<uint4*>(ah + du) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+          if constexpr (THREE)
+            *reinterpret_cast<uint4*>(ah + A_BYTES + du) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+        }
+        fence_async_shared();  // the operand rows are read by the tensor cores (async proxy)
+        __syncwarp();
+        if (lane == 0) {
+          mbar_arrive(&f_empty[fs]);
+          mbar_arrive(&a_full[as]);
+        }
+        if (++fs == S32) { fs = 0; fph ^= 1u; }
+        if (++as == SA) { as = 0; aph ^= 1u; }
+      }
+    }
+  } else if (warp >= 8) {  // epilogue: warp 8 + q drains accumulator lanes 32q .. 32q + 31
+    const int quarter = warp & 3;
+    uint32_t cs = 0, cph = 0;
+    for (int tile = blockIdx.x; tile < P.tiles; tile += gridDim.x) {
+      const int m0 = (tile / P.tiles_n) * TC_BM, n0 = (tile % P.tiles_n) * BN;
+      if (!mbar_wait(&c_full[cs], cph, &s_abort, P.err, 17, 2000)) break;
+      tc_fence_after();
+      const uint32_t trow = tmem + ((uint32_t)(quarter * 32) << 16) + cs * BSTR;
+      const int row = m0 + quarter * 32 + lane;
+      for (int c = 0; c < BN; c += 32) {
+        uint32_t r[32];
+        tc_ld32(trow + (uint32_t)c, r);
+        const int col0 = n0 + c;
+        if (row >= P.M || col0 >= P.N) continue;
+        if (P.pbf && col0 + 32 <= P.split) {
+          uint32_t hw[16], lw[16];
+#pragma unroll
+          for (int j = 0; j < 16; ++j) {
+            const float x0 = __uint_as_float(r[2 * j]), x1 = __uint_as_float(r[2 * j + 1]);
+            const __nv_bfloat162 h = __floats2bfloat162_rn(x0, x1);
+            const float2 hf = __bfloat1622float2(h);
+            const __nv_bfloat162 l = __floats2bfloat162_rn(x0 - hf.x, x1 - hf.y);
+            hw[j] = *reinterpret_cast<const uint32_t*>(&h);
+            lw[j] = *reinterpret_cast<const uint32_t*>(&l);
+          }
+          uint4* dh = reinterpret_cast<uint4*>(P.pbf + (int64_t)row * P.split + col0);
+#pragma unroll
+          for (int j = 0; j < 4; ++j) dh[j] = make_uint4(hw[4 * j], hw[4 * j + 1], hw[4 * j + 2], hw[4 * j + 3]);
+          if (P.pbf_two) {
+            uint4* dl = reinterpret_cast<uint4*>(P.pbf + ((int64_t)P.M + row) * P.split + col0);
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+              dl[j] = make_uint4(lw[4 * j], lw[4 * j + 1], lw[4 * j + 2], lw[4 * j + 3]);
+          }
+        }
+        const bool whole = col0 + 32 <= P.N && (col0 + 32 <= P.split || col0 >= P.split);
+        if (whole) {
+          float* dst = col0 < P.split ? P.out0 + (int64_t)row * P.ld0 + col0
+                                      : P.out1 + (int64_t)row * P.ld1 + (col0 - P.split);
+          if ((reinterpret_cast<uintptr_t>(dst) & 15) == 0) {
+            float4* d4 = reinterpret_cast<float4*>(dst);
+#pragma unroll
+            for (int j = 0; j < 8; ++j)
+              d4[j] = make_float4(__uint_as_float(r[4 * j]), __uint_as_float(r[4 * j + 1]),
+                                  __uint_as_float(r[4 * j + 2]), __uint_as_float(r[4 * j + 3]));
+          } else {
+#pragma unroll
+            for (int j = 0; j < 32; ++j) dst[j] = __uint_as_float(r[j]);
+          }
+        } else {
+#pragma unroll
+          for (int j = 0; j < 32; ++j) {
+            const int col = col0 + j;
+            if (col >= P.N) break;
+            if (col < P.split) P.out0[(int64_t)row * P.ld0 + col] = __uint_as_float(r[j]);
+            else P.out1[(int64_t)row * P.ld1 + (col - P.split)] = __uint_as_float(r[j]);
+          }
+        }
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&c_empty[cs]);
+      cs ^= 1u;
+      if (cs == 0) cph ^= 1u;
+    }
   }
   tc_fence_before();
   __syncthreads();
@@ -574,6 +888,21 @@ CUtensorMap make_map(const void* base, uint64_t rows, uint64_t K, uint32_t box_r
   return m;
 }
 
+// float32 rows (K contiguous) read as 128-byte swizzled boxes of 32 floats x box_rows
+CUtensorMap make_map_f32(const float* base, uint64_t rows, uint64_t K, uint32_t box_rows) {
+  CUtensorMap m;
+  cuuint64_t dims[2] = {K, rows};
+  cuuint64_t strides[1] = {K * 4};
+  cuuint32_t box[2] = {32, box_rows};
+  cuuint32_t es[2] = {1, 1};
+  CUresult r = encode_fn()(&m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(base), dims,
+                           strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                           CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) fail(MRQ_ECUDA, "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")");
+  return m;
+}
+
 // The pipeline error word (and a page-locked host copy for asynchronous readback) of
 // each device, made on first use with that device current: a kernel only ever writes
 // the word of the device it runs on.
@@ -600,6 +929,28 @@ void launch_tc(const void* A2, const void* B2, const TcArgs& a, cudaStream_t st)
   ensure_smem((const void*)k_gemm_tc<BN, PSEL, STAGES, F8>, smem);
   dim3 grid(ceil_div(a.M, TC_BM), ceil_div(a.N, BN));
   k_gemm_tc<BN, PSEL, STAGES, F8><<<grid, 256, smem, st>>>(ta, tb, a);
+  MRQ_CHECK_LAUNCH();
+}
+
+int sm_count() {
+  int dev = 0, n = 0;
+  MRQ_CUDA(cudaGetDevice(&dev));
+  MRQ_CUDA(cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev));
+  return n;
+}
+
+template <int BN, int SA, int SB, int S32, bool THREE>
+void launch_proj(const float* Q, const __nv_bfloat16* W2, ProjArgs a, cudaStream_t st) {
+  constexpr int AST = TC_BM * TC_BK * 2 * (THREE ? 2 : 1);
+  constexpr int BST = BN * TC_BK * 2 * (THREE ? 2 : 1);
+  const size_t smem = (size_t)SA * AST + (size_t)SB * BST + (size_t)S32 * PJ_F32_STAGE + 1024;
+  CUtensorMap tq = make_map_f32(Q, (uint64_t)a.M, (uint64_t)a.K, TC_BM);
+  CUtensorMap tw = make_map(W2, (uint64_t)a.N * (THREE ? 2 : 1), a.K, BN);
+  a.tiles_n = ceil_div(a.N, BN);
+  a.tiles = ceil_div(a.M, TC_BM) * a.tiles_n;
+  ensure_smem((const void*)k_proj_tc<BN, SA, SB, S32, THREE>, smem);
+  const int grid = std::min(a.tiles, sm_count());
+  k_proj_tc<BN, SA, SB, S32, THREE><<<grid, PJ_THREADS, smem, st>>>(tq, tw, a);
   MRQ_CHECK_LAUNCH();
 }
 
@@ -680,9 +1031,58 @@ int tc_check_error() {
   return h;
 }
 
-void project_tc(const float* Q, const float* mu, const __nv_bfloat16* W2, int M, int D, int d,
-                bool split3, __nv_bfloat16* qbf, float* qd, float* qr, cudaStream_t st,
-                __nv_bfloat16* probe_bf) {
+// The fused projection when its operands allow it (float32 query rows in device memory,
+// which its TMA loads read; rows and centre 16-byte aligned; D a multiple
+// of 8); false leaves the work to the split + GEMM path.
+bool project_fused(const float* Q, const float* mu, const __nv_bfloat16* W2, int M, int D, int d,
+                   bool split3, float* qd, int ldd, float* qr, int ldr, __nv_bfloat16* probe_bf,
+                   int* err, cudaStream_t st) {
+  auto al16 = [](const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; };
+  if (M <= 0 || D % 8 != 0 || !al16(Q) || !al16(mu)) return false;
+  cudaPointerAttributes pa{};
+  if (cudaPointerGetAttributes(&pa, Q) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  if (pa.type != cudaMemoryTypeDevice) return false;
+  ProjArgs a{};
+  a.M = M; a.N = D; a.K = D;
+  a.b_lo = D;
+  a.mu = mu;
+  a.out0 = qd; a.ld0 = ldd; a.out1 = qr; a.ld1 = ldr; a.split = d;
+  a.pbf = (d % 32 == 0) ? probe_bf : nullptr;
+  a.pbf_two = split3 ? 1 : 0;
+  a.err = err;
+  // the operand traffic of a CTA (float32 query rows, bf16 rows of W) grows with the
+  // tiles it runs: pick the tile width whose busiest SM moves the fewest bytes
+  const int sms = sm_count();
+  auto busiest = [&](int bn) {
+    const int64_t tiles = (int64_t)ceil_div(M, TC_BM) * ceil_div(D, bn);
+    const int64_t per_tile = (int64_t)D * (TC_BM * 4 + (int64_t)bn * 2 * (split3 ? 2 : 1));
+    return ((tiles + sms - 1) / sms) * per_tile;
+  };
+  // rings (A stages, B stages, float32 stages) within 227 KB of shared memory
+  if (split3) {
+    if (D <= 64) launch_proj<64, 2, 3, 2, true>(Q, W2, a, st);
+    else launch_proj<128, 2, 2, 2, true>(Q, W2, a, st);
+  } else if (D <= 64) {
+    launch_proj<64, 2, 4, 4, false>(Q, W2, a, st);
+  } else if (D <= 128) {
+    launch_proj<128, 2, 4, 3, false>(Q, W2, a, st);
+  } else {
+    const int64_t c128 = busiest(128), c192 = busiest(192), c256 = busiest(256);
+    if (c256 <= c192 && c256 <= c128) launch_proj<256, 2, 3, 3, false>(Q, W2, a, st);
+    else if (c192 <= c128) launch_proj<192, 2, 4, 3, false>(Q, W2, a, st);
+    else launch_proj<128, 2, 4, 3, false>(Q, W2, a, st);
+  }
+  return true;
+}
+
+int project_tc(const float* Q, const float* mu, const __nv_bfloat16* W2, int M, int D, int d,
+               bool split3, __nv_bfloat16* qbf, float* qd, float* qr, cudaStream_t st,
+               __nv_bfloat16* probe_bf) {
+  if (project_fused(Q, mu, W2, M, D, d, split3, qd, d, qr, D - d, probe_bf, tc_error_word(), st))
+    return 1;
   split_bf16(Q, M, D, D, mu, split3, qbf, st);
   TcArgs a{};
   a.M = M; a.N = D; a.K = D;
@@ -693,6 +1093,7 @@ void project_tc(const float* Q, const float* mu, const __nv_bfloat16* W2, int M,
   a.pbf = (d % 32 == 0) ? probe_bf : nullptr;
   a.pbf_two = split3 ? 1 : 0;
   run_tc(qbf, W2, a, st);
+  return 2;
 }
 
 void quantize_rows_fp8(const float* X, int M, int K, int ld, const float* shift, uint8_t* out,
@@ -839,24 +1240,27 @@ void project_noalloc(mrq_index* idx, const float* q, int64_t nq, int precision, 
   int* err = reinterpret_cast<int*>(base);
   __nv_bfloat16* qbf = reinterpret_cast<__nv_bfloat16*>(base + 256);
   MRQ_CUDA(cudaMemsetAsync(err, 0, sizeof(int), st));
-  split_bf16(q, (int)nq, D, D, idx->mu.p, split3, qbf, st);
-  TcArgs a{};
-  a.M = (int)nq; a.N = D; a.K = D;
-  a.phases = split3 ? 3 : 1;
-  a.a_lo = (int)nq; a.b_lo = D;
-  a.epi = 0;
-  a.out0 = qp; a.ld0 = D; a.out1 = qp + d; a.ld1 = D; a.split = d;
-  a.err = err;
-  const bool short_k = (int64_t)((a.K + TC_BK - 1) / TC_BK) * a.phases <= 2;
-  if (a.N <= 64) {
-    if (short_k) launch_tc<64, 4, 2>(qbf, idx->W2.p, a, st);
-    else launch_tc<64, 4, 4>(qbf, idx->W2.p, a, st);
-  } else if (a.N <= 128) {
-    if (short_k) launch_tc<128, 4, 2>(qbf, idx->W2.p, a, st);
-    else launch_tc<128, 4, 4>(qbf, idx->W2.p, a, st);
-  } else {
-    if (short_k) launch_tc<256, 4, 2>(qbf, idx->W2.p, a, st);
-    else launch_tc<256, 4, 4>(qbf, idx->W2.p, a, st);
+  if (!project_fused(q, idx->mu.p, idx->W2.p, (int)nq, D, d, split3, qp, D, qp + d, D, nullptr,
+                     err, st)) {
+    split_bf16(q, (int)nq, D, D, idx->mu.p, split3, qbf, st);
+    TcArgs a{};
+    a.M = (int)nq; a.N = D; a.K = D;
+    a.phases = split3 ? 3 : 1;
+    a.a_lo = (int)nq; a.b_lo = D;
+    a.epi = 0;
+    a.out0 = qp; a.ld0 = D; a.out1 = qp + d; a.ld1 = D; a.split = d;
+    a.err = err;
+    const bool short_k = (int64_t)((a.K + TC_BK - 1) / TC_BK) * a.phases <= 2;
+    if (a.N <= 64) {
+      if (short_k) launch_tc<64, 4, 2>(qbf, idx->W2.p, a, st);
+      else launch_tc<64, 4, 4>(qbf, idx->W2.p, a, st);
+    } else if (a.N <= 128) {
+      if (short_k) launch_tc<128, 4, 2>(qbf, idx->W2.p, a, st);
+      else launch_tc<128, 4, 4>(qbf, idx->W2.p, a, st);
+    } else {
+      if (short_k) launch_tc<256, 4, 2>(qbf, idx->W2.p, a, st);
+      else launch_tc<256, 4, 4>(qbf, idx->W2.p, a, st);
+    }
   }
   int h = 0;
   MRQ_CUDA(cudaMemcpyAsync(&h, err, sizeof(int), cudaMemcpyDeviceToHost, st));

@@ -276,6 +276,91 @@ __global__ void __launch_bounds__(PS_NT) k_probe_select(const float* __restrict_
     __syncthreads();
     g = gs;
   }
+  // linear buckets over [min, max]: bin(g) = floor((g - min) * 1024 / (max - min)) is
+  // monotone in g, so the buckets up to the one where the running count reaches nprobe
+  // hold the nprobe smallest g (equal values share a bucket); those few are sorted
+  // exactly below.  Too many in them (or a constant row): the radix select.
+  {
+    __shared__ float s_mm[2][PS_NT / 32];
+    __shared__ int lhist[1024];
+    __shared__ int s_b;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    float mn = FINF, mx = -FINF;
+    for (int i = threadIdx.x; i < nlist; i += PS_NT) {
+      const float v = g[i];
+      mn = fminf(mn, v);
+      mx = fmaxf(mx, v);
+    }
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+      mn = fminf(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+      mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    }
+    if (lane == 0) { s_mm[0][wid] = mn; s_mm[1][wid] = mx; }
+    for (int i = threadIdx.x; i < 1024; i += PS_NT) lhist[i] = 0;
+    __syncthreads();
+    mn = s_mm[0][0];
+    mx = s_mm[1][0];
+#pragma unroll
+    for (int w = 1; w < PS_NT / 32; ++w) { mn = fminf(mn, s_mm[0][w]); mx = fmaxf(mx, s_mm[1][w]); }
+    const float scale = 1024.f / (mx - mn);
+    const bool spread = mx > mn && scale < FINF;
+    if (spread) {
+      for (int i = threadIdx.x; i < nlist; i += PS_NT)
+        atomicAdd(&lhist[min(1023, (int)((g[i] - mn) * scale))], 1);
+    }
+    __syncthreads();
+    if (threadIdx.x < 32) {
+      int c[32], tot = 0;
+#pragma unroll
+      for (int j = 0; j < 32; ++j) { c[j] = lhist[lane * 32 + j]; tot += c[j]; }
+      int incl = tot;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += t;
+      }
+      int acc = incl - tot;
+      if (lane == 0) s_b = -1;
+      __syncwarp();
+      if (acc < nprobe && nprobe <= incl) {
+        int bsel = lane * 32 + 31;
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+          acc += c[j];
+          if (acc >= nprobe) { bsel = lane * 32 + j; s_cnt = (unsigned)acc; break; }
+        }
+        s_b = bsel;
+      }
+    }
+    __syncthreads();
+    const int bsel = s_b;
+    if (spread && bsel >= 0 && (int)s_cnt <= cap) {
+      __syncthreads();
+      if (threadIdx.x == 0) s_cnt = 0u;
+      __syncthreads();
+      for (int i = threadIdx.x; i < nlist; i += PS_NT) {
+        const float v = g[i];
+        if (min(1023, (int)((v - mn) * scale)) <= bsel) {
+          const unsigned at = atomicAdd(&s_cnt, 1u);
+          sel[at] = ((unsigned long long)fkey(v) << 32) | (uint32_t)i;
+        }
+      }
+      __syncthreads();
+      const int n = (int)s_cnt;
+      int n2 = 1;
+      while (n2 < n) n2 <<= 1;
+      for (int i = n + threadIdx.x; i < n2; i += PS_NT) sel[i] = ~0ull;
+      block_bitonic<PS_NT>(sel, n2);
+      for (int r = threadIdx.x; r < nprobe; r += PS_NT) {
+        const unsigned long long v = sel[r];
+        plist[q * nprobe + r] = (int32_t)(v & 0xffffffffu);
+        pg[q * nprobe + r] = fkey_inv((uint32_t)(v >> 32));
+      }
+      return;
+    }
+    __syncthreads();
+  }
   const uint32_t T = block_radix_kth<PS_NT>(g, nlist, nprobe, hist, shv);
   if (threadIdx.x == 0) s_cnt = 0u;
   __syncthreads();
@@ -422,6 +507,8 @@ struct ScanParams {
   const int64_t* items;   // (pair << 32 | chunk) work items, or NULL: one item per pair
   const int* nitems;      // device count of items
   int chunk;              // candidates per chunk when items != NULL
+  int seed;               // 1: publish the running bound only, write no survivor (the
+                          // seed pass over the start of each query's nearest list)
   unsigned int* work;
   unsigned int* qcnt;
   unsigned int* gtau;
@@ -436,14 +523,9 @@ struct ScanParams {
   int32_t* dbg_idot;
 };
 
-__device__ __forceinline__ int64_t code_word(int64_t pp, int w, int words, int vw) {
-  int64_t blk = pp >> 5;
-  int lane = (int)(pp & 31);
-  return ((blk * (words / vw) + w / vw) * 32 + lane) * vw + (w % vw);
-}
-
 constexpr int SCAN_WARPS = 8;
 constexpr int SCAN_CHUNK = 4096;  // candidates per scan work item for long lists
+constexpr int SEED_CHUNK = 1024;  // candidates of each query's nearest list in the seed pass
 
 // KM: 0 = warp-sorted top-k list (k <= 32); 1 = per-lane top-m (m = ceil(k/32) <= 4);
 //     2 = no running threshold (k > 128).  QUANT: query quantized to qbits.
@@ -636,7 +718,7 @@ __global__ void __launch_bounds__(SCAN_WARPS * 32) k_scan(ScanParams P) {
         atomicMin(P.gtau + q, fkey(tau));
       }
       if (KM != 2) gt = fminf(gt, tau);
-      const bool surv = valid && lb <= tau;
+      const bool surv = valid && lb <= tau && !P.seed;
       const unsigned sm = __ballot_sync(0xffffffffu, surv);
       if (sm) {
         unsigned base = 0;
@@ -951,7 +1033,7 @@ __global__ void __launch_bounds__(SCAN_WARPS * 32, scan_q_min_ctas(NCH, BITS * N
         sm[u] = __ballot_sync(0xffffffffu, lb[u] <= tau);   // invalid lanes hold +inf
         any |= sm[u];
       }
-      if (any) {
+      if (any && !P.seed) {
 #pragma unroll
         for (int u = 0; u < U; ++u) {
           const int cnt = __popc(sm[u]);
@@ -971,24 +1053,40 @@ __global__ void __launch_bounds__(SCAN_WARPS * 32, scan_q_min_ctas(NCH, BITS * N
   }
 }
 
+// seed items: the first chunk of every query's nearest list (pair q * nprobe, chunk 0)
+__global__ void k_seed_items(int64_t nq, int nprobe, int64_t* __restrict__ items,
+                             int* __restrict__ nitems) {
+  const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= nq) return;
+  items[q] = (q * nprobe) << 32;
+  if (q == 0) *nitems = (int)nq;
+}
+
 // work items: the pairs w = i * stride (i < n) contribute max(1, ceil(size/chunk))
 // items each, (w << 32 | chunk index)
+// the pair of item slot i: w = i * stride, or, with rm_nq > 0 (rm_nq queries, n / rm_nq
+// probes each), probe-rank-major: every query's nearest list first, then the second, ...
+__device__ __forceinline__ int64_t chunk_pair(int64_t i, int64_t n, int stride, int64_t rm_nq) {
+  return rm_nq > 0 ? (i % rm_nq) * (n / rm_nq) + i / rm_nq : i * stride;
+}
+
 __global__ void k_chunk_count(const int32_t* __restrict__ plist, const int64_t* __restrict__ loff,
-                              int64_t n, int stride, int chunk, int* __restrict__ cnt) {
+                              int64_t n, int stride, int chunk, int* __restrict__ cnt,
+                              int64_t rm_nq) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  const int j = plist[i * stride];
+  const int j = plist[chunk_pair(i, n, stride, rm_nq)];
   const int64_t sz = loff[j + 1] - loff[j];
   const int64_t c = (sz + chunk - 1) / chunk;
   cnt[i] = c > 0 ? (int)c : 1;
 }
 __global__ void k_chunk_scatter(const int* __restrict__ cnt, const int* __restrict__ off,
                                 int64_t n, int stride, int64_t* __restrict__ items,
-                                int* __restrict__ nitems) {
+                                int* __restrict__ nitems, int64_t rm_nq) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const int o = off[i], c = cnt[i];
-  const int64_t w = i * stride;
+  const int64_t w = chunk_pair(i, n, stride, rm_nq);
   for (int t = 0; t < c; ++t) items[o + t] = (w << 32) | (int64_t)t;
   if (i == n - 1) *nitems = o + c;
 }
@@ -1732,6 +1830,43 @@ __global__ void __launch_bounds__(FW_WARPS * 32) k_fin_s1(FinParams P) {
   }
 }
 
+// A query whose stage-1 region overflowed is searched again; its bound for that search
+// is the k-th smallest UB1 over the survivors its region holds.  They are a subset of its
+// candidates, so the bound is never below tau_A, and they came from its nearest lists
+// first, so it is close to tau_A -- much tighter than the per-list bounds that its scan
+// published.  Queries that did not overflow are left alone.
+__global__ void __launch_bounds__(FW_WARPS * 32) k_ovf_seed(FinParams P, float* __restrict__ seed,
+                                                           int64_t base) {
+  __shared__ int hist_all[FW_WARPS][256];
+  __shared__ float filt_all[FW_WARPS][FW_FILT];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int64_t q = (int64_t)blockIdx.x * FW_WARPS + wid;
+  if (q >= P.nq || (int64_t)P.qcnt[q] <= P.cap) return;
+  const float* ub = P.sub + q * P.cap;
+  const int M = (int)P.cap;
+  float t = FINF;
+  if (M >= P.k) {
+    const float hint = fkey_inv(__ldcg(P.gtau + q));
+    if (P.k <= 32) {
+      uint32_t kt = warp_kth_small(ub, M, P.k, hint);
+      if (kt == 0xffffffffu) kt = warp_kth_small(ub, M, P.k, FINF);
+      t = fkey_inv(kt);
+    } else {
+      t = fkey_inv(warp_kth_filtered(ub, M, P.k, hint, filt_all[wid], FW_FILT, hist_all[wid]));
+    }
+  }
+  if (lane == 0) seed[base + q] = t;
+}
+
+// the running bound of a query searched again starts from its recorded seed (by row)
+__global__ void k_seed_gtau(unsigned int* __restrict__ gtau, int64_t nq,
+                            const float* __restrict__ seed, const int* __restrict__ rows) {
+  const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= nq) return;
+  const float t = seed[rows[q]];
+  if (t < FINF) gtau[q] = fkey(t);
+}
+
 // 1 bit + refinement, stage 1b: the full B-bit estimate (Eq. 4) and bounds (Eq. 5 plus
 // the Chebyshev term) of every stage-1a survivor (S1a, in s2pos), UB1b -> s2a,
 // LB1b -> s2b.  One CTA per query.  A survivor's pair (its probed list) is found by a
@@ -1859,6 +1994,75 @@ __global__ void __launch_bounds__(256) k_fin_stage2(FinParams P) {
       P.s2a[base + b + lane] = diso + em;
       P.s2b[base + b + lane] = diso - em;
       P.sub[base + b + lane] = myd2;
+    }
+  }
+}
+
+// Stage 2 for d = 32 * NC (NC = 1, 2, 4, 8): one CTA per query, each 8-lane group of a
+// warp owns a row of x_d' at a time (lane j of the group reads the row's float4 chunks
+// j, j + 8, ...; the query's matching chunks stay in registers), two rows per group in
+// flight; the dot and |x_d' - q_d'|^2 of a row are summed over its 8 lanes in 3 steps.
+template <int NC>
+__global__ void __launch_bounds__(256) k_fin_stage2_g(FinParams P) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int j = lane & 7, grp = wid * 4 + (lane >> 3);   // 32 groups of 8 lanes
+  const int64_t q = blockIdx.x;
+  const int M1 = P.qm1[q];
+  if (M1 == 0) return;
+  constexpr int d = NC * 32;
+  const float4* qv = reinterpret_cast<const float4*>(P.qd + q * d);
+  float4 qc[NC];
+#pragma unroll
+  for (int t = 0; t < NC; ++t) qc[t] = __ldg(qv + j + 8 * t);
+  const int64_t base = q * P.cap;
+  const float em = P.m * P.qstat[q * 4 + 1];
+  const float qp2 = P.qstat[q * 4 + 2];
+  for (int r0 = grp; r0 < M1; r0 += 64) {
+    const int r1 = r0 + 32;
+    const bool has1 = r1 < M1;
+    const int p0 = P.s2pos[base + r0];
+    const int p1 = has1 ? P.s2pos[base + r1] : p0;
+    const float4* x0 = reinterpret_cast<const float4*>(P.xd + (int64_t)p0 * d);
+    const float4* x1 = reinterpret_cast<const float4*>(P.xd + (int64_t)p1 * d);
+    float4 a[NC], b[NC];
+#pragma unroll
+    for (int t = 0; t < NC; ++t) a[t] = __ldg(x0 + j + 8 * t);
+#pragma unroll
+    for (int t = 0; t < NC; ++t) b[t] = __ldg(x1 + j + 8 * t);
+    float da = 0.f, ea = 0.f, db = 0.f, eb = 0.f;
+#pragma unroll
+    for (int t = 0; t < NC; ++t) {
+      const float4 c = qc[t];
+      float u;
+      da = fmaf(a[t].x, c.x, da); da = fmaf(a[t].y, c.y, da);
+      da = fmaf(a[t].z, c.z, da); da = fmaf(a[t].w, c.w, da);
+      u = a[t].x - c.x; ea = fmaf(u, u, ea); u = a[t].y - c.y; ea = fmaf(u, u, ea);
+      u = a[t].z - c.z; ea = fmaf(u, u, ea); u = a[t].w - c.w; ea = fmaf(u, u, ea);
+      db = fmaf(b[t].x, c.x, db); db = fmaf(b[t].y, c.y, db);
+      db = fmaf(b[t].z, c.z, db); db = fmaf(b[t].w, c.w, db);
+      u = b[t].x - c.x; eb = fmaf(u, u, eb); u = b[t].y - c.y; eb = fmaf(u, u, eb);
+      u = b[t].z - c.z; eb = fmaf(u, u, eb); u = b[t].w - c.w; eb = fmaf(u, u, eb);
+    }
+    // the groups of a warp may run different numbers of rows: the reduction names only
+    // this group's 8 lanes (offsets 4, 2, 1 stay inside the group)
+    const unsigned gmask = 0xffu << (lane & 24);
+#pragma unroll
+    for (int o = 4; o; o >>= 1) {
+      da += __shfl_xor_sync(gmask, da, o);
+      ea += __shfl_xor_sync(gmask, ea, o);
+      db += __shfl_xor_sync(gmask, db, o);
+      eb += __shfl_xor_sync(gmask, eb, o);
+    }
+    if (j == 0) {
+      const float diso = __ldg(P.xn2 + p0) + qp2 - 2.f * da;
+      P.s2a[base + r0] = diso + em;
+      P.s2b[base + r0] = diso - em;
+      P.sub[base + r0] = ea;
+    } else if (j == 1 && has1) {
+      const float diso = __ldg(P.xn2 + p1) + qp2 - 2.f * db;
+      P.s2a[base + r1] = diso + em;
+      P.s2b[base + r1] = diso - em;
+      P.sub[base + r1] = eb;
     }
   }
 }
@@ -2521,11 +2725,12 @@ static void mark(mrq_index* idx, int s, cudaStream_t st) {
   MRQ_CUDA(cudaEventRecord(idx->prof_ev[i], st));
 }
 
-void project_batch(mrq_index* idx, Workspace& ws, const float* q, int64_t nq, int precision,
-                   float* qd, float* qr, cudaStream_t st, __nv_bfloat16* probe_bf) {
+int project_batch(mrq_index* idx, Workspace& ws, const float* q, int64_t nq, int precision,
+                  float* qd, float* qr, cudaStream_t st, __nv_bfloat16* probe_bf) {
   const int D = idx->D, d = idx->d, r = D - d;
   if (precision == MRQ_PREC_FP32) {
     gemm_nt_f32(q, D, idx->mu.p, idx->W.p, D, (int)nq, D, D, qd, d, qr, r, d, st);
+    return 1;
   } else if (precision == MRQ_PREC_FP8) {
     MRQ_REQUIRE(tc_available(), "tensor-core projection needs an sm_103 device");
     MRQ_REQUIRE(idx->W8.p != nullptr, "FP8 projection needs D to be a multiple of 16 (16-byte e4m3 rows)");
@@ -2533,12 +2738,17 @@ void project_batch(mrq_index* idx, Workspace& ws, const float* q, int64_t nq, in
     ws.q8s.reserve((size_t)nq);
     project_fp8(q, idx->mu.p, idx->W8.p, idx->W8s.p, (int)nq, D, d, ws.q8.p, ws.q8s.p, qd, d, qr, r,
                 st, probe_bf, nullptr);
+    return 2;
   } else {
     MRQ_REQUIRE(tc_available(), "tensor-core projection needs an sm_103 device");
     MRQ_REQUIRE(D % 8 == 0, "tensor-core precisions need D to be a multiple of 8 (16-byte bf16 rows)");
-    ws.qbf.reserve((size_t)nq * D * 2);
-    project_tc(q, idx->mu.p, idx->W2.p, (int)nq, D, d, precision == MRQ_PREC_BF16X3,
-               ws.qbf.p, qd, qr, st, probe_bf);
+    const bool s3 = precision == MRQ_PREC_BF16X3;
+    if (project_fused(q, idx->mu.p, idx->W2.p, (int)nq, D, d, s3, qd, d, qr, r, probe_bf,
+                      tc_error_word(), st))
+      return 1;
+    ws.qbf.reserve((size_t)nq * D * 2);  // the split path's bf16 queries
+    return project_tc(q, idx->mu.p, idx->W2.p, (int)nq, D, d, precision == MRQ_PREC_BF16X3,
+                      ws.qbf.p, qd, qr, st, probe_bf);
   }
 }
 
@@ -2575,6 +2785,32 @@ ScanConfig scan_config(mrq_index* idx, const mrq_search_opts& o, int64_t nq, int
   return c;
 }
 
+// rows[i] of src (n x D) into row i of dst
+__global__ void k_gather_qrows(const float* __restrict__ src, int D, const int* __restrict__ rows,
+                               int64_t n, float* __restrict__ dst) {
+  const int64_t i = blockIdx.x;
+  if (i >= n) return;
+  const float* s = src + (int64_t)rows[i] * D;
+  for (int c = threadIdx.x; c < D; c += blockDim.x) dst[i * D + c] = s[c];
+}
+
+// row i of the redone answers (and counters) to row rows[i] of the caller's outputs
+__global__ void k_scatter_answers(const int64_t* __restrict__ ids, const float* __restrict__ d,
+                                  const int64_t* __restrict__ st, int k, const int* __restrict__ rows,
+                                  int64_t n, int64_t* __restrict__ out_ids, float* __restrict__ out_d,
+                                  int64_t* __restrict__ out_st) {
+  const int64_t i = blockIdx.x;
+  if (i >= n) return;
+  const int64_t row = rows[i];
+  for (int t = threadIdx.x; t < k; t += blockDim.x) {
+    if (out_ids) {
+      out_ids[row * k + t] = ids[i * k + t];
+      out_d[row * k + t] = d[i * k + t];
+    }
+  }
+  if (threadIdx.x < 3) out_st[row * 3 + threadIdx.x] = st[i * 3 + threadIdx.x];
+}
+
 // queries whose stage-1 survivors overflowed their region: listed for a second search
 __global__ void k_overflow(const unsigned int* __restrict__ qcnt, int64_t nq, int64_t cap,
                            int64_t base, int* __restrict__ ovf) {
@@ -2582,6 +2818,21 @@ __global__ void k_overflow(const unsigned int* __restrict__ qcnt, int64_t nq, in
   if (q >= nq || (int64_t)qcnt[q] <= cap) return;
   const int slot = atomicAdd(ovf, 1);
   ovf[1 + slot] = (int)(base + q);
+}
+
+void gather_query_rows(const float* src, int D, const int* rows, int64_t n, float* dst,
+                       cudaStream_t st) {
+  if (n <= 0) return;
+  k_gather_qrows<<<(unsigned)n, 128, 0, st>>>(src, D, rows, n, dst);
+  MRQ_CHECK_LAUNCH();
+}
+
+void scatter_answers(const int64_t* ids, const float* d, const int64_t* stats, int k, const int* rows,
+                     int64_t n, int64_t* out_ids, float* out_d, int64_t* out_stats, cudaStream_t st) {
+  if (n <= 0) return;
+  k_scatter_answers<<<(unsigned)n, 128, 0, st>>>(ids, d, stats, k, rows, n, out_ids, out_d,
+                                                  out_stats);
+  MRQ_CHECK_LAUNCH();
 }
 
 void search_batch(mrq_index* idx, Workspace& ws, const float* q, int64_t nq, int k, int nprobe,
@@ -2616,10 +2867,15 @@ void search_batch(mrq_index* idx, Workspace& ws, const float* q, int64_t nq, int
   const bool tc_probe = o.precision != MRQ_PREC_FP32 && d >= 64;
   if (tc_probe) ws.qbf2.reserve((size_t)nq * d * 2);
   mark(idx, MRQ_STAGE_PROJECT, st);
-  project_batch(idx, ws, q, nq, o.precision, ws.qd.p, ws.qr.p, st, tc_probe ? ws.qbf2.p : nullptr);
-  idx->launches += o.precision == MRQ_PREC_FP32 ? 1 : 2;
+  idx->launches +=
+      project_batch(idx, ws, q, nq, o.precision, ws.qd.p, ws.qr.p, st, tc_probe ? ws.qbf2.p : nullptr);
   mark(idx, MRQ_STAGE_QSTATS, st);
   qstats(idx, ws.qd.p, ws.qr.p, nq, ws.qstat.p, st, ws.qcnt.p, ws.gtau.p, ws.work.p);
+  if (ws.seed_tau) {  // a search again of overflowed queries: their recorded bounds
+    k_seed_gtau<<<ceil_div(nq, 256), 256, 0, st>>>(ws.gtau.p, nq, ws.seed_tau, ws.seed_rows);
+    MRQ_CHECK_LAUNCH();
+    idx->launches += 1;
+  }
   // 3. probe
   mark(idx, MRQ_STAGE_PROBE, st);
   // the fused probe emits nprobe candidates per (column tile, half tile) of each row
@@ -2627,13 +2883,11 @@ void search_batch(mrq_index* idx, Workspace& ws, const float* q, int64_t nq, int
   const bool fused = o.precision != MRQ_PREC_FP32 && d >= 64 && nprobe <= 16 &&
                      (int64_t)tiles_ * nprobe <= 512;
   if (fused) {
-    ws.qbf.reserve((size_t)nq * D * 2);
     ws.ppart.reserve((size_t)nq * tiles_ * nprobe);
     probe_tc_topk(ws.qd.p, ws.qstat.p, idx->cent2.p, idx->cent_n2.p, (int)nq, nlist, d,
                   o.precision == MRQ_PREC_BF16X3, nprobe, ws.qbf2.p, ws.ppart.p, st, true);
     idx->launches += 1;
   } else if (o.precision != MRQ_PREC_FP32 && d >= 64) {
-    ws.qbf.reserve((size_t)nq * D * 2);
     probe_tc(ws.qd.p, ws.qstat.p, idx->cent2.p, idx->cent_n2.p, (int)nq, nlist, d,
              o.precision == MRQ_PREC_BF16X3, ws.qbf2.p, ws.gmat.p, st, true);
     idx->launches += 1;
@@ -2700,21 +2954,21 @@ void search_batch(mrq_index* idx, Workspace& ws, const float* q, int64_t nq, int
     sp.ferr = idx->ferr1.p;
   }
   // per-pair work items (w = i * stride, i < n), long lists split into cfg.chunk chunks
-  auto build_items = [&](int64_t n, int stride) {
+  auto build_items = [&](int64_t n, int stride, int64_t rm_nq = 0) {
     const int64_t max_items = n + (nq * idx->cap_by_nprobe[nprobe]) / cfg.chunk + 1;
     ws.ccnt.reserve(n);
     ws.coff.reserve(n);
     ws.items.reserve(max_items);
     ws.nitems.reserve(1);
     k_chunk_count<<<ceil_div(n, 256), 256, 0, st>>>(ws.plist.p, idx->loff.p, n, stride,
-                                                   cfg.chunk, ws.ccnt.p);
+                                                   cfg.chunk, ws.ccnt.p, rm_nq);
     MRQ_CHECK_LAUNCH();
     size_t tb = 0;
     MRQ_CUDA(cub::DeviceScan::ExclusiveSum(nullptr, tb, ws.ccnt.p, ws.coff.p, (int)n, st));
     ws.cubtmp.reserve(tb + 16);
     MRQ_CUDA(cub::DeviceScan::ExclusiveSum(ws.cubtmp.p, tb, ws.ccnt.p, ws.coff.p, (int)n, st));
     k_chunk_scatter<<<ceil_div(n, 256), 256, 0, st>>>(ws.ccnt.p, ws.coff.p, n, stride, ws.items.p,
-                                                     ws.nitems.p);
+                                                     ws.nitems.p, rm_nq);
     MRQ_CHECK_LAUNCH();
     sp.items = ws.items.p;
     sp.nitems = ws.nitems.p;
@@ -2900,7 +3154,27 @@ void search_batch(mrq_index* idx, Workspace& ws, const float* q, int64_t nq, int
     }
   }
   int64_t grid_items = nq * nprobe;
-  if (!batched && idx->max_list > cfg.chunk) grid_items = build_items(nq * nprobe, 1);
+  if (!batched && idx->max_list > cfg.chunk) {
+    // long (Zipf-sized) lists: before their chunks start together, a seed pass over the
+    // first SEED_CHUNK candidates of each query's nearest list publishes a running bound
+    // (the same kernel and arithmetic, so it is a k-th smallest of true UB1 values and
+    // never below tau_A); it writes no survivors -- the main scan revisits those candidates
+    if (o.query_bits > 0 && !refine && k <= 128) {
+      ws.sitems.reserve(nq);
+      ws.nitems.reserve(2);
+      k_seed_items<<<ceil_div(nq, 256), 256, 0, st>>>(nq, nprobe, ws.sitems.p, ws.nitems.p + 1);
+      MRQ_CHECK_LAUNCH();
+      ScanParams ss = sp;
+      ss.items = ws.sitems.p;
+      ss.nitems = ws.nitems.p + 1;
+      ss.chunk = SEED_CHUNK;
+      ss.seed = 1;
+      ss.work = ws.work.p + 3;
+      launch_scan(ss, nq, st, false);
+      idx->launches += 2;
+    }
+    grid_items = build_items(nq * nprobe, 1, nq);
+  }
   if (refine) {  // the pairs' quantized queries, for stage 1b
     const int64_t np_ = nq * nprobe;
     ws.pq.reserve(np_ * sizeof(PairQ));
@@ -2933,6 +3207,11 @@ void search_batch(mrq_index* idx, Workspace& ws, const float* q, int64_t nq, int
     fp.qtau = ws.qtau.p; fp.qm1 = ws.qm1.p; fp.qm2 = ws.qm2.p; fp.nq = nq;
     fp.gtau = ws.gtau.p;
     const unsigned gw = ceil_div(nq, FW_WARPS);
+    if (limited && ws.seed_out) {
+      k_ovf_seed<<<gw, FW_WARPS * 32, 0, st>>>(fp, ws.seed_out, ws.ovf_base);
+      MRQ_CHECK_LAUNCH();
+      idx->launches += 1;
+    }
     k_fin_s1<<<gw, FW_WARPS * 32, 0, st>>>(fp);
     MRQ_CHECK_LAUNCH();
     if (refine) {
@@ -2953,12 +3232,17 @@ void search_batch(mrq_index* idx, Workspace& ws, const float* q, int64_t nq, int
     }
     mark(idx, MRQ_STAGE_STAGE2, st);
     if (o.mode == MRQ_MODE_MRQ_PLUS) {
-      k_fin_stage2<<<(unsigned)nq, 256, (size_t)((d + 3) & ~3) * 4, st>>>(fp);
+      if (d == 32) k_fin_stage2_g<1><<<(unsigned)nq, 256, 0, st>>>(fp);
+      else if (d == 64) k_fin_stage2_g<2><<<(unsigned)nq, 256, 0, st>>>(fp);
+      else if (d == 128) k_fin_stage2_g<4><<<(unsigned)nq, 256, 0, st>>>(fp);
+      else if (d == 256) k_fin_stage2_g<8><<<(unsigned)nq, 256, 0, st>>>(fp);
+      else k_fin_stage2<<<(unsigned)nq, 256, (size_t)((d + 3) & ~3) * 4, st>>>(fp);
       MRQ_CHECK_LAUNCH();
     }
     mark(idx, MRQ_STAGE_TAU_B, st);
     k_fin_s2<<<gw, FW_WARPS * 32, 0, st>>>(fp);
     MRQ_CHECK_LAUNCH();
+    idx->launches += o.mode == MRQ_MODE_MRQ_PLUS ? 2 : 1;
     mark(idx, MRQ_STAGE_EXACT, st);
     if (o.mode == MRQ_MODE_MRQ_PLUS && (r & 3) == 0) {
       // the d-part of every exact distance came out of stage 2
@@ -2973,7 +3257,7 @@ void search_batch(mrq_index* idx, Workspace& ws, const float* q, int64_t nq, int
     MRQ_CHECK_LAUNCH();
     mark(idx, MRQ_STAGE_TOPK, st);
     k_fin_topk<<<gw, FW_WARPS * 32, 0, st>>>(fp);
-    idx->launches += o.mode == MRQ_MODE_MRQ_PLUS ? 4 : 3;
+    idx->launches += 2;  // exact, top-k (the first finalize launch is counted below)
   } else {
     size_t fsm = (size_t)((((d + 3) & ~3) + r + 3) & ~3) * sizeof(float) + FN_SORT * 8;
     ensure_smem((const void*)k_finalize, fsm);

@@ -317,6 +317,29 @@ def test_batched_form_equals_per_pair_scan(request, fixture):
     _check_answers(S, ids.cpu().numpy(), dists.cpu().numpy(), ref, w.k)
 
 
+def test_graph_captured_again_after_scratch_grows(small):
+    # a captured graph holds the scratch addresses it was captured with: a larger search
+    # in between grows (reallocates) the scratch, and the next call with the same
+    # arguments captures again instead of replaying addresses that were freed
+    S = small
+    w = S["w"]
+    q = torch.from_numpy(S["queries"]).cuda()
+    ids = torch.empty((q.shape[0], w.k), dtype=torch.int64, device="cuda")
+    dists = torch.empty((q.shape[0], w.k), dtype=torch.float32, device="cuda")
+    o = mrq.mrq_search_opts(query_bits=4, graph=1)
+    ref_i, ref_d = mrq.mrq_search(S["gidx"], q, w.k, w.nprobe, mrq.mrq_search_opts(query_bits=4))
+    mrq.mrq_search(S["gidx"], q, w.k, w.nprobe, o, out=(ids, dists))   # run, capture
+    big = torch.cat([q] * 40)
+    bi, _ = mrq.mrq_search(S["gidx"], big, w.k, w.nprobe, mrq.mrq_search_opts(query_bits=4))
+    np.testing.assert_array_equal(bi[:len(q)].cpu().numpy(), ref_i.cpu().numpy())
+    for _ in range(2):
+        ids.fill_(-7)
+        mrq.mrq_search(S["gidx"], q, w.k, w.nprobe, o, out=(ids, dists))
+        torch.cuda.synchronize()
+        np.testing.assert_array_equal(ids.cpu().numpy(), ref_i.cpu().numpy())
+        np.testing.assert_array_equal(dists.cpu().numpy(), ref_d.cpu().numpy())
+
+
 def test_graph_replay(small):
     # a captured search graph replays the same pipeline: identical answers, and new
     # query values written into the same buffer are picked up by the replay

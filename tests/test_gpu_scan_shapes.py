@@ -139,3 +139,15 @@ def test_bench_shape_other_forms(gist_shape, form):
     ref = _ref(S, k, NPROBE, form["query_bits"], form.get("mode", omrq.MODE_MRQ_PLUS))
     ids, dists = _search(S, k, NPROBE, **form)
     check_answers(S["base"], S["queries"], ids, dists, ref, k, label=f"GIST-like d128 {form}")
+
+
+@pytest.mark.parametrize("nprobe", [33, 40, 64])
+def test_probe_selection_above_32_lists(gist_shape, nprobe):
+    # nprobe > 32: the distance matrix is written and the CTA selection picks the lists
+    # (linear buckets over the row's range, an exact sort of the candidates)
+    S = gist_shape
+    ref = _ref(S, 10, nprobe, 4)
+    ids, dists = _search(S, 10, nprobe, query_bits=4)
+    check_answers(S["base"], S["queries"], ids, dists, ref, 10, label=f"GIST-like nprobe={nprobe}")
+    st = mrq.mrq_last_search_stats(S["gidx"], len(S["queries"]))
+    np.testing.assert_array_equal(st["n_cand"], ref.n_cand)

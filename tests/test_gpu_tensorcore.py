@@ -91,3 +91,28 @@ def test_tensor_core_precision_needs_whole_bf16_rows():
     with pytest.raises(mrq.MRQError) as e:
         mrq.mrq_search(gi, queries, 5, 2, mrq.mrq_search_opts(precision=mrq.PREC_BF16))
     assert e.value.code == mrq.MRQ_EINVAL and "multiple of 8" in str(e.value)
+
+
+@pytest.mark.parametrize("D,d,n", [(96, 64, 333), (128, 64, 4097), (960, 128, 1000)])
+def test_fused_projection_equals_split_path(tmp_path, D, d, n):
+    # 16-byte aligned device queries take the fused projection (float32 rows loaded by
+    # TMA, centred and split to bf16 inside the GEMM); the same rows 4 bytes off a
+    # 16-byte boundary take the split kernel + GEMM.  One bf16 product per term in the
+    # same order: bitwise equal.  The hi+lo form orders its three products per K slice
+    # instead of per pass: equal to float32 accumulation rounding.
+    w, base, queries, st, gi = _oracle_index(tmp_path, D, d, 4000, 16)
+    q = np.concatenate([queries] * (n // len(queries) + 1))[:n].astype(np.float32)
+    dev = torch.from_numpy(q).cuda()
+    buf = torch.zeros(n * D + 4, dtype=torch.float32, device="cuda")
+    buf[1:1 + n * D] = dev.reshape(-1)
+    off = buf[1:1 + n * D].view(n, D)
+    assert off.data_ptr() % 16 == 4 and dev.data_ptr() % 16 == 0
+    scale = np.linalg.norm(q - st.mu, axis=1)[:, None]
+    for prec in (mrq.PREC_BF16, mrq.PREC_BF16X3):
+        o = mrq.mrq_search_opts(precision=prec)
+        a = mrq.mrq_project(gi, dev, o).cpu().numpy()
+        b = mrq.mrq_project(gi, off, o).cpu().numpy()
+        if prec == mrq.PREC_BF16:
+            np.testing.assert_array_equal(a, b)
+        else:
+            assert float(np.max(np.abs(a - b) / scale)) < 2e-6
