@@ -347,6 +347,9 @@ bool project_fused(const float* Q, const float* mu, const __nv_bfloat16* W2, int
 void probe_tc(const float* qd, const float* qstat, const __nv_bfloat16* C2, const float* cn2,
               int M, int nlist, int d, bool split3, __nv_bfloat16* qbf, float* gmat,
               cudaStream_t st, bool presplit = false);
+// candidate lists per row that probe_tc_topk writes (its part array holds M x parts x nsel
+// keys)
+int probe_tc_parts(int nlist);
 int probe_tc_topk(const float* qd, const float* qstat, const __nv_bfloat16* C2, const float* cn2,
                   int M, int nlist, int d, bool split3, int nsel, __nv_bfloat16* qbf,
                   unsigned long long* part, cudaStream_t st, bool presplit = false);

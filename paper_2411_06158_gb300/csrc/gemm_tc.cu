@@ -1136,6 +1136,11 @@ void probe_tc(const float* qd, const float* qstat, const __nv_bfloat16* C2, cons
 
 // Probe with the top-nsel fused into the epilogue: part[m][tile][nsel] receives, for
 // every query row and 256-column tile, the nsel smallest (fkey(g) << 32 | list).
+int probe_tc_parts(int nlist) {
+  const int bn = nlist <= 64 ? 64 : nlist <= 128 ? 128 : 256;
+  return 2 * ceil_div(nlist, bn);  // column tiles x two halves
+}
+
 int probe_tc_topk(const float* qd, const float* qstat, const __nv_bfloat16* C2, const float* cn2,
                   int M, int nlist, int d, bool split3, int nsel, __nv_bfloat16* qbf,
                   unsigned long long* part, cudaStream_t st, bool presplit) {

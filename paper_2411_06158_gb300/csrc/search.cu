@@ -2879,7 +2879,7 @@ void search_batch(mrq_index* idx, Workspace& ws, const float* q, int64_t nq, int
   // 3. probe
   mark(idx, MRQ_STAGE_PROBE, st);
   // the fused probe emits nprobe candidates per (column tile, half tile) of each row
-  const int tiles_ = 2 * (nlist <= 64 ? 1 : nlist <= 128 ? 1 : ceil_div(nlist, 256));
+  const int tiles_ = probe_tc_parts(nlist);
   const bool fused = o.precision != MRQ_PREC_FP32 && d >= 64 && nprobe <= 16 &&
                      (int64_t)tiles_ * nprobe <= 512;
   if (fused) {

@@ -116,3 +116,46 @@ def test_fused_projection_equals_split_path(tmp_path, D, d, n):
             np.testing.assert_array_equal(a, b)
         else:
             assert float(np.max(np.abs(a - b) / scale)) < 2e-6
+
+
+def _bf16(x):
+    """float32 -> bf16 (round to nearest even), returned as float64"""
+    b = np.ascontiguousarray(x, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    b = ((b + 0x7FFF + ((b >> 16) & 1)) >> 16) << 16
+    return b.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+@pytest.mark.parametrize("prec", ["bf16", "bf16x3"])
+@pytest.mark.parametrize("d,nlist,nprobe,nq", [(64, 1000, 3, 1000), (128, 4096, 7, 5000),
+                                                (192, 600, 16, 777), (128, 256, 4, 3000)])
+def test_fused_probe_selects_the_nearest_lists(prec, d, nlist, nprobe, nq):
+    # IVF probing (Algorithm 2) on the tensor cores with the per-row running selection:
+    # the lists it probes (seen through the candidate count, a sum of list sizes) are the
+    # nprobe smallest g = |q_d'|^2 + |c'|^2 - 2 <bf16 q_d', bf16 c'> recomputed in float64
+    # from the GPU's own projected queries and the index's centroids, for every query whose
+    # nprobe-th and next g are apart by more than float32 rounding.  Shapes cover one and
+    # several query blocks per CTA, ragged list tiles and a zero-filled K slice (d 192).
+    w = datagen.workload("small", D=256, d=d, n=max(20 * nlist, 12000), nlist=nlist,
+                         n_comp=64, n_query=nq)
+    base, queries = datagen.base_and_queries(w)
+    gi = mrq.mrq_build(base, d, 1, nlist, mrq.mrq_build_opts(kmeans_iters=2))
+    p = mrq.PREC_BF16 if prec == "bf16" else mrq.PREC_BF16X3
+    o = mrq.mrq_search_opts(precision=p, query_bits=4)
+    q = torch.from_numpy(queries).cuda()
+    mrq.mrq_search(gi, q, 10, nprobe, o)
+    n_cand = mrq.mrq_last_search_stats(gi, nq)["n_cand"]
+    qd = mrq.mrq_project(gi, q, o).cpu().numpy()[:, :d].astype(np.float64)
+    C = mrq.mrq_index_export(gi, "CENT").astype(np.float64)
+    sizes = np.diff(mrq.mrq_index_export(gi, "LOFF"))
+    qh, ch = _bf16(qd), _bf16(C)
+    dot = qh @ ch.T
+    if prec == "bf16x3":
+        dot += qh @ _bf16(C - ch).T + _bf16(qd - qh) @ ch.T
+    g = (qd ** 2).sum(1)[:, None] + (C ** 2).sum(1)[None, :] - 2.0 * dot
+    order = np.argsort(g, axis=1, kind="stable")
+    gs = np.take_along_axis(g, order, axis=1)
+    scale = np.abs(gs[:, :nprobe + 1]).max(axis=1) + 1e-12
+    clear = gs[:, nprobe] - gs[:, nprobe - 1] > 1e-5 * scale
+    expect = sizes[order[:, :nprobe]].sum(axis=1)
+    assert clear.mean() > 0.8
+    np.testing.assert_array_equal(n_cand[clear], expect[clear])
