@@ -157,9 +157,9 @@ class ClockSampler:
 # run matches that configuration exactly.
 NCU_TRAFFIC_SOURCE = "profiles/dram_gist-1M-d960_tuned-bf16_nprobe3.md"
 NCU_TRAFFIC = {
-    ("k_fin_exact_r", "gist-like-1M-d960", 128, 1, "tuned_bf16_q4", 3, 1.0, 1.0): 1346259456,
-    ("k_fin_stage2", "gist-like-1M-d960", 128, 1, "tuned_bf16_q4", 3, 1.0, 1.0): 529399040,
-    ("k_scan_q", "gist-like-1M-d960", 128, 1, "tuned_bf16_q4", 3, 1.0, 1.0): 41613824,
+    ("k_fin_exact_r", "gist-like-1M-d960", 128, 1, "tuned_bf16_q4", 3, 1.0, 1.0): 1346254848,
+    ("k_fin_stage2_g", "gist-like-1M-d960", 128, 1, "tuned_bf16_q4", 3, 1.0, 1.0): 529420288,
+    ("k_scan_q", "gist-like-1M-d960", 128, 1, "tuned_bf16_q4", 3, 1.0, 1.0): 39446016,
 }
 
 
@@ -897,7 +897,8 @@ def main(argv=None):
                    else "k_scan_q" if fixed else "k_scan")
     per_q = {
         "scan": (scan_kernel, B["cand_per_query"] * (w.bits * w.d / 8 + 12)),
-        "stage2": ("k_fin_stage2", B["s1_per_query"] * (4 * w.d + 20)),
+        "stage2": ("k_fin_stage2_g" if w.d in (32, 64, 128, 256) else "k_fin_stage2",
+                   B["s1_per_query"] * (4 * w.d + 20)),
         "exact": ("k_fin_exact_r", B["exact_per_query"] * (4 * (w.D - w.d) + 12)),
     }
     dom = max(per_q, key=lambda s_: B["stage_ms"][s_])
