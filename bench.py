@@ -83,6 +83,20 @@ def parse_args(argv=None):
     return p.parse_args(argv)
 
 
+def workload_label(w) -> str:
+    """The workload's shape name with its actual size and dimension (a run may override
+    the base shape's n and D), e.g. gist-like-6M-d160."""
+    name = w.name
+    suffix = ""
+    if name.endswith("-zipf"):
+        name, suffix = name[: -len("-zipf")], "-zipf"
+    stem = name.rsplit("-", 2)[0]
+    n = w.n
+    size = f"{n // 1_000_000}M" if n % 1_000_000 == 0 else (
+        f"{n // 1000}k" if n % 1000 == 0 else str(n))
+    return f"{stem}-{size}-d{w.D}{suffix}"
+
+
 def workload_of(args):
     import datagen
     over = {}
@@ -369,7 +383,7 @@ def run_reference(args):
     line = {"metric": METRIC, "value": value, "unit": UNIT, "impl": "reference",
             "n_gpus": args.gpus, "steps": len(times), "warmup": args.warmup, "ms_per_step": ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": w.name, "n": w.n, "D": w.D, "d": w.d,
+            "data": "synthetic", "config": {"workload": workload_label(w), "n": w.n, "D": w.D, "d": w.d,
                                             "bits": w.bits, "nlist": w.nlist, "nprobe": nprobe,
                                             "eps0": pt["eps0"], "m": pt["m"],
                                             "query_bits": pt["query_bits"], "k": w.k},
@@ -450,7 +464,7 @@ def run_serving(args):
                           "p50_ms": stats["p50_us"] / 1000.0, "p99_ms": stats["p99_us"] / 1000.0,
                           "max_ms": stats["max_us"] / 1000.0, "batches": stats["batches"],
                           "slots": args.serve_slots, "max_wait_us": args.serve_wait_us,
-                          "recall@10_k10": rec, "workload": w.name, "n": w.n, "D": w.D,
+                          "recall@10_k10": rec, "workload": workload_label(w), "n": w.n, "D": w.D,
                           "d": w.d, "bits": w.bits, "nlist": w.nlist,
                           "k_choices": [10, 50, 100], "nprobe_choices": nprobes.tolist()}))
     return 0
@@ -535,7 +549,7 @@ def run_precision_report(args):
             if ids_fp32 is None:
                 ids_fp32 = ids
             print(json.dumps({
-                "metric": "precision form", "workload": w.name, "n": w.n, "D": w.D, "d": d,
+                "metric": "precision form", "workload": workload_label(w), "n": w.n, "D": w.D, "d": d,
                 "bits": w.bits, "nlist": w.nlist, "nprobe": nprobe, "k": w.k,
                 "queries": int(q_t.shape[0]), "precision": name,
                 "projection_rel_err_max": float(rel.max()),
@@ -621,7 +635,7 @@ def run_sweep(args):
                 cand = float(st["n_cand"].mean())
                 scan_bytes = cand * w.n_query * (bits * d / 8 + 12)
                 gbs = scan_bytes / (scan_ms / 1000.0) / 1e9 if scan_ms else None
-                pt = {"metric": "QPS-vs-recall", "workload": w.name, "n": w.n, "D": w.D, "d": d,
+                pt = {"metric": "QPS-vs-recall", "workload": workload_label(w), "n": w.n, "D": w.D, "d": d,
                       "bits": bits, "nlist": w.nlist, "k": w.k, "queries": w.n_query,
                       "nprobe": npb, "eps0": 1.9, "m": 4.0, "form": name,
                       "dtype": form_dtype(mrq.mrq_search_opts(**kw)), "recall@10": r,
@@ -906,7 +920,7 @@ def main(argv=None):
     launch_ms = B["stage_ms"][dom] / n_batches
     alg_bytes = bpq * w.n_query / n_batches
     achieved = alg_bytes / (launch_ms / 1000.0) / 1e9
-    tkey = (kname, w.name, w.d, w.bits, best, B["nprobe"], round(B["m"], 3), round(B["eps0"], 3))
+    tkey = (kname, workload_label(w), w.d, w.bits, best, B["nprobe"], round(B["m"], 3), round(B["eps0"], 3))
     traffic = NCU_TRAFFIC.get(tkey) if w.n_query == 10_000 else None
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
             "frac": achieved / peak, "traffic": traffic,
@@ -936,7 +950,7 @@ def main(argv=None):
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": form_dtype(forms[best]),
         "data": "synthetic",
-        "config": {"workload": w.name, "n": w.n, "D": w.D, "d": w.d, "bits": w.bits,
+        "config": {"workload": workload_label(w), "n": w.n, "D": w.D, "d": w.d, "bits": w.bits,
                    "nlist": w.nlist, "k": w.k, "queries_per_step": w.n_query,
                    "nprobe": B["nprobe"], "m": B["m"], "eps0": B["eps0"], "recall@10": B["recall"],
                    "form": best,

@@ -1782,6 +1782,34 @@ __device__ __forceinline__ int warp_compact_val(const int32_t* src, const float*
   return n;
 }
 
+// Register-resident selection for short survivor lists: entry lane + 32 t of a query's
+// list sits in register t of the lane (FR registers: up to 256 entries), all of them
+// loaded in one memory round trip.  k-th smallest key (k <= 32) among the M entries whose
+// key is <= hk, 0xffffffff when fewer than k are -- the insertions of warp_kth_small,
+// without its loads.
+constexpr int FR = 8;
+__device__ uint32_t warp_kth_regs(const uint32_t (&x)[FR], int M, int k, uint32_t hk) {
+  const int lane = threadIdx.x & 31;
+  uint32_t lst = 0xffffffffu, kth = 0xffffffffu;
+#pragma unroll
+  for (int t = 0; t < FR; ++t) {
+    if (32 * t >= M) break;
+    unsigned cand = __ballot_sync(0xffffffffu, x[t] < kth && x[t] <= hk);
+    while (cand) {
+      const int src = __ffs(cand) - 1;
+      cand &= cand - 1;
+      const uint32_t y = __shfl_sync(0xffffffffu, x[t], src);
+      if (y < kth) {
+        const int pos = __popc(__ballot_sync(0xffffffffu, lst < y));
+        const uint32_t up = __shfl_up_sync(0xffffffffu, lst, 1);
+        lst = lane > pos ? up : (lane == pos ? y : lst);
+        kth = __shfl_sync(0xffffffffu, lst, k - 1);
+      }
+    }
+  }
+  return kth;
+}
+
 constexpr int FW_WARPS = 8;   // queries per CTA in the per-query warp phases
 constexpr int FW_BUF = 128;   // per-warp (distance, id) sort buffer: up to k = 128 entries
 
@@ -1801,6 +1829,20 @@ __global__ void __launch_bounds__(FW_WARPS * 32) k_fin_s1(FinParams P) {
   if (q >= P.nq) return;
   int* hist = hist_all[wid];
   const int64_t base = q * P.cap;
+  // the first 32 FR entries of the query's region, loaded before its survivor count
+  // arrives (one round trip less for the short lists that most queries have)
+  const int lim = (int)min((int64_t)(32 * FR), P.cap);
+  uint32_t x[FR];
+  float lb[FR];
+  int32_t ps[FR];
+#pragma unroll
+  for (int t = 0; t < FR; ++t) {
+    const int i = 32 * t + lane;
+    const bool in = i < lim;
+    x[t] = in ? fkey(P.sub[base + i]) : 0xffffffffu;
+    lb[t] = in ? P.slb[base + i] : FINF;
+    ps[t] = in ? P.spos[base + i] : 0;
+  }
   const int M = (int)min((int64_t)P.qcnt[q], P.cap);
   int64_t nc = 0;
   for (int r = lane; r < P.nprobe; r += 32) {
@@ -1810,6 +1852,28 @@ __global__ void __launch_bounds__(FW_WARPS * 32) k_fin_s1(FinParams P) {
 #pragma unroll
   for (int o = 16; o; o >>= 1) nc += __shfl_xor_sync(0xffffffffu, nc, o);
   float tauA = FINF;
+  int M1 = 0;
+  if (M <= 32 * FR && P.k <= 32) {
+    // short list: its UB1, LB1 and positions are in registers (entries past M masked)
+#pragma unroll
+    for (int t = 0; t < FR; ++t)
+      if (32 * t + lane >= M) { x[t] = 0xffffffffu; lb[t] = FINF; }
+    if (M >= P.k) {
+      const uint32_t hk = P.gtau ? __ldcg(P.gtau + q) : 0xffffffffu;
+      uint32_t kt = warp_kth_regs(x, M, P.k, hk);
+      if (kt == 0xffffffffu) kt = warp_kth_regs(x, M, P.k, 0xffffffffu);  // hint too low
+      tauA = fkey_inv(kt);
+    }
+    const unsigned below = (1u << lane) - 1;
+#pragma unroll
+    for (int t = 0; t < FR; ++t) {  // ordered compaction of S1 = {LB1 <= tau_A}
+      const bool keep = 32 * t + lane < M && lb[t] <= tauA;
+      const unsigned m = __ballot_sync(0xffffffffu, keep);
+      if (keep) P.s2pos[base + M1 + __popc(m & below)] = ps[t];
+      M1 += __popc(m);
+    }
+    __syncwarp();
+  } else {
   if (M >= P.k) {
     const float hint = P.gtau ? fkey_inv(__ldcg(P.gtau + q)) : FINF;
     if (P.k <= 32) {
@@ -1821,8 +1885,8 @@ __global__ void __launch_bounds__(FW_WARPS * 32) k_fin_s1(FinParams P) {
     }
   }
   const float* slb = P.slb + base;
-  const int M1 = warp_compact(P.spos + base, M, P.s2pos + base,
-                              [&](int i) { return slb[i] <= tauA; });
+  M1 = warp_compact(P.spos + base, M, P.s2pos + base, [&](int i) { return slb[i] <= tauA; });
+  }
   if (lane == 0) {
     P.qtau[q] = tauA;
     P.qm1[q] = M1;
@@ -2111,7 +2175,42 @@ __global__ void __launch_bounds__(FW_WARPS * 32) k_fin_s2(FinParams P) {
   const int64_t base = q * P.cap;
   const int M1 = P.qm1[q];
   int M2;
-  if (P.mode == MRQ_MODE_MRQ_PLUS) {
+  if (P.mode == MRQ_MODE_MRQ_PLUS && M1 <= 32 * FR && P.k <= 32) {
+    // short list: UB2, LB2, positions and stage-2 terms in registers, one round trip
+    const float tauA = P.qtau[q];
+    uint32_t x[FR];
+    float lb[FR], e2[FR];
+    int32_t ps[FR];
+#pragma unroll
+    for (int t = 0; t < FR; ++t) {
+      const int i = 32 * t + lane;
+      const bool in = i < M1;
+      x[t] = in ? fkey(P.s2a[base + i]) : 0xffffffffu;
+      lb[t] = in ? P.s2b[base + i] : FINF;
+      ps[t] = in ? P.s2pos[base + i] : 0;
+      e2[t] = in ? P.sub[base + i] : 0.f;
+    }
+    // only upper bounds <= tau_A can lower tau_B = min(tau_A, k-th smallest UB2)
+    float tauB = tauA;
+    if (M1 >= P.k) {
+      const uint32_t kt = warp_kth_regs(x, M1, P.k, fkey(tauA));
+      if (kt != 0xffffffffu) tauB = fminf(tauA, fkey_inv(kt));
+    }
+    const unsigned below = (1u << lane) - 1;
+    M2 = 0;
+#pragma unroll
+    for (int t = 0; t < FR; ++t) {  // ordered compaction of S2 = {LB2 <= tau_B}
+      const bool keep = 32 * t + lane < M1 && lb[t] <= tauB;
+      const unsigned m = __ballot_sync(0xffffffffu, keep);
+      if (keep) {
+        const int at = M2 + __popc(m & below);
+        P.spos[base + at] = ps[t];
+        P.slb[base + at] = e2[t];
+      }
+      M2 += __popc(m);
+    }
+    __syncwarp();
+  } else if (P.mode == MRQ_MODE_MRQ_PLUS) {
     const float tauA = P.qtau[q];
     // only upper bounds <= tau_A can lower tau_B = min(tau_A, k-th smallest UB2)
     float tauB = tauA;
@@ -2234,8 +2333,57 @@ __global__ void __launch_bounds__(FW_WARPS * 32) k_fin_topk(FinParams P) {
   if (q >= P.nq) return;
   unsigned long long* buf = buf_all[wid];
   const int64_t base = q * P.cap;
-  const int M2 = P.qm2[q];
   const float* dist = P.slb + base;
+  // the first 64 entries' distances and positions, loaded before the count arrives
+  float dv[2];
+  int32_t pv[2];
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const int i = 32 * h + lane;
+    const bool in = i < P.cap;
+    dv[h] = in ? dist[i] : FINF;
+    pv[h] = in ? P.spos[base + i] : 0;
+  }
+  const int M2 = P.qm2[q];
+  if (M2 <= 64 && P.k <= 32) {
+    // short list: the (distance, id) keys of all M2 entries in two registers a lane
+    // (entry lane and lane + 32), sorted by a bitonic network over the warp; the k
+    // smallest are the answer (ties at the k-th distance: smallest ids first)
+    unsigned long long v[2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int i = 32 * h + lane;
+      v[h] = i < M2 ? ((unsigned long long)fkey(dv[h]) << 32) | (uint32_t)P.ids[pv[h]] : ~0ull;
+    }
+    for (int size = 2; size <= 64; size <<= 1) {
+      for (int stride = size >> 1; stride > 0; stride >>= 1) {
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int e = 32 * h + lane;
+          const bool up = (e & size) == 0;
+          if (stride == 32) {  // partner in this lane's other register
+            if (h == 0) {
+              const bool swap = (v[0] > v[1]) == up;
+              const unsigned long long lo = swap ? v[1] : v[0], hi = swap ? v[0] : v[1];
+              v[0] = lo;
+              v[1] = hi;
+            }
+          } else {
+            const unsigned long long o = __shfl_xor_sync(0xffffffffu, v[h], stride);
+            const bool lower = (e & stride) == 0;  // this entry is the pair's first
+            const bool take_min = lower == up;
+            v[h] = take_min ? (o < v[h] ? o : v[h]) : (o > v[h] ? o : v[h]);
+          }
+        }
+      }
+    }
+    if (lane < P.k) {
+      const bool has = v[0] != ~0ull;
+      P.out_ids[q * P.k + lane] = has ? (int64_t)(uint32_t)(v[0] & 0xffffffffu) : -1;
+      P.out_d[q * P.k + lane] = has ? fkey_inv((uint32_t)(v[0] >> 32)) : FINF;
+    }
+    return;
+  }
   const uint32_t T = M2 > P.k ? (P.k <= 32 ? warp_kth_small(dist, M2, P.k, FINF)
                                            : warp_radix_kth(dist, M2, P.k, hist_all[wid]))
                               : 0xffffffffu;
