@@ -1575,6 +1575,9 @@ __global__ void __launch_bounds__(FN_NT) k_finalize(FinParams P) {
 
 // Warp-local radix select: smallest key T with #{i : fkey(vals[i]) <= T} >= k.
 // hist: 256 ints of this warp's shared memory.  Requires M >= k.
+// chunks of 32 values a warp loop keeps in flight (one load round trip each)
+constexpr int WU = 4;
+
 __device__ uint32_t warp_radix_kth(const float* vals, int M, int k, int* hist) {
   const int lane = threadIdx.x & 31;
   uint32_t prefix = 0u, mask = 0u;
@@ -1583,15 +1586,15 @@ __device__ uint32_t warp_radix_kth(const float* vals, int M, int k, int* hist) {
 #pragma unroll
     for (int i = 0; i < 8; ++i) hist[lane * 8 + i] = 0;
     __syncwarp();
-    for (int b = 0; b < M; b += 128) {  // four independent loads in flight per lane
-      uint32_t key[4];
+    for (int b = 0; b < M; b += 32 * WU) {  // WU independent loads in flight per lane
+      uint32_t key[WU];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
+      for (int u = 0; u < WU; ++u) {
         const int i = b + 32 * u + lane;
         key[u] = i < M ? fkey(vals[i]) : 0u;
       }
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
+      for (int u = 0; u < WU; ++u) {
         const bool in = b + 32 * u + lane < M && (key[u] & mask) == prefix;
         const unsigned act = __ballot_sync(0xffffffffu, in);
         if (in) {
@@ -1636,20 +1639,52 @@ __device__ uint32_t warp_radix_kth(const float* vals, int M, int k, int* hist) {
 // kept sorted across the lanes (lane i holds the i-th smallest); values arrive 32 at
 // a time and only those below the current k-th (and not above `hint`, an upper bound
 // of the answer, or +inf) are inserted, one at a time.
+// The k (<= 32) smallest keys of vals[0..M) that are <= hk, sorted across the lanes (lane
+// i holds the i-th, 0xffffffff past the end): the streaming insertions of warp_kth_small.
+__device__ uint32_t warp_topk_list(const float* vals, int M, int k, uint32_t hk) {
+  const int lane = threadIdx.x & 31;
+  uint32_t lst = 0xffffffffu, kth = 0xffffffffu;
+  for (int b = 0; b < M; b += 32 * WU) {
+    uint32_t x[WU];
+#pragma unroll
+    for (int u = 0; u < WU; ++u) {
+      const int i = b + 32 * u + lane;
+      x[u] = i < M ? fkey(vals[i]) : 0xffffffffu;
+    }
+#pragma unroll
+    for (int u = 0; u < WU; ++u) {
+      unsigned cand = __ballot_sync(0xffffffffu, x[u] < kth && x[u] <= hk);
+      while (cand) {
+        const int src = __ffs(cand) - 1;
+        cand &= cand - 1;
+        const uint32_t y = __shfl_sync(0xffffffffu, x[u], src);
+        if (y < kth) {
+          const int pos = __popc(__ballot_sync(0xffffffffu, lst < y));
+          const uint32_t up = __shfl_up_sync(0xffffffffu, lst, 1);
+          lst = lane > pos ? up : (lane == pos ? y : lst);
+          lst = lane < k ? lst : 0xffffffffu;
+          kth = __shfl_sync(0xffffffffu, lst, k - 1);
+        }
+      }
+    }
+  }
+  return lst;
+}
+
 __device__ uint32_t warp_kth_small(const float* vals, int M, int k, float hint) {
   const int lane = threadIdx.x & 31;
   const uint32_t hk = fkey(hint);
   uint32_t lst = 0xffffffffu;
   uint32_t kth = 0xffffffffu;
-  for (int b = 0; b < M; b += 128) {  // four chunks of loads in flight
-    uint32_t x[4];
+  for (int b = 0; b < M; b += 32 * WU) {  // WU chunks of loads in flight
+    uint32_t x[WU];
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
+    for (int u = 0; u < WU; ++u) {
       const int i = b + 32 * u + lane;
       x[u] = i < M ? fkey(vals[i]) : 0xffffffffu;
     }
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
+    for (int u = 0; u < WU; ++u) {
       unsigned cand = __ballot_sync(0xffffffffu, x[u] < kth && x[u] <= hk);
       while (cand) {
         const int src = __ffs(cand) - 1;
@@ -1672,15 +1707,15 @@ __device__ __forceinline__ int warp_filter_le(const float* vals, int M, float h,
   const int lane = threadIdx.x & 31;
   const unsigned below = (1u << lane) - 1;
   int c = 0;
-  for (int b = 0; b < M; b += 128) {  // four independent loads in flight per lane
-    float v[4];
+  for (int b = 0; b < M; b += 32 * WU) {  // WU independent loads in flight per lane
+    float v[WU];
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
+    for (int u = 0; u < WU; ++u) {
       const int i = b + 32 * u + lane;
       v[u] = i < M ? vals[i] : FINF;
     }
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
+    for (int u = 0; u < WU; ++u) {
       const bool keep = v[u] <= h && b + 32 * u + lane < M;
       const unsigned m = __ballot_sync(0xffffffffu, keep);
       const int at = c + __popc(m & below);
@@ -1735,15 +1770,15 @@ __device__ __forceinline__ int warp_compact(const int32_t* src, int M, int32_t* 
   const int lane = threadIdx.x & 31;
   const unsigned below = (1u << lane) - 1;
   int n = 0;
-  for (int b = 0; b < M; b += 128) {  // four independent tests in flight per lane
-    bool k[4];
+  for (int b = 0; b < M; b += 32 * WU) {  // WU independent tests in flight per lane
+    bool k[WU];
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
+    for (int u = 0; u < WU; ++u) {
       const int i = b + 32 * u + lane;
       k[u] = i < M && keep(i);
     }
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
+    for (int u = 0; u < WU; ++u) {
       const unsigned m = __ballot_sync(0xffffffffu, k[u]);
       if (k[u]) out[n + __popc(m & below)] = src[b + 32 * u + lane];
       n += __popc(m);
@@ -1760,15 +1795,15 @@ __device__ __forceinline__ int warp_compact_val(const int32_t* src, const float*
   const int lane = threadIdx.x & 31;
   const unsigned below = (1u << lane) - 1;
   int n = 0;
-  for (int b = 0; b < M; b += 128) {
-    bool k[4];
+  for (int b = 0; b < M; b += 32 * WU) {
+    bool k[WU];
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
+    for (int u = 0; u < WU; ++u) {
       const int i = b + 32 * u + lane;
       k[u] = i < M && keep(i);
     }
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
+    for (int u = 0; u < WU; ++u) {
       const unsigned m = __ballot_sync(0xffffffffu, k[u]);
       if (k[u]) {
         const int at = n + __popc(m & below);
@@ -1931,6 +1966,118 @@ __global__ void k_seed_gtau(unsigned int* __restrict__ gtau, int64_t nq,
   if (t < FINF) gtau[q] = fkey(t);
 }
 
+// tau_A / tau_B and the S1 / S2 compactions for a few queries with long survivor lists
+// (a search again of overflowed queries; k <= 32): one CTA per query, its eight warps each
+// taking an eighth of the list -- each warp's k smallest upper bounds (streamed, one round
+// trip per WU chunks), the k-th smallest of those 8k in one warp (the k smallest of the
+// union are among them), then an ordered compaction (per-warp counts, their prefix, the
+// warps' writes at their offsets).  The same values as k_fin_s1 / k_fin_s2.
+__device__ uint32_t cta_kth_of_slices(const float* vals, int M, int k, uint32_t hk,
+                                      uint32_t (*s_l)[32], volatile uint32_t* s_out) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int per = (M + 7) / 8, lo = min(M, wid * per), hi = min(M, lo + per);
+  s_l[wid][lane] = warp_topk_list(vals + lo, hi - lo, k, hk);
+  __syncthreads();
+  if (wid == 0) {
+    uint32_t x[FR];
+#pragma unroll
+    for (int t = 0; t < FR; ++t) x[t] = s_l[t][lane];
+    const uint32_t kt = warp_kth_regs(x, 32 * FR, k, 0xffffffffu);
+    if (lane == 0) *s_out = kt;
+  }
+  __syncthreads();
+  return *s_out;
+}
+
+__global__ void __launch_bounds__(256) k_fin_s1_wide(FinParams P) {
+  __shared__ uint32_t s_l[8][32];
+  __shared__ int s_cnt[8];
+  __shared__ uint32_t s_kt;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int64_t q = blockIdx.x;
+  const int64_t base = q * P.cap;
+  const int M = (int)min((int64_t)P.qcnt[q], P.cap);
+  float tauA = FINF;
+  if (M >= P.k) {
+    uint32_t kt = cta_kth_of_slices(P.sub + base, M, P.k, __ldcg(P.gtau + q), s_l, &s_kt);
+    if (kt == 0xffffffffu)  // the hint too low: without it
+      kt = cta_kth_of_slices(P.sub + base, M, P.k, 0xffffffffu, s_l, &s_kt);
+    tauA = fkey_inv(kt);
+  }
+  const int per = (M + 7) / 8, lo = min(M, wid * per), hi = min(M, lo + per);
+  const float* slb = P.slb + base + lo;
+  int c = 0;
+  for (int b = 0; b < hi - lo; b += 32 * WU) {
+#pragma unroll
+    for (int u = 0; u < WU; ++u) {
+      const int i = b + 32 * u + lane;
+      c += __popc(__ballot_sync(0xffffffffu, i < hi - lo && slb[i] <= tauA));
+    }
+  }
+  if (lane == 0) s_cnt[wid] = c;
+  __syncthreads();
+  int off = 0, M1 = 0;
+#pragma unroll
+  for (int w = 0; w < 8; ++w) {
+    off += w < wid ? s_cnt[w] : 0;
+    M1 += s_cnt[w];
+  }
+  warp_compact(P.spos + base + lo, hi - lo, P.s2pos + base + off,
+               [&](int i) { return slb[i] <= tauA; });
+  if (threadIdx.x == 0) {
+    int64_t nc = 0;
+    for (int r = 0; r < P.nprobe; ++r) {
+      const int j = P.plist[q * P.nprobe + r];
+      nc += P.loff[j + 1] - P.loff[j];
+    }
+    P.qtau[q] = tauA;
+    P.qm1[q] = M1;
+    if (P.stats) { P.stats[q * 3 + 0] = nc; P.stats[q * 3 + 1] = M1; }
+  }
+}
+
+__global__ void __launch_bounds__(256) k_fin_s2_wide(FinParams P) {
+  __shared__ uint32_t s_l[8][32];
+  __shared__ int s_cnt[8];
+  __shared__ uint32_t s_kt;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int64_t q = blockIdx.x;
+  const int64_t base = q * P.cap;
+  const int M1 = P.qm1[q];
+  const float tauA = P.qtau[q];
+  // only upper bounds <= tau_A can lower tau_B = min(tau_A, k-th smallest UB2)
+  float tauB = tauA;
+  if (M1 >= P.k) {
+    const uint32_t kt = cta_kth_of_slices(P.s2a + base, M1, P.k, fkey(tauA), s_l, &s_kt);
+    if (kt != 0xffffffffu) tauB = fminf(tauA, fkey_inv(kt));
+  }
+  const int per = (M1 + 7) / 8, lo = min(M1, wid * per), hi = min(M1, lo + per);
+  const float* lb2 = P.s2b + base + lo;
+  int c = 0;
+  for (int b = 0; b < hi - lo; b += 32 * WU) {
+#pragma unroll
+    for (int u = 0; u < WU; ++u) {
+      const int i = b + 32 * u + lane;
+      c += __popc(__ballot_sync(0xffffffffu, i < hi - lo && lb2[i] <= tauB));
+    }
+  }
+  if (lane == 0) s_cnt[wid] = c;
+  __syncthreads();
+  int off = 0, M2 = 0;
+#pragma unroll
+  for (int w = 0; w < 8; ++w) {
+    off += w < wid ? s_cnt[w] : 0;
+    M2 += s_cnt[w];
+  }
+  // positions to spos, their |x_d' - q_d'|^2 (stage 2, in sub) to slb
+  warp_compact_val(P.s2pos + base + lo, P.sub + base + lo, hi - lo, P.spos + base + off,
+                   P.slb + base + off, [&](int i) { return lb2[i] <= tauB; });
+  if (threadIdx.x == 0) {
+    P.qm2[q] = M2;
+    if (P.stats) P.stats[q * 3 + 2] = M2;
+  }
+}
+
 // 1 bit + refinement, stage 1b: the full B-bit estimate (Eq. 4) and bounds (Eq. 5 plus
 // the Chebyshev term) of every stage-1a survivor (S1a, in s2pos), UB1b -> s2a,
 // LB1b -> s2b.  One CTA per query.  A survivor's pair (its probed list) is found by a
@@ -2066,13 +2213,20 @@ __global__ void __launch_bounds__(256) k_fin_stage2(FinParams P) {
 // warp owns a row of x_d' at a time (lane j of the group reads the row's float4 chunks
 // j, j + 8, ...; the query's matching chunks stay in registers), two rows per group in
 // flight; the dot and |x_d' - q_d'|^2 of a row are summed over its 8 lanes in 3 steps.
-template <int NC>
+template <int NC, bool SPLIT>
 __global__ void __launch_bounds__(256) k_fin_stage2_g(FinParams P) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int j = lane & 7, grp = wid * 4 + (lane >> 3);   // 32 groups of 8 lanes
   const int64_t q = blockIdx.x;
   const int M1 = P.qm1[q];
   if (M1 == 0) return;
+  // SPLIT: the query's rows split over gridDim.y CTAs (a few queries with long lists)
+  int c0 = 0, c1 = M1;
+  if constexpr (SPLIT) {
+    const int share = (M1 + (int)gridDim.y - 1) / (int)gridDim.y;
+    c0 = min(M1, (int)blockIdx.y * share);
+    c1 = min(M1, c0 + share);
+  }
   constexpr int d = NC * 32;
   const float4* qv = reinterpret_cast<const float4*>(P.qd + q * d);
   float4 qc[NC];
@@ -2081,9 +2235,9 @@ __global__ void __launch_bounds__(256) k_fin_stage2_g(FinParams P) {
   const int64_t base = q * P.cap;
   const float em = P.m * P.qstat[q * 4 + 1];
   const float qp2 = P.qstat[q * 4 + 2];
-  for (int r0 = grp; r0 < M1; r0 += 64) {
+  for (int r0 = c0 + grp; r0 < c1; r0 += 64) {
     const int r1 = r0 + 32;
-    const bool has1 = r1 < M1;
+    const bool has1 = r1 < c1;
     const int p0 = P.s2pos[base + r0];
     const int p1 = has1 ? P.s2pos[base + r1] : p0;
     const float4* x0 = reinterpret_cast<const float4*>(P.xd + (int64_t)p0 * d);
@@ -2283,7 +2437,11 @@ __global__ void __launch_bounds__(256) k_fin_exact_r(FinParams P) {
   const float4* qv = reinterpret_cast<const float4*>(sq);
   const int M2 = P.qm2[q];
   const int64_t base = q * P.cap;
-  const int per = (M2 + 7) / 8, lo = min(M2, wid * per), hi = min(M2, lo + per);
+  // the query's rows split over gridDim.y CTAs (one unless a few queries hold long lists),
+  // each CTA's share split evenly over its 8 warps
+  const int share = (M2 + (int)gridDim.y - 1) / (int)gridDim.y;
+  const int r0 = min(M2, (int)blockIdx.y * share), r1 = min(M2, r0 + share);
+  const int per = (r1 - r0 + 7) / 8, lo = min(r1, r0 + wid * per), hi = min(r1, lo + per);
   for (int b = lo; b < hi; b += 32) {
     const int cnt = min(32, hi - b);
     const int myp = lane < cnt ? P.spos[base + b + lane] : 0;
@@ -3355,12 +3513,21 @@ void search_batch(mrq_index* idx, Workspace& ws, const float* q, int64_t nq, int
     fp.qtau = ws.qtau.p; fp.qm1 = ws.qm1.p; fp.qm2 = ws.qm2.p; fp.nq = nq;
     fp.gtau = ws.gtau.p;
     const unsigned gw = ceil_div(nq, FW_WARPS);
+    // a few queries with long survivor lists (a search again of overflowed queries): each
+    // query's selections run on a whole CTA and its gathers are split over several CTAs
+    const unsigned fsplit =
+        (nq <= 8192 && cap > 4096)
+            ? (unsigned)std::min<int64_t>(ceil_div(cap, 4096), std::max<int64_t>(1, 65536 / nq))
+            : 1u;
+    const dim3 fgrid((unsigned)nq, fsplit);
+    const bool wide = fsplit > 1 && k <= 32 && !refine;
     if (limited && ws.seed_out) {
       k_ovf_seed<<<gw, FW_WARPS * 32, 0, st>>>(fp, ws.seed_out, ws.ovf_base);
       MRQ_CHECK_LAUNCH();
       idx->launches += 1;
     }
-    k_fin_s1<<<gw, FW_WARPS * 32, 0, st>>>(fp);
+    if (wide) k_fin_s1_wide<<<(unsigned)nq, 256, 0, st>>>(fp);
+    else k_fin_s1<<<gw, FW_WARPS * 32, 0, st>>>(fp);
     MRQ_CHECK_LAUNCH();
     if (refine) {
       RefineParams rp{};
@@ -3380,15 +3547,20 @@ void search_batch(mrq_index* idx, Workspace& ws, const float* q, int64_t nq, int
     }
     mark(idx, MRQ_STAGE_STAGE2, st);
     if (o.mode == MRQ_MODE_MRQ_PLUS) {
-      if (d == 32) k_fin_stage2_g<1><<<(unsigned)nq, 256, 0, st>>>(fp);
-      else if (d == 64) k_fin_stage2_g<2><<<(unsigned)nq, 256, 0, st>>>(fp);
-      else if (d == 128) k_fin_stage2_g<4><<<(unsigned)nq, 256, 0, st>>>(fp);
-      else if (d == 256) k_fin_stage2_g<8><<<(unsigned)nq, 256, 0, st>>>(fp);
+#define MRQ_S2G(NCv)                                                                   \
+      (fsplit > 1 ? k_fin_stage2_g<NCv, true><<<fgrid, 256, 0, st>>>(fp)               \
+                  : k_fin_stage2_g<NCv, false><<<fgrid, 256, 0, st>>>(fp))
+      if (d == 32) MRQ_S2G(1);
+      else if (d == 64) MRQ_S2G(2);
+      else if (d == 128) MRQ_S2G(4);
+      else if (d == 256) MRQ_S2G(8);
+#undef MRQ_S2G
       else k_fin_stage2<<<(unsigned)nq, 256, (size_t)((d + 3) & ~3) * 4, st>>>(fp);
       MRQ_CHECK_LAUNCH();
     }
     mark(idx, MRQ_STAGE_TAU_B, st);
-    k_fin_s2<<<gw, FW_WARPS * 32, 0, st>>>(fp);
+    if (wide && o.mode == MRQ_MODE_MRQ_PLUS) k_fin_s2_wide<<<(unsigned)nq, 256, 0, st>>>(fp);
+    else k_fin_s2<<<gw, FW_WARPS * 32, 0, st>>>(fp);
     MRQ_CHECK_LAUNCH();
     idx->launches += o.mode == MRQ_MODE_MRQ_PLUS ? 2 : 1;
     mark(idx, MRQ_STAGE_EXACT, st);
@@ -3396,7 +3568,7 @@ void search_batch(mrq_index* idx, Workspace& ws, const float* q, int64_t nq, int
       // the d-part of every exact distance came out of stage 2
       const size_t esm = (size_t)std::max(r, 4) * 4;
       ensure_smem((const void*)k_fin_exact_r, esm);
-      k_fin_exact_r<<<(unsigned)nq, 256, esm, st>>>(fp);
+      k_fin_exact_r<<<fgrid, 256, esm, st>>>(fp);
     } else {
       const size_t esm = (size_t)(((d + 3) & ~3) + r) * 4;
       ensure_smem((const void*)k_fin_exact, esm);
