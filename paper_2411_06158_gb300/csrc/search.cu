@@ -1989,19 +1989,73 @@ __device__ uint32_t cta_kth_of_slices(const float* vals, int M, int k, uint32_t 
   return *s_out;
 }
 
+// k-th smallest key of vals[0..M) among the keys <= hk over a whole CTA (k <= 128): the
+// values <= the hint are gathered into the shared buffer (warp-aggregated appends), and
+// when k to C of them are, warp 0 selects in the buffer (radix select); fewer than k:
+// 0xffffffff; more than C: warp 0 runs the warp's filtered selection over all M values.
+constexpr int WIDE_BUF = 4096;
+__device__ uint32_t cta_kth_filtered(const float* vals, int M, int k, uint32_t hk, float* buf,
+                                     int* hist, float* filt, volatile int* s_n,
+                                     volatile uint32_t* s_out) {
+  const int lane = threadIdx.x & 31;
+  const unsigned below = (1u << lane) - 1;
+  if (threadIdx.x == 0) *s_n = 0;
+  __syncthreads();
+  for (int b = 0; b < M; b += 256 * WU) {
+    float v[WU];
+#pragma unroll
+    for (int u = 0; u < WU; ++u) {
+      const int i = b + 256 * u + (int)threadIdx.x;
+      v[u] = i < M ? vals[i] : FINF;
+    }
+#pragma unroll
+    for (int u = 0; u < WU; ++u) {
+      const int i = b + 256 * u + (int)threadIdx.x;
+      const bool keep = i < M && fkey(v[u]) <= hk;
+      const unsigned m = __ballot_sync(0xffffffffu, keep);
+      if (m) {
+        int at = 0;
+        if (lane == __ffs(m) - 1) at = atomicAdd((int*)s_n, __popc(m));
+        at = __shfl_sync(0xffffffffu, at, __ffs(m) - 1) + __popc(m & below);
+        if (keep && at < WIDE_BUF) buf[at] = v[u];
+      }
+    }
+  }
+  __syncthreads();
+  const int n = *s_n;
+  if (threadIdx.x < 32) {
+    uint32_t kt = 0xffffffffu;
+    if (n >= k && n <= WIDE_BUF) kt = warp_radix_kth(buf, n, k, hist);
+    else if (n > WIDE_BUF)
+      kt = warp_kth_filtered(vals, M, k, hk == 0xffffffffu ? FINF : fkey_inv(hk), filt, FW_FILT,
+                             hist);
+    if (lane == 0) *s_out = kt;
+  }
+  __syncthreads();
+  return *s_out;
+}
+
 __global__ void __launch_bounds__(256) k_fin_s1_wide(FinParams P) {
   __shared__ uint32_t s_l[8][32];
   __shared__ int s_cnt[8];
   __shared__ uint32_t s_kt;
+  __shared__ int s_n;
+  __shared__ float s_buf[WIDE_BUF];
+  __shared__ int s_hist[256];
+  __shared__ float s_filt[FW_FILT];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int64_t q = blockIdx.x;
   const int64_t base = q * P.cap;
   const int M = (int)min((int64_t)P.qcnt[q], P.cap);
   float tauA = FINF;
   if (M >= P.k) {
-    uint32_t kt = cta_kth_of_slices(P.sub + base, M, P.k, __ldcg(P.gtau + q), s_l, &s_kt);
-    if (kt == 0xffffffffu)  // the hint too low: without it
-      kt = cta_kth_of_slices(P.sub + base, M, P.k, 0xffffffffu, s_l, &s_kt);
+    auto kth = [&](uint32_t hk) {
+      return P.k <= 32 ? cta_kth_of_slices(P.sub + base, M, P.k, hk, s_l, &s_kt)
+                       : cta_kth_filtered(P.sub + base, M, P.k, hk, s_buf, s_hist, s_filt, &s_n,
+                                          &s_kt);
+    };
+    uint32_t kt = kth(__ldcg(P.gtau + q));
+    if (kt == 0xffffffffu) kt = kth(0xffffffffu);  // the hint too low: without it
     tauA = fkey_inv(kt);
   }
   const int per = (M + 7) / 8, lo = min(M, wid * per), hi = min(M, lo + per);
@@ -2040,6 +2094,10 @@ __global__ void __launch_bounds__(256) k_fin_s2_wide(FinParams P) {
   __shared__ uint32_t s_l[8][32];
   __shared__ int s_cnt[8];
   __shared__ uint32_t s_kt;
+  __shared__ int s_n;
+  __shared__ float s_buf[WIDE_BUF];
+  __shared__ int s_hist[256];
+  __shared__ float s_filt[FW_FILT];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int64_t q = blockIdx.x;
   const int64_t base = q * P.cap;
@@ -2048,7 +2106,10 @@ __global__ void __launch_bounds__(256) k_fin_s2_wide(FinParams P) {
   // only upper bounds <= tau_A can lower tau_B = min(tau_A, k-th smallest UB2)
   float tauB = tauA;
   if (M1 >= P.k) {
-    const uint32_t kt = cta_kth_of_slices(P.s2a + base, M1, P.k, fkey(tauA), s_l, &s_kt);
+    const uint32_t kt =
+        P.k <= 32 ? cta_kth_of_slices(P.s2a + base, M1, P.k, fkey(tauA), s_l, &s_kt)
+                  : cta_kth_filtered(P.s2a + base, M1, P.k, fkey(tauA), s_buf, s_hist, s_filt,
+                                     &s_n, &s_kt);
     if (kt != 0xffffffffu) tauB = fminf(tauA, fkey_inv(kt));
   }
   const int per = (M1 + 7) / 8, lo = min(M1, wid * per), hi = min(M1, lo + per);
@@ -3520,7 +3581,7 @@ void search_batch(mrq_index* idx, Workspace& ws, const float* q, int64_t nq, int
             ? (unsigned)std::min<int64_t>(ceil_div(cap, 4096), std::max<int64_t>(1, 65536 / nq))
             : 1u;
     const dim3 fgrid((unsigned)nq, fsplit);
-    const bool wide = fsplit > 1 && k <= 32 && !refine;
+    const bool wide = fsplit > 1 && !refine;
     if (limited && ws.seed_out) {
       k_ovf_seed<<<gw, FW_WARPS * 32, 0, st>>>(fp, ws.seed_out, ws.ovf_base);
       MRQ_CHECK_LAUNCH();

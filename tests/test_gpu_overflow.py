@@ -69,3 +69,24 @@ def test_negative_region_is_rejected(zipf):
     with pytest.raises(mrq.MRQError) as e:
         mrq.mrq_search(gi, queries[:4], 10, 6, mrq.mrq_search_opts(survivor_region=-1))
     assert e.value.code == mrq.MRQ_EINVAL
+
+
+@pytest.mark.parametrize("k", [10, 50])
+def test_wide_finalize_equals_per_warp_finalize(zipf, k):
+    # a batch of few queries with a large region takes the wide finalize (tau_A / tau_B on a
+    # CTA per query, gathers split over CTAs); the same queries inside a batch of more than
+    # 8192 take the per-warp kernels: the answers and counts are bitwise the same
+    w, queries, gi = zipf
+    q = torch.from_numpy(queries).cuda()
+    o = mrq.mrq_search_opts(eps0=1.9, m=4.0, query_bits=4)
+    small_i, small_d = mrq.mrq_search(gi, q, k, 6, o)
+    small_st = mrq.mrq_last_search_stats(gi, len(queries))
+    reps = 8200 // len(queries) + 1
+    big = torch.cat([q] * reps)
+    big_i, big_d = mrq.mrq_search(gi, big, k, 6, o)
+    big_st = mrq.mrq_last_search_stats(gi, big.shape[0])
+    n = len(queries)
+    np.testing.assert_array_equal(big_i[:n].cpu().numpy(), small_i.cpu().numpy())
+    np.testing.assert_array_equal(big_d[:n].cpu().numpy(), small_d.cpu().numpy())
+    for key in ("n_cand", "n_s1", "n_exact"):
+        np.testing.assert_array_equal(big_st[key][:n], small_st[key])
