@@ -36,3 +36,16 @@ def test_reference_arm_other_ranks_exit_quietly():
                         "--workload", "small", "--steps", "1", "--warmup", "0"], cwd=ROOT,
                        env=env, capture_output=True, text=True, timeout=600)
     assert r.returncode == 0 and r.stdout.strip() == ""
+
+
+def test_workload_label_names_the_actual_shape():
+    # a run that overrides n or D reports its own shape, and the label of the default
+    # GIST-like run is the key the recorded DRAM traffic is stored under
+    sys.path.insert(0, ROOT)
+    import bench
+    import datagen
+    assert bench.workload_label(datagen.workload("gist")) == "gist-like-1M-d960"
+    assert bench.workload_label(datagen.workload("gist", n=6_000_000, D=160)) == "gist-like-6M-d160"
+    assert bench.workload_label(datagen.workload("deep")) == "deep-like-10M-d96-zipf"
+    assert bench.workload_label(datagen.workload("serve", n=200_000)) == "msmarco-like-200k-d1024"
+    assert all(key[1] == "gist-like-1M-d960" for key in bench.NCU_TRAFFIC)
