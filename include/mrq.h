@@ -104,8 +104,10 @@ typedef struct {
                        (k, nprobe, query_bits), else batched when nq * nprobe / nlist >= 16 */
   int profile;      /* 1 = record CUDA events around each stage (see mrq_last_search_profile) */
   int graph;        /* 1 = replay a captured CUDA graph when queries, ids and dists are device
-                       memory and every argument equals the previous graph call's (the first
-                       such call runs normally, then captures); ignored with profile = 1 */
+                       memory or page-locked host memory (the copies become graph nodes) and
+                       every argument equals the previous graph call's (the first such call
+                       runs normally, then captures; a call after the library's search
+                       scratch has grown captures again); ignored with profile = 1 */
   int refine;       /* 1 = "1 bit + refinement" stage 1 for codes of bits > 1: the sign plane
                        of every code (the 1-bit code of o', with its own Eq. 4 / Eq. 5
                        factors) is scanned first, tau_A' = k-th smallest of its upper bounds,
@@ -190,7 +192,8 @@ int mrq_build(const float* base, int64_t n, int D, int d, int bits, int nlist,
  * Thresholds follow an order-independent contract (tau_A = k-th smallest stage-1
  * upper bound, tau_B = min(tau_A, k-th smallest stage-2 upper bound), survivors
  * are the candidates whose lower bound does not exceed the threshold), so the
- * answer of a query does not depend on the batch it is searched in.
+ * answer of a query does not depend on the batch it is searched in.  Host queries
+ * are copied to device memory once per batch before the projection.
  */
 int mrq_search(mrq_index* index, const float* queries, int64_t nq, int k, int nprobe,
                const mrq_search_opts* opt, int64_t* ids, float* dists);
