@@ -233,9 +233,12 @@ int mrq_project(mrq_index* index, const float* queries, int64_t nq,
  * on opt->cuda_stream (NULL opt or stream: the legacy default stream).  The
  * call returns once qp is written (it synchronises that stream).
  *
- * Scratch: MRQ_PREC_FP32 needs none.  The tensor-core precisions stage the
- * bf16 operand of the query in a fixed static device array of
- * MRQ_PROJECT_NOALLOC_MAX_BYTES bytes that the library owns; a request that
+ * Scratch: MRQ_PREC_FP32 needs none.  The tensor-core precisions use a fixed
+ * static device array of MRQ_PROJECT_NOALLOC_MAX_BYTES bytes that the library
+ * owns: its pipeline error word, and, when the query rows are not 16-byte
+ * aligned (the fused kernel then cannot take them) or at MRQ_PREC_FP8, the
+ * bf16 or e4m3 copy of the centred queries.  The size limit below holds
+ * whichever kernel runs; a request that
  * needs more (nq * D > 4194304 at MRQ_PREC_BF16, > 2097152 at MRQ_PREC_BF16X3; at
  * MRQ_PREC_FP8 whenever 256 * ceil(nq * D / 256) + 4 * nq > 8388608, e.g.
  * nq > 63550 at D = 128) returns MRQ_EINVAL without launching anything: split
