@@ -32,7 +32,6 @@ namespace {
 
 constexpr int TC_BM = 128;
 constexpr int TC_BK = 64;      // 64 bf16 = one 128-byte swizzle row
-constexpr int TC_STAGES = 4;
 constexpr uint64_t WAIT_NS = 2000000000ull;
 #define FLT_MAX_F __int_as_float(0x7f7fffff)
 #define FLT_INF_F __int_as_float(0x7f800000)
@@ -185,7 +184,6 @@ struct TcArgs {
   const float* cscale;
 };
 
-constexpr int TC_PSEL = 16;  // largest nprobe selected inside the probe epilogue
 
 template <int BN, int PSEL, int STAGES, bool F8 = false>
 __global__ void __launch_bounds__(256, 1)
@@ -877,7 +875,7 @@ CUtensorMap make_map(const void* base, uint64_t rows, uint64_t K, uint32_t box_r
   CUtensorMap m;
   cuuint64_t dims[2] = {K, rows};
   cuuint64_t strides[1] = {K * (f8 ? 1 : 2)};
-  cuuint32_t box[2] = {f8 ? 2 * TC_BK : TC_BK, box_rows};
+  cuuint32_t box[2] = {(cuuint32_t)(f8 ? 2 * TC_BK : TC_BK), box_rows};
   cuuint32_t es[2] = {1, 1};
   CUresult r = encode_fn()(&m, f8 ? CU_TENSOR_MAP_DATA_TYPE_UINT8 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16,
                            2, const_cast<void*>(base), dims,
