@@ -3578,7 +3578,8 @@ void search_batch(mrq_index* idx, Workspace& ws, const float* q, int64_t nq, int
     // query's selections run on a whole CTA and its gathers are split over several CTAs
     const unsigned fsplit =
         (nq <= 8192 && cap > 4096)
-            ? (unsigned)std::min<int64_t>(ceil_div(cap, 4096), std::max<int64_t>(1, 65536 / nq))
+            ? (unsigned)std::min<int64_t>({ceil_div(cap, 4096), std::max<int64_t>(1, 65536 / nq),
+                                           65535})
             : 1u;
     const dim3 fgrid((unsigned)nq, fsplit);
     const bool wide = fsplit > 1 && !refine;
